@@ -1,0 +1,826 @@
+/*
+ * pic_oracle.c -- FP64 CPU oracle of the explicit 1D3V ES PIC-MCC step.
+ *
+ * TEST INFRASTRUCTURE (see pic_oracle.h): loaded only by the tests, by
+ * __graft_entry__.smoke() and by bench.py's CPU legs.  Plain loops, one
+ * particle at a time, in the step order stated at or_step().  Nothing here is
+ * blocked, fused or reordered for speed.
+ *
+ * Parity status of each part and what pins it (tests/test_oracle_*.py):
+ *   Philox4x32-10 ........ pinned: Triton's Philox run by its CPU interpreter
+ *   deposit (CIC) ........ pinned: charge conservation, single-particle weights
+ *   Poisson .............. pinned: dense LU (numpy), parabola, periodic sine mode
+ *   Boris ................ pinned: |v| invariance, exact rotation angle, ExB drift
+ *   leapfrog + CIC field . pinned: cold plasma frequency; Landau root (scipy wofz)
+ *   null-collision MCC ... pinned: constant-nu decay exp(-nu t), binomial counts,
+ *                          exponential free flights, elastic/inelastic energy balance
+ *   walls and SEE ........ pinned: binomial emission counts, flux balance
+ *   ionization append .... pinned: one electron + one ion per event, energy balance
+ *   moments .............. pinned: uniform-plasma density, Maxwellian Te
+ */
+#include "pic_oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ELEM 1.602176634e-19      /* C */
+#define EPS0 8.8541878128e-12     /* F/m */
+#define KBOLTZ 1.380649e-23       /* J/K */
+#define TWO32 4294967296.0
+#define GRID_EMIN 1e-3
+#define GRID_EMAX 1e3
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11 "Parallel random numbers: */
+/* as easy as 1, 2, 3").  Each round: two 32x32->64 products of the even      */
+/* counter words with the round multipliers, the high halves xor'ed with the  */
+/* odd words and the key, the words permuted; the key is bumped by the Weyl   */
+/* constants between rounds.                                                  */
+/* ------------------------------------------------------------------------ */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += PHILOX_W0;
+        k1 += PHILOX_W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* A 32-bit word to a uniform in (0,1): the top 23 bits, centred in their
+ * interval, ((r >> 9) + 1/2) 2^-23.  The result has at most 24 significant
+ * bits, so it is the same number in FP32 and FP64. */
+double or_uniform(uint32_t r) { return ((double)(r >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+/* The draw of block `blk` for particle `id` of species `sp` during step `n`:
+ * counter (id, n, sp<<16 | blk, 0), key (seed_lo, seed_hi). */
+static void draw(const or_case *c, uint32_t id, int64_t n, int sp, uint32_t blk, uint32_t out[4]);
+
+enum { BLK_MCC = 0, BLK_AUX = 1, BLK_NEWION = 2, BLK_SEE = 3, BLK_SEE_V = 4, BLK_CHILD = 0xFFFF };
+
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n, cap;
+    double *xi, *vx, *vy, *vz;
+    uint32_t *id;
+    double *margin;
+    int32_t *event;
+} species_t;
+
+typedef struct {
+    int kind;
+    double thr;
+    double nu[OR_NGRID];       /* collision frequency at the grid energies, 1/s */
+} proc_t;
+
+struct or_case {
+    or_params p;
+    int n_nodes;
+    double dx;
+    species_t sp[OR_MAX_SPECIES];
+    species_t pend[OR_MAX_SPECIES];   /* particles created during the current step */
+    int n_proc[OR_MAX_SPECIES];
+    proc_t proc[OR_MAX_SPECIES][OR_MAX_PROC];
+    double numax[OR_MAX_SPECIES];
+    double *phi, *E, *rho;
+    int64_t *R[OR_MAX_SPECIES];
+    int initialised;
+    int64_t step;
+    or_counters cnt;
+    double *dens, *phi_sum, *en, *dens_diag, eepf[OR_EEPF_BINS], ke[OR_MAX_SPECIES], pw[OR_MAX_SPECIES];
+    double *fe_hist; int64_t fe_n, fe_cap;
+};
+
+static void draw(const or_case *c, uint32_t id, int64_t n, int sp, uint32_t blk, uint32_t out[4])
+{
+    uint32_t ctr[4] = { id, (uint32_t)n, ((uint32_t)sp << 16) | blk, 0u };
+    uint32_t key[2] = { (uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32) };
+    or_philox4x32_10(ctr, key, out);
+}
+
+static int sp_reserve(species_t *s, int64_t cap)
+{
+    if (cap <= s->cap) return 0;
+    int64_t nc = s->cap ? s->cap : 1024;
+    while (nc < cap) nc *= 2;
+#define GROW(f, T) do { void *q = realloc(s->f, (size_t)nc * sizeof(T)); if (!q) return -1; s->f = q; } while (0)
+    GROW(xi, double); GROW(vx, double); GROW(vy, double); GROW(vz, double);
+    GROW(id, uint32_t); GROW(margin, double); GROW(event, int32_t);
+#undef GROW
+    s->cap = nc;
+    return 0;
+}
+
+static int sp_push(species_t *s, double xi, double vx, double vy, double vz, uint32_t id)
+{
+    if (sp_reserve(s, s->n + 1)) return -1;
+    int64_t k = s->n++;
+    s->xi[k] = xi; s->vx[k] = vx; s->vy[k] = vy; s->vz[k] = vz; s->id[k] = id;
+    s->margin[k] = INFINITY; s->event[k] = 0;
+    return 0;
+}
+
+static void sp_free(species_t *s)
+{
+    free(s->xi); free(s->vx); free(s->vy); free(s->vz); free(s->id); free(s->margin); free(s->event);
+    memset(s, 0, sizeof(*s));
+}
+
+or_case *or_create(const or_params *p)
+{
+    if (!p || p->n_cells < 2 || p->n_species < 1 || p->n_species > OR_MAX_SPECIES || p->dt <= 0 || p->length <= 0)
+        return NULL;
+    or_case *c = calloc(1, sizeof(*c));
+    if (!c) return NULL;
+    c->p = *p;
+    c->n_nodes = p->periodic ? p->n_cells : p->n_cells + 1;
+    c->dx = p->length / p->n_cells;
+    int nn = c->n_nodes;
+    c->phi = calloc(nn, sizeof(double)); c->E = calloc(nn, sizeof(double)); c->rho = calloc(nn, sizeof(double));
+    c->phi_sum = calloc(nn, sizeof(double));
+    c->dens = calloc((size_t)nn * OR_MAX_SPECIES, sizeof(double));
+    c->en = calloc((size_t)nn * OR_MAX_SPECIES, sizeof(double));
+    c->dens_diag = calloc((size_t)nn * OR_MAX_SPECIES, sizeof(double));
+    for (int s = 0; s < OR_MAX_SPECIES; ++s) c->R[s] = calloc(nn, sizeof(int64_t));
+    if (p->const_nu_e > 0) c->numax[0] = p->const_nu_e;
+    return c;
+}
+
+void or_destroy(or_case *c)
+{
+    if (!c) return;
+    for (int s = 0; s < OR_MAX_SPECIES; ++s) { sp_free(&c->sp[s]); sp_free(&c->pend[s]); free(c->R[s]); }
+    free(c->phi); free(c->E); free(c->rho); free(c->phi_sum); free(c->dens); free(c->en); free(c->dens_diag);
+    free(c->fe_hist);
+    free(c);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cross sections (paper §1: tabulated cross sections in the LXCat format).    */
+/* Reading: the raw table is sampled, by linear interpolation in energy, onto  */
+/* a grid of OR_NGRID energies log-spaced on [1e-3, 1e3] eV (held constant     */
+/* beyond its ends, zero below the threshold of an inelastic process); the    */
+/* collision frequency nu_k = N sigma_k(eps) g(eps) is stored at the grid      */
+/* energies, with g the electron speed, or for ions the relative speed at the  */
+/* centre-of-mass energy eps; between grid energies nu_k is linear in ln eps.  */
+/* ------------------------------------------------------------------------ */
+static double grid_energy(int i)
+{
+    return GRID_EMIN * exp((double)i * log(GRID_EMAX / GRID_EMIN) / (OR_NGRID - 1));
+}
+
+static double raw_sigma(const double *e, const double *s, int n, double eps)
+{
+    if (eps <= e[0]) return s[0];
+    if (eps >= e[n - 1]) return s[n - 1];
+    int k = 0;
+    while (k + 1 < n && e[k + 1] < eps) ++k;
+    double t = (eps - e[k]) / (e[k + 1] - e[k]);
+    return s[k] + t * (s[k + 1] - s[k]);
+}
+
+/* reduced mass of the pair that defines the energy axis of species sp */
+static double pair_mass(const or_case *c, int sp)
+{
+    double m = c->p.m[sp];
+    if (sp == 0) return m;                 /* electrons: the atom is at rest */
+    return m * c->p.gas_mass / (m + c->p.gas_mass);
+}
+
+static void update_numax(or_case *c, int sp)
+{
+    double best = 0;
+    for (int i = 0; i < OR_NGRID; ++i) {
+        double tot = 0;
+        for (int k = 0; k < c->n_proc[sp]; ++k) tot += c->proc[sp][k].nu[i];
+        if (tot > best) best = tot;
+    }
+    c->numax[sp] = best;
+}
+
+int or_load_xsec(or_case *c, int sp, int kind, double thr, const double *e, const double *s, int n)
+{
+    if (!c || sp < 0 || sp >= c->p.n_species || n < 1 || c->n_proc[sp] >= OR_MAX_PROC) return -1;
+    if (sp == 0 && c->p.const_nu_e > 0) return -1;
+    proc_t *pr = &c->proc[sp][c->n_proc[sp]++];
+    pr->kind = kind;
+    pr->thr = thr;
+    double mu = pair_mass(c, sp);
+    for (int i = 0; i < OR_NGRID; ++i) {
+        double eps = grid_energy(i);
+        double sig = (eps < thr) ? 0.0 : raw_sigma(e, s, n, eps);
+        double g = sqrt(2.0 * eps * ELEM / mu);
+        pr->nu[i] = c->p.gas_density * sig * g;
+    }
+    update_numax(c, sp);
+    return 0;
+}
+
+/* nu_k(eps) between grid energies: linear in ln eps; zero below threshold */
+static double nu_at(const proc_t *pr, double eps)
+{
+    if (eps < pr->thr) return 0.0;
+    double s;
+    if (eps <= GRID_EMIN) s = 0.0;
+    else if (eps >= GRID_EMAX) s = OR_NGRID - 1;
+    else s = log(eps / GRID_EMIN) / (log(GRID_EMAX / GRID_EMIN) / (OR_NGRID - 1));
+    int i = (int)floor(s);
+    if (i > OR_NGRID - 2) i = OR_NGRID - 2;
+    double t = s - i;
+    return (1.0 - t) * pr->nu[i] + t * pr->nu[i + 1];
+}
+
+/* ------------------------------------------------------------------------ */
+int or_load_particles(or_case *c, int sp, int64_t n, const double *xi, const double *vx,
+                      const double *vy, const double *vz, const uint32_t *id)
+{
+    if (!c || sp < 0 || sp >= c->p.n_species || n < 0) return -1;
+    species_t *s = &c->sp[sp];
+    for (int64_t k = 0; k < n; ++k) {
+        if (!(xi[k] >= 0 && xi[k] < c->p.n_cells)) return -2;
+        if (sp_push(s, xi[k], vx[k], vy[k], vz[k], id[k])) return -3;
+    }
+    c->initialised = 0;
+    c->step = 0;
+    c->fe_n = 0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Charge assignment.  Reading: linear (cloud-in-cell) weighting, held as an   */
+/* integer count in units of 2^-32 particle: a particle at offset delta in     */
+/* cell j gives node j the weight 2^32 - f and node j+1 the weight f, with     */
+/* f = floor(delta * 2^32).  Periodic: node n_cells is node 0.                 */
+/* ------------------------------------------------------------------------ */
+void or_deposit(int n_cells, int periodic, int64_t n, const double *xi, int64_t *R)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        double j = floor(xi[k]);
+        double delta = xi[k] - j;
+        int64_t f = (int64_t)floor(delta * TWO32);
+        int jn = (int)j + 1;
+        if (periodic && jn == n_cells) jn = 0;
+        R[(int)j] += ((int64_t)1 << 32) - f;
+        R[jn] += f;
+    }
+}
+
+/* node volume per unit area: dx, and dx/2 at an electrode */
+static double node_vol(const or_case *c, int i)
+{
+    if (!c->p.periodic && (i == 0 || i == c->n_nodes - 1)) return 0.5 * c->dx;
+    return c->dx;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Poisson's equation (paper §1), second-order differences:                    */
+/*   (phi_{i-1} - 2 phi_i + phi_{i+1}) / dx^2 = -rho_i / eps0.                 */
+/* Bounded: phi_0 = phi_left, phi_N = 0, Thomas algorithm on nodes 1..N-1.     */
+/* Periodic: the mean of rho is removed, phi_0 is fixed at 0 and the same      */
+/* Dirichlet system is solved on nodes 1..N-1 (the equation at node 0 then    */
+/* holds because sum(rho) = 0); the mean of phi is removed at the end.         */
+/* ------------------------------------------------------------------------ */
+static void thomas(int m, const double *d, double *x)
+{
+    /* solves x_{i-1} - 2 x_i + x_{i+1} = d_i, i = 0..m-1, with x_{-1} = x_m = 0 */
+    double *cp = malloc(sizeof(double) * (m > 0 ? m : 1));
+    double *dp = malloc(sizeof(double) * (m > 0 ? m : 1));
+    for (int i = 0; i < m; ++i) {
+        double a = (i > 0) ? 1.0 : 0.0, b = -2.0, cc = (i < m - 1) ? 1.0 : 0.0;
+        double den = b - a * (i > 0 ? cp[i - 1] : 0.0);
+        cp[i] = cc / den;
+        dp[i] = (d[i] - a * (i > 0 ? dp[i - 1] : 0.0)) / den;
+    }
+    for (int i = m - 1; i >= 0; --i) x[i] = dp[i] - (i < m - 1 ? cp[i] * x[i + 1] : 0.0);
+    free(cp); free(dp);
+}
+
+int or_poisson(int n_cells, int periodic, double dx, const double *rho, double phi_left, double *phi)
+{
+    int N = n_cells;
+    double k2 = dx * dx / EPS0;
+    if (!periodic) {
+        int m = N - 1;
+        double *d = malloc(sizeof(double) * m);
+        for (int i = 1; i <= m; ++i) d[i - 1] = -rho[i] * k2;
+        d[0] -= phi_left;                       /* phi_N = 0 adds nothing */
+        thomas(m, d, phi + 1);
+        phi[0] = phi_left;
+        phi[N] = 0.0;
+        free(d);
+    } else {
+        double mean = 0;
+        for (int i = 0; i < N; ++i) mean += rho[i];
+        mean /= N;
+        int m = N - 1;
+        double *d = malloc(sizeof(double) * m);
+        for (int i = 1; i <= m; ++i) d[i - 1] = -(rho[i] - mean) * k2;
+        thomas(m, d, phi + 1);
+        phi[0] = 0.0;
+        double pm = 0;
+        for (int i = 0; i < N; ++i) pm += phi[i];
+        pm /= N;
+        for (int i = 0; i < N; ++i) phi[i] -= pm;
+        free(d);
+    }
+    return 0;
+}
+
+/* E = -dphi/dx at the nodes.  Interior: central difference.  Periodic: the
+ * same with wrap-around.  Electrode nodes (reading): Gauss's law over the
+ * half cell next to the wall, E_0 = -(phi_1-phi_0)/dx - rho_0 dx/(2 eps0) and
+ * E_N = -(phi_N-phi_{N-1})/dx + rho_N dx/(2 eps0). */
+static void field_from_phi(or_case *c)
+{
+    int N = c->p.n_cells, nn = c->n_nodes;
+    double dx = c->dx;
+    if (c->p.periodic) {
+        for (int i = 0; i < nn; ++i) {
+            int ip = (i + 1) % nn, im = (i - 1 + nn) % nn;
+            c->E[i] = -(c->phi[ip] - c->phi[im]) / (2.0 * dx);
+        }
+    } else {
+        for (int i = 1; i < N; ++i) c->E[i] = -(c->phi[i + 1] - c->phi[i - 1]) / (2.0 * dx);
+        c->E[0] = -(c->phi[1] - c->phi[0]) / dx - c->rho[0] * dx / (2.0 * EPS0);
+        c->E[N] = -(c->phi[N] - c->phi[N - 1]) / dx + c->rho[N] * dx / (2.0 * EPS0);
+    }
+}
+
+/* electrode voltage at x = 0, V(t) = sum_h A_h cos(2 pi f_h t + theta_h)
+ * (paper §1 "voltage waveform"; the two-harmonic form of §3.3) */
+static double drive_voltage(const or_case *c, double t)
+{
+    double v = 0;
+    for (int h = 0; h < c->p.n_harm && h < 4; ++h)
+        v += c->p.harm_amp[h] * cos(2.0 * M_PI * c->p.harm_freq[h] * t + c->p.harm_phase[h]);
+    return v;
+}
+
+/* deposit every species, form rho, solve for phi and E at time t */
+static void solve_field(or_case *c, double t)
+{
+    int nn = c->n_nodes;
+    for (int s = 0; s < c->p.n_species; ++s) {
+        memset(c->R[s], 0, sizeof(int64_t) * nn);
+        or_deposit(c->p.n_cells, c->p.periodic, c->sp[s].n, c->sp[s].xi, c->R[s]);
+    }
+    for (int i = 0; i < nn; ++i) {
+        double r = c->p.bg_charge;
+        for (int s = 0; s < c->p.n_species; ++s)
+            r += c->p.q[s] * c->p.w[s] * ((double)c->R[s][i] / TWO32) / node_vol(c, i);
+        c->rho[i] = r;
+    }
+    or_poisson(c->p.n_cells, c->p.periodic, c->dx, c->rho, c->p.periodic ? 0.0 : drive_voltage(c, t), c->phi);
+    field_from_phi(c);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Boris pusher (paper §1), one velocity update over a time h:                 */
+/* half electric kick, rotation about B by the angle 2 atan(qBh/2m), half kick.*/
+/* ------------------------------------------------------------------------ */
+void or_boris(double qm, double h, const double E[3], const double B[3], double v[3])
+{
+    double a = 0.5 * qm * h;
+    double vm[3] = { v[0] + a * E[0], v[1] + a * E[1], v[2] + a * E[2] };
+    double t[3] = { a * B[0], a * B[1], a * B[2] };
+    double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    double s[3] = { 2 * t[0] / (1 + t2), 2 * t[1] / (1 + t2), 2 * t[2] / (1 + t2) };
+    double vp[3] = { vm[0] + (vm[1] * t[2] - vm[2] * t[1]),
+                     vm[1] + (vm[2] * t[0] - vm[0] * t[2]),
+                     vm[2] + (vm[0] * t[1] - vm[1] * t[0]) };
+    double vq[3] = { vm[0] + (vp[1] * s[2] - vp[2] * s[1]),
+                     vm[1] + (vp[2] * s[0] - vp[0] * s[2]),
+                     vm[2] + (vp[0] * s[1] - vp[1] * s[0]) };
+    v[0] = vq[0] + a * E[0];
+    v[1] = vq[1] + a * E[1];
+    v[2] = vq[2] + a * E[2];
+}
+
+/* linear gather of the mesh field at xi, plus the imposed field */
+static void gather(const or_case *c, double xi, double E[3])
+{
+    int j = (int)floor(xi);
+    double d = xi - j;
+    int jn = j + 1;
+    if (c->p.periodic && jn == c->n_nodes) jn = 0;
+    E[0] = (1.0 - d) * c->E[j] + d * c->E[jn] + c->p.E_ext[0];
+    E[1] = c->p.E_ext[1];
+    E[2] = c->p.E_ext[2];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Scattering kinematics (readings: isotropic scattering; electrons scatter    */
+/* on an atom at rest with the elastic recoil loss (2m/M)(1-cos chi) eps;      */
+/* ions scatter isotropically in the centre-of-mass frame; charge exchange     */
+/* gives the ion the velocity of its gas partner; ionization shares the        */
+/* energy above threshold uniformly between the two electrons).               */
+/* ------------------------------------------------------------------------ */
+static void iso_dir(double ucos, double uphi, double n[3])
+{
+    double ct = 1.0 - 2.0 * ucos;
+    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double ph = 2.0 * M_PI * uphi;
+    n[0] = st * cos(ph); n[1] = st * sin(ph); n[2] = ct;
+}
+
+static void box_muller(double a, double b, double *n0, double *n1)
+{
+    double r = sqrt(-2.0 * log(a));
+    *n0 = r * cos(2.0 * M_PI * b);
+    *n1 = r * sin(2.0 * M_PI * b);
+}
+
+static double fminabs(double m, double v) { v = fabs(v); return v < m ? v : m; }
+
+/* one electron collision test; returns event code, updates v and margin */
+static int collide_electron(or_case *c, int64_t k, double *margin)
+{
+    species_t *s = &c->sp[0];
+    double m = c->p.m[0];
+    uint32_t r[4];
+    draw(c, s->id[k], c->step, 0, BLK_MCC, r);
+    double u0 = or_uniform(r[0]), u1 = or_uniform(r[1]);
+    double pnull = 1.0 - exp(-c->numax[0] * c->p.dt);
+    *margin = fminabs(*margin, u0 - pnull);
+    if (u0 >= pnull) return 0;
+    c->cnt.candidates[0]++;
+    double v2 = s->vx[k] * s->vx[k] + s->vy[k] * s->vy[k] + s->vz[k] * s->vz[k];
+    double eps = 0.5 * m * v2 / ELEM;
+    double x = u1 * c->numax[0];
+    int proc = -1, kind = OR_ELASTIC;
+    double thr = 0;
+    if (c->p.const_nu_e > 0) {
+        proc = 0;                               /* every candidate collides */
+    } else {
+        double cum = 0;
+        for (int q = 0; q < c->n_proc[0]; ++q) {
+            const proc_t *pr = &c->proc[0][q];
+            if (pr->thr > 0) *margin = fminabs(*margin, (eps - pr->thr) / pr->thr);
+            cum += nu_at(pr, eps);
+            *margin = fminabs(*margin, (x - cum) / c->numax[0]);
+            if (proc < 0 && x < cum) { proc = q; kind = pr->kind; thr = pr->thr; }
+        }
+        if (proc < 0) return 1;                 /* null collision */
+    }
+    c->cnt.collisions[0][proc]++;
+    double speed = sqrt(v2);
+    double n[3];
+    iso_dir(or_uniform(r[2]), or_uniform(r[3]), n);
+    if (kind == OR_ELASTIC) {
+        double cchi = speed > 0 ? (s->vx[k] * n[0] + s->vy[k] * n[1] + s->vz[k] * n[2]) / speed : 1.0;
+        double epsn = eps * (1.0 - 2.0 * m / c->p.gas_mass * (1.0 - cchi));
+        double sp = sqrt(2.0 * epsn * ELEM / m);
+        s->vx[k] = sp * n[0]; s->vy[k] = sp * n[1]; s->vz[k] = sp * n[2];
+    } else if (kind == OR_EXCITATION) {
+        double epsn = fmax(0.0, eps - thr);
+        double sp = sqrt(2.0 * epsn * ELEM / m);
+        s->vx[k] = sp * n[0]; s->vy[k] = sp * n[1]; s->vz[k] = sp * n[2];
+    } else if (kind == OR_IONIZATION) {
+        uint32_t a[4], b[4], ids[4];
+        draw(c, s->id[k], c->step, 0, BLK_AUX, a);
+        draw(c, s->id[k], c->step, 0, BLK_NEWION, b);
+        draw(c, s->id[k], c->step, 0, BLK_CHILD, ids);
+        double avail = fmax(0.0, eps - thr);
+        double eej = or_uniform(a[0]) * avail;
+        double esc = avail - eej;
+        double sp = sqrt(2.0 * esc * ELEM / m);
+        s->vx[k] = sp * n[0]; s->vy[k] = sp * n[1]; s->vz[k] = sp * n[2];
+        double ne[3];
+        iso_dir(or_uniform(a[1]), or_uniform(a[2]), ne);
+        double spe = sqrt(2.0 * eej * ELEM / m);
+        sp_push(&c->pend[0], s->xi[k], spe * ne[0], spe * ne[1], spe * ne[2], ids[0]);
+        if (c->p.n_species > 1) {
+            double g0, g1, g2, g3;
+            box_muller(or_uniform(b[0]), or_uniform(b[1]), &g0, &g1);
+            box_muller(or_uniform(b[2]), or_uniform(b[3]), &g2, &g3);
+            double vt = sqrt(KBOLTZ * c->p.gas_temp / c->p.m[1]);
+            sp_push(&c->pend[1], s->xi[k], vt * g0, vt * g1, vt * g2, ids[1]);
+        }
+        c->cnt.ionizations++;
+    }
+    return 2 + proc;
+}
+
+static int collide_ion(or_case *c, int64_t k, double *margin)
+{
+    species_t *s = &c->sp[1];
+    double m = c->p.m[1], M = c->p.gas_mass;
+    uint32_t r[4], a[4];
+    draw(c, s->id[k], c->step, 1, BLK_MCC, r);
+    double u0 = or_uniform(r[0]), u1 = or_uniform(r[1]);
+    double pnull = 1.0 - exp(-c->numax[1] * c->p.dt);
+    *margin = fminabs(*margin, u0 - pnull);
+    if (u0 >= pnull) return 0;
+    c->cnt.candidates[1]++;
+    /* gas partner drawn from the Maxwellian at the gas temperature */
+    draw(c, s->id[k], c->step, 1, BLK_AUX, a);
+    double g0, g1, g2, g3;
+    box_muller(or_uniform(a[0]), or_uniform(a[1]), &g0, &g1);
+    box_muller(or_uniform(a[2]), or_uniform(a[3]), &g2, &g3);
+    double vt = sqrt(KBOLTZ * c->p.gas_temp / M);
+    double vg[3] = { vt * g0, vt * g1, vt * g2 };
+    double gr[3] = { s->vx[k] - vg[0], s->vy[k] - vg[1], s->vz[k] - vg[2] };
+    double g2n = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+    double mu = m * M / (m + M);
+    double eps = 0.5 * mu * g2n / ELEM;
+    double x = u1 * c->numax[1];
+    double cum = 0;
+    int proc = -1, kind = OR_ISO;
+    for (int q = 0; q < c->n_proc[1]; ++q) {
+        const proc_t *pr = &c->proc[1][q];
+        if (pr->thr > 0) *margin = fminabs(*margin, (eps - pr->thr) / pr->thr);
+        cum += nu_at(pr, eps);
+        *margin = fminabs(*margin, (x - cum) / c->numax[1]);
+        if (proc < 0 && x < cum) { proc = q; kind = pr->kind; }
+    }
+    if (proc < 0) return 1;
+    c->cnt.collisions[1][proc]++;
+    if (kind == OR_CX) {
+        s->vx[k] = vg[0]; s->vy[k] = vg[1]; s->vz[k] = vg[2];
+    } else {
+        double n[3];
+        iso_dir(or_uniform(r[2]), or_uniform(r[3]), n);
+        double gm = sqrt(g2n);
+        double vc[3] = { (m * s->vx[k] + M * vg[0]) / (m + M), (m * s->vy[k] + M * vg[1]) / (m + M),
+                         (m * s->vz[k] + M * vg[2]) / (m + M) };
+        double f = M / (m + M) * gm;
+        s->vx[k] = vc[0] + f * n[0]; s->vy[k] = vc[1] + f * n[1]; s->vz[k] = vc[2] + f * n[2];
+    }
+    return 2 + proc;
+}
+
+/* Secondary emission (paper §1 "walls and secondary emission").  Reading: an
+ * ion reaching a wall releases an electron with probability gamma; the
+ * electron leaves the wall with a flux-weighted half-Maxwellian velocity at
+ * see_temp_ev (normal component Rayleigh, tangential components Gaussian),
+ * placed a random fraction of one step's flight into the gap. */
+static void emit_secondary(or_case *c, uint32_t ion_id, int wall, double *margin)
+{
+    uint32_t r[4], b[4], ids[4];
+    draw(c, ion_id, c->step, 1, BLK_SEE, r);
+    double u = or_uniform(r[0]);
+    *margin = fminabs(*margin, u - c->p.see_gamma);
+    if (u >= c->p.see_gamma) return;
+    draw(c, ion_id, c->step, 1, BLK_SEE_V, b);
+    draw(c, ion_id, c->step, 1, BLK_CHILD, ids);
+    double vth = sqrt(c->p.see_temp_ev * ELEM / c->p.m[0]);
+    double vn = vth * sqrt(-2.0 * log(or_uniform(r[1])));
+    double t0, t1;
+    box_muller(or_uniform(b[0]), or_uniform(b[1]), &t0, &t1);
+    double d = or_uniform(r[2]) * vn * c->p.dt / c->dx;     /* cells from the wall */
+    double N = c->p.n_cells;
+    if (d >= N) d = 0.5 * N;
+    double xi = wall == 0 ? d : N - d;
+    if (xi >= N) xi = nextafter(N, 0.0);
+    double vx = wall == 0 ? vn : -vn;
+    sp_push(&c->pend[0], xi, vx, vth * t0, vth * t1, ids[0]);
+    c->cnt.see_emitted++;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Leapfrog start (reading): the first step solves the field of the loaded     */
+/* state at t = 0 and pushes the velocities back by dt/2 with a Boris step.   */
+/* ------------------------------------------------------------------------ */
+static void initialise(or_case *c)
+{
+    solve_field(c, 0.0);
+    if (c->p.rewind) {
+        for (int s = 0; s < c->p.n_species; ++s) {
+            species_t *sp = &c->sp[s];
+            double qm = c->p.q[s] / c->p.m[s];
+            for (int64_t k = 0; k < sp->n; ++k) {
+                double E[3], v[3] = { sp->vx[k], sp->vy[k], sp->vz[k] };
+                gather(c, sp->xi[k], E);
+                or_boris(qm, -0.5 * c->p.dt, E, c->p.B, v);
+                sp->vx[k] = v[0]; sp->vy[k] = v[1]; sp->vz[k] = v[2];
+            }
+        }
+    }
+    c->initialised = 1;
+}
+
+static int is_diag_step(const or_case *c)
+{
+    return c->p.diag_interval > 0 && ((c->step + 1) % c->p.diag_interval) == 0;
+}
+
+/* CIC weights of a position onto its two nodes, as fractions */
+static void cic(const or_case *c, double xi, int *j, int *jn, double *w0, double *w1)
+{
+    *j = (int)floor(xi);
+    double d = xi - *j;
+    *jn = *j + 1;
+    if (c->p.periodic && *jn == c->n_nodes) *jn = 0;
+    *w0 = 1.0 - d; *w1 = d;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One time step n -> n+1.  Order (state x^n, v^{n-1/2}, E^n on entry):        */
+/*   1 gather E^n at x^n; 2 Boris v^{n-1/2} -> v^{n+1/2}; 3 x^{n+1} = x^n +    */
+/*   v_x dt; 4 walls: absorb, secondary emission; 5 null-collision MCC with    */
+/*   v^{n+1/2} at x^{n+1}; 6 append the particles created in 4-5 (they are     */
+/*   not moved or collided in the step that creates them); 7 deposit rho^{n+1}*/
+/*   of all particles; 8 Poisson at t^{n+1} with V(t^{n+1}); 9 E^{n+1};        */
+/*   10 moments.                                                               */
+/* ------------------------------------------------------------------------ */
+static int one_step(or_case *c)
+{
+    const or_params *p = &c->p;
+    int N = p->n_cells, nn = c->n_nodes;
+    double dtdx = p->dt / c->dx;
+    int diag = is_diag_step(c);
+    for (int s = 0; s < p->n_species; ++s) c->pend[s].n = 0;
+
+    for (int s = 0; s < p->n_species; ++s) {
+        species_t *sp = &c->sp[s];
+        double qm = p->q[s] / p->m[s];
+        int64_t keep = 0;
+        for (int64_t k = 0; k < sp->n; ++k) {
+            double margin = INFINITY;
+            int event = 0;
+            double E[3], v[3] = { sp->vx[k], sp->vy[k], sp->vz[k] };
+            gather(c, sp->xi[k], E);                                 /* 1 */
+            or_boris(qm, p->dt, E, p->B, v);                         /* 2 */
+            sp->vx[k] = v[0]; sp->vy[k] = v[1]; sp->vz[k] = v[2];
+            double xn = sp->xi[k] + v[0] * dtdx;                     /* 3 */
+            margin = fminabs(margin, xn - floor(xn + 0.5));
+            int absorbed = -1;
+            if (p->periodic) {
+                if (xn < 0) xn += N;
+                if (xn >= N) xn -= N;
+            } else if (xn < 0) {
+                absorbed = 0;
+            } else if (xn >= N) {
+                absorbed = 1;
+            }
+            if (diag)                                                /* J.E with the mesh field */
+                c->pw[s] += p->q[s] * p->w[s] * v[0] * (E[0] - p->E_ext[0]);
+            if (absorbed >= 0) {                                     /* 4 */
+                c->cnt.absorbed[s][absorbed]++;
+                if (s == 1 && p->see_gamma > 0) emit_secondary(c, sp->id[k], absorbed, &margin);
+                continue;
+            }
+            sp->xi[k] = xn;
+            if (c->numax[s] > 0) {                                   /* 5, 6 */
+                if (s == 0) event = collide_electron(c, k, &margin);
+                else event = collide_ion(c, k, &margin);
+            }
+            if (diag) {
+                double v2 = sp->vx[k] * sp->vx[k] + sp->vy[k] * sp->vy[k] + sp->vz[k] * sp->vz[k];
+                double eps = 0.5 * p->m[s] * v2 / ELEM;
+                int j, jn; double w0, w1;
+                cic(c, xn, &j, &jn, &w0, &w1);
+                c->en[s * nn + j] += p->w[s] * eps * w0 / node_vol(c, j);
+                c->en[s * nn + jn] += p->w[s] * eps * w1 / node_vol(c, jn);
+                c->dens_diag[s * nn + j] += p->w[s] * w0 / node_vol(c, j);
+                c->dens_diag[s * nn + jn] += p->w[s] * w1 / node_vol(c, jn);
+                c->ke[s] += 0.5 * p->m[s] * p->w[s] * v2;
+                if (s == 0 && xn >= 0.45 * N && xn < 0.55 * N) {
+                    int b = (int)floor(eps / 0.25);
+                    if (b < OR_EEPF_BINS) c->eepf[b] += 1.0;
+                }
+            }
+            /* compact in place */
+            sp->xi[keep] = sp->xi[k]; sp->vx[keep] = sp->vx[k]; sp->vy[keep] = sp->vy[k];
+            sp->vz[keep] = sp->vz[k]; sp->id[keep] = sp->id[k];
+            sp->margin[keep] = margin; sp->event[keep] = event;
+            ++keep;
+        }
+        sp->n = keep;
+    }
+    for (int s = 0; s < p->n_species; ++s) {                          /* 6 */
+        species_t *pd = &c->pend[s];
+        for (int64_t k = 0; k < pd->n; ++k)
+            if (sp_push(&c->sp[s], pd->xi[k], pd->vx[k], pd->vy[k], pd->vz[k], pd->id[k])) return -1;
+    }
+    solve_field(c, (double)(c->step + 1) * p->dt);                    /* 7, 8, 9 */
+    /* 10: moments */
+    for (int s = 0; s < p->n_species; ++s)
+        for (int i = 0; i < nn; ++i)
+            c->dens[s * nn + i] += p->w[s] * ((double)c->R[s][i] / TWO32) / node_vol(c, i);
+    for (int i = 0; i < nn; ++i) c->phi_sum[i] += c->phi[i];
+    c->cnt.n_steps++;
+    if (diag) c->cnt.n_diag++;
+    double fe = 0;
+    for (int i = 0; i < nn; ++i) fe += 0.5 * EPS0 * c->E[i] * c->E[i] * node_vol(c, i);
+    if (c->fe_n == c->fe_cap) {
+        int64_t nc = c->fe_cap ? 2 * c->fe_cap : 4096;
+        double *q = realloc(c->fe_hist, sizeof(double) * nc);
+        if (!q) return -1;
+        c->fe_hist = q; c->fe_cap = nc;
+    }
+    c->fe_hist[c->fe_n++] = fe;
+    c->step++;
+    c->cnt.step = c->step;
+    return 0;
+}
+
+int or_step(or_case *c, int64_t n_steps)
+{
+    if (!c) return -1;
+    if (!c->initialised) initialise(c);
+    for (int64_t i = 0; i < n_steps; ++i)
+        if (one_step(c)) return -1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+int64_t or_count(const or_case *c, int sp) { return (c && sp >= 0 && sp < OR_MAX_SPECIES) ? c->sp[sp].n : -1; }
+
+int or_get_particles(const or_case *c, int sp, double *xi, double *vx, double *vy, double *vz,
+                     uint32_t *id, double *margin, int32_t *event)
+{
+    if (!c || sp < 0 || sp >= c->p.n_species) return -1;
+    const species_t *s = &c->sp[sp];
+    size_t n = (size_t)s->n;
+    if (xi) memcpy(xi, s->xi, n * sizeof(double));
+    if (vx) memcpy(vx, s->vx, n * sizeof(double));
+    if (vy) memcpy(vy, s->vy, n * sizeof(double));
+    if (vz) memcpy(vz, s->vz, n * sizeof(double));
+    if (id) memcpy(id, s->id, n * sizeof(uint32_t));
+    if (margin) memcpy(margin, s->margin, n * sizeof(double));
+    if (event) memcpy(event, s->event, n * sizeof(int32_t));
+    return 0;
+}
+
+int or_get_field(const or_case *c, double *phi, double *E)
+{
+    if (!c) return -1;
+    if (phi) memcpy(phi, c->phi, sizeof(double) * c->n_nodes);
+    if (E) memcpy(E, c->E, sizeof(double) * c->n_nodes);
+    return 0;
+}
+
+int or_get_deposit(const or_case *c, int sp, int64_t *R)
+{
+    if (!c || sp < 0 || sp >= c->p.n_species) return -1;
+    memcpy(R, c->R[sp], sizeof(int64_t) * c->n_nodes);
+    return 0;
+}
+
+int or_get_numax(const or_case *c, int sp, double *numax)
+{
+    if (!c || sp < 0 || sp >= OR_MAX_SPECIES) return -1;
+    *numax = c->numax[sp];
+    return 0;
+}
+
+int or_get_nu_table(const or_case *c, int sp, int k, double *nu)
+{
+    if (!c || sp < 0 || sp >= OR_MAX_SPECIES || k < 0 || k >= c->n_proc[sp]) return -1;
+    memcpy(nu, c->proc[sp][k].nu, sizeof(double) * OR_NGRID);
+    return 0;
+}
+
+void or_get_counters(const or_case *c, or_counters *out) { *out = c->cnt; }
+
+int or_get_moments(const or_case *c, double *dens, double *phi_sum, double *en, double *dens_diag,
+                   double *eepf, double *ke, double *pw)
+{
+    if (!c) return -1;
+    size_t nn = (size_t)c->n_nodes;
+    if (dens) memcpy(dens, c->dens, sizeof(double) * nn * OR_MAX_SPECIES);
+    if (phi_sum) memcpy(phi_sum, c->phi_sum, sizeof(double) * nn);
+    if (en) memcpy(en, c->en, sizeof(double) * nn * OR_MAX_SPECIES);
+    if (dens_diag) memcpy(dens_diag, c->dens_diag, sizeof(double) * nn * OR_MAX_SPECIES);
+    if (eepf) memcpy(eepf, c->eepf, sizeof(double) * OR_EEPF_BINS);
+    if (ke) memcpy(ke, c->ke, sizeof(double) * OR_MAX_SPECIES);
+    if (pw) memcpy(pw, c->pw, sizeof(double) * OR_MAX_SPECIES);
+    return 0;
+}
+
+void or_reset_moments(or_case *c)
+{
+    size_t nn = (size_t)c->n_nodes;
+    memset(c->dens, 0, sizeof(double) * nn * OR_MAX_SPECIES);
+    memset(c->phi_sum, 0, sizeof(double) * nn);
+    memset(c->en, 0, sizeof(double) * nn * OR_MAX_SPECIES);
+    memset(c->dens_diag, 0, sizeof(double) * nn * OR_MAX_SPECIES);
+    memset(c->eepf, 0, sizeof(c->eepf));
+    memset(c->ke, 0, sizeof(c->ke));
+    memset(c->pw, 0, sizeof(c->pw));
+    int64_t step = c->cnt.step;
+    memset(&c->cnt, 0, sizeof(c->cnt));
+    c->cnt.step = step;
+}
+
+int64_t or_get_field_energy(const or_case *c, double *out, int64_t max_n)
+{
+    int64_t n = c->fe_n < max_n ? c->fe_n : max_n;
+    if (out) memcpy(out, c->fe_hist, sizeof(double) * (size_t)n);
+    return c->fe_n;
+}

@@ -1,0 +1,511 @@
+"""Pins of the FP64 oracle against results fixed by the paper, by mathematics or
+by an independent library -- never against the oracle itself.
+
+Each test names the plausible mistake it would catch.
+"""
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+from scipy.optimize import fsolve
+from scipy.special import wofz
+
+import oracle
+from paper_2609_17151_b300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = json.load(open(os.path.join(HERE, "golden", "paper_values.json")))
+EPS0 = W.EPS0
+E = W.E_CHARGE
+
+
+# --------------------------------------------------------------------------- Philox
+_TRITON_SCRIPT = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import torch, triton, triton.language as tl
+@triton.jit
+def k(out, c0p, c1p, c2p, c3p, seed, N: tl.constexpr):
+    i = tl.arange(0, N)
+    a, b, c, d = tl.philox(seed, tl.load(c0p + i), tl.load(c1p + i), tl.load(c2p + i), tl.load(c3p + i))
+    tl.store(out + 4 * i, a); tl.store(out + 4 * i + 1, b)
+    tl.store(out + 4 * i + 2, c); tl.store(out + 4 * i + 3, d)
+cases = json.loads(sys.argv[1])
+res = []
+for seed, ctrs in cases:
+    N = len(ctrs)
+    cols = [torch.tensor([c[j] for c in ctrs], dtype=torch.int64).to(torch.uint32) for j in range(4)]
+    out = torch.zeros(4 * N, dtype=torch.int64).to(torch.uint32)
+    k[(1,)](out, cols[0], cols[1], cols[2], cols[3], seed, N=N)
+    res.append([int(x) & 0xFFFFFFFF for x in out.view(torch.int32).tolist()])
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_triton_library():
+    """Philox4x32-10 against Triton's implementation run by Triton's CPU
+    interpreter (an independent library).  Catches a wrong multiplier, Weyl
+    constant, word permutation or round count."""
+    rng = np.random.default_rng(7)
+    cases = []
+    for seed in (0, 1, 0x9E3779B97F4A7C15 & 0x7FFFFFFFFFFFFFFF, 123456789123):
+        ctrs = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4]]
+        ctrs += rng.integers(0, 2**32, size=(5, 4), dtype=np.uint64).astype(int).tolist()
+        cases.append([seed, ctrs])
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    out = subprocess.check_output([sys.executable, "-c", _TRITON_SCRIPT, json.dumps(cases)], env=env,
+                                  timeout=600)
+    ref = json.loads(out.decode().strip().splitlines()[-1])
+    for (seed, ctrs), got in zip(cases, ref):
+        key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
+        for j, ctr in enumerate(ctrs):
+            assert oracle.philox4x32_10(ctr, key) == got[4 * j:4 * j + 4], (seed, ctr)
+
+
+def test_uniform_is_exact_in_fp32_and_open_interval():
+    for r in (0, 1, 255, 256, 0x7FFFFFFF, 0xFFFFFF00, 0xFFFFFFFF):
+        u = oracle.uniform(r)
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u
+
+
+# --------------------------------------------------------------------------- deposit
+def test_deposit_conserves_charge_and_splits_linearly():
+    """Sum of the deposit is N * 2^32 exactly; a single particle splits
+    (1-delta, delta) between its two nodes; periodic wraps onto node 0.
+    Catches a swapped weight pair or a lost wrap-around."""
+    rng = np.random.default_rng(3)
+    n_cells = 37
+    xi = rng.uniform(0, n_cells, 10001)
+    for periodic in (0, 1):
+        R = oracle.deposit(n_cells, periodic, xi)
+        assert int(R.sum()) == xi.size * 2**32
+    R = oracle.deposit(8, 0, [2.25])
+    assert R[2] == 3 * 2**30 and R[3] == 2**30 and R.sum() == 2**32
+    R = oracle.deposit(8, 1, [7.75])
+    assert R[7] == 2**30 and R[0] == 3 * 2**30
+    # first-moment: sum_j j R_j = sum_p xi_p 2^32 (to the 2^-32 truncation)
+    R = oracle.deposit(n_cells, 0, xi)
+    m1 = (np.arange(n_cells + 1) * R.astype(np.float64)).sum() / 2**32
+    assert abs(m1 - xi.sum()) < xi.size * 2**-31 + 1e-6
+
+
+# --------------------------------------------------------------------------- Poisson
+def _dense_bounded(n, dx, rho, vl):
+    m = n - 1
+    A = np.zeros((m, m))
+    for i in range(m):
+        A[i, i] = -2.0
+        if i > 0:
+            A[i, i - 1] = 1.0
+        if i < m - 1:
+            A[i, i + 1] = 1.0
+    b = -rho[1:n] * dx * dx / EPS0
+    b[0] -= vl
+    return np.concatenate([[vl], np.linalg.solve(A, b), [0.0]])
+
+
+def test_poisson_bounded_matches_dense_lu():
+    rng = np.random.default_rng(5)
+    for n in (2, 3, 17, 64):
+        dx = 1e-4
+        rho = rng.normal(0, 1e-6, n + 1)
+        phi = oracle.poisson(n, False, dx, rho, 37.5)
+        ref = _dense_bounded(n, dx, rho, 37.5)
+        assert np.allclose(phi, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_poisson_uniform_charge_gives_exact_parabola():
+    """Second differences are exact on quadratics:
+    phi(x) = V (1 - x/L) + rho x (L - x) / (2 eps0)."""
+    n, L, V, rho0 = 50, 0.02, 120.0, 3e-6
+    dx = L / n
+    x = np.arange(n + 1) * dx
+    phi = oracle.poisson(n, False, dx, np.full(n + 1, rho0), V)
+    ref = V * (1 - x / L) + rho0 * x * (L - x) / (2 * EPS0)
+    assert np.allclose(phi, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+
+
+def test_poisson_periodic_sine_mode():
+    """rho = sin(kx) on a periodic grid gives phi = rho / (eps0 kappa^2) with
+    kappa = 2 sin(k dx / 2) / dx (the 3-point Laplacian's eigenvalue), and a
+    constant added to rho changes nothing (neutralised)."""
+    n, L = 64, 0.03
+    dx = L / n
+    x = np.arange(n) * dx
+    for mode in (1, 3, 17):
+        k = 2 * np.pi * mode / L
+        kap2 = (2 * np.sin(k * dx / 2) / dx) ** 2
+        rho = 1e-6 * np.sin(k * x)
+        phi = oracle.poisson(n, True, dx, rho + 5e-7)
+        ref = rho / (EPS0 * kap2)
+        assert np.allclose(phi, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+
+
+def test_poisson_periodic_matches_dense_with_gauge():
+    rng = np.random.default_rng(11)
+    n, dx = 24, 1e-4
+    rho = rng.normal(0, 1e-6, n)
+    phi = oracle.poisson(n, True, dx, rho)
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, i] = -2
+        A[i, (i + 1) % n] = 1
+        A[i, (i - 1) % n] = 1
+    b = -(rho - rho.mean()) * dx * dx / EPS0
+    ref = np.linalg.lstsq(A, b, rcond=None)[0]      # minimum-norm = zero-mean solution
+    assert np.allclose(phi, ref - ref.mean(), rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+    assert abs(phi.mean()) < 1e-12 * np.abs(phi).max()
+
+
+# --------------------------------------------------------------------------- Boris
+def test_boris_pure_rotation_is_exact():
+    """E = 0: |v| is invariant and each step rotates v_perp by exactly
+    2 atan(omega_c dt / 2) (about B, in the sense of the charge).  Catches a
+    wrong s = 2t/(1+t^2), a sign of the cross products, or a missing half."""
+    qm = -E / W.M_E
+    B = np.array([0.0, 0.0, 0.01])
+    dt = 1e-11
+    wc = abs(qm) * B[2]
+    v = np.array([3e5, 0.0, 1e5])
+    speed0 = np.linalg.norm(v)
+    for _ in range(10000):
+        v = oracle.boris(qm, dt, [0, 0, 0], B, v)
+    assert abs(np.linalg.norm(v) - speed0) < 1e-13 * speed0 * 100
+    v1 = oracle.boris(qm, dt, [0, 0, 0], B, [1.0, 0.0, 0.0])
+    ang = math.atan2(v1[1], v1[0])
+    assert abs(abs(ang) - 2 * math.atan(wc * dt / 2)) < 1e-14
+    assert ang > 0  # electrons gyrate counter-clockwise about +z
+    vi = oracle.boris(E / W.M_AR, 1e-8, [0, 0, 0], B, [1.0, 0.0, 0.0])
+    assert math.atan2(vi[1], vi[0]) < 0  # ions the other way (paper Fig. 11)
+
+
+def test_exb_drift_same_for_both_species_and_gyroradius_ratio():
+    """E x B drift: both species drift at E x B / B^2 whatever their charge and
+    mass; gyroradii at equal perpendicular energy are in the ratio sqrt(M/m)
+    (paper §4 and Figure 11)."""
+    Ef = np.array([0.0, 0.0, 2e4])
+    B = np.array([0.0, 0.02, 0.0])
+    vE = np.cross(Ef, B) / np.dot(B, B)
+    for q, m in ((-E, W.M_E), (E, W.M_XE)):
+        wc = abs(q) * 0.02 / m
+        dt = 0.05 / wc
+        n = int(round(100 * 2 * np.pi / 0.05))
+        v = np.zeros(3)
+        acc = np.zeros(3)
+        for _ in range(n):
+            v = oracle.boris(q / m, dt, Ef, B, v)
+            acc += v
+        mean = acc / n
+        assert abs(mean[0] - vE[0]) < 0.01 * abs(vE[0]), (m, mean, vE)
+    eps = 10 * E
+    r_e = math.sqrt(2 * W.M_E * eps) / (E * 0.02)
+    r_i = math.sqrt(2 * W.M_XE * eps) / (E * 0.02)
+    assert abs(r_i / r_e - math.sqrt(W.M_XE / W.M_E)) < 1e-9 * r_i / r_e
+    g = GOLDEN["ecdi_wavelength"]
+    wce = E * g["B_T"] / W.M_E
+    lam = 2 * np.pi * (g["E_V_per_m"] / g["B_T"]) / wce
+    assert abs(lam * 1e3 - g["lambda_cyclotron_mm"]) < 0.001
+
+
+# --------------------------------------------------------------------------- leapfrog + field
+def _mode1_amplitudes(case, n_cells, steps):
+    amps = []
+    for _ in range(steps):
+        case.step(1)
+        _, Ef = case.field()
+        amps.append(abs(np.fft.rfft(Ef)[1]) * 2 / n_cells)
+    return np.array(amps)
+
+
+def _load(case, parts):
+    for s, p in enumerate(parts):
+        case.load_particles(s, W.as_xi(p), p["vx"], p["vy"], p["vz"], p["id"])
+
+
+def test_cold_plasma_oscillation_leapfrog_frequency():
+    """Cold, long-wavelength plasma oscillation (k lambda_D = 0.01): the
+    leapfrog frequency is (2/dt) asin(omega_p dt / 2) times a grid factor
+    within 0.3 % below 1 (64 cells per wavelength).  At omega_p dt = 1 the
+    leapfrog shift is +4.7 %, so an integrator of another order fails."""
+    wpdt = 1.0
+    cfg, parts = W.langmuir_case(seed=2, k_lambda_d=0.01, wpdt=wpdt, amp=0.002, ppc=50, slab=2)
+    c = oracle.Case(cfg)
+    _load(c, parts)
+    sig = []
+    for _ in range(60):
+        c.step(1)
+        sig.append(np.fft.rfft(c.field()[1])[1])
+    sig = np.array(sig)
+    y = sig.imag if np.abs(sig.imag).max() > np.abs(sig.real).max() else sig.real
+    tz = [(i + y[i - 1] / (y[i - 1] - y[i])) * wpdt for i in range(1, y.size) if y[i - 1] * y[i] < 0]
+    w_meas = np.pi / np.mean(np.diff(tz))
+    w_leap = 2 / wpdt * math.asin(wpdt / 2)
+    assert 0.997 * w_leap < w_meas < 1.0005 * w_leap, (w_meas, w_leap)
+
+
+def kinetic_root(klD):
+    """Root of 1 + (1 + zeta Z(zeta)) / (k lambda_D)^2 = 0, omega in units of
+    omega_p, with the plasma dispersion function Z from scipy's Faddeeva."""
+    def f(x):
+        w = x[0] + 1j * x[1]
+        z = w / (math.sqrt(2) * klD)
+        Z = 1j * math.sqrt(math.pi) * wofz(z)
+        D = 1 + (1 + z * Z) / klD**2
+        return [D.real, D.imag]
+    re, im = fsolve(f, [1.0 + 1.5 * klD**2, -0.05], xtol=1e-13)
+    return re, -im
+
+
+def fit_landau(amps, wpdt, t_lo=4.0, t_hi=35.0):
+    t = (np.arange(amps.size) + 1) * wpdt
+    pk = [i for i in range(1, amps.size - 1) if amps[i] > amps[i - 1] and amps[i] >= amps[i + 1]
+          and t_lo < t[i] < t_hi]
+    tt = t[pk]
+    gamma = -np.polyfit(tt, np.log(amps[pk]), 1)[0]
+    omega = math.pi / np.mean(np.diff(tt))
+    return omega, gamma
+
+
+def test_kinetic_root_reproduces_paper_numbers():
+    """The kinetic dispersion root at k lambda_D = 0.38 gives the paper's
+    damping rate and frequency shift (§3.1, Fig. 3)."""
+    g = GOLDEN["landau_klD038"]
+    w, gam = kinetic_root(g["k_lambda_d"])
+    assert abs(gam - g["gamma_over_wpe"]) < 0.001
+    w_bg = math.sqrt(1 + 3 * g["k_lambda_d"] ** 2)
+    assert abs(w / w_bg - g["omega_over_bohm_gross"]) < 0.005
+    assert abs(w / g["k_lambda_d"] - g["phase_velocity_over_vth"]) < 0.05
+
+
+@pytest.mark.parametrize("klD", [0.4, 0.38])
+def test_landau_damping_matches_kinetic_root(klD):
+    """The oracle's Langmuir wave (paper §3.1) damps at the kinetic Landau rate
+    and oscillates at the kinetic frequency.  64 cells, 1000 electrons per
+    cell (the 100-per-cell load's thermal noise is as large as a 1 % seed)."""
+    cfg, parts = W.langmuir_case(seed=1, k_lambda_d=klD, ppc=1000, slab=16)
+    c = oracle.Case(cfg)
+    _load(c, parts)
+    amps = _mode1_amplitudes(c, cfg["n_cells"], 360)
+    w, gam = fit_landau(amps, 0.1)
+    w0, g0 = kinetic_root(klD)
+    assert abs(w - w0) < 0.01 * w0, (w, w0)
+    assert abs(gam - g0) < 0.06 * g0, (gam, g0)
+    if klD == 0.38:
+        assert abs(gam - GOLDEN["landau_klD038"]["gamma_over_wpe"]) < 0.004
+
+
+def test_langmuir_total_energy_conserved():
+    """Field plus kinetic energy stays constant in the linear Landau case
+    (paper §3.1: mean energy flat, total energy constant)."""
+    cfg, parts = W.langmuir_case(seed=3, ppc=200, slab=8)
+    cfg["diag_interval"] = 1
+    c = oracle.Case(cfg)
+    _load(c, parts)
+    tot, fe = [], []
+    for _ in range(20):
+        c.reset_moments()
+        c.step(10)
+        ke = c.moments()["ke_sum"][0] / 10
+        f = c.field_energy()[-10:].mean()
+        tot.append(ke + f)
+        fe.append(f)
+    tot = np.array(tot)
+    # the wave's energy (~1e-4 of the thermal energy) must reappear as kinetic energy
+    assert np.ptp(tot) < 0.25 * (max(fe) - min(fe)), (np.ptp(tot), max(fe) - min(fe))
+
+
+# --------------------------------------------------------------------------- collisions
+def _beam_case(n, energy_ev, *, const_nu=0.0, tables=True, gas_mass=W.M_AR, seed=9, dt=1e-11,
+               n_cells=64, periodic=1, species=1, mtorr=30.0):
+    """isotropic monoenergetic electrons in the middle of a box; the weight is
+    so small that the space-charge field does no measurable work"""
+    ng = mtorr * 1e-3 * W.TORR / (W.K_B * 300.0)
+    sp = [dict(q=-E, m=W.M_E, w=1e-6), dict(q=E, m=W.M_AR, w=1e-6)][:species]
+    cfg = dict(periodic=periodic, n_cells=n_cells, length=n_cells * 1e-4, dt=dt, gas_density=ng,
+               gas_temp=300.0, gas_mass=gas_mass, const_nu_e=const_nu, species=sp, seed=seed,
+               rewind=0, xsec=[t for t in W.argon_tables() if t["species"] < species] if tables else [])
+    rng = np.random.default_rng(seed)
+    speed = math.sqrt(2 * energy_ev * E / W.M_E)
+    mu = rng.uniform(-1, 1, n)
+    ph = rng.uniform(0, 2 * np.pi, n)
+    s = np.sqrt(1 - mu**2)
+    xi = rng.uniform(n_cells * 0.4, n_cells * 0.6, n)
+    vx, vy, vz = speed * s * np.cos(ph), speed * s * np.sin(ph), speed * mu
+    return cfg, (xi, vx, vy, vz, np.arange(n, dtype=np.uint32))
+
+
+def test_constant_nu_velocity_decay_is_exponential():
+    """Constant collision frequency, isotropic scattering off infinitely heavy
+    atoms: <v_x>(t) = v0 exp(-nu t) exactly (each step collides with
+    probability 1 - exp(-nu dt)), and speeds never change."""
+    nu, dt, n = 2e9, 1e-10, 200_000
+    cfg, (xi, vx, vy, vz, ids) = _beam_case(n, 5.0, const_nu=nu, tables=False, gas_mass=1e10, dt=dt)
+    v0 = math.sqrt(2 * 5.0 * E / W.M_E)
+    c2 = oracle.Case(cfg)
+    c2.load_particles(0, xi, np.full(n, v0), np.zeros(n), np.zeros(n), ids)
+    for steps in (1, 4, 10):
+        c2.step(steps - c2.counters()["step"])
+        p = c2.particles(0)
+        expect = v0 * math.exp(-nu * dt * steps)
+        # the component along x after a collision averages to zero: sigma ~ v0/sqrt(3n)
+        assert abs(p["vx"].mean() - expect) < 5 * v0 / math.sqrt(3 * n), steps
+        sp = np.sqrt(p["vx"] ** 2 + p["vy"] ** 2 + p["vz"] ** 2)
+        assert np.allclose(sp, v0, rtol=1e-12)
+
+
+def test_null_collision_counts_are_binomial():
+    """Monoenergetic electrons at a grid energy of the synthetic argon tables:
+    per-process counts in one step follow Binomial(N, (1 - exp(-numax dt))
+    nu_k / numax), with nu_k = N_gas sigma_k(eps) v computed here from the
+    analytic cross sections, and numax the largest total over the grid."""
+    e_grid = W.table_energies()
+    eps = float(e_grid[850])          # ~ 63 eV: all three processes open
+    n = 400_000
+    cfg, (xi, vx, vy, vz, ids) = _beam_case(n, eps, dt=2e-11, species=2)
+    c = oracle.Case(cfg)
+    c.load_particles(0, xi, vx, vy, vz, ids)
+    c.step(1)
+    cnt = c.counters()
+    ng = cfg["gas_density"]
+    tabs = [t for t in W.argon_tables() if t["species"] == 0]
+    v = np.sqrt(2 * e_grid * E / W.M_E)
+    tot = sum(ng * t["sigma"] * v for t in tabs)
+    numax = tot.max()
+    pnull = 1 - math.exp(-numax * cfg["dt"])
+    speed = math.sqrt(2 * eps * E / W.M_E)
+    probs = [pnull * ng * t["sigma"][850] * speed / numax for t in tabs]
+    obs = cnt["collisions"][0][:3]
+    for o, p in zip(obs, probs):
+        mean, sd = n * p, math.sqrt(n * p * (1 - p))
+        assert abs(o - mean) < 5 * sd, (o, mean, sd)
+    assert abs(cnt["candidates"][0] - n * pnull) < 5 * math.sqrt(n * pnull)
+    assert cnt["ionizations"] == obs[2]
+    assert c.count(0) == n + obs[2] and c.count(1) == obs[2]
+
+
+def test_free_flight_times_are_geometric():
+    """Steps between real collisions at constant nu are geometric with
+    p = 1 - exp(-nu dt): mean 1/p (paper §4, free-flight-time distribution)."""
+    nu, dt, n = 5e8, 1e-10, 20_000
+    cfg, (xi, vx, vy, vz, ids) = _beam_case(n, 2.0, const_nu=nu, tables=False, gas_mass=1e10, dt=dt)
+    c = oracle.Case(cfg)
+    c.load_particles(0, xi, vx, vy, vz, ids)
+    first = np.full(n, -1)
+    for s in range(200):
+        c.step(1)
+        p = c.particles(0)
+        hit = (p["event"] >= 2) & (first[p["id"]] < 0)
+        first[p["id"][hit]] = s + 1
+    p_ = 1 - math.exp(-nu * dt)
+    done = first[first > 0]
+    # truncated geometric at 200 steps: compare the survival curve at a few points
+    for k in (1, 5, 20, 60):
+        surv = np.mean((first > k) | (first < 0))
+        assert abs(surv - (1 - p_) ** k) < 5 * math.sqrt((1 - p_) ** k / n) + 1e-3, k
+    assert done.size > 0
+
+
+def test_elastic_recoil_mean_loss_is_2m_over_M():
+    """Isotropic elastic scattering on an atom of mass M at rest loses on
+    average the fraction 2m/M of the energy per collision."""
+    M = 100 * W.M_E
+    nu, dt, n = 1e10, 1e-10, 200_000
+    cfg, (xi, vx, vy, vz, ids) = _beam_case(n, 4.0, const_nu=nu, tables=False, gas_mass=M, dt=dt)
+    c = oracle.Case(cfg)
+    c.load_particles(0, xi, vx, vy, vz, ids)
+    c.step(1)
+    p = c.particles(0)
+    hit = p["event"] >= 2
+    e1 = 0.5 * W.M_E * (p["vx"] ** 2 + p["vy"] ** 2 + p["vz"] ** 2) / E
+    loss = (4.0 - e1[hit]) / 4.0
+    assert abs(loss.mean() - 2 * W.M_E / M) < 5 * loss.std() / math.sqrt(hit.sum())
+    assert np.all(loss >= -1e-12) and np.all(loss <= 4 * W.M_E / M + 1e-12)
+
+
+def test_inelastic_energy_balance_and_pair_creation():
+    """With recoil switched off (M -> inf), the electron energy lost in one step
+    equals 11.5 eV per excitation plus 15.8 eV per ionization, and every
+    ionization appends exactly one electron and one ion at the parent's position."""
+    n = 100_000
+    cfg, (xi, vx, vy, vz, ids) = _beam_case(n, 120.0, gas_mass=1e30, species=2, dt=5e-11)
+    c = oracle.Case(cfg)
+    c.load_particles(0, xi, vx, vy, vz, ids)
+    e_before = 0.5 * W.M_E * (vx**2 + vy**2 + vz**2).sum() / E
+    c.step(1)
+    cnt = c.counters()
+    p = c.particles(0)
+    e_after = 0.5 * W.M_E * (p["vx"] ** 2 + p["vy"] ** 2 + p["vz"] ** 2).sum() / E
+    n_exc, n_iz = cnt["collisions"][0][1], cnt["collisions"][0][2]
+    assert n_iz > 100 and n_exc > 100
+    assert abs(e_before - e_after - 11.5 * n_exc - 15.8 * n_iz) < 1e-9 * e_before
+    assert c.count(0) == n + n_iz and c.count(1) == n_iz
+    ions = c.particles(1)
+    parents = set(p["xi"][:n].tolist())          # electrons that existed before the step
+    assert all(x in parents for x in ions["xi"].tolist())
+
+
+def test_secondary_emission_is_binomial_and_inward():
+    """Ions driven into both walls: emitted electrons ~ Binomial(hits, gamma),
+    each moving away from its wall and placed within the first cells."""
+    n, gamma = 50_000, 0.3
+    cfg = dict(periodic=0, n_cells=32, length=32e-4, dt=1e-11, gas_density=0.0, gas_temp=300.0,
+               gas_mass=W.M_AR, see_gamma=gamma, see_temp_ev=2.0,
+               species=[dict(q=-E, m=W.M_E, w=1e10), dict(q=E, m=W.M_AR, w=1e10)], seed=4, rewind=0)
+    rng = np.random.default_rng(4)
+    side = rng.integers(0, 2, n)
+    xi = np.where(side == 0, rng.uniform(0.0, 0.001, n), rng.uniform(31.999, 32.0, n))
+    vx = np.where(side == 0, -2e4, 2e4)
+    c = oracle.Case(cfg)
+    c.load_particles(1, xi, vx, np.zeros(n), np.zeros(n), np.arange(n, dtype=np.uint32))
+    c.step(1)
+    cnt = c.counters()
+    hits = int(cnt["absorbed"][1].sum())
+    assert hits == n
+    em = cnt["see_emitted"]
+    assert abs(em - hits * gamma) < 5 * math.sqrt(hits * gamma * (1 - gamma))
+    e = c.particles(0)
+    assert e["xi"].size == em
+    left = e["xi"] < 16
+    assert np.all(e["vx"][left] > 0) and np.all(e["vx"][~left] < 0)
+    vth = math.sqrt(2.0 * E / W.M_E)
+    dist = np.minimum(e["xi"], 32 - e["xi"])                 # cells from the wall
+    assert np.all(dist <= np.abs(e["vx"]) * cfg["dt"] / 1e-4 + 1e-9)
+    # normal speed is Rayleigh with scale vth: mean vth sqrt(pi/2)
+    assert abs(np.abs(e["vx"]).mean() / (vth * math.sqrt(np.pi / 2)) - 1) < 0.02
+
+
+# --------------------------------------------------------------------------- moments
+def test_uniform_plasma_density_moment_including_half_wall_cells():
+    """A uniform load between electrodes gives the loaded density at every node,
+    wall nodes included (their volume is dx/2)."""
+    n_cells, N = 40, 400_000
+    n0 = 1e15
+    L = 0.01
+    xi = (np.arange(N) + 0.5) / N * n_cells
+    cfg = dict(periodic=0, n_cells=n_cells, length=L, dt=1e-15, gas_density=0.0, gas_temp=300.0,
+               gas_mass=W.M_AR, species=[dict(q=E, m=W.M_AR, w=n0 * L / N)], seed=1, rewind=0)
+    c = oracle.Case(cfg)
+    c.load_particles(0, xi, np.zeros(N), np.zeros(N), np.zeros(N), np.arange(N, dtype=np.uint32))
+    c.step(1)
+    d = c.moments()["dens_sum"][0]
+    assert np.allclose(d[: n_cells + 1], n0, rtol=1e-6)
+
+
+def test_maxwellian_temperature_moment():
+    """Te = (2/3) <eps> of a Maxwellian load is its temperature (paper §3.2's
+    T_eff definition), to sampling error."""
+    cfg, parts = W.ccp_case(seed=2, n_cells=32, n_per_species=100_000, te_ev=3.0, volts=0.0, mtorr=0.0)
+    cfg["diag_interval"] = 1
+    cfg["xsec"] = []
+    cfg["dt"] = 1e-14
+    c = oracle.Case(cfg)
+    _load(c, parts)
+    c.step(1)
+    m = c.moments()
+    te = 2.0 / 3.0 * m["en_sum"][0][2:-2].sum() / m["dens_diag_sum"][0][2:-2].sum()
+    assert abs(te - 3.0) < 0.03
