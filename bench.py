@@ -1,0 +1,289 @@
+#!/usr/bin/env python
+"""Throughput of the 1D3V PIC-MCC particle step on B300.
+
+One "step" is one pass of the whole hot path (particle step of both species,
+FP64 field solve, and the periodic counting sort) over the E x B Hall-thruster
+workload: 2048 periodic cells, 2500 particles per cell per species
+(10.24M particles), imposed E = 20 kV/m and B = 0.02 T, constant-frequency
+electron-neutral collisions.  The particle state (245 MB) is larger than L2.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s on 1 B300 + % HBM roofline; batched & warm-start vs plain"
+UNIT = "particle-steps/s"
+ALGO_BYTES = 40          # per particle-step: cell, offset, vx, vy, vz read and written (4 B each)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ppc", type=int, default=2500, help="particles per cell per species")
+    ap.add_argument("--sort-interval", type=int, default=16)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(ppc):
+    return f"exb_hall_azimuthal_2048cells_{ppc}ppc_x2species"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- CPU legs
+def oracle_rate(ppc, steps, seed=1):
+    """Time the FP64 oracle (single thread, as it stands) on the same workload at
+    `ppc` particles per cell per species, `steps` steps after its field start."""
+    import oracle
+    from paper_2609_17151_b300 import workloads as W
+    cfg, parts = W.ecdi_case(seed=seed, ppc=ppc)
+    c = oracle.Case(cfg)
+    for s, p in enumerate(parts):
+        c.load_particles(s, W.as_xi(p), p["vx"], p["vy"], p["vz"], p["id"])
+    c.step(1)
+    n = c.count(0) + c.count(1)
+    t0 = time.perf_counter()
+    c.step(steps)
+    dt = time.perf_counter() - t0
+    return n * steps / dt, n, dt
+
+
+def cpu_baseline(target_s=12.0):
+    ppc = 50
+    rate, n, dt = oracle_rate(ppc, 2)
+    steps = max(2, int(target_s * rate / n))
+    rate, n, dt = oracle_rate(ppc, steps)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{workload_name(ppc)} ({n} particles), {steps} steps, {dt:.1f} s, FP64 C oracle, 1 thread"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2609_17151_b300 import workloads as W
+    ppc = 100
+    cfg, parts = W.ecdi_case(seed=1, ppc=ppc)
+    c = oracle.Case(cfg)
+    for s, p in enumerate(parts):
+        c.load_particles(s, W.as_xi(p), p["vx"], p["vy"], p["vz"], p["id"])
+    c.step(max(3, args.warmup))
+    n = c.count(0) + c.count(1)
+    t0 = time.perf_counter()
+    c.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt
+    sample = f"{workload_name(ppc)} ({n} particles): each step a 1/25 sample of the 2500-per-cell workload"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(2500), "sample_ppc": ppc, "n_cells": 2048, "parallelism": "none"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU leg
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2609_17151_b300 import pic
+    from paper_2609_17151_b300 import workloads as W
+
+    cfg, parts = W.ecdi_case(seed=1 + rank, ppc=args.ppc)
+    n_particles = sum(p["id"].size for p in parts)
+    stream = torch.cuda.Stream()
+    case = pic.Case(cfg, parts, stream=stream.cuda_stream, sort_interval=args.sort_interval)
+    case.step(max(3, args.warmup))
+    case.sync()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    n0 = sum(case.count())
+    # timed region 1 (the reported value): K steps, events only at its ends
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    case.step(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    case.sync()
+    n1 = sum(case.count())
+    # timed region 2 (roofline): the same K steps with CUDA events around every launch
+    case.profile(True)
+    barrier()
+    case.step(args.steps)
+    case.sync()
+    barrier()
+    prof = case.profile_read()
+    case.profile(False)
+    n2 = sum(case.count())
+    clk = clocks.stop()
+    ms_t = torch.tensor([ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    p_steps = 0.5 * (n0 + n1) * args.steps
+    p_steps2 = 0.5 * (n1 + n2) * args.steps
+    value = p_steps * world / (ms_max * 1e-3)
+
+    ps = prof["particle_step"]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peak = peaks["hbm_gbs"] if peaks else 6400.0
+    achieved = ALGO_BYTES * p_steps2 / (ps["total_ms"] * 1e-3) / 1e9 if ps["total_ms"] > 0 else None
+    launches = sum(v["launches"] for v in prof.values())
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        traffic = json.load(open(tpath)).get("particle_step_bytes_per_launch")
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the C ABI: load from pinned host buffers, K steps, moments back to host
+        pinned = []
+        for p in parts:
+            pinned.append({k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in p.items()})
+        ec = pic.Case(cfg, None, stream=stream.cuda_stream, sort_interval=args.sort_interval)
+        h2d = sum(t.numel() * t.element_size() for p in pinned for t in p.values())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s, p in enumerate(pinned):
+            pic.check(pic.lib.pic_load_particles(ec.h, s, p["id"].numel(), p["cell"].data_ptr(), p["off"].data_ptr(),
+                                                 p["vx"].data_ptr(), p["vy"].data_ptr(), p["vz"].data_ptr(),
+                                                 p["id"].data_ptr(), 0))
+        ec.step(args.steps)
+        mom = ec.moments()
+        t1 = time.perf_counter()
+        d2h = 8 * (mom["dens_sum"].size + mom["phi_sum"].size + mom["en_sum"].size + mom["dens_diag_sum"].size
+                   + mom["eepf"].size) + 512
+        e2e = {"value": n_particles * args.steps * world / (t1 - t0), "unit": UNIT,
+               "h2d_bytes_per_step": int(round(h2d / args.steps)), "d2h_bytes_per_step": int(round(d2h / args.steps)),
+               "note": f"load from pinned host + {args.steps} steps + moments to host, per job of {args.steps} steps"}
+        ec.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(args.ppc), "n_cells": 2048, "particles": n_particles,
+                       "particles_per_rank": n_particles, "dt_s": cfg["dt"], "sort_interval": args.sort_interval,
+                       "field": "f64 Poisson + field", "l2": "inputs larger than L2 (particle state "
+                       f"{24 * n_particles / 1e6:.0f} MB)", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "kernel": "k_particle_step", "algorithmic_bytes_per_particle_step": ALGO_BYTES,
+                         "peak_source": "measured" if peaks else "fallback",
+                         "kernel_ms_per_step": ps["total_ms"] / args.steps},
+            "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"]} for k, v in prof.items()},
+            "gpu_launches": launches,
+            "gpu_launches_note": "counted by the library in the profiled copy of the timed region (same K steps)",
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    case.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

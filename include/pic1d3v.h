@@ -1,0 +1,220 @@
+/*
+ * pic1d3v.h -- C ABI of the B300 (sm_103a) explicit 1D3V electrostatic
+ * PIC-MCC particle step.
+ *
+ * The method is the one the paper states in §1: charged super-particles move
+ * in the electric field computed on a mesh from their own charge (explicit
+ * leapfrog, Boris pusher with a static imposed B), collide with the neutral
+ * gas by the null-collision Monte Carlo method against tabulated cross
+ * sections, are absorbed at the electrodes with secondary electron emission,
+ * and Poisson's equation is solved on the mesh every step.  A case is set up
+ * with the quantities the paper's dialog asks for (§1: gas, pressure, gap,
+ * voltage waveform, magnetic field, walls and secondary emission).
+ *
+ * Conventions for every call:
+ *   - Returns a pic_status; calls never abort, exit or trap on the device.
+ *   - Work is enqueued on the case's stream; errors raised by device work
+ *     (capacity overflow, non-finite field, a device wait that gave up)
+ *     surface at the next call that synchronises (pic_read_*, pic_sync).
+ *   - Host pointers are read during the call only; the library keeps copies.
+ *   - A pic_case is not thread-safe; distinct cases are independent.
+ *   - pic_last_error() gives a human-readable message for the calling thread.
+ *
+ * Particle layout (species s, slot k): SoA, int32 cell[k] in [0, n_cells),
+ * float32 offset[k] in [0, 1) (position x = (cell + offset) dx), float32
+ * vx, vy, vz (m/s), uint32 id (keys the counter-based random numbers).
+ * Species 0 are electrons, species 1 ions.
+ */
+#ifndef PIC1D3V_H
+#define PIC1D3V_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_EINVAL = 1,      /* bad argument or descriptor */
+    PIC_ENOMEM = 2,      /* device allocation failed */
+    PIC_ECUDA = 3,       /* a CUDA runtime call failed (message in pic_last_error) */
+    PIC_ECAPACITY = 4,   /* particles exceeded a species' capacity; the overflow was not stored */
+    PIC_ENUMERIC = 5,    /* the field solve produced a non-finite value */
+    PIC_ETIMEOUT = 6,    /* a bounded device wait gave up */
+    PIC_ESTATE = 7       /* call not valid in the current state (e.g. step before load) */
+} pic_status;
+
+/* collision process kinds (cumulative sums follow the load order) */
+enum { PIC_ELASTIC = 0, PIC_EXCITATION = 1, PIC_IONIZATION = 2, PIC_ISO = 3, PIC_CX = 4 };
+
+#define PIC_DESC_VERSION 1u
+#define PIC_MAX_PROC 4
+#define PIC_NGRID 1000          /* cross-section grid: 1000 energies log-spaced on [1e-3, 1e3] eV */
+#define PIC_EEPF_BINS 240       /* 0..60 eV in 0.25 eV bins */
+
+/* Case descriptor: versioned plain data, SI units (paper §1's dialog). */
+typedef struct {
+    uint32_t struct_size;         /* sizeof(pic_case_desc) */
+    uint32_t version;             /* PIC_DESC_VERSION */
+    int32_t periodic;             /* 1: periodic box; 0: electrodes at x = 0 (driven) and x = L (grounded) */
+    int32_t n_cells;              /* 2 .. 4096 */
+    double length_m;
+    double dt_s;
+    double gas_density_m3;        /* N = p / (k_B T_gas) */
+    double gas_temp_k;
+    double gas_mass_kg;
+    double B_T[3];                /* static uniform magnetic field */
+    double E_ext_V_per_m[3];      /* static uniform imposed field, added to the mesh field */
+    int32_t n_harm;               /* V(t) = sum_h amp_h cos(2 pi f_h t + phase_h) at x = 0 (paper §3.3 form) */
+    double harm_freq_hz[4], harm_amp_v[4], harm_phase_rad[4];
+    double see_gamma;             /* electrons emitted per ion reaching an electrode */
+    double see_temp_ev;           /* temperature of the emitted electrons */
+    double background_charge_C_per_m3;   /* immobile uniform charge (paper §3.1 immobile ions) */
+    double const_nu_e_per_s;      /* > 0: constant-frequency electron-neutral elastic model instead of tables */
+    int32_t n_species;            /* 1 (electrons) or 2 (electrons, ions) */
+    double charge_C[2], mass_kg[2], weight_per_m2[2];
+    int64_t capacity[2];          /* particle slots per species; 0 = 2x the first load (min 65536) */
+    uint64_t seed;                /* Philox key */
+    int32_t sort_interval;        /* steps between counting sorts by cell (which also compact); 0 = 16 */
+    int32_t diag_interval;        /* energy moments / EEPF every diag_interval steps; 0 = never */
+    int32_t rewind;               /* 1: velocities given to pic_load_particles are at t = 0 and are
+                                     pushed back by dt/2 before the first step (leapfrog start) */
+    int32_t field_history;        /* field-energy history length kept on the device; 0 = 65536 */
+    void *stream;                 /* cudaStream_t to enqueue on; NULL = a stream owned by the case */
+    /* optional device allocator (e.g. a framework's caching allocator); NULL = cudaMalloc */
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *ctx);
+    void *alloc_ctx;
+} pic_case_desc;
+
+typedef struct pic_case pic_case;
+
+/* Create a case on the current CUDA device.  Copies the descriptor.
+ * Errors: PIC_EINVAL (sizes, version), PIC_ENOMEM, PIC_ECUDA. */
+pic_status pic_create_case(const pic_case_desc *desc, pic_case **out);
+
+/* Load one collision process of one species from a raw table (paper §1:
+ * tabulated cross sections, LXCat format): n points of energy (eV,
+ * ascending) and cross section (m^2).  The table is sampled onto the
+ * 1000-point log grid by linear interpolation in energy (constant beyond
+ * its ends, zero below threshold_ev); the collision frequency
+ * nu = N sigma g is tabulated there (g: electron speed; for ions the
+ * relative speed at centre-of-mass energy eps) and interpolated linearly in
+ * ln(eps) during the step.  At most PIC_MAX_PROC processes per species.
+ * Errors: PIC_EINVAL (species, kind, n < 1, too many processes, tables
+ * combined with the constant-frequency model). */
+pic_status pic_load_xsec_table(pic_case *c, int species, int kind, double threshold_ev,
+                               const double *energy_ev, const double *sigma_m2, int n);
+
+/* Replace the particles of one species with n particles in the layout above
+ * (id may be NULL: ids 0..n-1).  on_device != 0: the pointers are device
+ * pointers.  The case restarts at step 0; the next pic_step first solves the
+ * field of the loaded state at t = 0 and, if desc.rewind, pushes the
+ * velocities back by dt/2.  Errors: PIC_EINVAL (a cell outside [0,n_cells)
+ * or offset outside [0,1) is reported by the next synchronising call as
+ * PIC_EINVAL), PIC_ECAPACITY (n above capacity). */
+pic_status pic_load_particles(pic_case *c, int species, int64_t n, const int32_t *cell,
+                              const float *offset, const float *vx, const float *vy,
+                              const float *vz, const uint32_t *id, int on_device);
+
+/* Enqueue n_steps time steps (paper §1 scheme; step order in the design
+ * notes) on the case stream.  Returns after enqueueing.  Errors:
+ * PIC_ESTATE (no particles loaded), PIC_ECUDA (launch failure). */
+pic_status pic_step(pic_case *c, int64_t n_steps);
+
+/* Wait for the case stream and report any error raised by device work. */
+pic_status pic_sync(pic_case *c);
+
+/* Live particle count per species (synchronises). */
+pic_status pic_count(pic_case *c, int64_t n_alive[2]);
+
+/* Copy the live particles of a species to host buffers of max_n entries
+ * (order unspecified).  *n_out = live count; PIC_ECAPACITY if max_n is
+ * smaller (nothing beyond max_n written).  Any output pointer may be NULL. */
+pic_status pic_read_particles(pic_case *c, int species, int64_t max_n, int64_t *n_out,
+                              int32_t *cell, float *offset, float *vx, float *vy, float *vz,
+                              uint32_t *id);
+
+/* Copy the FP64 potential and field at the nodes (n_nodes = n_cells for a
+ * periodic case, n_cells + 1 otherwise) and, if rho_raw is not NULL, the
+ * raw fixed-point deposit of each species (int64, units of 2^-32 particle,
+ * n_species x n_nodes) of the last step.  Any pointer may be NULL. */
+pic_status pic_read_field(pic_case *c, double *phi, double *E, int64_t *rho_raw);
+
+/* Moment sums accumulated since the last reset (paper §1 diagnostics:
+ * density and potential profiles, EEPF, currents).  Caller-owned buffers;
+ * any array pointer may be NULL.  Sums over steps: divide by n_steps
+ * (n_diag for the diagnostic-step sums). */
+typedef struct {
+    uint32_t struct_size;          /* sizeof(pic_moments) */
+    int32_t n_nodes;               /* out */
+    int64_t step;                  /* out: completed steps since load */
+    int64_t n_steps, n_diag;       /* out: steps / diagnostic steps in the sums */
+    int64_t n_alive[2];            /* out */
+    int64_t absorbed[2][2];        /* out: per species, per electrode (x = 0, x = L) */
+    int64_t see_emitted, ionizations;
+    int64_t candidates[2];         /* out: null-collision candidates */
+    int64_t collisions[2][PIC_MAX_PROC];
+    double ke_sum[2];              /* out: kinetic energy per area (J/m^2), diagnostic steps */
+    double pw_sum[2];              /* out: sum q w v_x E_x(mesh) (W/m^2), diagnostic steps */
+    double *dens_sum;              /* [n_species * n_nodes] number density (m^-3), every step */
+    double *phi_sum;               /* [n_nodes] potential (V), every step */
+    double *en_sum;                /* [n_species * n_nodes] sum w eps (eV m^-3), diagnostic steps */
+    double *dens_diag_sum;         /* [n_species * n_nodes] density on diagnostic steps */
+    double *eepf;                  /* [PIC_EEPF_BINS] electron counts in the central 10 % of the gap */
+    double *field_energy;          /* [field_energy_cap] field energy per area (J/m^2) per step */
+    int64_t field_energy_cap;      /* in */
+    int64_t field_energy_n;        /* out: entries written */
+    int32_t reset;                 /* in: nonzero = clear the sums after reading */
+} pic_moments;
+
+pic_status pic_read_moments(pic_case *c, pic_moments *out);
+
+/* Free everything the case owns.  Safe on NULL. */
+pic_status pic_destroy(pic_case *c);
+
+/* Per-kernel timing of the step (CUDA events on the case stream around each
+ * launch) and launch counts.  pic_profile(c, 1) clears the records and starts
+ * recording events; pic_profile(c, 0) stops recording (launch counts are
+ * always kept).  pic_profile_read synchronises and returns one entry per
+ * kernel class ("particle_step", "field_solve", "sort", "init"). */
+typedef struct {
+    char name[32];
+    int64_t launches;      /* launches since the last pic_profile(c, 1) */
+    int64_t timed;         /* launches bracketed by events */
+    double total_ms;       /* summed event time of the timed launches */
+} pic_kernel_stat;
+
+pic_status pic_profile(pic_case *c, int enable);
+pic_status pic_profile_read(pic_case *c, pic_kernel_stat *out, int max_entries, int *n_out);
+
+const char *pic_status_str(pic_status s);
+const char *pic_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Kernel-level entry points (device pointers, enqueued on `stream`, a
+ * cudaStream_t or NULL for the default stream).  They expose single steps of
+ * the method for unit checks and for callers that manage their own particles.
+ * ------------------------------------------------------------------------- */
+
+/* Philox4x32-10 (Salmon et al., SC'11), the counter-based generator that keys
+ * every random draw of the step on (particle id, step, stream word): for
+ * i < n, out[4i..4i+3] = Philox(key, counter_i) with counter_i =
+ * (ctr[4i], ctr[4i+1], ctr[4i+2], ctr[4i+3]).  ctr, out: device, 4n uint32. */
+pic_status pic_philox(uint64_t seed, int64_t n, const uint32_t *ctr, uint32_t *out, void *stream);
+
+/* Linear (cloud-in-cell) charge assignment in fixed point (paper §1: the
+ * field is computed on the mesh from the particles' own charge): each of the
+ * n particles adds 2^32 - f to node cell and f to node cell+1 (periodic: node
+ * n_cells is node 0), f = floor(offset 2^32); particles with a cell outside
+ * [0, n_cells) or an offset outside [0, 1) are skipped.  R: device int64[n_nodes],
+ * accumulated into (not cleared).  Integer sums: bit-reproducible. */
+pic_status pic_deposit(int32_t n_cells, int32_t periodic, int64_t n, const int32_t *cell,
+                       const float *offset, int64_t *R, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

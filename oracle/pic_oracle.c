@@ -679,21 +679,6 @@ static int one_step(or_case *c)
                 if (s == 0) event = collide_electron(c, k, &margin);
                 else event = collide_ion(c, k, &margin);
             }
-            if (diag) {
-                double v2 = sp->vx[k] * sp->vx[k] + sp->vy[k] * sp->vy[k] + sp->vz[k] * sp->vz[k];
-                double eps = 0.5 * p->m[s] * v2 / ELEM;
-                int j, jn; double w0, w1;
-                cic(c, xn, &j, &jn, &w0, &w1);
-                c->en[s * nn + j] += p->w[s] * eps * w0 / node_vol(c, j);
-                c->en[s * nn + jn] += p->w[s] * eps * w1 / node_vol(c, jn);
-                c->dens_diag[s * nn + j] += p->w[s] * w0 / node_vol(c, j);
-                c->dens_diag[s * nn + jn] += p->w[s] * w1 / node_vol(c, jn);
-                c->ke[s] += 0.5 * p->m[s] * p->w[s] * v2;
-                if (s == 0 && xn >= 0.45 * N && xn < 0.55 * N) {
-                    int b = (int)floor(eps / 0.25);
-                    if (b < OR_EEPF_BINS) c->eepf[b] += 1.0;
-                }
-            }
             /* compact in place */
             sp->xi[keep] = sp->xi[k]; sp->vx[keep] = sp->vx[k]; sp->vy[keep] = sp->vy[k];
             sp->vz[keep] = sp->vz[k]; sp->id[keep] = sp->id[k];
@@ -708,10 +693,33 @@ static int one_step(or_case *c)
             if (sp_push(&c->sp[s], pd->xi[k], pd->vx[k], pd->vy[k], pd->vz[k], pd->id[k])) return -1;
     }
     solve_field(c, (double)(c->step + 1) * p->dt);                    /* 7, 8, 9 */
-    /* 10: moments */
+    /* 10: moments.  Every step: density and potential.  Diagnostic steps:
+     * energy moment, EEPF, kinetic energy over every particle alive after
+     * the append (v^{n+1/2} at x^{n+1}), and the density of that step. */
     for (int s = 0; s < p->n_species; ++s)
-        for (int i = 0; i < nn; ++i)
-            c->dens[s * nn + i] += p->w[s] * ((double)c->R[s][i] / TWO32) / node_vol(c, i);
+        for (int i = 0; i < nn; ++i) {
+            double d = p->w[s] * ((double)c->R[s][i] / TWO32) / node_vol(c, i);
+            c->dens[s * nn + i] += d;
+            if (diag) c->dens_diag[s * nn + i] += d;
+        }
+    if (diag) {
+        for (int s = 0; s < p->n_species; ++s) {
+            species_t *sp = &c->sp[s];
+            for (int64_t k = 0; k < sp->n; ++k) {
+                double v2 = sp->vx[k] * sp->vx[k] + sp->vy[k] * sp->vy[k] + sp->vz[k] * sp->vz[k];
+                double eps = 0.5 * p->m[s] * v2 / ELEM;
+                int j, jn; double w0, w1;
+                cic(c, sp->xi[k], &j, &jn, &w0, &w1);
+                c->en[s * nn + j] += p->w[s] * eps * w0 / node_vol(c, j);
+                c->en[s * nn + jn] += p->w[s] * eps * w1 / node_vol(c, jn);
+                c->ke[s] += 0.5 * p->m[s] * p->w[s] * v2;
+                if (s == 0 && sp->xi[k] >= 0.45 * N && sp->xi[k] < 0.55 * N) {
+                    int b = (int)floor(eps / 0.25);
+                    if (b < OR_EEPF_BINS) c->eepf[b] += 1.0;
+                }
+            }
+        }
+    }
     for (int i = 0; i < nn; ++i) c->phi_sum[i] += c->phi[i];
     c->cnt.n_steps++;
     if (diag) c->cnt.n_diag++;

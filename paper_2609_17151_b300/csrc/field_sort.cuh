@@ -1,0 +1,361 @@
+// field_sort.cuh -- FP64 field solve (one CTA) and the counting sort by cell.
+#pragma once
+#include "pic_device.cuh"
+
+namespace pic {
+
+// In-place inclusive scan of a[0..M) in shared memory by one CTA, in a fixed
+// order (bit-identical on every run).  `warp_tot` needs blockDim/32 doubles.
+__device__ void block_scan_inclusive(double *a, int M, double *warp_tot)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int k = (M + blockDim.x - 1) / blockDim.x;
+    const int lo = min(tid * k, M), hi = min(lo + k, M);
+    double s = 0.0;
+    for (int i = lo; i < hi; ++i) s += a[i];
+    double incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        double w = lane < nw ? warp_tot[lane] : 0.0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) warp_tot[lane] = w;
+    }
+    __syncthreads();
+    double run = (incl - s) + (warp > 0 ? warp_tot[warp - 1] : 0.0);
+    __syncthreads();
+    for (int i = lo; i < hi; ++i) { run += a[i]; a[i] = run; }
+    __syncthreads();
+}
+
+// Sum of v over the CTA (fixed order), result broadcast to every thread.
+__device__ double block_sum(double v, double *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// Exclusive prefix of one 64-bit integer per thread over the CTA (exact).
+__device__ unsigned long long block_exclusive_u64(unsigned long long v, unsigned long long *red,
+                                                  unsigned long long *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) red[warp] = incl;
+    __syncthreads();
+    unsigned long long off = 0, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+        if (w < warp) off += red[w];
+        tot += red[w];
+    }
+    *total = tot;
+    return off + incl - v;
+}
+
+// Exclusive prefix of one FP64 value per thread over the CTA (fixed order).
+__device__ double block_exclusive_f64(double v, double *red, double *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) red[warp] = incl;
+    __syncthreads();
+    double off = 0.0, tot = 0.0;
+    for (int w = 0; w < nw; ++w) {
+        if (w < warp) off += red[w];
+        tot += red[w];
+    }
+    *total = tot;
+    return off + (incl - v);
+}
+
+// Poisson's equation (paper §1) and the node field, FP64, one CTA.
+// (phi_{i-1} - 2 phi_i + phi_{i+1}) / dx^2 = -rho_i / eps0 on the interior
+// nodes; bounded: phi_0 = V(t), phi_N = 0; periodic: neutralised rho, phi_0 = 0
+// on the N-1 interior equations (the one at node 0 then holds), mean of phi
+// removed.  With r_k = rho_k dx^2/eps0, S_m = sum_{k=1..m} r_k and
+// T_i = sum_{m<i} S_m, the difference equation integrates exactly to
+//   phi_i = phi_0 + i d_0 - T_i,   d_0 = (T_N - phi_0) / N.
+// The charge enters as exact integer prefix sums of the fixed-point deposits,
+// P_s[m] = sum_{k=1..m} R_s[k], so S_m = sum_s c_s P_s[m] + b m with
+// c_s = (dx/eps0) q_s w_s 2^-32 and b the uniform part; only the second sum
+// and the per-node potential, field and energy use FP64 (B300's FP64 rate
+// is low, so the solve is written to need about a dozen FP64 operations per
+// node and no division).  E: central differences inside; Gauss's law over the
+// half cell at an electrode; wrap-around when periodic.
+// mode 0: field of the loaded state at t = 0; mode 1: end of a step
+// (t = (step+1) dt, moments accumulated, counters advanced).
+__global__ void __launch_bounds__(kFieldThreads) k_field(const __grid_constant__ StepConst P, int mode,
+                                                          unsigned long long *R_last)
+{
+    extern __shared__ __align__(16) double fsm[];
+    __shared__ unsigned long long ured[kFieldThreads / 32];
+    __shared__ double red[kFieldThreads / 32];
+    __shared__ double s_bcast[4];
+    const int N = P.n_cells, nn = P.n_nodes, tid = threadIdx.x, ns = P.n_species;
+    double *phi = fsm;                                                   // [N + 1]
+    double *T = fsm + (N + 1);                                           // [N + 1]
+    unsigned long long *Ps = reinterpret_cast<unsigned long long *>(fsm + 2 * (N + 1));   // [2][N + 1]
+    Ctrl *ctrl = P.ctrl;
+    const long long step = ctrl->step;
+    const bool diag = mode == 1 && P.diag_interval > 0 && ((step + 1) % P.diag_interval) == 0;
+    // each thread owns the contiguous nodes [lo, hi) of 0..N
+    const int per = (N + 1 + blockDim.x - 1) / blockDim.x;
+    const int lo = min(tid * per, N + 1), hi = min(lo + per, N + 1);
+
+    // 1. raw deposits (periodic: node N folds onto node 0), integer moment sums
+    unsigned long long tot_s[2] = {0ull, 0ull}, seg_s[2] = {0ull, 0ull};
+    for (int s = 0; s < ns; ++s) {
+        for (int i = lo; i < hi; ++i) {
+            unsigned long long r = 0ull;
+            if (i < nn) {
+                r = P.R[s][i];
+                if (P.periodic && i == 0) r += P.R[s][N];
+                R_last[s * nn + i] = r;
+                if (mode == 1) {
+                    P.Rsum[s * nn + i] += r;
+                    if (diag) P.Rdiag[s * nn + i] += r;
+                }
+            }
+            Ps[s * (N + 1) + i] = r;
+            if (i < nn) tot_s[s] += r;                        // all nodes (periodic mean)
+            if (i >= 1 && i <= N - 1) seg_s[s] += r;          // interior (Poisson sum)
+        }
+    }
+    __syncthreads();
+    for (int s = 0; s < ns; ++s)
+        for (int i = tid; i <= N; i += blockDim.x) P.R[s][i] = 0ull;
+    // 2. exact integer prefix sums P_s[m] = sum_{k=1..m} R_s[k] (interior nodes)
+    unsigned long long all_s[2] = {0ull, 0ull};
+    for (int s = 0; s < ns; ++s) {
+        unsigned long long total;
+        unsigned long long run = block_exclusive_u64(seg_s[s], ured, &total);
+        unsigned long long tsum;
+        (void)block_exclusive_u64(tot_s[s], ured, &tsum);
+        all_s[s] = tsum;
+        for (int i = lo; i < hi; ++i) {
+            if (i >= 1 && i <= N - 1) run += Ps[s * (N + 1) + i];
+            Ps[s * (N + 1) + i] = run;                        // P_s[i] (P_s[0] = 0)
+        }
+    }
+    // 3. S_m = sum_s c_s P_s[m] + b m; T_i = sum_{m<i} S_m (FP64, fixed order)
+    double b = P.bg_r;
+    if (P.periodic) {
+        double q = 0.0;
+        for (int s = 0; s < ns; ++s) q += P.cq[s] * (double)(long long)all_s[s];
+        b = -q / N;                                           // neutralising part (bg cancels)
+    }
+    double segS = 0.0;
+    for (int i = lo; i < hi; ++i) {
+        if (i < N) {
+            double S = b * (double)i;
+            for (int s = 0; s < ns; ++s) S = fma(P.cq[s], (double)(long long)Ps[s * (N + 1) + i], S);
+            T[i] = S;
+            segS += S;
+        }
+    }
+    double totS;
+    double runT = block_exclusive_f64(segS, red, &totS);
+    for (int i = lo; i < hi; ++i) {
+        const double S = i < N ? T[i] : 0.0;
+        T[i] = runT;                                          // T_i = sum_{m<i} S_m
+        runT += S;
+    }
+    if (tid == 0) {
+        double phi0 = 0.0;
+        if (!P.periodic) {
+            const double t = mode == 0 ? 0.0 : (double)(step + 1) * P.dt;
+            for (int h = 0; h < P.n_harm; ++h) phi0 += P.harm_a[h] * cos(2.0 * M_PI * P.harm_f[h] * t + P.harm_p[h]);
+        }
+        s_bcast[0] = phi0;
+        s_bcast[1] = (totS - phi0) / N;                       // d_0, T_N = sum of all S
+    }
+    __syncthreads();
+    const double phi0 = s_bcast[0], d0 = s_bcast[1];
+    double segT = 0.0;
+    for (int i = lo; i < hi; ++i) {
+        const double v = fma((double)i, d0, phi0) - T[i];
+        phi[i] = v;
+        if (i < N) segT += v;
+    }
+    if (P.periodic) {
+        double totT;
+        (void)block_exclusive_f64(segT, red, &totT);
+        const double pm = totT / N;
+        for (int i = lo; i < hi; ++i) phi[i] -= pm;
+    } else if (hi == N + 1 && lo <= N) {
+        phi[N] = 0.0;
+    }
+    __syncthreads();
+    // 4. node field, FP32 copy for the gather, field energy, potential sum
+    double fe = 0.0;
+    bool bad = false;
+    for (int i = lo; i < hi && i < nn; ++i) {
+        double E;
+        if (P.periodic) {
+            const int ip = i + 1 == N ? 0 : i + 1, im = i == 0 ? N - 1 : i - 1;
+            E = (phi[im] - phi[ip]) * P.inv_2dx;
+            fe = fma(E, E, fe);
+        } else if (i == 0 || i == N) {
+            double rq = P.bg_charge;                           // charge density of the wall node
+            for (int s = 0; s < ns; ++s) rq = fma(P.rho_wall[s], (double)(long long)R_last[s * nn + i], rq);
+            E = i == 0 ? (phi[0] - phi[1]) * P.inv_dx - rq * P.half_dx_eps0
+                       : (phi[N - 1] - phi[N]) * P.inv_dx + rq * P.half_dx_eps0;
+            fe = fma(0.5 * E, E, fe);
+        } else {
+            E = (phi[i - 1] - phi[i + 1]) * P.inv_2dx;
+            fe = fma(E, E, fe);
+        }
+        P.E[i] = E;
+        P.phi[i] = phi[i];
+        P.E32[i] = (float)E;
+        if (P.periodic && i == 0) P.E32[N] = (float)E;
+        if (mode == 1) P.phi_sum[i] += phi[i];
+        bad |= !isfinite(phi[i]) || !isfinite(E);
+    }
+    fe = block_sum(fe, red) * P.fe_c;
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(&ctrl->err, kErrNumeric);
+    if (tid == 0 && mode == 1) {
+        P.fe_hist[ctrl->fe_n % (unsigned long long)P.fe_cap] = fe;
+        ctrl->fe_n += 1;
+        ctrl->n_steps_acc += 1;
+        if (diag) ctrl->n_diag_acc += 1;
+        for (int s = 0; s < ns; ++s) {
+            unsigned long long nt = ctrl->n_total[s];
+            if (nt > P.cap[s]) nt = P.cap[s];
+            ctrl->n_total[s] = nt;
+            ctrl->n_active[s] = nt;
+        }
+        ctrl->step = step + 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Counting sort by cell (also drops absorbed slots, cell < 0):
+// count -> exclusive scan -> scatter into the other ping-pong half -> flip.
+// ---------------------------------------------------------------------------
+__global__ void k_sort_count(const __grid_constant__ StepConst P, int sp)
+{
+    extern __shared__ unsigned cnt_s[];
+    const int N = P.n_cells;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) cnt_s[j] = 0u;
+    __syncthreads();
+    const SpeciesBufs B = P.buf[sp][P.ctrl->cur[sp]];
+    const long long n = (long long)P.ctrl->n_active[sp];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = B.cell[i];
+        if (c >= 0) atomicAdd(&cnt_s[c], 1u);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x)
+        if (cnt_s[j]) atomicAdd(&P.sort_count[j], cnt_s[j]);
+}
+
+__global__ void __launch_bounds__(kFieldThreads) k_sort_scan(const __grid_constant__ StepConst P)
+{
+    extern __shared__ __align__(16) double ssm[];
+    __shared__ double red[kFieldThreads / 32];
+    const int N = P.n_cells;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) ssm[j] = (double)P.sort_count[j];
+    __syncthreads();
+    block_scan_inclusive(ssm, N, red);      // counts < 2^53: exact in FP64
+    for (int j = threadIdx.x; j < N; j += blockDim.x)
+        P.sort_cursor[j] = (unsigned long long)(ssm[j] - (double)P.sort_count[j]);
+    if (threadIdx.x == 0) P.sort_cursor[N] = (unsigned long long)ssm[N - 1];
+}
+
+constexpr int kSortChunk = 8192;
+
+__global__ void k_sort_scatter(const __grid_constant__ StepConst P, int sp)
+{
+    extern __shared__ __align__(16) unsigned char xsm[];
+    const int N = P.n_cells;
+    unsigned long long *base = reinterpret_cast<unsigned long long *>(xsm);
+    unsigned *lcnt = reinterpret_cast<unsigned *>(xsm + 8 * (size_t)N);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) lcnt[j] = 0u;
+    __syncthreads();
+    const int half = P.ctrl->cur[sp];
+    const SpeciesBufs A = P.buf[sp][half], D = P.buf[sp][half ^ 1];
+    const long long n = (long long)P.ctrl->n_active[sp];
+    const long long lo = (long long)blockIdx.x * kSortChunk, hi = min(lo + kSortChunk, n);
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const int c = A.cell[i];
+        if (c >= 0) atomicAdd(&lcnt[c], 1u);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const unsigned k = lcnt[j];
+        base[j] = k ? atomicAdd(&P.sort_cursor[j], (unsigned long long)k) : 0ull;
+        lcnt[j] = 0u;
+    }
+    __syncthreads();
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const int c = A.cell[i];
+        if (c < 0) continue;
+        const unsigned long long p = base[c] + atomicAdd(&lcnt[c], 1u);
+        D.cell[p] = c; D.off[p] = A.off[i]; D.vx[p] = A.vx[i]; D.vy[p] = A.vy[i]; D.vz[p] = A.vz[i];
+        D.id[p] = A.id[i];
+    }
+}
+
+__global__ void k_sort_finish(const __grid_constant__ StepConst P, int sp)
+{
+    const int N = P.n_cells;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Ctrl *ctrl = P.ctrl;
+        const unsigned long long live = P.sort_cursor[N];
+        ctrl->cur[sp] ^= 1;
+        ctrl->n_total[sp] = live;
+        ctrl->n_active[sp] = live;
+        ctrl->n_dead[sp] = 0ull;
+    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) P.sort_count[j] = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel-level entry points
+// ---------------------------------------------------------------------------
+__global__ void k_philox(uint32_t k0, uint32_t k1, long long n, const uint4 *ctr, uint4 *out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+__global__ void k_deposit_plain(int N, int periodic, long long n, const int32_t *cell, const float *off,
+                                unsigned long long *R)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = cell[i];
+        const float o = off[i];
+        if (c < 0 || c >= N || !(o >= 0.0f && o < 1.0f)) continue;     // outside the grid: not deposited
+        const uint32_t f = __float2uint_rz(o * 4294967296.0f);
+        const int c1 = (periodic && c + 1 == N) ? 0 : c + 1;
+        atomicAdd(&R[c], (1ull << 32) - f);
+        atomicAdd(&R[c1], (unsigned long long)f);
+    }
+}
+
+} // namespace pic

@@ -1,0 +1,528 @@
+// particle_step.cuh -- the fused per-species particle step (the hot loop).
+//
+// One persistent launch per species per step.  Each CTA stages the FP32 node
+// field and the species' collision-frequency table into shared memory with a
+// bulk asynchronous copy, then streams a contiguous range of particles in
+// chunks of four (int4/float4 loads and stores), doing for each particle:
+//   gather E^n (linear)  ->  Boris v^{n-1/2} -> v^{n+1/2}  ->  x^{n+1}
+//   -> electrode absorption (+ secondary emission)  ->  null-collision MCC
+//   -> append of the ionization products  ->  fixed-point CIC deposit of
+//   rho^{n+1} into a shared-memory histogram, flushed once per CTA.
+// Particle state is updated in place; absorbed particles get cell = -1 and
+// are compacted by the next counting sort.
+#pragma once
+#include "pic_device.cuh"
+
+namespace pic {
+
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Stage `bytes` (multiple of 16, 16-byte aligned) from global to shared with a
+// bulk copy tracked by an mbarrier (issued by one thread).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(mbar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_addr(mbar)), "r"(count) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" :: "r"(smem_addr(mbar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_addr(mbar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the staging copy: gives up after a fixed number of polls,
+// raises kErrTimeout, then polls again (bounded) so no copy is left in
+// flight when the CTA returns.  Returns false if the data never arrived.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, Ctrl *ctrl)
+{
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(mbar, 0)) return true;
+    atomicOr(&ctrl->err, kErrTimeout);
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(mbar, 0)) return false;
+    return false;
+}
+
+// nu_k(eps): linear in ln(eps) between the grid energies; zero below threshold.
+__device__ __forceinline__ float nu_at(const float *tab, float eps, float thr, float inv_dlog)
+{
+    if (eps < thr) return 0.0f;
+    float s = logf(eps * (1.0f / kGridEmin)) * inv_dlog;
+    s = fminf(fmaxf(s, 0.0f), (float)(kNGrid - 1));
+    int i = min((int)s, kNGrid - 2);
+    const float t = s - (float)i;
+    return (1.0f - t) * tab[i] + t * tab[i + 1];
+}
+
+struct Cell { int c; float o; };
+
+// Append one particle to species `sp` (slot from the global counter), deposit
+// it into rho^{n+1} directly and add it to the diagnostic-step moments.
+__device__ void append_particle(const StepConst &P, int sp, int half, int c, float o, float vx, float vy,
+                                float vz, uint32_t id, bool diag)
+{
+    Ctrl *ctrl = P.ctrl;
+    const unsigned long long slot = atomicAdd(&ctrl->n_total[sp], 1ull);
+    if (slot >= P.cap[sp]) {
+        atomicOr(&ctrl->err, kErrCapacity);
+        return;
+    }
+    const SpeciesBufs &B = P.buf[sp][half];
+    B.cell[slot] = c; B.off[slot] = o; B.vx[slot] = vx; B.vy[slot] = vy; B.vz[slot] = vz; B.id[slot] = id;
+    const uint32_t f = __float2uint_rz(o * 4294967296.0f);
+    atomicAdd(&P.R[sp][c], (1ull << 32) - f);
+    atomicAdd(&P.R[sp][c + 1], (unsigned long long)f);
+    if (diag) {
+        const SpConst &S = P.sp[sp];
+        const float v2 = vx * vx + vy * vy + vz * vz;
+        const float eps = S.m_over_2e * v2;
+        const int nn = P.n_nodes;
+        const int c1 = (P.periodic && c + 1 == P.n_cells) ? 0 : c + 1;
+        const double iv0 = (!P.periodic && c == 0) ? 1.0 / P.vol_wall : 1.0 / P.vol_interior;
+        const double iv1 = (!P.periodic && c1 == P.n_cells) ? 1.0 / P.vol_wall : 1.0 / P.vol_interior;
+        atomicAdd(&P.en_sum[sp * nn + c], S.w * (double)eps * (1.0 - (double)o) * iv0);
+        atomicAdd(&P.en_sum[sp * nn + c1], S.w * (double)eps * (double)o * iv1);
+        atomicAdd(&P.ke_sum[sp], 0.5 * S.m * S.w * (double)v2);
+        const float xi = (float)c + o;
+        if (sp == 0 && xi >= P.eepf_lo && xi < P.eepf_hi) {
+            const int b = (int)(eps * 4.0f);
+            if (b < kEepfBins) atomicAdd(&P.eepf[b], 1ull);
+        }
+    }
+}
+
+// Electron collision (null-collision method).  Returns the process index
+// (-1: no real collision) and updates v.
+__device__ __forceinline__ void collide_electron(const StepConst &P, const float *nus, uint32_t id, uint32_t step,
+                                                 int c, float o, float3 &v, int half_e, int half_i, bool diag,
+                                                 unsigned *s_cnt)
+{
+    const SpConst &S = P.sp[0];
+    const uint4 r = draw(P, id, step, 0, kBlkMcc);
+    if (u01(r.x) >= S.pnull) return;
+    atomicAdd(&s_cnt[0], 1u);
+    const float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
+    const float eps = S.m_over_2e * v2;
+    const float x = u01(r.y) * S.numax;
+    int proc = -1, kind = 0;
+    float thr = 0.0f;
+    if (S.mcc == 2) {
+        proc = 0;
+    } else {
+        float cum = 0.0f;
+        for (int k = 0; k < S.nproc; ++k) {
+            cum += nu_at(nus + k * kNGrid, eps, S.thr[k], P.inv_dlog);
+            if (x < cum) { proc = k; kind = S.kind[k]; thr = S.thr[k]; break; }
+        }
+        if (proc < 0) return;
+    }
+    atomicAdd(&s_cnt[1 + proc], 1u);
+    const float3 n = iso_dir(u01(r.z), u01(r.w));
+    if (kind == 0) {                                    // elastic, atom at rest
+        const float speed = sqrtf(v2);
+        const float cchi = speed > 0.0f ? (v.x * n.x + v.y * n.y + v.z * n.z) / speed : 1.0f;
+        const float epsn = eps * (1.0f - S.recoil * (1.0f - cchi));
+        const float sp = S.v_of_sqrt_eps * sqrtf(fmaxf(epsn, 0.0f));
+        v = make_float3(sp * n.x, sp * n.y, sp * n.z);
+    } else if (kind == 1) {                             // excitation
+        const float sp = S.v_of_sqrt_eps * sqrtf(fmaxf(eps - thr, 0.0f));
+        v = make_float3(sp * n.x, sp * n.y, sp * n.z);
+    } else {                                            // ionization: share eps - thr
+        const uint4 a = draw(P, id, step, 0, kBlkAux);
+        const uint4 ids = draw(P, id, step, 0, kBlkChild);
+        const float avail = fmaxf(eps - thr, 0.0f);
+        const float eej = u01(a.x) * avail;
+        const float esc = avail - eej;
+        const float sp = S.v_of_sqrt_eps * sqrtf(esc);
+        v = make_float3(sp * n.x, sp * n.y, sp * n.z);
+        const float3 ne = iso_dir(u01(a.y), u01(a.z));
+        const float spe = S.v_of_sqrt_eps * sqrtf(eej);
+        append_particle(P, 0, half_e, c, o, spe * ne.x, spe * ne.y, spe * ne.z, ids.x, diag);
+        if (P.n_species > 1) {
+            const uint4 b = draw(P, id, step, 0, kBlkNewIon);
+            const float2 g01 = box_muller(u01(b.x), u01(b.y));
+            const float2 g23 = box_muller(u01(b.z), u01(b.w));
+            const float vt = S.vt_newion;
+            append_particle(P, 1, half_i, c, o, vt * g01.x, vt * g01.y, vt * g23.x, ids.y, diag);
+        }
+        atomicAdd(&s_cnt[1 + kMaxProc], 1u);
+    }
+}
+
+__device__ __forceinline__ void collide_ion(const StepConst &P, const float *nus, uint32_t id, uint32_t step,
+                                            float3 &v, unsigned *s_cnt)
+{
+    const SpConst &S = P.sp[1];
+    const uint4 r = draw(P, id, step, 1, kBlkMcc);
+    if (u01(r.x) >= S.pnull) return;
+    atomicAdd(&s_cnt[0], 1u);
+    const uint4 a = draw(P, id, step, 1, kBlkAux);
+    const float2 g01 = box_muller(u01(a.x), u01(a.y));
+    const float2 g23 = box_muller(u01(a.z), u01(a.w));
+    const float3 vg = make_float3(S.vt_gas * g01.x, S.vt_gas * g01.y, S.vt_gas * g23.x);
+    const float3 g = make_float3(v.x - vg.x, v.y - vg.y, v.z - vg.z);
+    const float g2 = g.x * g.x + g.y * g.y + g.z * g.z;
+    const float eps = S.mu_over_2e * g2;
+    const float x = u01(r.y) * S.numax;
+    float cum = 0.0f;
+    int proc = -1, kind = 3;
+    for (int k = 0; k < S.nproc; ++k) {
+        cum += nu_at(nus + k * kNGrid, eps, S.thr[k], P.inv_dlog);
+        if (x < cum) { proc = k; kind = S.kind[k]; break; }
+    }
+    if (proc < 0) return;
+    atomicAdd(&s_cnt[1 + proc], 1u);
+    if (kind == 4) {                                    // charge exchange
+        v = vg;
+    } else {                                            // isotropic in the centre-of-mass frame
+        const float3 n = iso_dir(u01(r.z), u01(r.w));
+        const float f = S.Mfrac * sqrtf(g2);
+        v = make_float3(S.mfrac * v.x + S.Mfrac * vg.x + f * n.x, S.mfrac * v.y + S.Mfrac * vg.y + f * n.y,
+                        S.mfrac * v.z + S.Mfrac * vg.z + f * n.z);
+    }
+}
+
+// Secondary electron from an ion that reached electrode `wall`.
+__device__ __forceinline__ void emit_secondary(const StepConst &P, uint32_t id, uint32_t step, int wall, int half_e,
+                                               bool diag, unsigned *s_see)
+{
+    const uint4 r = draw(P, id, step, 1, kBlkSee);
+    if (u01(r.x) >= P.see_gamma) return;
+    const uint4 b = draw(P, id, step, 1, kBlkSeeV);
+    const uint4 ids = draw(P, id, step, 1, kBlkChild);
+    const float vn = P.see_vth * sqrtf(-2.0f * logf(u01(r.y)));
+    const float2 t = box_muller(u01(b.x), u01(b.y));
+    const int N = P.n_cells;
+    float d = u01(r.z) * vn * P.see_dtdx;
+    if (d >= (float)N) d = 0.5f * (float)N;
+    const float fl = floorf(d);
+    int c;
+    float o;
+    if (wall == 0) {
+        c = (int)fl; o = d - fl;
+    } else {
+        c = N - 1 - (int)fl; o = 1.0f - (d - fl);
+        if (o >= 1.0f) { o = 0.0f; c += 1; }
+        if (c >= N) { c = N - 1; o = 0.99999994f; }
+    }
+    if (o >= 1.0f) { o = 0.0f; c += 1; }
+    if (c >= N) { c = N - 1; o = 0.99999994f; }
+    const float vx = wall == 0 ? vn : -vn;
+    append_particle(P, 0, half_e, c, o, vx, P.see_vth * t.x, P.see_vth * t.y, ids.x, diag);
+    atomicAdd(s_see, 1u);
+}
+
+// Add a (cell, count, sum f) run to the shared histogram.
+__device__ __forceinline__ void hist_run(unsigned long long *h, int c, unsigned n, unsigned long long sf)
+{
+    atomicAdd(&h[c], ((unsigned long long)n << 32) - sf);
+    atomicAdd(&h[c + 1], sf);
+}
+
+// Shared memory layout of the step kernel (bytes, 16-aligned pieces).
+__host__ __device__ inline unsigned align16(unsigned x) { return (x + 15u) & ~15u; }
+struct StepSmem {
+    unsigned e_off, h_off, nu_off, en_off, eepf_off, total;
+    __host__ __device__ StepSmem(int n_cells, int nproc)
+    {
+        e_off = 0;
+        h_off = align16(e_off + (unsigned)(n_cells + 1) * 4u);
+        nu_off = align16(h_off + (unsigned)(n_cells + 1) * 8u);
+        en_off = align16(nu_off + (unsigned)nproc * kNGrid * 4u);
+        eepf_off = align16(en_off + (unsigned)(n_cells + 1) * 4u);
+        total = align16(eepf_off + kEepfBins * 4u);
+    }
+};
+
+template <int SP, bool PERIODIC, int MCC>
+__global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_constant__ StepConst P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint64_t mbar;
+    __shared__ unsigned s_cnt[2 + 2 * kMaxProc];        // candidates, per process, ionizations
+    __shared__ unsigned s_abs[2], s_see;
+    __shared__ float s_red[2][kStepThreads / 32];
+
+    const SpConst &S = P.sp[SP];
+    const int N = P.n_cells;
+    const StepSmem L(N, MCC == 1 ? S.nproc : 0);
+    float *Es = reinterpret_cast<float *>(smem + L.e_off);
+    unsigned long long *hist = reinterpret_cast<unsigned long long *>(smem + L.h_off);
+    float *nus = reinterpret_cast<float *>(smem + L.nu_off);
+    float *hen = reinterpret_cast<float *>(smem + L.en_off);
+    unsigned *heepf = reinterpret_cast<unsigned *>(smem + L.eepf_off);
+
+    Ctrl *ctrl = P.ctrl;
+    const int tid = threadIdx.x;
+    const unsigned e_bytes = align16((unsigned)(N + 1) * 4u);
+    const unsigned nu_bytes = MCC == 1 ? (unsigned)S.nproc * kNGrid * 4u : 0u;
+    if (tid == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(&mbar, e_bytes + nu_bytes);
+        bulk_g2s(Es, P.E32, e_bytes, &mbar);
+        if (MCC == 1) bulk_g2s(nus, P.nu_tab[SP], nu_bytes, &mbar);
+    }
+    const long long step_ll = ctrl->step;
+    const uint32_t step = (uint32_t)step_ll;
+    const bool diag = P.diag_interval > 0 && ((step_ll + 1) % P.diag_interval) == 0;
+    for (int j = tid; j <= N; j += blockDim.x) { hist[j] = 0ull; if (diag) hen[j] = 0.0f; }
+    if (diag) for (int j = tid; j < kEepfBins; j += blockDim.x) heepf[j] = 0u;
+    if (tid < 2 + 2 * kMaxProc) s_cnt[tid] = 0u;
+    if (tid < 2) s_abs[tid] = 0u;
+    if (tid == 0) s_see = 0u;
+    const bool staged = mbar_wait_bounded(&mbar, ctrl);
+    __syncthreads();
+    if (!__syncthreads_and(staged)) return;
+
+    const int half = ctrl->cur[SP];
+    const int half_e = ctrl->cur[0];
+    const int half_i = P.n_species > 1 ? ctrl->cur[1] : 0;
+    const SpeciesBufs B = P.buf[SP][half];
+    const long long n = (long long)ctrl->n_active[SP];
+    const long long n_chunks = (n + 3) / 4;
+    long long per = (n_chunks + gridDim.x - 1) / gridDim.x;
+    per = (per + 31) & ~31ll;
+    const long long beg = (long long)blockIdx.x * per;
+    const long long end = min(beg + per, n_chunks);
+
+    const float dtdx = P.dtdx;
+    const int lane = tid & 31, warp = tid >> 5;
+    float ke_acc = 0.0f, pw_acc = 0.0f;
+
+    for (long long base = beg + warp * 32; base < end; base += blockDim.x) {
+        const long long ch = base + lane;
+        const bool live_chunk = ch < end;
+        const long long i0 = ch * 4;
+        int4 c4 = make_int4(-1, -1, -1, -1);
+        float4 o4 = make_float4(0, 0, 0, 0), x4 = o4, y4 = o4, z4 = o4;
+        uint4 id4 = make_uint4(0, 0, 0, 0);
+        if (live_chunk) {
+            c4 = *reinterpret_cast<const int4 *>(B.cell + i0);
+            o4 = *reinterpret_cast<const float4 *>(B.off + i0);
+            x4 = *reinterpret_cast<const float4 *>(B.vx + i0);
+            y4 = *reinterpret_cast<const float4 *>(B.vy + i0);
+            z4 = *reinterpret_cast<const float4 *>(B.vz + i0);
+            if (MCC != 0 || (SP == 1 && !PERIODIC)) id4 = *reinterpret_cast<const uint4 *>(B.id + i0);
+        }
+        int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+        float oo[4] = {o4.x, o4.y, o4.z, o4.w};
+        float vx[4] = {x4.x, x4.y, x4.z, x4.w};
+        float vy[4] = {y4.x, y4.y, y4.z, y4.w};
+        float vz[4] = {z4.x, z4.y, z4.z, z4.w};
+        const uint32_t ids[4] = {id4.x, id4.y, id4.z, id4.w};
+        int dc[4];
+        uint32_t df[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            dc[q] = -1;
+            df[q] = 0;
+            int c = cc[q];
+            if (!live_chunk || i0 + q >= n || c < 0) continue;
+            float o = oo[q];
+            // 1. gather E^n (linear weights), plus the imposed field
+            const float e_mesh = (1.0f - o) * Es[c] + o * Es[c + 1];
+            const float ex = e_mesh + P.Ex_ext;
+            // 2. Boris: half kick, rotation, half kick
+            const float hx = S.c_e * ex;
+            float3 vm = make_float3(vx[q] + hx, vy[q] + S.cEy, vz[q] + S.cEz);
+            const float3 vp = make_float3(vm.x + (vm.y * S.tB[2] - vm.z * S.tB[1]),
+                                          vm.y + (vm.z * S.tB[0] - vm.x * S.tB[2]),
+                                          vm.z + (vm.x * S.tB[1] - vm.y * S.tB[0]));
+            float3 v = make_float3(vm.x + (vp.y * S.sB[2] - vp.z * S.sB[1]) + hx,
+                                   vm.y + (vp.z * S.sB[0] - vp.x * S.sB[2]) + S.cEy,
+                                   vm.z + (vp.x * S.sB[1] - vp.y * S.sB[0]) + S.cEz);
+            if (diag) pw_acc += v.x * e_mesh;
+            // 3. move
+            float on = fmaf(v.x, dtdx, o);
+            const float fl = floorf(on);
+            on -= fl;
+            c += (int)fl;
+            if (on >= 1.0f) { on = 0.0f; c += 1; }
+            if (PERIODIC) {
+                if ((unsigned)c >= (unsigned)N) { c %= N; if (c < 0) c += N; }
+            } else if ((unsigned)c >= (unsigned)N) {
+                // 4. electrode absorption (+ secondary emission by ions)
+                const int wall = c < 0 ? 0 : 1;
+                atomicAdd(&s_abs[wall], 1u);
+                if (SP == 1 && P.see_gamma > 0.0f) emit_secondary(P, ids[q], step, wall, half_e, diag, &s_see);
+                cc[q] = -1;
+                oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
+                continue;
+            }
+            // 5-6. null-collision MCC with v^{n+1/2} at x^{n+1}; products appended
+            if (MCC != 0) {
+                if (SP == 0) collide_electron(P, nus, ids[q], step, c, on, v, half_e, half_i, diag, s_cnt);
+                else collide_ion(P, nus, ids[q], step, v, s_cnt);
+            }
+            cc[q] = c; oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
+            dc[q] = c;
+            df[q] = __float2uint_rz(on * 4294967296.0f);
+            if (diag) {
+                const float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
+                const float eps = S.m_over_2e * v2;
+                ke_acc += v2;
+                atomicAdd(&hen[c], eps * (1.0f - on));
+                atomicAdd(&hen[c + 1], eps * on);
+                if (SP == 0) {
+                    const float xi = (float)c + on;
+                    if (xi >= P.eepf_lo && xi < P.eepf_hi) {
+                        const int b = (int)(eps * 4.0f);
+                        if (b < kEepfBins) atomicAdd(&heepf[b], 1u);
+                    }
+                }
+            }
+        }
+        // write back (never past n: slots beyond belong to this step's appends)
+        if (live_chunk) {
+            if (i0 + 4 <= n) {
+                *reinterpret_cast<int4 *>(B.cell + i0) = make_int4(cc[0], cc[1], cc[2], cc[3]);
+                *reinterpret_cast<float4 *>(B.off + i0) = make_float4(oo[0], oo[1], oo[2], oo[3]);
+                *reinterpret_cast<float4 *>(B.vx + i0) = make_float4(vx[0], vx[1], vx[2], vx[3]);
+                *reinterpret_cast<float4 *>(B.vy + i0) = make_float4(vy[0], vy[1], vy[2], vy[3]);
+                *reinterpret_cast<float4 *>(B.vz + i0) = make_float4(vz[0], vz[1], vz[2], vz[3]);
+            } else {
+                for (int q = 0; q < 4; ++q) {
+                    if (i0 + q >= n) break;
+                    B.cell[i0 + q] = cc[q]; B.off[i0 + q] = oo[q];
+                    B.vx[i0 + q] = vx[q]; B.vy[i0 + q] = vy[q]; B.vz[i0 + q] = vz[q];
+                }
+            }
+        }
+        // 7. deposit: merge equal-cell runs in the thread, then one warp-wide
+        // reduction when the whole warp's 128 particles share one cell.
+        int acc_c = -1;
+        unsigned acc_n = 0;
+        unsigned long long acc_f = 0;
+        bool split = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (dc[q] < 0) continue;
+            if (dc[q] == acc_c) { acc_n++; acc_f += df[q]; }
+            else {
+                if (acc_c >= 0) { hist_run(hist, acc_c, acc_n, acc_f); split = true; }
+                acc_c = dc[q]; acc_n = 1; acc_f = df[q];
+            }
+        }
+        const int c0 = __shfl_sync(0xffffffffu, acc_c, 0);
+        const bool uni = !split && acc_c == c0 && acc_c >= 0;
+        if (__all_sync(0xffffffffu, uni)) {
+            const unsigned nw = __reduce_add_sync(0xffffffffu, acc_n);
+            const unsigned hi = __reduce_add_sync(0xffffffffu, (unsigned)(acc_f >> 16));
+            const unsigned lo = __reduce_add_sync(0xffffffffu, (unsigned)(acc_f & 0xFFFFull));
+            if (lane == 0) hist_run(hist, c0, nw, ((unsigned long long)hi << 16) + lo);
+        } else if (acc_c >= 0) {
+            hist_run(hist, acc_c, acc_n, acc_f);
+        }
+    }
+    // CTA epilogue: flush the histogram and counters
+    __syncthreads();
+    unsigned long long *R = P.R[SP];
+    for (int j = tid; j <= N; j += blockDim.x) {
+        const unsigned long long h = hist[j];
+        if (h) atomicAdd(&R[(PERIODIC && j == N) ? 0 : j], h);
+    }
+    if (diag) {
+        const int nn = P.n_nodes;
+        for (int j = tid; j <= N; j += blockDim.x) {
+            const float h = hen[j];
+            if (h != 0.0f) {
+                const int jj = (PERIODIC && j == N) ? 0 : j;
+                const double iv = (!PERIODIC && (jj == 0 || jj == N)) ? 1.0 / P.vol_wall : 1.0 / P.vol_interior;
+                atomicAdd(&P.en_sum[SP * nn + jj], S.w * (double)h * iv);
+            }
+        }
+        if (SP == 0)
+            for (int j = tid; j < kEepfBins; j += blockDim.x)
+                if (heepf[j]) atomicAdd(&P.eepf[j], (unsigned long long)heepf[j]);
+        // block reductions of the kinetic-energy and J.E sums
+        for (int o = 16; o > 0; o >>= 1) {
+            ke_acc += __shfl_xor_sync(0xffffffffu, ke_acc, o);
+            pw_acc += __shfl_xor_sync(0xffffffffu, pw_acc, o);
+        }
+        if (lane == 0) { s_red[0][warp] = ke_acc; s_red[1][warp] = pw_acc; }
+        __syncthreads();
+        if (tid == 0) {
+            double ke = 0, pw = 0;
+            for (int w = 0; w < (int)(blockDim.x / 32); ++w) { ke += s_red[0][w]; pw += s_red[1][w]; }
+            atomicAdd(&P.ke_sum[SP], 0.5 * S.m * S.w * ke);
+            atomicAdd(&P.pw_sum[SP], S.q * S.w * pw);
+        }
+    }
+    if (tid == 0) {
+        if (s_abs[0]) { atomicAdd(&ctrl->absorbed[SP][0], (unsigned long long)s_abs[0]); }
+        if (s_abs[1]) { atomicAdd(&ctrl->absorbed[SP][1], (unsigned long long)s_abs[1]); }
+        if (s_abs[0] + s_abs[1]) atomicAdd(&ctrl->n_dead[SP], (unsigned long long)(s_abs[0] + s_abs[1]));
+        if (s_see) atomicAdd(&ctrl->see, (unsigned long long)s_see);
+        if (s_cnt[0]) atomicAdd(&ctrl->cand[SP], (unsigned long long)s_cnt[0]);
+        for (int k = 0; k < kMaxProc; ++k)
+            if (s_cnt[1 + k]) atomicAdd(&ctrl->coll[SP][k], (unsigned long long)s_cnt[1 + k]);
+        if (s_cnt[1 + kMaxProc]) atomicAdd(&ctrl->iz, (unsigned long long)s_cnt[1 + kMaxProc]);
+    }
+}
+
+// Leapfrog start: v(0) -> v(-dt/2) by a Boris step of -dt/2 in E^0.
+template <int SP>
+__global__ void k_rewind(const __grid_constant__ StepConst P)
+{
+    const SpConst &S = P.sp[SP];
+    const SpeciesBufs B = P.buf[SP][P.ctrl->cur[SP]];
+    const long long n = (long long)P.ctrl->n_active[SP];
+    // half-step constants: a = q(-dt/2)/(2m) = -c_e/2; t = a B; s = 2t/(1+t^2)
+    const float a = -0.5f * S.c_e;
+    const float t0 = -0.5f * S.tB[0] / 1.0f, t1 = -0.5f * S.tB[1], t2 = -0.5f * S.tB[2];
+    const float tt = t0 * t0 + t1 * t1 + t2 * t2;
+    const float s0 = 2.0f * t0 / (1.0f + tt), s1 = 2.0f * t1 / (1.0f + tt), s2 = 2.0f * t2 / (1.0f + tt);
+    const float ey = S.cEy * -0.5f, ez = S.cEz * -0.5f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = B.cell[i];
+        if (c < 0) continue;
+        const float o = B.off[i];
+        const float ex = (1.0f - o) * P.E32[c] + o * P.E32[c + 1] + P.Ex_ext;
+        const float hx = a * ex;
+        const float3 vm = make_float3(B.vx[i] + hx, B.vy[i] + ey, B.vz[i] + ez);
+        const float3 vp = make_float3(vm.x + (vm.y * t2 - vm.z * t1), vm.y + (vm.z * t0 - vm.x * t2),
+                                      vm.z + (vm.x * t1 - vm.y * t0));
+        B.vx[i] = vm.x + (vp.y * s2 - vp.z * s1) + hx;
+        B.vy[i] = vm.y + (vp.z * s0 - vp.x * s2) + ey;
+        B.vz[i] = vm.z + (vp.x * s1 - vp.y * s0) + ez;
+    }
+}
+
+// Deposit of all particles of a species (the state at load), and validation
+// of the loaded cells/offsets.
+__global__ void k_deposit_species(const __grid_constant__ StepConst P, int sp)
+{
+    const SpeciesBufs B = P.buf[sp][P.ctrl->cur[sp]];
+    const long long n = (long long)P.ctrl->n_active[sp];
+    const int N = P.n_cells;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = B.cell[i];
+        const float o = B.off[i];
+        if (c < 0) continue;
+        if (c >= N || !(o >= 0.0f && o < 1.0f)) { atomicOr(&P.ctrl->err, kErrLoad); B.cell[i] = -1; continue; }
+        const uint32_t f = __float2uint_rz(o * 4294967296.0f);
+        const int c1 = (P.periodic && c + 1 == N) ? 0 : c + 1;
+        atomicAdd(&P.R[sp][c], (1ull << 32) - f);
+        atomicAdd(&P.R[sp][c1], (unsigned long long)f);
+    }
+}
+
+} // namespace pic

@@ -1,0 +1,753 @@
+// pic_api.cu -- host runtime behind the C ABI of include/pic1d3v.h.
+#include "pic1d3v.h"
+#include "pic_device.cuh"
+#include "particle_step.cuh"
+#include "field_sort.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace pic;
+
+namespace {
+
+constexpr double kElem = 1.602176634e-19;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kBoltz = 1.380649e-23;
+constexpr double kEmin = 1e-3, kEmax = 1e3;
+
+thread_local std::string g_err;
+
+pic_status fail(pic_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+#define CU(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(PIC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct Proc {
+    int kind;
+    double thr;
+    std::vector<double> nu;   // collision frequency at the grid energies (FP64)
+};
+
+} // namespace
+
+struct pic_case {
+    pic_case_desc d{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, num_sms = 0;
+    int n_nodes = 0;
+    StepConst P{};
+    std::vector<std::pair<void *, size_t>> allocs;
+    std::vector<Proc> proc[2];
+    float *d_nu[2] = {nullptr, nullptr};
+    unsigned long long *R_last = nullptr;
+    bool loaded[2] = {false, false};
+    bool need_init = true;
+    long long host_step = 0;
+    int step_grid[2] = {0, 0};
+    unsigned step_smem[2] = {0, 0};
+    unsigned field_smem = 0;
+    // profiling: per kernel class, launch counts and event pairs
+    static constexpr int kClasses = 4;
+    bool prof = false;
+    long long launches[kClasses] = {0, 0, 0, 0};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    std::vector<std::pair<int, size_t>> ev_used;   // (class, pool index)
+
+    void *dalloc(size_t bytes)
+    {
+        void *p = nullptr;
+        if (d.alloc) p = d.alloc(bytes, d.alloc_ctx);
+        else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+        if (p) allocs.push_back({p, bytes});
+        return p;
+    }
+    void dfree(void *p)
+    {
+        for (size_t i = 0; i < allocs.size(); ++i)
+            if (allocs[i].first == p) {
+                if (d.free) d.free(p, allocs[i].second, d.alloc_ctx);
+                else cudaFree(p);
+                allocs.erase(allocs.begin() + i);
+                return;
+            }
+    }
+};
+
+namespace {
+
+enum { KC_STEP = 0, KC_FIELD = 1, KC_SORT = 2, KC_INIT = 3 };
+const char *kClassName[4] = {"particle_step", "field_solve", "sort", "init"};
+
+// Bracket one launch (or launch group) of class k with events when profiling.
+struct Timed {
+    pic_case *c;
+    int k;
+    size_t idx = (size_t)-1;
+    Timed(pic_case *c_, int k_, int n_launches) : c(c_), k(k_)
+    {
+        c->launches[k] += n_launches;
+        if (!c->prof) return;
+        idx = c->ev_used.size();
+        if (idx >= c->ev_pool.size()) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            c->ev_pool.push_back({a, b});
+        }
+        c->ev_used.push_back({k, idx});
+        cudaEventRecord(c->ev_pool[idx].first, c->stream);
+    }
+    ~Timed()
+    {
+        if (idx != (size_t)-1) cudaEventRecord(c->ev_pool[idx].second, c->stream);
+    }
+};
+
+double grid_energy(int i) { return kEmin * std::exp((double)i * std::log(kEmax / kEmin) / (kNGrid - 1)); }
+
+// LXCat-style linear interpolation of a raw table, held constant beyond its ends
+double sample_table(const double *e, const double *s, int n, double eps)
+{
+    if (eps <= e[0]) return s[0];
+    if (eps >= e[n - 1]) return s[n - 1];
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (e[mid] < eps) lo = mid; else hi = mid;
+    }
+    return s[lo] + (eps - e[lo]) / (e[hi] - e[lo]) * (s[hi] - s[lo]);
+}
+
+double reduced_mass(const pic_case *c, int sp)
+{
+    const double m = c->d.mass_kg[sp];
+    return sp == 0 ? m : m * c->d.gas_mass_kg / (m + c->d.gas_mass_kg);
+}
+
+// Species constants of the step (FP64 on the host, rounded to FP32 once).
+void fill_species(pic_case *c, int sp)
+{
+    SpConst &S = c->P.sp[sp];
+    const pic_case_desc &d = c->d;
+    const double q = d.charge_C[sp], m = d.mass_kg[sp], dt = d.dt_s, M = d.gas_mass_kg;
+    const double ce = q * dt / (2.0 * m);
+    double t[3], tt = 0;
+    for (int k = 0; k < 3; ++k) { t[k] = ce * d.B_T[k]; tt += t[k] * t[k]; }
+    S.c_e = (float)ce;
+    for (int k = 0; k < 3; ++k) { S.tB[k] = (float)t[k]; S.sB[k] = (float)(2.0 * t[k] / (1.0 + tt)); }
+    S.cEy = (float)(ce * d.E_ext_V_per_m[1]);
+    S.cEz = (float)(ce * d.E_ext_V_per_m[2]);
+    S.m_over_2e = (float)(m / (2.0 * kElem));
+    S.v_of_sqrt_eps = (float)std::sqrt(2.0 * kElem / m);
+    S.recoil = M > 0 ? (float)(2.0 * m / M) : 0.0f;
+    S.vt_gas = M > 0 ? (float)std::sqrt(kBoltz * d.gas_temp_k / M) : 0.0f;
+    S.mfrac = (float)(m / (m + M));
+    S.Mfrac = (float)(M / (m + M));
+    S.mu_over_2e = (float)(reduced_mass(c, sp) / (2.0 * kElem));
+    S.vt_newion = d.n_species > 1 ? (float)std::sqrt(kBoltz * d.gas_temp_k / d.mass_kg[1]) : 0.0f;
+    S.q = q; S.m = m; S.w = d.weight_per_m2[sp];
+    double numax = 0.0;
+    S.nproc = (int)c->proc[sp].size();
+    for (int k = 0; k < kMaxProc; ++k) {
+        S.kind[k] = k < S.nproc ? c->proc[sp][k].kind : 0;
+        S.thr[k] = k < S.nproc ? (float)c->proc[sp][k].thr : 0.0f;
+    }
+    if (sp == 0 && d.const_nu_e_per_s > 0) {
+        S.mcc = 2;
+        numax = d.const_nu_e_per_s;
+        S.nproc = 1;
+        S.kind[0] = PIC_ELASTIC;
+    } else if (S.nproc > 0) {
+        S.mcc = 1;
+        for (int i = 0; i < kNGrid; ++i) {
+            double tot = 0;
+            for (auto &p : c->proc[sp]) tot += p.nu[i];
+            numax = std::max(numax, tot);
+        }
+    } else {
+        S.mcc = 0;
+    }
+    S.numax = (float)numax;
+    S.pnull = (float)(1.0 - std::exp(-numax * dt));
+}
+
+pic_status upload_tables(pic_case *c, int sp)
+{
+    const auto &pr = c->proc[sp];
+    if (pr.empty()) return PIC_OK;
+    if (!c->d_nu[sp]) {
+        c->d_nu[sp] = (float *)c->dalloc(sizeof(float) * kNGrid * kMaxProc);
+        if (!c->d_nu[sp]) return fail(PIC_ENOMEM, "table allocation failed");
+    }
+    std::vector<float> h(kNGrid * pr.size());
+    for (size_t k = 0; k < pr.size(); ++k)
+        for (int i = 0; i < kNGrid; ++i) h[k * kNGrid + i] = (float)pr[k].nu[i];
+    CU(cudaMemcpyAsync(c->d_nu[sp], h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->P.nu_tab[sp] = c->d_nu[sp];
+    return PIC_OK;
+}
+
+template <int SP, bool PER, int MCC>
+cudaError_t launch_step_t(pic_case *c)
+{
+    auto k = k_particle_step<SP, PER, MCC>;
+    const unsigned smem = StepSmem(c->d.n_cells, MCC == 1 ? c->P.sp[SP].nproc : 0).total;
+    if (c->step_smem[SP] != smem || c->step_grid[SP] == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kStepThreads, smem);
+        if (e != cudaSuccess) return e;
+        c->step_grid[SP] = std::max(1, occ) * c->num_sms;
+        c->step_smem[SP] = smem;
+    }
+    Timed t(c, KC_STEP, 1);
+    k<<<c->step_grid[SP], kStepThreads, smem, c->stream>>>(c->P);
+    return cudaGetLastError();
+}
+
+template <int SP>
+cudaError_t launch_step_sp(pic_case *c)
+{
+    const int mcc = c->P.sp[SP].mcc;
+    if (c->d.periodic) {
+        if (mcc == 0) return launch_step_t<SP, true, 0>(c);
+        if (mcc == 1) return launch_step_t<SP, true, 1>(c);
+        return launch_step_t<SP, true, 2>(c);
+    }
+    if (mcc == 0) return launch_step_t<SP, false, 0>(c);
+    if (mcc == 1) return launch_step_t<SP, false, 1>(c);
+    return launch_step_t<SP, false, 2>(c);
+}
+
+cudaError_t launch_field(pic_case *c, int mode)
+{
+    Timed t(c, mode == 0 ? KC_INIT : KC_FIELD, 1);
+    k_field<<<1, kFieldThreads, c->field_smem, c->stream>>>(c->P, mode, c->R_last);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(pic_case *c, int sp)
+{
+    const int N = c->d.n_cells;
+    const long long cap = (long long)c->P.cap[sp];
+    Timed t(c, KC_SORT, 4);
+    int gc = std::min<long long>(c->num_sms * 4, std::max<long long>(1, cap / 1024));
+    k_sort_count<<<gc, 512, N * sizeof(unsigned), c->stream>>>(c->P, sp);
+    k_sort_scan<<<1, kFieldThreads, N * sizeof(double), c->stream>>>(c->P);
+    const long long nchunks = (cap + kSortChunk - 1) / kSortChunk;
+    k_sort_scatter<<<(unsigned)nchunks, 512, 12 * (size_t)N, c->stream>>>(c->P, sp);
+    k_sort_finish<<<4, 256, 0, c->stream>>>(c->P, sp);
+    return cudaGetLastError();
+}
+
+pic_status device_error(pic_case *c)
+{
+    Ctrl h;
+    CU(cudaMemcpyAsync(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (h.err & kErrLoad) return fail(PIC_EINVAL, "loaded particle outside the grid (cell or offset)");
+    if (h.err & kErrCapacity) return fail(PIC_ECAPACITY, "particle capacity exceeded during a step");
+    if (h.err & kErrNumeric) return fail(PIC_ENUMERIC, "non-finite potential or field");
+    if (h.err & kErrTimeout) return fail(PIC_ETIMEOUT, "a bounded device wait gave up");
+    return PIC_OK;
+}
+
+pic_status alloc_species(pic_case *c, int sp, long long need)
+{
+    long long cap = c->d.capacity[sp] > 0 ? c->d.capacity[sp] : std::max<long long>(2 * need, 65536);
+    if (need > cap) return fail(PIC_ECAPACITY, "load exceeds the species capacity");
+    if ((long long)c->P.cap[sp] >= cap && c->P.buf[sp][0].cell) return PIC_OK;
+    for (int h = 0; h < 2; ++h) {
+        SpeciesBufs &B = c->P.buf[sp][h];
+        c->dfree(B.cell); c->dfree(B.off); c->dfree(B.vx); c->dfree(B.vy); c->dfree(B.vz); c->dfree(B.id);
+    }
+    const long long slots = (cap + 3) / 4 * 4 + 4;   // float4 access never leaves the buffer
+    for (int h = 0; h < 2; ++h) {
+        SpeciesBufs &B = c->P.buf[sp][h];
+        B.cell = (int32_t *)c->dalloc(slots * 4); B.off = (float *)c->dalloc(slots * 4);
+        B.vx = (float *)c->dalloc(slots * 4); B.vy = (float *)c->dalloc(slots * 4);
+        B.vz = (float *)c->dalloc(slots * 4); B.id = (uint32_t *)c->dalloc(slots * 4);
+        if (!B.cell || !B.off || !B.vx || !B.vy || !B.vz || !B.id) return fail(PIC_ENOMEM, "particle allocation failed");
+    }
+    c->P.cap[sp] = (unsigned long long)cap;
+    return PIC_OK;
+}
+
+pic_status initialise(pic_case *c)
+{
+    for (int s = 0; s < c->d.n_species; ++s) fill_species(c, s);
+    const int N = c->d.n_cells;
+    for (int s = 0; s < c->d.n_species; ++s)
+        CU(cudaMemsetAsync(c->P.R[s], 0, sizeof(unsigned long long) * (N + 1), c->stream));
+    Timed t(c, KC_INIT, c->d.n_species * (c->d.rewind ? 2 : 1));
+    for (int s = 0; s < c->d.n_species; ++s) {
+        k_deposit_species<<<c->num_sms * 4, 256, 0, c->stream>>>(c->P, s);
+        CU(cudaGetLastError());
+    }
+    CU(launch_field(c, 0));
+    if (c->d.rewind) {
+        k_rewind<0><<<c->num_sms * 4, 256, 0, c->stream>>>(c->P);
+        if (c->d.n_species > 1) k_rewind<1><<<c->num_sms * 4, 256, 0, c->stream>>>(c->P);
+        CU(cudaGetLastError());
+    }
+    c->need_init = false;
+    return PIC_OK;
+}
+
+__global__ void k_reset_counters(Ctrl *ctrl)
+{
+    ctrl->absorbed[0][0] = ctrl->absorbed[0][1] = ctrl->absorbed[1][0] = ctrl->absorbed[1][1] = 0;
+    ctrl->see = ctrl->iz = 0;
+    ctrl->cand[0] = ctrl->cand[1] = 0;
+    for (int s = 0; s < 2; ++s)
+        for (int k = 0; k < kMaxProc; ++k) ctrl->coll[s][k] = 0;
+    ctrl->fe_n = 0;
+    ctrl->n_steps_acc = ctrl->n_diag_acc = 0;
+}
+
+pic_status reset_moments(pic_case *c)
+{
+    const size_t nn = (size_t)c->n_nodes;
+    CU(cudaMemsetAsync(c->P.Rsum, 0, sizeof(unsigned long long) * 2 * nn, c->stream));
+    CU(cudaMemsetAsync(c->P.Rdiag, 0, sizeof(unsigned long long) * 2 * nn, c->stream));
+    CU(cudaMemsetAsync(c->P.en_sum, 0, sizeof(double) * 2 * nn, c->stream));
+    CU(cudaMemsetAsync(c->P.phi_sum, 0, sizeof(double) * nn, c->stream));
+    CU(cudaMemsetAsync(c->P.ke_sum, 0, sizeof(double) * 2, c->stream));
+    CU(cudaMemsetAsync(c->P.pw_sum, 0, sizeof(double) * 2, c->stream));
+    CU(cudaMemsetAsync(c->P.eepf, 0, sizeof(unsigned long long) * kEepfBins, c->stream));
+    k_reset_counters<<<1, 1, 0, c->stream>>>(c->P.ctrl);
+    CU(cudaGetLastError());
+    return PIC_OK;
+}
+
+} // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char *pic_status_str(pic_status s)
+{
+    switch (s) {
+    case PIC_OK: return "ok";
+    case PIC_EINVAL: return "invalid argument";
+    case PIC_ENOMEM: return "out of device memory";
+    case PIC_ECUDA: return "CUDA error";
+    case PIC_ECAPACITY: return "particle capacity exceeded";
+    case PIC_ENUMERIC: return "non-finite field";
+    case PIC_ETIMEOUT: return "device wait timed out";
+    case PIC_ESTATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char *pic_last_error(void) { return g_err.c_str(); }
+
+pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
+{
+    if (!desc || !out) return fail(PIC_EINVAL, "null descriptor or output");
+    *out = nullptr;
+    if (desc->struct_size != sizeof(pic_case_desc) || desc->version != PIC_DESC_VERSION)
+        return fail(PIC_EINVAL, "descriptor size/version mismatch");
+    if (desc->n_cells < 2 || desc->n_cells > 4096) return fail(PIC_EINVAL, "n_cells must be in [2, 4096]");
+    if (desc->n_species < 1 || desc->n_species > 2) return fail(PIC_EINVAL, "n_species must be 1 or 2");
+    if (!(desc->dt_s > 0) || !(desc->length_m > 0)) return fail(PIC_EINVAL, "dt and length must be positive");
+    if (desc->n_harm < 0 || desc->n_harm > 4) return fail(PIC_EINVAL, "n_harm must be in [0, 4]");
+    for (int s = 0; s < desc->n_species; ++s)
+        if (!(desc->mass_kg[s] > 0)) return fail(PIC_EINVAL, "species mass must be positive");
+    pic_case *c = new pic_case();
+    c->d = *desc;
+    if (c->d.sort_interval <= 0) c->d.sort_interval = 16;
+    if (c->d.field_history <= 0) c->d.field_history = 65536;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) { delete c; return fail(PIC_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e)); }
+    if (desc->stream) c->stream = (cudaStream_t)desc->stream;
+    else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c; return fail(PIC_ECUDA, "stream creation failed");
+        }
+        c->own_stream = true;
+    }
+    const int N = desc->n_cells;
+    c->n_nodes = desc->periodic ? N : N + 1;
+    StepConst &P = c->P;
+    P.n_cells = N; P.n_nodes = c->n_nodes; P.periodic = desc->periodic; P.n_species = desc->n_species;
+    const double dx = desc->length_m / N;
+    P.dx = dx; P.dt = desc->dt_s; P.eps0 = kEps0;
+    P.dtdx = (float)(desc->dt_s / dx);
+    P.Ex_ext = (float)desc->E_ext_V_per_m[0];
+    P.key0 = (uint32_t)desc->seed; P.key1 = (uint32_t)(desc->seed >> 32);
+    P.see_gamma = (float)desc->see_gamma;
+    P.see_vth = (float)std::sqrt(desc->see_temp_ev * kElem / desc->mass_kg[0]);
+    P.see_dtdx = (float)(desc->dt_s / dx);
+    P.eepf_lo = (float)(0.45 * N); P.eepf_hi = (float)(0.55 * N);
+    P.inv_dlog = (float)(1.0 / (std::log(kEmax / kEmin) / (kNGrid - 1)));
+    P.diag_interval = desc->diag_interval;
+    P.vol_interior = dx; P.vol_wall = desc->periodic ? dx : 0.5 * dx;
+    P.bg_charge = desc->background_charge_C_per_m3;
+    P.bg_r = P.bg_charge * dx * dx / kEps0;
+    P.inv_dx = 1.0 / dx;
+    P.inv_2dx = 0.5 / dx;
+    P.half_dx_eps0 = 0.5 * dx / kEps0;
+    P.fe_c = 0.5 * kEps0 * dx;
+    for (int s = 0; s < 2; ++s) {
+        const double qw = s < desc->n_species ? desc->charge_C[s] * desc->weight_per_m2[s] / 4294967296.0 : 0.0;
+        P.cq[s] = qw * dx / kEps0;
+        P.rho_wall[s] = qw / (0.5 * dx);
+    }
+    P.n_harm = desc->n_harm;
+    for (int h = 0; h < 4; ++h) { P.harm_f[h] = desc->harm_freq_hz[h]; P.harm_a[h] = desc->harm_amp_v[h]; P.harm_p[h] = desc->harm_phase_rad[h]; }
+    const size_t nn = (size_t)c->n_nodes;
+    P.E32 = (float *)c->dalloc(sizeof(float) * (((N + 1) + 3) / 4 * 4));
+    P.E = (double *)c->dalloc(sizeof(double) * nn);
+    P.phi = (double *)c->dalloc(sizeof(double) * nn);
+    for (int s = 0; s < 2; ++s) P.R[s] = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * (N + 1));
+    c->R_last = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * 2 * nn);
+    P.ctrl = (Ctrl *)c->dalloc(sizeof(Ctrl));
+    P.Rsum = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * 2 * nn);
+    P.Rdiag = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * 2 * nn);
+    P.en_sum = (double *)c->dalloc(sizeof(double) * 2 * nn);
+    P.phi_sum = (double *)c->dalloc(sizeof(double) * nn);
+    P.ke_sum = (double *)c->dalloc(sizeof(double) * 2);
+    P.pw_sum = (double *)c->dalloc(sizeof(double) * 2);
+    P.eepf = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * kEepfBins);
+    P.fe_cap = c->d.field_history;
+    P.fe_hist = (double *)c->dalloc(sizeof(double) * (size_t)P.fe_cap);
+    P.sort_count = (unsigned *)c->dalloc(sizeof(unsigned) * N);
+    P.sort_cursor = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * (N + 1));
+    if (!P.E32 || !P.E || !P.phi || !P.R[0] || !P.R[1] || !c->R_last || !P.ctrl || !P.Rsum || !P.Rdiag ||
+        !P.en_sum || !P.phi_sum || !P.ke_sum || !P.pw_sum || !P.eepf || !P.fe_hist || !P.sort_count || !P.sort_cursor) {
+        pic_destroy(c);
+        return fail(PIC_ENOMEM, "device allocation failed");
+    }
+    cudaMemsetAsync(P.E32, 0, sizeof(float) * (((N + 1) + 3) / 4 * 4), c->stream);
+    cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), c->stream);
+    cudaMemsetAsync(P.sort_count, 0, sizeof(unsigned) * N, c->stream);
+    cudaMemsetAsync(c->R_last, 0, sizeof(unsigned long long) * 2 * nn, c->stream);
+    c->field_smem = (unsigned)(4 * (N + 1) * sizeof(double));
+    if (cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->field_smem) != cudaSuccess) {
+        pic_destroy(c);
+        return fail(PIC_ECUDA, "field kernel shared memory attribute");
+    }
+    pic_status st = reset_moments(c);
+    if (st != PIC_OK) { pic_destroy(c); return st; }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) { pic_destroy(c); return fail(PIC_ECUDA, "create sync"); }
+    *out = c;
+    return PIC_OK;
+}
+
+pic_status pic_load_xsec_table(pic_case *c, int species, int kind, double thr, const double *e, const double *s, int n)
+{
+    if (!c || species < 0 || species >= c->d.n_species || !e || !s || n < 1) return fail(PIC_EINVAL, "bad table arguments");
+    if (kind < PIC_ELASTIC || kind > PIC_CX) return fail(PIC_EINVAL, "unknown process kind");
+    if ((int)c->proc[species].size() >= kMaxProc) return fail(PIC_EINVAL, "too many processes for this species");
+    if (species == 0 && c->d.const_nu_e_per_s > 0) return fail(PIC_EINVAL, "tables and the constant-frequency model are exclusive");
+    for (int i = 1; i < n; ++i)
+        if (!(e[i] >= e[i - 1])) return fail(PIC_EINVAL, "table energies must ascend");
+    Proc p;
+    p.kind = kind;
+    p.thr = thr;
+    p.nu.resize(kNGrid);
+    const double mu = reduced_mass(c, species);
+    for (int i = 0; i < kNGrid; ++i) {
+        const double eps = grid_energy(i);
+        const double sig = eps < thr ? 0.0 : sample_table(e, s, n, eps);
+        p.nu[i] = c->d.gas_density_m3 * sig * std::sqrt(2.0 * eps * kElem / mu);
+    }
+    c->proc[species].push_back(std::move(p));
+    fill_species(c, species);
+    return upload_tables(c, species);
+}
+
+pic_status pic_load_particles(pic_case *c, int sp, int64_t n, const int32_t *cell, const float *off, const float *vx,
+                              const float *vy, const float *vz, const uint32_t *id, int on_device)
+{
+    if (!c || sp < 0 || sp >= c->d.n_species || n < 0) return fail(PIC_EINVAL, "bad load arguments");
+    if (n > 0 && (!cell || !off || !vx || !vy || !vz)) return fail(PIC_EINVAL, "null particle array");
+    CU(cudaStreamSynchronize(c->stream));
+    pic_status st = alloc_species(c, sp, n);
+    if (st != PIC_OK) return st;
+    for (int s = 0; s < c->d.n_species; ++s)
+        if (!c->P.buf[s][0].cell) {
+            st = alloc_species(c, s, 0);
+            if (st != PIC_OK) return st;
+        }
+    Ctrl h;
+    CU(cudaMemcpy(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    // a load restarts the case: particles of the other species move back to half 0
+    for (int s = 0; s < c->d.n_species; ++s) {
+        if (s == sp || h.cur[s] == 0 || !c->loaded[s]) continue;
+        const SpeciesBufs &A = c->P.buf[s][1], &D = c->P.buf[s][0];
+        const size_t b = (size_t)h.n_total[s] * 4;
+        CU(cudaMemcpyAsync(D.cell, A.cell, b, cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(D.off, A.off, b, cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(D.vx, A.vx, b, cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(D.vy, A.vy, b, cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(D.vz, A.vz, b, cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(D.id, A.id, b, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    const SpeciesBufs &B = c->P.buf[sp][0];
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (n > 0) {
+        CU(cudaMemcpyAsync(B.cell, cell, n * 4, k, c->stream));
+        CU(cudaMemcpyAsync(B.off, off, n * 4, k, c->stream));
+        CU(cudaMemcpyAsync(B.vx, vx, n * 4, k, c->stream));
+        CU(cudaMemcpyAsync(B.vy, vy, n * 4, k, c->stream));
+        CU(cudaMemcpyAsync(B.vz, vz, n * 4, k, c->stream));
+        if (id) CU(cudaMemcpyAsync(B.id, id, n * 4, k, c->stream));
+    }
+    if (n > 0 && !id) {
+        std::vector<uint32_t> seq((size_t)n);
+        for (int64_t i = 0; i < n; ++i) seq[(size_t)i] = (uint32_t)i;
+        CU(cudaMemcpyAsync(B.id, seq.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    Ctrl z;
+    std::memset(&z, 0, sizeof(z));
+    for (int s = 0; s < 2; ++s) {
+        const unsigned long long cnt = s == sp ? (unsigned long long)n : (c->loaded[s] ? h.n_total[s] : 0ull);
+        z.n_total[s] = z.n_active[s] = cnt;
+    }
+    CU(cudaMemcpyAsync(c->P.ctrl, &z, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
+    st = reset_moments(c);
+    if (st != PIC_OK) return st;
+    CU(cudaStreamSynchronize(c->stream));
+    c->loaded[sp] = true;
+    c->need_init = true;
+    c->host_step = 0;
+    return PIC_OK;
+}
+
+pic_status pic_step(pic_case *c, int64_t n_steps)
+{
+    if (!c || n_steps < 0) return fail(PIC_EINVAL, "bad step arguments");
+    for (int s = 0; s < c->d.n_species; ++s)
+        if (!c->loaded[s] && !(s == 1 && c->loaded[0])) return fail(PIC_ESTATE, "particles not loaded");
+    if (c->need_init) {
+        pic_status st = initialise(c);
+        if (st != PIC_OK) return st;
+    }
+    for (int64_t i = 0; i < n_steps; ++i) {
+        CU(launch_step_sp<0>(c));
+        if (c->d.n_species > 1) CU(launch_step_sp<1>(c));
+        CU(launch_field(c, 1));
+        c->host_step++;
+        if (c->host_step % c->d.sort_interval == 0)
+            for (int s = 0; s < c->d.n_species; ++s) CU(launch_sort(c, s));
+    }
+    return PIC_OK;
+}
+
+pic_status pic_sync(pic_case *c)
+{
+    if (!c) return fail(PIC_EINVAL, "null case");
+    CU(cudaStreamSynchronize(c->stream));
+    return device_error(c);
+}
+
+pic_status pic_count(pic_case *c, int64_t n_alive[2])
+{
+    if (!c || !n_alive) return fail(PIC_EINVAL, "null argument");
+    Ctrl h;
+    CU(cudaMemcpyAsync(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    for (int s = 0; s < 2; ++s)
+        n_alive[s] = s < c->d.n_species ? (int64_t)(h.n_total[s] - h.n_dead[s]) : 0;
+    return device_error(c);
+}
+
+pic_status pic_read_particles(pic_case *c, int sp, int64_t max_n, int64_t *n_out, int32_t *cell, float *off, float *vx,
+                              float *vy, float *vz, uint32_t *id)
+{
+    if (!c || sp < 0 || sp >= c->d.n_species || max_n < 0) return fail(PIC_EINVAL, "bad read arguments");
+    Ctrl h;
+    CU(cudaMemcpyAsync(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    const size_t n = (size_t)h.n_total[sp];
+    const SpeciesBufs &B = c->P.buf[sp][h.cur[sp]];
+    std::vector<int32_t> hc(n);
+    std::vector<float> ho(n), hx(n), hy(n), hz(n);
+    std::vector<uint32_t> hi(n);
+    if (n) {
+        CU(cudaMemcpy(hc.data(), B.cell, n * 4, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(ho.data(), B.off, n * 4, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(hx.data(), B.vx, n * 4, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(hy.data(), B.vy, n * 4, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(hz.data(), B.vz, n * 4, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(hi.data(), B.id, n * 4, cudaMemcpyDeviceToHost));
+    }
+    int64_t k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        if (hc[i] < 0) continue;
+        if (k < max_n) {
+            if (cell) cell[k] = hc[i];
+            if (off) off[k] = ho[i];
+            if (vx) vx[k] = hx[i];
+            if (vy) vy[k] = hy[i];
+            if (vz) vz[k] = hz[i];
+            if (id) id[k] = hi[i];
+        }
+        ++k;
+    }
+    if (n_out) *n_out = k;
+    if (k > max_n) return fail(PIC_ECAPACITY, "output buffers smaller than the live count");
+    return device_error(c);
+}
+
+pic_status pic_read_field(pic_case *c, double *phi, double *E, int64_t *rho_raw)
+{
+    if (!c) return fail(PIC_EINVAL, "null case");
+    const size_t nn = (size_t)c->n_nodes;
+    if (phi) CU(cudaMemcpyAsync(phi, c->P.phi, nn * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (E) CU(cudaMemcpyAsync(E, c->P.E, nn * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (rho_raw) CU(cudaMemcpyAsync(rho_raw, c->R_last, (size_t)c->d.n_species * nn * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return device_error(c);
+}
+
+pic_status pic_read_moments(pic_case *c, pic_moments *m)
+{
+    if (!c || !m || m->struct_size != sizeof(pic_moments)) return fail(PIC_EINVAL, "bad moments struct");
+    const size_t nn = (size_t)c->n_nodes;
+    const size_t ns = (size_t)c->d.n_species;
+    Ctrl h;
+    CU(cudaMemcpyAsync(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+    double ke[2], pw[2];
+    CU(cudaMemcpyAsync(ke, c->P.ke_sum, 16, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(pw, c->P.pw_sum, 16, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<unsigned long long> rs(2 * nn), rd(2 * nn);
+    CU(cudaMemcpyAsync(rs.data(), c->P.Rsum, 2 * nn * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(rd.data(), c->P.Rdiag, 2 * nn * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (m->phi_sum) CU(cudaMemcpyAsync(m->phi_sum, c->P.phi_sum, nn * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (m->en_sum) CU(cudaMemcpyAsync(m->en_sum, c->P.en_sum, ns * nn * 8, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<unsigned long long> ee(kEepfBins);
+    CU(cudaMemcpyAsync(ee.data(), c->P.eepf, kEepfBins * 8, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<double> fe((size_t)c->P.fe_cap);
+    CU(cudaMemcpyAsync(fe.data(), c->P.fe_hist, fe.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    m->n_nodes = (int32_t)nn;
+    m->step = h.step;
+    m->n_steps = (int64_t)h.n_steps_acc;
+    m->n_diag = (int64_t)h.n_diag_acc;
+    for (int s = 0; s < 2; ++s) {
+        m->n_alive[s] = s < (int)ns ? (int64_t)(h.n_total[s] - h.n_dead[s]) : 0;
+        m->absorbed[s][0] = (int64_t)h.absorbed[s][0];
+        m->absorbed[s][1] = (int64_t)h.absorbed[s][1];
+        m->candidates[s] = (int64_t)h.cand[s];
+        for (int k = 0; k < PIC_MAX_PROC; ++k) m->collisions[s][k] = (int64_t)h.coll[s][k];
+        m->ke_sum[s] = s < (int)ns ? ke[s] : 0.0;
+        m->pw_sum[s] = s < (int)ns ? pw[s] : 0.0;
+    }
+    // densities from the exact integer deposit sums: w R 2^-32 / node volume
+    for (size_t s = 0; s < ns; ++s)
+        for (size_t i = 0; i < nn; ++i) {
+            const double vol = (!c->d.periodic && (i == 0 || i == nn - 1)) ? c->P.vol_wall : c->P.vol_interior;
+            const double f = c->d.weight_per_m2[s] / 4294967296.0 / vol;
+            if (m->dens_sum) m->dens_sum[s * nn + i] = f * (double)rs[s * nn + i];
+            if (m->dens_diag_sum) m->dens_diag_sum[s * nn + i] = f * (double)rd[s * nn + i];
+        }
+    m->see_emitted = (int64_t)h.see;
+    m->ionizations = (int64_t)h.iz;
+    if (m->eepf) for (int b = 0; b < kEepfBins; ++b) m->eepf[b] = (double)ee[b];
+    const long long have = std::min<long long>((long long)h.fe_n, c->P.fe_cap);
+    long long want = m->field_energy ? std::min<long long>(have, m->field_energy_cap) : 0;
+    for (long long i = 0; i < want; ++i) {
+        const long long idx = (long long)h.fe_n - have + i;
+        m->field_energy[i] = fe[(size_t)(idx % c->P.fe_cap)];
+    }
+    m->field_energy_n = want;
+    pic_status st = device_error(c);
+    if (m->reset) {
+        pic_status r = reset_moments(c);
+        if (r != PIC_OK) return r;
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return st;
+}
+
+pic_status pic_profile(pic_case *c, int enable)
+{
+    if (!c) return fail(PIC_EINVAL, "null case");
+    CU(cudaStreamSynchronize(c->stream));
+    c->prof = enable != 0;
+    if (enable) {
+        c->ev_used.clear();
+        for (int k = 0; k < pic_case::kClasses; ++k) c->launches[k] = 0;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_profile_read(pic_case *c, pic_kernel_stat *out, int max_entries, int *n_out)
+{
+    if (!c || (max_entries > 0 && !out)) return fail(PIC_EINVAL, "bad profile arguments");
+    CU(cudaStreamSynchronize(c->stream));
+    double ms[pic_case::kClasses] = {0, 0, 0, 0};
+    long long timed[pic_case::kClasses] = {0, 0, 0, 0};
+    for (auto &u : c->ev_used) {
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, c->ev_pool[u.second].first, c->ev_pool[u.second].second));
+        ms[u.first] += t;
+        timed[u.first] += 1;
+    }
+    const int n = std::min(max_entries, pic_case::kClasses);
+    for (int k = 0; k < n; ++k) {
+        std::memset(out[k].name, 0, sizeof(out[k].name));
+        std::strncpy(out[k].name, kClassName[k], sizeof(out[k].name) - 1);
+        out[k].launches = c->launches[k];
+        out[k].timed = timed[k];
+        out[k].total_ms = ms[k];
+    }
+    if (n_out) *n_out = n;
+    return PIC_OK;
+}
+
+pic_status pic_destroy(pic_case *c)
+{
+    if (!c) return PIC_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    while (!c->allocs.empty()) c->dfree(c->allocs.back().first);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return PIC_OK;
+}
+
+pic_status pic_philox(uint64_t seed, int64_t n, const uint32_t *ctr, uint32_t *out, void *stream)
+{
+    if (n < 0 || (n > 0 && (!ctr || !out))) return fail(PIC_EINVAL, "bad philox arguments");
+    if (((uintptr_t)ctr | (uintptr_t)out) & 15) return fail(PIC_EINVAL, "philox buffers must be 16-byte aligned");
+    if (n == 0) return PIC_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 65535);
+    k_philox<<<grid, 256, 0, (cudaStream_t)stream>>>((uint32_t)seed, (uint32_t)(seed >> 32), n,
+                                                      (const uint4 *)ctr, (uint4 *)out);
+    CU(cudaGetLastError());
+    return PIC_OK;
+}
+
+pic_status pic_deposit(int32_t n_cells, int32_t periodic, int64_t n, const int32_t *cell, const float *off, int64_t *R,
+                       void *stream)
+{
+    if (n_cells < 2 || n < 0 || (n > 0 && (!cell || !off || !R))) return fail(PIC_EINVAL, "bad deposit arguments");
+    if (n == 0) return PIC_OK;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 65535);
+    k_deposit_plain<<<grid, 256, 0, (cudaStream_t)stream>>>(n_cells, periodic, n, cell, off, (unsigned long long *)R);
+    CU(cudaGetLastError());
+    return PIC_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,152 @@
+// pic_device.cuh -- device-side types and helpers of the 1D3V PIC-MCC step.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pic {
+
+constexpr int kMaxProc = 4;
+constexpr int kNGrid = 1000;            // cross-section grid, log-spaced on [1e-3, 1e3] eV
+constexpr float kGridEmin = 1e-3f;
+constexpr int kEepfBins = 240;          // 0..60 eV, 0.25 eV bins
+constexpr int kStepThreads = 512;
+constexpr int kFieldThreads = 512;
+
+// device error word bits
+constexpr unsigned kErrCapacity = 1u;
+constexpr unsigned kErrNumeric = 2u;
+constexpr unsigned kErrTimeout = 4u;
+constexpr unsigned kErrLoad = 8u;
+
+// Random-draw blocks: counter word 2 is (species << 16) | block.
+constexpr uint32_t kBlkMcc = 0, kBlkAux = 1, kBlkNewIon = 2, kBlkSee = 3, kBlkSeeV = 4, kBlkChild = 0xFFFF;
+
+struct SpeciesBufs {                    // one half of a species' ping-pong storage
+    int32_t *cell;
+    float *off, *vx, *vy, *vz;
+    uint32_t *id;
+};
+
+// Device-resident control block: counts, step, errors, event counters.
+struct Ctrl {
+    unsigned long long n_total[2];      // slots in use (append counter)
+    unsigned long long n_active[2];     // slots the current step processes
+    int32_t cur[2];                     // current ping-pong half per species
+    long long step;                     // completed steps since load
+    unsigned int err;
+    unsigned int pad;
+    unsigned long long absorbed[2][2];
+    unsigned long long see, iz;
+    unsigned long long cand[2];
+    unsigned long long coll[2][kMaxProc];
+    unsigned long long n_dead[2];       // absorbed slots not yet compacted
+    unsigned long long fe_n;            // field-energy history entries written
+    unsigned long long n_steps_acc, n_diag_acc;
+};
+
+struct SpConst {
+    float c_e;                          // q dt / (2 m): half electric kick per V/m
+    float tB[3], sB[3];                 // Boris rotation vectors t = (q dt / 2m) B, s = 2t/(1+t^2)
+    float cEy, cEz;                     // c_e * E_ext_y, c_e * E_ext_z
+    float m_over_2e;                    // eps[eV] = m/(2e) |v|^2
+    float v_of_sqrt_eps;                // |v| = sqrt(2e/m) sqrt(eps)
+    float pnull;                        // 1 - exp(-numax dt)
+    float numax;
+    int nproc;
+    int kind[kMaxProc];
+    float thr[kMaxProc];
+    float recoil;                       // 2 m / M_gas
+    float vt_gas;                       // sqrt(k T_gas / M_gas)
+    float mfrac, Mfrac;                 // m/(m+M), M/(m+M)
+    float mu_over_2e;                   // centre-of-mass energy eps = mu/(2e) |g|^2
+    float vt_newion;                    // sqrt(k T_gas / m_ion)
+    double q, m, w;
+    int mcc;                            // 0 none, 1 tables, 2 constant frequency
+};
+
+struct StepConst {
+    int n_cells, n_nodes, periodic, n_species;
+    float dtdx;                         // dt / dx
+    float Ex_ext;                       // imposed field along x
+    uint32_t key0, key1;                // Philox key
+    float see_gamma, see_vth, see_dtdx;
+    float eepf_lo, eepf_hi;             // cells: central 10 % of the gap
+    float inv_dlog;                     // 1 / (ln(emax/emin)/(NGRID-1)) for the ln-eps interpolation
+    int diag_interval;
+    double dx, dt, eps0;
+    double vol_interior, vol_wall;
+    double bg_charge;
+    int n_harm;
+    double harm_f[4], harm_a[4], harm_p[4];
+    SpConst sp[2];
+    const float *nu_tab[2];             // [nproc][kNGrid] per species
+    float *E32;                         // [n_cells + 1 padded]: periodic ghost at n_cells
+    double *E, *phi;                    // [n_nodes]
+    unsigned long long *R[2];           // [n_cells + 1] raw fixed-point deposit
+    SpeciesBufs buf[2][2];              // [species][half]
+    unsigned long long cap[2];
+    Ctrl *ctrl;
+    unsigned long long *Rsum, *Rdiag;   // [2][n_nodes] raw deposit summed over steps / diagnostic steps
+    double *phi_sum, *en_sum;           // [n_nodes], [2][n_nodes]
+    double cq[2];                       // (dx/eps0) q_s w_s 2^-32: Poisson source per raw unit (interior)
+    double rho_wall[2];                 // q_s w_s 2^-32 / (dx/2): charge density per raw unit at a wall node
+    double bg_r;                        // bg dx^2 / eps0
+    double inv_dx, inv_2dx, half_dx_eps0, fe_c;   // 1/dx, 1/(2dx), dx/(2 eps0), eps0 dx / 2
+    double *ke_sum, *pw_sum;            // [2]
+    unsigned long long *eepf;           // [kEepfBins]
+    double *fe_hist;                    // [fe_cap]
+    long long fe_cap;
+    unsigned int *sort_count;           // [n_cells]
+    unsigned long long *sort_cursor;    // [n_cells]
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Ten rounds; each forms
+// the 64-bit products of counter words 0 and 2 with the round multipliers,
+// xors the high halves with words 1 and 3 and the key, and permutes; the key
+// advances by the Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// 32-bit word -> uniform in (0,1): ((r >> 9) + 1/2) 2^-23, exact in FP32.
+__device__ __forceinline__ float u01(uint32_t r)
+{
+    return __fmaf_rn((float)(r >> 9), 1.0f / 8388608.0f, 0.5f / 8388608.0f);
+}
+
+__device__ __forceinline__ uint4 draw(const StepConst &P, uint32_t id, uint32_t step, int sp, uint32_t blk)
+{
+    return philox4x32_10(make_uint4(id, step, ((uint32_t)sp << 16) | blk, 0u), P.key0, P.key1);
+}
+
+// isotropic unit vector from two uniforms: cos(theta) = 1 - 2u, phi = 2 pi u'
+__device__ __forceinline__ float3 iso_dir(float ucos, float uphi)
+{
+    const float ct = 1.0f - 2.0f * ucos;
+    const float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+    float s, c;
+    sincospif(2.0f * uphi, &s, &c);
+    return make_float3(st * c, st * s, ct);
+}
+
+// Box-Muller pair
+__device__ __forceinline__ float2 box_muller(float a, float b)
+{
+    const float r = sqrtf(-2.0f * logf(a));
+    float s, c;
+    sincospif(2.0f * b, &s, &c);
+    return make_float2(r * c, r * s);
+}
+
+} // namespace pic

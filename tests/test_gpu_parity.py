@@ -1,0 +1,254 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+identical seeded inputs.
+
+Bars: bit-exact for Philox words, the fixed-point deposit and the cell
+indices; <= 1e-5 per single step for the FP32 particle state (positions in
+cell units, velocities relative to the speed); a particle may differ beyond
+that only where the oracle reports a discrete decision within 1e-5 of its
+threshold (a cell crossing, the null-collision test, the process choice),
+and such flips must be rare.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_17151_b300 import workloads as W
+
+from .gpu_helpers import compare_species, gpu_case, oracle_case
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_2609_17151_b300 import pic  # noqa: E402
+
+
+def small_ccp(seed=3, n=20001, te=20.0, ti_ev=None, see=0.5, n_cells=64, volts=200.0):
+    gap = n_cells * (0.025 / 512)
+    cfg, parts = W.ccp_case(seed=seed, n_cells=n_cells, gap=gap, n_per_species=n, te_ev=te, volts=volts,
+                            see_gamma=see)
+    if ti_ev is not None:
+        rng = np.random.default_rng(seed + 100)
+        parts[1] = W.maxwellian_load(rng, n, n_cells, ti_ev, W.M_AR)
+    return cfg, parts
+
+
+def compare_all(cfg, gc, oc, steps=1, **kw):
+    dtdx = cfg["dt"] / (cfg["length"] / cfg["n_cells"])
+    stats = []
+    for s in range(len(cfg["species"])):
+        stats.append(compare_species(gc.particles(s), oc.particles(s), cfg["n_cells"], bool(cfg["periodic"]),
+                                     dtdx=dtdx, steps=steps, **kw))
+    return stats
+
+
+# --------------------------------------------------------------------------- primitives
+def test_philox_bit_exact():
+    rng = np.random.default_rng(1)
+    n = 100_003
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:3] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4]]
+    seed = 0x0123456789ABCDEF
+    d_ctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+    d_out = torch.zeros_like(d_ctr)
+    pic.philox(seed, d_ctr, d_out, n)
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy().view(np.uint32)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for i in list(range(50)) + list(rng.integers(0, n, 200)):
+        assert oracle.philox4x32_10(ctr[i].tolist(), key) == got[i].tolist(), i
+
+
+@pytest.mark.parametrize("periodic", [0, 1])
+@pytest.mark.parametrize("n", [0, 1, 7, 4099, 300_001])
+def test_deposit_bit_exact(periodic, n):
+    rng = np.random.default_rng(n + periodic)
+    n_cells = 67
+    xi = rng.uniform(0, n_cells, n)
+    cell = np.floor(xi).astype(np.int32)
+    off = (xi - cell).astype(np.float32)
+    off[off >= 1] = 0
+    if n > 10:
+        off[:5] = [0.0, np.nextafter(np.float32(1), np.float32(0)), 0.5, 2**-24, 0.25]
+        cell[:5] = [0, n_cells - 1, n_cells - 1, 3, 0]
+    nn = n_cells if periodic else n_cells + 1
+    R = torch.zeros(nn, dtype=torch.int64, device="cuda")
+    if n:
+        pic.deposit(n_cells, periodic, torch.from_numpy(cell).cuda(), torch.from_numpy(off).cuda(), R)
+    torch.cuda.synchronize()
+    ref = oracle.deposit(n_cells, periodic, cell.astype(np.float64) + off.astype(np.float64))
+    assert np.array_equal(R.cpu().numpy(), ref)
+
+
+# --------------------------------------------------------------------------- one step
+def test_langmuir_one_step_parity_and_field():
+    cfg, parts = W.langmuir_case(seed=1)
+    oc = oracle_case(cfg, parts)
+    oc.step(1)
+    gc = gpu_case(cfg, parts)
+    gc.step(1)
+    st = compare_all(cfg, gc, oc)
+    assert st[0]["flips"] <= 2
+    phi_g, E_g, R_g = gc.field()
+    phi_o, E_o = oc.field()
+    assert int(R_g[0].sum()) == 6400 * 2**32            # charge conserved exactly
+    assert np.allclose(E_g, E_o, rtol=0, atol=1e-4 * np.abs(E_o).max())
+    assert np.allclose(phi_g, phi_o, rtol=0, atol=1e-4 * np.abs(phi_o).max())
+    gc.close()
+
+
+@pytest.mark.parametrize("steps", [1, 4])
+def test_ccp_small_parity_all_processes(steps):
+    """Bounded argon case with hot electrons and hot ions so that one step
+    exercises absorption, secondary emission, elastic, excitation,
+    ionization (with the append of both products), isotropic ion scattering
+    and charge exchange."""
+    cfg, parts = small_ccp(ti_ev=400.0)
+    oc = oracle_case(cfg, parts)
+    oc.step(steps)
+    gc = gpu_case(cfg, parts)
+    gc.step(steps)
+    st = compare_all(cfg, gc, oc, steps=steps)
+    m = gc.moments()
+    co = oc.counters()
+    assert co["ionizations"] > 0 and co["see_emitted"] > 0 and co["absorbed"].sum() > 0
+    for s in range(2):
+        assert abs(int(m["absorbed"][s].sum()) - int(co["absorbed"][s].sum())) <= max(2, st[s]["flips"])
+    assert abs(m["ionizations"] - co["ionizations"]) <= max(2, st[0]["flips"])
+    assert abs(m["see_emitted"] - co["see_emitted"]) <= max(2, st[1]["flips"])
+    gc.close()
+
+
+def test_full_size_ccp_one_step():
+    """The 4e5-particle argon CCP workload at full size, one step, every particle."""
+    cfg, parts = W.ccp_case(seed=1)
+    oc = oracle_case(cfg, parts)
+    oc.step(1)
+    gc = gpu_case(cfg, parts)
+    gc.step(1)
+    compare_all(cfg, gc, oc)
+    gc.close()
+
+
+def test_full_size_exb_one_step():
+    """The 1.02e7-particle E x B workload (2048 cells, 2500 per cell per species)
+    at full size, one step, every particle, in the bench's launch configuration."""
+    cfg, parts = W.ecdi_case(seed=1)
+    oc = oracle_case(cfg, parts)
+    oc.step(1)
+    gc = gpu_case(cfg, parts)
+    gc.step(1)
+    st = compare_all(cfg, gc, oc)
+    phi_g, E_g, R_g = gc.field()
+    assert int(R_g[0].sum()) == parts[0]["id"].size * 2**32
+    assert int(R_g[1].sum()) == parts[1]["id"].size * 2**32
+    assert st[0]["n"] == parts[0]["id"].size
+    gc.close()
+
+
+# --------------------------------------------------------------------------- properties
+def test_sort_interval_does_not_change_results():
+    """Reordering particles (counting sort every step) leaves every particle
+    bit-identical: the update of a particle depends only on its own state, the
+    field, its id and the step, and the integer deposit is order-free."""
+    cfg, parts = small_ccp(seed=5, ti_ev=400.0)
+    a = gpu_case(cfg, parts, sort_interval=1)
+    b = gpu_case(cfg, parts, sort_interval=100000)
+    a.step(12)
+    b.step(12)
+    for s in range(2):
+        pa, pb = a.particles(s), b.particles(s)
+        ia, ib = np.argsort(pa["id"], kind="stable"), np.argsort(pb["id"], kind="stable")
+        for k in ("id", "cell", "off", "vx", "vy", "vz"):
+            assert np.array_equal(pa[k][ia], pb[k][ib]), (s, k)
+    # after a sort step the storage order is by cell
+    c = gpu_case(cfg, parts, sort_interval=3)
+    c.step(3)
+    for s in range(2):
+        assert np.all(np.diff(c.particles(s)["cell"]) >= 0)
+    a.close(); b.close(); c.close()
+
+
+def test_capacity_overflow_is_reported_not_dropped():
+    cfg, parts = small_ccp(seed=7, n=5000, te=60.0)
+    gc = gpu_case(cfg, parts, capacity=(5000 + 8, 5000 + 8))
+    gc.step(5)
+    with pytest.raises(pic.PicError) as ei:
+        gc.sync()
+    assert ei.value.status == 4
+    gc.close()
+
+
+def test_invalid_load_is_rejected():
+    cfg, parts = W.langmuir_case(seed=1)
+    parts[0]["cell"] = parts[0]["cell"].copy()
+    parts[0]["cell"][10] = cfg["n_cells"] + 5
+    gc = gpu_case(cfg, parts)
+    gc.step(1)
+    with pytest.raises(pic.PicError) as ei:
+        gc.sync()
+    assert ei.value.status == 1
+    gc.close()
+
+
+def test_ragged_and_tiny_loads():
+    for n in (1, 2, 3, 5, 130, 1027):
+        cfg, parts = small_ccp(seed=n, n=n, te=20.0, ti_ev=400.0)
+        oc = oracle_case(cfg, parts)
+        oc.step(2)
+        gc = gpu_case(cfg, parts)
+        gc.step(2)
+        compare_all(cfg, gc, oc, steps=2)
+        gc.close()
+
+
+def test_electrons_only_with_empty_ion_species():
+    cfg, parts = small_ccp(seed=9, n=3001)
+    parts[1] = {k: v[:0] for k, v in parts[1].items()}
+    oc = oracle_case(cfg, parts)
+    oc.step(3)
+    gc = gpu_case(cfg, parts)
+    gc.step(3)
+    compare_all(cfg, gc, oc, steps=3)
+    gc.close()
+
+
+# --------------------------------------------------------------------------- physics on the GPU
+def test_landau_damping_on_gpu():
+    """FP32 particles on the GPU reproduce the kinetic Landau root (paper §3.1)."""
+    from .test_oracle_pins import fit_landau, kinetic_root
+    for klD in (0.4, 0.38):
+        cfg, parts = W.langmuir_case(seed=1, k_lambda_d=klD, ppc=1000, slab=16)
+        gc = gpu_case(cfg, parts)
+        amps = []
+        for _ in range(360):
+            gc.step(1)
+            _, E, _ = gc.field()
+            amps.append(abs(np.fft.rfft(E)[1]) * 2 / cfg["n_cells"])
+        w, g = fit_landau(np.array(amps), 0.1)
+        w0, g0 = kinetic_root(klD)
+        assert abs(w - w0) < 0.01 * w0 and abs(g - g0) < 0.06 * g0, (klD, w, g, w0, g0)
+        gc.close()
+
+
+def test_diagnostic_moments_match_oracle():
+    cfg, parts = small_ccp(seed=11, n=20001, te=5.0)
+    cfg["diag_interval"] = 2
+    oc = oracle_case(cfg, parts)
+    oc.step(6)
+    gc = gpu_case(cfg, parts)
+    gc.step(6)
+    mg = gc.moments()
+    mo = oc.moments()
+    assert mg["n_steps"] == 6 and mg["n_diag"] == 3
+    for k in ("dens_sum", "dens_diag_sum", "en_sum"):
+        ref = mo[k][: len(cfg["species"])]
+        assert np.allclose(mg[k], ref, rtol=2e-3, atol=2e-3 * np.abs(ref).max()), k
+    assert np.allclose(mg["phi_sum"], mo["phi_sum"], rtol=0, atol=1e-3 * np.abs(mo["phi_sum"]).max())
+    assert np.allclose(mg["ke_sum"], mo["ke_sum"], rtol=1e-4)
+    assert abs(mg["eepf"].sum() - mo["eepf"].sum()) <= 0.01 * mo["eepf"].sum() + 5
+    gc.close()
