@@ -214,6 +214,20 @@ pic_status pic_philox(uint64_t seed, int64_t n, const uint32_t *ctr, uint32_t *o
 pic_status pic_deposit(int32_t n_cells, int32_t periodic, int64_t n, const int32_t *cell,
                        const float *offset, int64_t *R, void *stream);
 
+/* Counting sort of particles by cell (the periodic sort of the step, as a
+ * stand-alone operation): the n input particles (SoA, device) with a cell in
+ * [0, n_cells) are written to the output arrays grouped by ascending cell;
+ * the others (absorbed: cell < 0, or cell >= n_cells) are dropped.  The order
+ * inside one cell is unspecified.  *n_live (device int64, may be NULL)
+ * receives the number written.  Inputs and outputs must not overlap.  Scratch
+ * (per-cell counts and cursors, 12 B per cell) comes from the stream-ordered
+ * allocator (cudaMallocAsync / cudaFreeAsync on `stream`).
+ * Errors: PIC_EINVAL (n_cells outside [1, 4096], n < 0, NULL array), PIC_ECUDA. */
+pic_status pic_sort_by_cell(int32_t n_cells, int64_t n, const int32_t *cell, const float *offset,
+                            const float *vx, const float *vy, const float *vz, const uint32_t *id,
+                            int32_t *cell_out, float *offset_out, float *vx_out, float *vy_out,
+                            float *vz_out, uint32_t *id_out, int64_t *n_live, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,8 @@ def _load():
     lib.or_deposit.argtypes = [C.c_int, C.c_int, C.c_int64, dp, C.POINTER(C.c_int64)]
     lib.or_poisson.argtypes = [C.c_int, C.c_int, C.c_double, dp, C.c_double, dp]
     lib.or_boris.argtypes = [C.c_double, C.c_double, dp, dp, dp]
+    lib.or_sort_by_cell.restype = C.c_int64
+    lib.or_sort_by_cell.argtypes = [C.c_int, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
     return lib
 
 
@@ -142,6 +144,16 @@ def boris(qm: float, h: float, E, B, v) -> np.ndarray:
     E = _f64(E); B = _f64(B); v = _f64(v).copy()
     _lib.or_boris(qm, h, _d(E), _d(B), _d(v))
     return v
+
+
+def sort_by_cell(n_cells: int, cell) -> np.ndarray:
+    """Indices of the particles with a cell in [0, n_cells), grouped by ascending
+    cell, input order kept inside a cell (counting sort)."""
+    cell = np.ascontiguousarray(cell, dtype=np.int32)
+    perm = np.zeros(cell.size, dtype=np.int64)
+    k = _lib.or_sort_by_cell(n_cells, cell.size, cell.ctypes.data_as(C.POINTER(C.c_int32)),
+                             perm.ctypes.data_as(C.POINTER(C.c_int64)))
+    return perm[:k]
 
 
 # --------------------------------------------------------------------------- case

@@ -826,6 +826,23 @@ void or_reset_moments(or_case *c)
     c->cnt.step = step;
 }
 
+/* Counting sort by cell (the periodic reordering of the particle arrays):
+ * the indices of the particles whose cell lies in [0, n_cells), grouped by
+ * ascending cell and, inside a cell, in input order.  Returns how many. */
+int64_t or_sort_by_cell(int n_cells, int64_t n, const int32_t *cell, int64_t *perm)
+{
+    int64_t *start = calloc((size_t)n_cells + 1, sizeof(int64_t));
+    if (!start) return -1;
+    for (int64_t k = 0; k < n; ++k)
+        if (cell[k] >= 0 && cell[k] < n_cells) start[cell[k] + 1]++;
+    for (int j = 0; j < n_cells; ++j) start[j + 1] += start[j];
+    int64_t kept = start[n_cells];
+    for (int64_t k = 0; k < n; ++k)
+        if (cell[k] >= 0 && cell[k] < n_cells) perm[start[cell[k]]++] = k;
+    free(start);
+    return kept;
+}
+
 int64_t or_get_field_energy(const or_case *c, double *out, int64_t max_n)
 {
     int64_t n = c->fe_n < max_n ? c->fe_n : max_n;

@@ -109,5 +109,6 @@ void or_deposit(int n_cells, int periodic, int64_t n, const double *xi, int64_t 
 int  or_poisson(int n_cells, int periodic, double dx, const double *rho,
                 double phi_left, double *phi);
 void or_boris(double qm, double h, const double E[3], const double B[3], double v[3]);
+int64_t or_sort_by_cell(int n_cells, int64_t n, const int32_t *cell, int64_t *perm);
 
 #endif

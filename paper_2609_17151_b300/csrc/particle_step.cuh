@@ -229,11 +229,37 @@ __device__ __forceinline__ void emit_secondary(const StepConst &P, uint32_t id, 
     atomicAdd(s_see, 1u);
 }
 
-// Add a (cell, count, sum f) run to the shared histogram.
-__device__ __forceinline__ void hist_run(unsigned long long *h, int c, unsigned n, unsigned long long sf)
+// Shared deposit histogram, per cell: particle count n and the sum of the
+// fixed-point offsets F = sum f split as (F >> 16, F & 0xFFFF) so that every
+// counter is a native 32-bit shared atomic.  At the flush, node c gets
+// n 2^32 - F and node c+1 gets F (exact).  A counter pair holds at least
+// 65536 particles per cell between flushes.
+struct DepHist {
+    unsigned *cnt, *fhi, *flo;
+};
+constexpr int kFlushParticles = 65536;
+
+__device__ __forceinline__ void hist_run(const DepHist &h, int c, unsigned n, unsigned long long sf)
 {
-    atomicAdd(&h[c], ((unsigned long long)n << 32) - sf);
-    atomicAdd(&h[c + 1], sf);
+    atomicAdd(&h.cnt[c], n);
+    atomicAdd(&h.fhi[c], (unsigned)(sf >> 16));
+    atomicAdd(&h.flo[c], (unsigned)(sf & 0xFFFFull));
+}
+
+// Add the CTA's histogram to the global deposit and clear it.
+__device__ __forceinline__ void hist_flush(const DepHist &h, int N, unsigned long long *R)
+{
+    __syncthreads();
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        const unsigned n = h.cnt[c];
+        if (n) {
+            const unsigned long long F = ((unsigned long long)h.fhi[c] << 16) + h.flo[c];
+            atomicAdd(&R[c], ((unsigned long long)n << 32) - F);
+            atomicAdd(&R[c + 1], F);
+            h.cnt[c] = 0u; h.fhi[c] = 0u; h.flo[c] = 0u;
+        }
+    }
+    __syncthreads();
 }
 
 // Shared memory layout of the step kernel (bytes, 16-aligned pieces).
@@ -244,7 +270,7 @@ struct StepSmem {
     {
         e_off = 0;
         h_off = align16(e_off + (unsigned)(n_cells + 1) * 4u);
-        nu_off = align16(h_off + (unsigned)(n_cells + 1) * 8u);
+        nu_off = align16(h_off + (unsigned)n_cells * 12u);
         en_off = align16(nu_off + (unsigned)nproc * kNGrid * 4u);
         eepf_off = align16(en_off + (unsigned)(n_cells + 1) * 4u);
         total = align16(eepf_off + kEepfBins * 4u);
@@ -264,7 +290,8 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_
     const int N = P.n_cells;
     const StepSmem L(N, MCC == 1 ? S.nproc : 0);
     float *Es = reinterpret_cast<float *>(smem + L.e_off);
-    unsigned long long *hist = reinterpret_cast<unsigned long long *>(smem + L.h_off);
+    const DepHist hist{reinterpret_cast<unsigned *>(smem + L.h_off), reinterpret_cast<unsigned *>(smem + L.h_off) + N,
+                       reinterpret_cast<unsigned *>(smem + L.h_off) + 2 * N};
     float *nus = reinterpret_cast<float *>(smem + L.nu_off);
     float *hen = reinterpret_cast<float *>(smem + L.en_off);
     unsigned *heepf = reinterpret_cast<unsigned *>(smem + L.eepf_off);
@@ -283,7 +310,8 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_
     const long long step_ll = ctrl->step;
     const uint32_t step = (uint32_t)step_ll;
     const bool diag = P.diag_interval > 0 && ((step_ll + 1) % P.diag_interval) == 0;
-    for (int j = tid; j <= N; j += blockDim.x) { hist[j] = 0ull; if (diag) hen[j] = 0.0f; }
+    for (int j = tid; j < N; j += blockDim.x) { hist.cnt[j] = 0u; hist.fhi[j] = 0u; hist.flo[j] = 0u; }
+    if (diag) for (int j = tid; j <= N; j += blockDim.x) hen[j] = 0.0f;
     if (diag) for (int j = tid; j < kEepfBins; j += blockDim.x) heepf[j] = 0u;
     if (tid < 2 + 2 * kMaxProc) s_cnt[tid] = 0u;
     if (tid < 2) s_abs[tid] = 0u;
@@ -307,9 +335,13 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_
     const int lane = tid & 31, warp = tid >> 5;
     float ke_acc = 0.0f, pw_acc = 0.0f;
 
-    for (long long base = beg + warp * 32; base < end; base += blockDim.x) {
+    // at most kFlushParticles per flush of the histogram (counter range)
+    for (long long sub = beg; sub < end; sub += kFlushParticles / 4) {
+    const long long sub_end = min(sub + kFlushParticles / 4, end);
+    if (sub > beg) hist_flush(hist, N, P.R[SP]);
+    for (long long base = sub + warp * 32; base < sub_end; base += blockDim.x) {
         const long long ch = base + lane;
-        const bool live_chunk = ch < end;
+        const bool live_chunk = ch < sub_end;
         const long long i0 = ch * 4;
         int4 c4 = make_int4(-1, -1, -1, -1);
         float4 o4 = make_float4(0, 0, 0, 0), x4 = o4, y4 = o4, z4 = o4;
@@ -432,13 +464,9 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_
             hist_run(hist, acc_c, acc_n, acc_f);
         }
     }
-    // CTA epilogue: flush the histogram and counters
-    __syncthreads();
-    unsigned long long *R = P.R[SP];
-    for (int j = tid; j <= N; j += blockDim.x) {
-        const unsigned long long h = hist[j];
-        if (h) atomicAdd(&R[(PERIODIC && j == N) ? 0 : j], h);
     }
+    // CTA epilogue: flush the histogram and counters
+    hist_flush(hist, N, P.R[SP]);
     if (diag) {
         const int nn = P.n_nodes;
         for (int j = tid; j <= N; j += blockDim.x) {

@@ -237,7 +237,7 @@ cudaError_t launch_step_sp(pic_case *c)
 cudaError_t launch_field(pic_case *c, int mode)
 {
     Timed t(c, mode == 0 ? KC_INIT : KC_FIELD, 1);
-    k_field<<<1, kFieldThreads, c->field_smem, c->stream>>>(c->P, mode, c->R_last);
+    k_field<<<kFieldCluster, kFieldThreads, c->field_smem, c->stream>>>(c->P, mode, c->R_last);
     return cudaGetLastError();
 }
 
@@ -246,12 +246,15 @@ cudaError_t launch_sort(pic_case *c, int sp)
     const int N = c->d.n_cells;
     const long long cap = (long long)c->P.cap[sp];
     Timed t(c, KC_SORT, 4);
-    int gc = std::min<long long>(c->num_sms * 4, std::max<long long>(1, cap / 1024));
-    k_sort_count<<<gc, 512, N * sizeof(unsigned), c->stream>>>(c->P, sp);
-    k_sort_scan<<<1, kFieldThreads, N * sizeof(double), c->stream>>>(c->P);
+    SortHalves H{{c->P.buf[sp][0], c->P.buf[sp][1]}};
+    const int32_t *cur = &c->P.ctrl->cur[sp];
+    const unsigned long long *n = &c->P.ctrl->n_active[sp];
+    const int gc = (int)std::min<long long>(c->num_sms * 4, std::max<long long>(1, cap / 1024));
+    k_cells_count<<<gc, 512, N * sizeof(unsigned), c->stream>>>(H, cur, n, 0, N, c->P.sort_count);
+    k_cells_scan<<<1, 1024, N * sizeof(double), c->stream>>>(c->P.sort_count, N, c->P.sort_cursor);
     const long long nchunks = (cap + kSortChunk - 1) / kSortChunk;
-    k_sort_scatter<<<(unsigned)nchunks, 512, 12 * (size_t)N, c->stream>>>(c->P, sp);
-    k_sort_finish<<<4, 256, 0, c->stream>>>(c->P, sp);
+    k_cells_scatter<<<(unsigned)nchunks, 512, 12 * (size_t)N, c->stream>>>(H, cur, n, 0, N, c->P.sort_cursor);
+    k_sort_finish<<<4, 256, 0, c->stream>>>(c->P, sp, c->P.sort_cursor + N);
     return cudaGetLastError();
 }
 
@@ -439,7 +442,7 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), c->stream);
     cudaMemsetAsync(P.sort_count, 0, sizeof(unsigned) * N, c->stream);
     cudaMemsetAsync(c->R_last, 0, sizeof(unsigned long long) * 2 * nn, c->stream);
-    c->field_smem = (unsigned)(4 * (N + 1) * sizeof(double));
+    c->field_smem = (unsigned)(4 * ((N + 1 + kFieldCluster - 1) / kFieldCluster) * sizeof(double));
     if (cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->field_smem) != cudaSuccess) {
         pic_destroy(c);
         return fail(PIC_ECUDA, "field kernel shared memory attribute");
@@ -747,6 +750,44 @@ pic_status pic_deposit(int32_t n_cells, int32_t periodic, int64_t n, const int32
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 65535);
     k_deposit_plain<<<grid, 256, 0, (cudaStream_t)stream>>>(n_cells, periodic, n, cell, off, (unsigned long long *)R);
     CU(cudaGetLastError());
+    return PIC_OK;
+}
+
+pic_status pic_sort_by_cell(int32_t n_cells, int64_t n, const int32_t *cell, const float *off, const float *vx,
+                            const float *vy, const float *vz, const uint32_t *id, int32_t *cell_out, float *off_out,
+                            float *vx_out, float *vy_out, float *vz_out, uint32_t *id_out, int64_t *n_live, void *stream)
+{
+    if (n_cells < 1 || n_cells > 4096 || n < 0) return fail(PIC_EINVAL, "bad sort sizes");
+    if (n > 0 && (!cell || !off || !vx || !vy || !vz || !id || !cell_out || !off_out || !vx_out || !vy_out ||
+                  !vz_out || !id_out))
+        return fail(PIC_EINVAL, "null sort array");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = n_cells;
+    // scratch: per-cell counts and cursors, from the stream-ordered pool
+    const size_t cnt_bytes = ((size_t)N * sizeof(unsigned) + 15) / 16 * 16;
+    const size_t bytes = cnt_bytes + (size_t)(N + 1) * sizeof(unsigned long long);
+    void *scratch = nullptr;
+    CU(cudaMallocAsync(&scratch, bytes, st));
+    unsigned *counts = (unsigned *)scratch;
+    unsigned long long *cursor = (unsigned long long *)((char *)scratch + cnt_bytes);
+    CU(cudaMemsetAsync(counts, 0, (size_t)N * sizeof(unsigned), st));
+    CU(cudaMemsetAsync(cursor + N, 0, sizeof(unsigned long long), st));
+    SortHalves H{{SpeciesBufs{const_cast<int32_t *>(cell), const_cast<float *>(off), const_cast<float *>(vx),
+                              const_cast<float *>(vy), const_cast<float *>(vz), const_cast<uint32_t *>(id)},
+                  SpeciesBufs{cell_out, off_out, vx_out, vy_out, vz_out, id_out}}};
+    if (n > 0) {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int gc = (int)std::min<long long>(sms * 4, std::max<long long>(1, n / 1024));
+        k_cells_count<<<gc, 512, N * sizeof(unsigned), st>>>(H, nullptr, nullptr, n, N, counts);
+        k_cells_scan<<<1, 1024, N * sizeof(double), st>>>(counts, N, cursor);
+        k_cells_scatter<<<(unsigned)((n + kSortChunk - 1) / kSortChunk), 512, 12 * (size_t)N, st>>>(H, nullptr, nullptr,
+                                                                                                   n, N, cursor);
+        CU(cudaGetLastError());
+    }
+    if (n_live) CU(cudaMemcpyAsync(n_live, cursor + N, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    CU(cudaFreeAsync(scratch, st));
     return PIC_OK;
 }
 

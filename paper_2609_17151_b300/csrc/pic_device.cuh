@@ -10,7 +10,8 @@ constexpr int kNGrid = 1000;            // cross-section grid, log-spaced on [1e
 constexpr float kGridEmin = 1e-3f;
 constexpr int kEepfBins = 240;          // 0..60 eV, 0.25 eV bins
 constexpr int kStepThreads = 512;
-constexpr int kFieldThreads = 512;
+constexpr int kFieldThreads = 256;
+constexpr int kFieldCluster = 8;       // CTAs (SMs) sharing one field solve
 
 // device error word bits
 constexpr unsigned kErrCapacity = 1u;

@@ -95,11 +95,12 @@ def _load_library():
     lib.pic_last_error.restype = C.c_char_p
     lib.pic_philox.argtypes = [C.c_uint64, i64, vp, vp, vp]
     lib.pic_deposit.argtypes = [i32, i32, i64, vp, vp, vp, vp]
+    lib.pic_sort_by_cell.argtypes = [i32, i64] + [vp] * 12 + [vp, vp]
     lib.pic_profile.argtypes = [vp, C.c_int]
     lib.pic_profile_read.argtypes = [vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]
     for f in ("pic_create_case", "pic_load_xsec_table", "pic_load_particles", "pic_step", "pic_sync", "pic_count",
               "pic_read_particles", "pic_read_field", "pic_read_moments", "pic_destroy", "pic_philox", "pic_deposit",
-              "pic_profile", "pic_profile_read"):
+              "pic_profile", "pic_profile_read", "pic_sort_by_cell"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -289,6 +290,13 @@ def philox(seed: int, ctr_dev, out_dev, n: int, stream=None):
 def deposit(n_cells, periodic, cell_dev, off_dev, R_dev, stream=None):
     check(lib.pic_deposit(int(n_cells), int(periodic), int(cell_dev.numel()), _ptr(cell_dev), _ptr(off_dev),
                           _ptr(R_dev), stream))
+
+
+def sort_by_cell(n_cells, src: dict, dst: dict, n_live_dev=None, stream=None):
+    """Counting sort of device SoA particles (dicts of torch tensors) by cell."""
+    keys = ("cell", "off", "vx", "vy", "vz", "id")
+    check(lib.pic_sort_by_cell(int(n_cells), int(src["cell"].numel()), *[_ptr(src[k]) for k in keys],
+                               *[_ptr(dst[k]) for k in keys], _ptr(n_live_dev), stream))
 
 
 class Case:

@@ -252,3 +252,30 @@ def test_diagnostic_moments_match_oracle():
     assert np.allclose(mg["ke_sum"], mo["ke_sum"], rtol=1e-4)
     assert abs(mg["eepf"].sum() - mo["eepf"].sum()) <= 0.01 * mo["eepf"].sum() + 5
     gc.close()
+
+
+@pytest.mark.parametrize("n_cells,n", [(1, 5), (64, 4099), (2048, 1_000_003)])
+def test_sort_by_cell_matches_oracle(n_cells, n):
+    """Counting sort entry point: the kept set, the per-cell counts and every
+    particle's fields are bit-exact; only the order inside a cell is free."""
+    rng = np.random.default_rng(n)
+    cell = rng.integers(-1, n_cells, n).astype(np.int32)
+    cell[: n // 3] = np.sort(cell[: n // 3])           # part sorted, part random
+    src = {"cell": cell, "off": rng.random(n, dtype=np.float32), "vx": rng.standard_normal(n).astype(np.float32),
+           "vy": rng.standard_normal(n).astype(np.float32), "vz": rng.standard_normal(n).astype(np.float32),
+           "id": rng.permutation(n).astype(np.uint32)}
+    d_src = {k: torch.from_numpy(v.view(np.int32) if v.dtype == np.uint32 else v).cuda() for k, v in src.items()}
+    d_dst = {k: torch.empty_like(v) for k, v in d_src.items()}
+    n_live = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pic.sort_by_cell(n_cells, d_src, d_dst, n_live)
+    torch.cuda.synchronize()
+    perm = oracle.sort_by_cell(n_cells, cell)
+    k = int(n_live.item())
+    assert k == perm.size
+    got = {kk: v.cpu().numpy()[:k] for kk, v in d_dst.items()}
+    got["id"] = got["id"].view(np.uint32)
+    assert np.array_equal(got["cell"], cell[perm])                  # grouped by ascending cell
+    og = np.lexsort((got["id"], got["cell"]))
+    oo = np.lexsort((src["id"][perm], cell[perm]))
+    for kk in src:
+        assert np.array_equal(got[kk][og], src[kk][perm][oo]), kk

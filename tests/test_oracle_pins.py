@@ -509,3 +509,15 @@ def test_maxwellian_temperature_moment():
     m = c.moments()
     te = 2.0 / 3.0 * m["en_sum"][0][2:-2].sum() / m["dens_diag_sum"][0][2:-2].sum()
     assert abs(te - 3.0) < 0.03
+
+
+# --------------------------------------------------------------------------- sort
+def test_sort_by_cell_is_the_stable_sort_dropping_absorbed():
+    """The counting sort equals numpy's stable argsort on the kept particles."""
+    rng = np.random.default_rng(12)
+    for n_cells, n in ((1, 10), (7, 1000), (300, 50_001)):
+        cell = rng.integers(-2, n_cells + 2, n).astype(np.int32)
+        perm = oracle.sort_by_cell(n_cells, cell)
+        keep = np.flatnonzero((cell >= 0) & (cell < n_cells))
+        ref = keep[np.argsort(cell[keep], kind="stable")]
+        assert np.array_equal(perm, ref)
