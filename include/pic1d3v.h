@@ -228,6 +228,29 @@ pic_status pic_sort_by_cell(int32_t n_cells, int64_t n, const int32_t *cell, con
                             int32_t *cell_out, float *offset_out, float *vx_out, float *vy_out,
                             float *vz_out, uint32_t *id_out, int64_t *n_live, void *stream);
 
+/* Allocation-free variant of pic_sort_by_cell.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * while they run (a fixed device-memory budget set at start-up, a plug-in
+ * whose host program owns the device heap, or code that cannot take the
+ * device-wide synchronisation cudaMalloc/cudaFree can imply).  Same arguments,
+ * layout and result as pic_sort_by_cell; the scratch (12 B per cell) is one
+ * fixed device array inside the library, sized for PIC_NOALLOC_MAX_CELLS
+ * cells, which every device that loads the library keeps until the process
+ * exits.  No cudaMalloc, cudaFree or allocating library routine is called.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress, once per device, with the device current); make
+ *     that first call before any stream capture.
+ *   - Every call on a device shares the one array: calls whose GPU work can
+ *     overlap (different streams without ordering, or concurrent host threads)
+ *     race on it.  Serialise them.
+ *   - Errors: PIC_EINVAL (n_cells outside [1, PIC_NOALLOC_MAX_CELLS], n < 0,
+ *     NULL array), PIC_ECUDA (message in pic_last_error). */
+#define PIC_NOALLOC_MAX_CELLS 4096
+pic_status pic_sort_by_cell_noalloc(int32_t n_cells, int64_t n, const int32_t *cell, const float *offset,
+                                    const float *vx, const float *vy, const float *vz, const uint32_t *id,
+                                    int32_t *cell_out, float *offset_out, float *vx_out, float *vy_out,
+                                    float *vz_out, uint32_t *id_out, int64_t *n_live, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

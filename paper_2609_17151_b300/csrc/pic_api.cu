@@ -340,6 +340,11 @@ pic_status reset_moments(pic_case *c)
 
 } // namespace
 
+// Message for pic_last_error() from the other translation units of the library.
+namespace pic {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}
+
 // ===========================================================================
 extern "C" {
 

@@ -96,11 +96,12 @@ def _load_library():
     lib.pic_philox.argtypes = [C.c_uint64, i64, vp, vp, vp]
     lib.pic_deposit.argtypes = [i32, i32, i64, vp, vp, vp, vp]
     lib.pic_sort_by_cell.argtypes = [i32, i64] + [vp] * 12 + [vp, vp]
+    lib.pic_sort_by_cell_noalloc.argtypes = [i32, i64] + [vp] * 12 + [vp, vp]
     lib.pic_profile.argtypes = [vp, C.c_int]
     lib.pic_profile_read.argtypes = [vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]
     for f in ("pic_create_case", "pic_load_xsec_table", "pic_load_particles", "pic_step", "pic_sync", "pic_count",
               "pic_read_particles", "pic_read_field", "pic_read_moments", "pic_destroy", "pic_philox", "pic_deposit",
-              "pic_profile", "pic_profile_read", "pic_sort_by_cell"):
+              "pic_profile", "pic_profile_read", "pic_sort_by_cell", "pic_sort_by_cell_noalloc"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -297,6 +298,13 @@ def sort_by_cell(n_cells, src: dict, dst: dict, n_live_dev=None, stream=None):
     keys = ("cell", "off", "vx", "vy", "vz", "id")
     check(lib.pic_sort_by_cell(int(n_cells), int(src["cell"].numel()), *[_ptr(src[k]) for k in keys],
                                *[_ptr(dst[k]) for k in keys], _ptr(n_live_dev), stream))
+
+
+def sort_by_cell_noalloc(n_cells, src: dict, dst: dict, n_live_dev=None, stream=None):
+    """The same sort with the library's fixed scratch array (no device allocation)."""
+    keys = ("cell", "off", "vx", "vy", "vz", "id")
+    check(lib.pic_sort_by_cell_noalloc(int(n_cells), int(src["cell"].numel()), *[_ptr(src[k]) for k in keys],
+                                       *[_ptr(dst[k]) for k in keys], _ptr(n_live_dev), stream))
 
 
 class Case:
