@@ -122,6 +122,7 @@ __global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldTh
     __shared__ double red[kFieldThreads / 32];
     __shared__ unsigned long long x_seg[2], x_tot[2];   // published CTA totals (integer charge)
     __shared__ double x_S, x_phi, x_fe, s_bcast[2];
+    __shared__ unsigned long long s_off[2], s_all[2];
     __shared__ int x_bad;
     const int rank = (int)cl.block_rank();
     const int N = P.n_cells, nn = P.n_nodes, tid = threadIdx.x, ns = P.n_species;
@@ -162,14 +163,25 @@ __global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldTh
         if (tid == 0) { x_seg[s] = t1; x_tot[s] = t2; }
     }
     cl.sync();                                                           // totals published; R fully read
+    // warp 0: lane r reads rank r's totals (parallel remote reads), combines them
+    if (tid < 32) {
+        const int lane = tid;
+        for (int s = 0; s < ns; ++s) {
+            const unsigned long long vs = lane < kFieldCluster ? cl.map_shared_rank(x_seg, lane)[s] : 0ull;
+            const unsigned long long vt = lane < kFieldCluster ? cl.map_shared_rank(x_tot, lane)[s] : 0ull;
+            unsigned long long below = lane < rank ? vs : 0ull, all = vt;
+            for (int o = 16; o > 0; o >>= 1) {
+                below += __shfl_xor_sync(0xffffffffu, below, o);
+                all += __shfl_xor_sync(0xffffffffu, all, o);
+            }
+            if (lane == 0) { s_off[s] = below; s_all[s] = all; }
+        }
+    }
+    __syncthreads();
     unsigned long long all_s[2] = {0ull, 0ull};
     for (int s = 0; s < ns; ++s) {
-        for (int r = 0; r < kFieldCluster; ++r) {
-            const unsigned long long *xs = cl.map_shared_rank(x_seg, r);
-            const unsigned long long *xt = cl.map_shared_rank(x_tot, r);
-            if (r < rank) run_s[s] += xs[s];
-            all_s[s] += xt[s];
-        }
+        run_s[s] += s_off[s];
+        all_s[s] = s_all[s];
         for (int i = lo; i < hi; ++i) {
             if (i >= 1 && i <= N - 1) run_s[s] += Ps[s * per_cta + (i - c_lo)];
             Ps[s * per_cta + (i - c_lo)] = run_s[s];                    // P_s[i], P_s[0] = 0
@@ -197,12 +209,20 @@ __global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldTh
     double runT = block_exclusive_f64(segS, red, &ctaS);
     if (tid == 0) x_S = ctaS;
     cl.sync();
-    double totS = 0.0;
-    for (int r = 0; r < kFieldCluster; ++r) {
-        const double v = *cl.map_shared_rank(&x_S, r);
-        if (r < rank) runT += v;
-        totS += v;
+    if (tid < 32) {                                                      // ranks' S totals, fixed order
+        double v = tid < kFieldCluster ? *cl.map_shared_rank(&x_S, tid) : 0.0;
+        double below = 0.0, all = 0.0;
+        for (int r = 0; r < kFieldCluster; ++r) {
+            const double y = __shfl_sync(0xffffffffu, v, r);
+            if (r < rank) below += y;
+            all += y;
+        }
+        if (tid == 0) { s_bcast[0] = below; s_bcast[1] = all; }
     }
+    __syncthreads();
+    runT += s_bcast[0];
+    const double totS = s_bcast[1];
+    __syncthreads();
     for (int i = lo; i < hi; ++i) {
         const double S = T[i - c_lo];
         T[i - c_lo] = runT;                                              // T_i
@@ -231,9 +251,14 @@ __global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldTh
         (void)block_exclusive_f64(segT, red, &ctaT);
         if (tid == 0) x_phi = ctaT;
         cl.sync();
-        double totT = 0.0;
-        for (int r = 0; r < kFieldCluster; ++r) totT += *cl.map_shared_rank(&x_phi, r);
-        const double pm = totT / N;
+        if (tid < 32) {
+            double v = tid < kFieldCluster ? *cl.map_shared_rank(&x_phi, tid) : 0.0;
+            double all = 0.0;
+            for (int r = 0; r < kFieldCluster; ++r) all += __shfl_sync(0xffffffffu, v, r);
+            if (tid == 0) s_bcast[0] = all;
+        }
+        __syncthreads();
+        const double pm = s_bcast[0] / N;
         for (int i = lo; i < hi; ++i) phi[i - c_lo] -= pm;
     }
     cl.sync();                                                           // every phi final and visible
@@ -273,13 +298,13 @@ __global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldTh
     bad = __syncthreads_or(bad);
     if (tid == 0) { x_fe = fe; x_bad = bad; }
     cl.sync();
-    if (rank == 0 && tid == 0) {
+    if (rank == 0 && tid < 32) {
+        const double v = tid < kFieldCluster ? *cl.map_shared_rank(&x_fe, tid) : 0.0;
+        const int bv = tid < kFieldCluster ? *cl.map_shared_rank(&x_bad, tid) : 0;
         double fe_all = 0.0;
-        int bad_all = 0;
-        for (int r = 0; r < kFieldCluster; ++r) {
-            fe_all += *cl.map_shared_rank(&x_fe, r);
-            bad_all |= *cl.map_shared_rank(&x_bad, r);
-        }
+        for (int r = 0; r < kFieldCluster; ++r) fe_all += __shfl_sync(0xffffffffu, v, r);
+        const int bad_all = __any_sync(0xffffffffu, bv != 0);
+        if (tid == 0) {
         if (bad_all) atomicOr(&ctrl->err, kErrNumeric);
         if (mode == 1) {
             P.fe_hist[ctrl->fe_n % (unsigned long long)P.fe_cap] = fe_all * P.fe_c;
@@ -293,6 +318,7 @@ __global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldTh
                 ctrl->n_active[s] = nt;
             }
             ctrl->step = step + 1;
+        }
         }
     }
     cl.sync();                                                           // no CTA leaves while read remotely
