@@ -35,10 +35,10 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ppc", type=int, default=2500, help="particles per cell per species")
-    ap.add_argument("--sort-interval", type=int, default=16)
+    ap.add_argument("--sort-interval", type=int, default=0, help="0 = the library's autotuner")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -209,6 +209,7 @@ def main():
     barrier()
     prof = case.profile_read()
     case.profile(False)
+    sort_k = case.moments()["sort_interval"]
     n2 = sum(case.count())
     clk = clocks.stop()
     ms_t = torch.tensor([ms], device="cuda")
@@ -264,7 +265,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(args.ppc), "n_cells": 2048, "particles": n_particles,
-                       "particles_per_rank": n_particles, "dt_s": cfg["dt"], "sort_interval": args.sort_interval,
+                       "particles_per_rank": n_particles, "dt_s": cfg["dt"], "sort_interval": sort_k,
+                       "sort_interval_source": "autotuner" if args.sort_interval == 0 else "fixed",
                        "field": "f64 Poisson + field", "l2": "inputs larger than L2 (particle state "
                        f"{24 * n_particles / 1e6:.0f} MB)", "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

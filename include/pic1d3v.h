@@ -77,7 +77,8 @@ typedef struct {
     double charge_C[2], mass_kg[2], weight_per_m2[2];
     int64_t capacity[2];          /* particle slots per species; 0 = 2x the first load (min 65536) */
     uint64_t seed;                /* Philox key */
-    int32_t sort_interval;        /* steps between counting sorts by cell (which also compact); 0 = 16 */
+    int32_t sort_interval;        /* steps between counting sorts by cell (which also compact); 0 = chosen by
+                                     the library's autotuner from timed steps (see pic_step) */
     int32_t diag_interval;        /* energy moments / EEPF every diag_interval steps; 0 = never */
     int32_t rewind;               /* 1: velocities given to pic_load_particles are at t = 0 and are
                                      pushed back by dt/2 before the first step (leapfrog start) */
@@ -120,7 +121,13 @@ pic_status pic_load_particles(pic_case *c, int species, int64_t n, const int32_t
                               const float *vz, const uint32_t *id, int on_device);
 
 /* Enqueue n_steps time steps (paper §1 scheme; step order in the design
- * notes) on the case stream.  Returns after enqueueing.  Errors:
+ * notes) on the case stream.  Returns after enqueueing; steps are replayed
+ * from a CUDA graph of up to 16 steps when no sort falls inside it.  With
+ * desc.sort_interval = 0, the first call that has 32 steps to run after the
+ * first step times one sort and 32 steps (this call then synchronises once)
+ * and picks the sort interval K minimising (sort time)/K + mean step time;
+ * the choice is kept per case shape for the process and, if the environment
+ * variable PIC1D3V_TUNE_CACHE names a file, in that file.  Errors:
  * PIC_ESTATE (no particles loaded), PIC_ECUDA (launch failure). */
 pic_status pic_step(pic_case *c, int64_t n_steps);
 
@@ -168,6 +175,8 @@ typedef struct {
     int64_t field_energy_cap;      /* in */
     int64_t field_energy_n;        /* out: entries written */
     int32_t reset;                 /* in: nonzero = clear the sums after reading */
+    int32_t sort_interval;         /* out: steps between sorts in use (chosen by the autotuner when
+                                      desc.sort_interval = 0) */
 } pic_moments;
 
 pic_status pic_read_moments(pic_case *c, pic_moments *out);

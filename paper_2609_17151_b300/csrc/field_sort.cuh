@@ -36,292 +36,321 @@ __device__ void block_scan_inclusive(double *a, int M, double *warp_tot)
     __syncthreads();
 }
 
-// Sum of v over the CTA (fixed order), result broadcast to every thread.
-__device__ double block_sum(double v, double *red)
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 shfl_up_u128(u128 v, int o)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += red[w];
-    __syncthreads();
-    return t;
+    const unsigned long long lo = __shfl_up_sync(0xffffffffu, (unsigned long long)v, o);
+    const unsigned long long hi = __shfl_up_sync(0xffffffffu, (unsigned long long)(v >> 64), o);
+    return ((u128)hi << 64) | lo;
+}
+__device__ __forceinline__ u128 shfl_u128(u128 v, int src)
+{
+    const unsigned long long lo = __shfl_sync(0xffffffffu, (unsigned long long)v, src);
+    const unsigned long long hi = __shfl_sync(0xffffffffu, (unsigned long long)(v >> 64), src);
+    return ((u128)hi << 64) | lo;
+}
+__device__ __forceinline__ double u128_to_double(u128 v)
+{
+    return fma((double)(unsigned long long)(v >> 64), 18446744073709551616.0, (double)(unsigned long long)v);
+}
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) & 0x7FF0000000000000ull) != 0x7FF0000000000000ull;
 }
 
-// Exclusive prefix of one 64-bit integer per thread over the CTA (exact).
-__device__ unsigned long long block_exclusive_u64(unsigned long long v, unsigned long long *red,
-                                                  unsigned long long *total)
+// Exclusive prefix over the CTA of NV integer values per thread (all summed
+// together in one pass), exact.  Warp totals are scanned by warp 0.
+template <typename T, int NV>
+__device__ void block_exclusive_vec(const T (&v)[NV], T (&excl)[NV], T (&total)[NV], T (*red)[NV])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned long long incl = v;
+    T incl[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) incl[j] = v[j];
     for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            T y;
+            if constexpr (sizeof(T) == 16) y = shfl_up_u128(incl[j], o);
+            else y = __shfl_up_sync(0xffffffffu, incl[j], o);
+            if (lane >= o) incl[j] += y;
+        }
     }
     __syncthreads();
-    if (lane == 31) red[warp] = incl;
+    if (lane == 31)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) red[warp][j] = incl[j];
     __syncthreads();
-    unsigned long long off = 0, tot = 0;
-    for (int w = 0; w < nw; ++w) {
-        if (w < warp) off += red[w];
-        tot += red[w];
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            T w = lane < nw ? red[lane][j] : T(0);
+            for (int o = 1; o < 32; o <<= 1) {
+                T y;
+                if constexpr (sizeof(T) == 16) y = shfl_up_u128(w, o);
+                else y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < nw) red[lane][j] = w;                        // inclusive over warps
+        }
     }
-    *total = tot;
-    return off + incl - v;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        excl[j] = (warp > 0 ? red[warp - 1][j] : T(0)) + incl[j] - v[j];
+        total[j] = red[nw - 1][j];
+    }
+    __syncthreads();
 }
 
-// Exclusive prefix of one FP64 value per thread over the CTA (fixed order).
-__device__ double block_exclusive_f64(double v, double *red, double *total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double incl = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    __syncthreads();
-    if (lane == 31) red[warp] = incl;
-    __syncthreads();
-    double off = 0.0, tot = 0.0;
-    for (int w = 0; w < nw; ++w) {
-        if (w < warp) off += red[w];
-        tot += red[w];
-    }
-    *total = tot;
-    return off + (incl - v);
-}
-
-// Poisson's equation (paper §1) and the node field, FP64, on a cluster of
-// kFieldCluster CTAs (one SM each) that exchange partial sums through
-// distributed shared memory.
+// Poisson's equation (paper §1) and the node field, on a cluster of
+// kFieldCluster CTAs (one SM each), each owning a contiguous slice of nodes,
+// one node per thread.
 // (phi_{i-1} - 2 phi_i + phi_{i+1}) / dx^2 = -rho_i / eps0 on the interior
 // nodes; bounded: phi_0 = V(t), phi_N = 0; periodic: neutralised rho, phi_0 = 0
 // on the N-1 interior equations (the one at node 0 then holds), mean of phi
-// removed.  With r_k = rho_k dx^2/eps0, S_m = sum_{k=1..m} r_k and
-// T_i = sum_{m<i} S_m, the difference equation integrates exactly to
-//   phi_i = phi_0 + i d_0 - T_i,   d_0 = (T_N - phi_0) / N.
-// The charge enters as exact integer prefix sums of the fixed-point deposits,
-// P_s[m] = sum_{k=1..m} R_s[k], so S_m = sum_s c_s P_s[m] + b m with
-// c_s = (dx/eps0) q_s w_s 2^-32 and b the uniform part; only the second sum
-// and the per-node potential, field and energy use FP64.  B300's FP64 rate is
-// low, so the nodes are split over the cluster's SMs and no division is done
-// per node.  Partial sums are combined in rank order (bit-identical runs).
-// E: central differences inside; Gauss's law over the half cell at an
-// electrode; wrap-around when periodic.
+// removed.  With the fixed-point deposits R_s, their exact prefix sums
+//   P_s[m] = sum_{k=1..m} R_s[k]   (u64),   Q_s[i] = sum_{m<i} P_s[m]   (u128),
+// c_s = (dx/eps0) q_s w_s 2^-32 and b the uniform part of the source, the
+// difference equation integrates exactly to
+//   S_m = sum_s c_s P_s[m] + b m,   d_m = phi_{m+1} - phi_m = d_0 - S_m,
+//   phi_i = phi_0 + i d_0 - T_i,    T_i = sum_s c_s Q_s[i] + b i(i-1)/2,
+//   d_0 = (T_N - phi_0) / N,
+// and the central-difference field is E_i = (S_i + S_{i-1} - 2 d_0) / (2dx)
+// (Gauss's law over the half cell at an electrode: E_0 = -d_0/dx - rho_0
+// dx/(2 eps0), E_N = -d_{N-1}/dx + rho_N dx/(2 eps0); periodic wrap uses
+// S_{N-1}).  Everything up to the per-node values is integer, so the FP64
+// work (slow on B300: 64-cycle latency, 2 lanes per clock per SM) is about
+// twenty operations per node plus the global terms, done by one lane.  The
+// cluster synchronises once: each CTA publishes integer moments of its slice
+// (charge, sum of its local prefixes, sum of their running sums) and every
+// CTA derives its offsets and the global terms from them in rank order.  The
+// field-energy diagnostic is reduced in FP32.  V(t) advances by an exact
+// rotation of each harmonic's (cos, sin) by 2 pi f dt per step.
 // mode 0: field of the loaded state at t = 0; mode 1: end of a step
 // (t = (step+1) dt, moments accumulated, counters advanced).
+struct FieldPart {
+    unsigned long long seg[2], all[2];  // interior / all-node raw charge of the slice
+    u128 qp[2];                         // sum over slice m < N of the local prefix p_s[m]
+    u128 qq[2];                         // sum over slice i < N of e_s[i] = sum_{c_lo <= m < i} p_s[m]
+};
+
 __global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldThreads)
     k_field(const __grid_constant__ StepConst P, int mode, unsigned long long *R_last)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
-    extern __shared__ __align__(16) double fsm[];
-    __shared__ unsigned long long ured[kFieldThreads / 32];
-    __shared__ double red[kFieldThreads / 32];
-    __shared__ unsigned long long x_seg[2], x_tot[2];   // published CTA totals (integer charge)
-    __shared__ double x_S, x_phi, x_fe, s_bcast[2];
-    __shared__ unsigned long long s_off[2], s_all[2];
-    __shared__ int x_bad;
+    extern __shared__ __align__(16) double Ssh[];                    // [kFieldThreads + 1]: S at node c_lo - 1 + t
+    __shared__ unsigned long long ured[kFieldThreads / 32][4];
+    __shared__ u128 wred[kFieldThreads / 32][2];
+    __shared__ float fred[kFieldThreads / 32];
+    __shared__ FieldPart pub;                                       // this CTA's published moments
+    __shared__ unsigned long long g_off[2], g_seg[2];               // slice prefix offset O_s, total interior charge
+    __shared__ u128 g_qoff[2];                                      // Q_s[c_lo]
+    __shared__ double g_b, g_d0, g_pm, g_phi0;
     const int rank = (int)cl.block_rank();
     const int N = P.n_cells, nn = P.n_nodes, tid = threadIdx.x, ns = P.n_species;
-    const int per_cta = (N + 1 + kFieldCluster - 1) / kFieldCluster;
+    const int per_cta = (N + 1 + kFieldCluster - 1) / kFieldCluster;   // <= kFieldThreads (n_cells <= 4096)
     const int c_lo = min(rank * per_cta, N + 1), c_hi = min(c_lo + per_cta, N + 1);
-    const int per = (c_hi - c_lo + blockDim.x - 1) / blockDim.x;
-    const int lo = min(c_lo + tid * per, c_hi), hi = min(lo + per, c_hi);
-    double *phi = fsm;                                                   // [per_cta], local index i - c_lo
-    double *T = fsm + per_cta;                                           // [per_cta]
-    unsigned long long *Ps = reinterpret_cast<unsigned long long *>(fsm + 2 * per_cta);   // [2][per_cta]
+    const int i = c_lo + tid;                                       // this thread's node
+    const bool own = i < c_hi;
     Ctrl *ctrl = P.ctrl;
     const long long step = ctrl->step;
+    const unsigned long long fe_n = ctrl->fe_n;
     const bool diag = mode == 1 && P.diag_interval > 0 && ((step + 1) % P.diag_interval) == 0;
 
-    // 1. raw deposits (periodic: node N folds onto node 0), integer moment sums
-    unsigned long long tot_s[2] = {0ull, 0ull}, seg_s[2] = {0ull, 0ull};
-    for (int s = 0; s < ns; ++s)
-        for (int i = lo; i < hi; ++i) {
-            unsigned long long r = 0ull;
-            if (i < nn) {
-                r = P.R[s][i];
-                if (P.periodic && i == 0) r += P.R[s][N];
-                R_last[s * nn + i] = r;
-                if (mode == 1) {
-                    P.Rsum[s * nn + i] += r;
-                    if (diag) P.Rdiag[s * nn + i] += r;
-                }
-                tot_s[s] += r;
-            }
-            Ps[s * per_cta + (i - c_lo)] = r;
-            if (i >= 1 && i <= N - 1) seg_s[s] += r;
-        }
-    unsigned long long run_s[2] = {0ull, 0ull};
-    for (int s = 0; s < ns; ++s) {
-        unsigned long long t1, t2;
-        run_s[s] = block_exclusive_u64(seg_s[s], ured, &t1);
-        (void)block_exclusive_u64(tot_s[s], ured, &t2);
-        if (tid == 0) { x_seg[s] = t1; x_tot[s] = t2; }
-    }
-    cl.sync();                                                           // totals published; R fully read
-    // warp 0: lane r reads rank r's totals (parallel remote reads), combines them
-    if (tid < 32) {
-        const int lane = tid;
+    // 1. raw deposit of the node (periodic: node N folds onto node 0); all loads issued first
+    unsigned long long r[2] = {0ull, 0ull}, rs[2] = {0ull, 0ull}, rd[2] = {0ull, 0ull};
+    const bool real = own && i < nn;
+    if (real) {
         for (int s = 0; s < ns; ++s) {
-            const unsigned long long vs = lane < kFieldCluster ? cl.map_shared_rank(x_seg, lane)[s] : 0ull;
-            const unsigned long long vt = lane < kFieldCluster ? cl.map_shared_rank(x_tot, lane)[s] : 0ull;
-            unsigned long long below = lane < rank ? vs : 0ull, all = vt;
-            for (int o = 16; o > 0; o >>= 1) {
-                below += __shfl_xor_sync(0xffffffffu, below, o);
-                all += __shfl_xor_sync(0xffffffffu, all, o);
+            r[s] = P.R[s][i];
+            if (P.periodic && i == 0) r[s] += P.R[s][N];
+            if (mode == 1) {
+                rs[s] = P.Rsum[s * nn + i];
+                if (diag) rd[s] = P.Rdiag[s * nn + i];
             }
-            if (lane == 0) { s_off[s] = below; s_all[s] = all; }
+        }
+        for (int s = 0; s < ns; ++s) {
+            R_last[s * nn + i] = r[s];
+            if (mode == 1) {
+                P.Rsum[s * nn + i] = rs[s] + r[s];
+                if (diag) P.Rdiag[s * nn + i] = rd[s] + r[s];
+            }
         }
     }
-    __syncthreads();
-    unsigned long long all_s[2] = {0ull, 0ull};
-    for (int s = 0; s < ns; ++s) {
-        run_s[s] += s_off[s];
-        all_s[s] = s_all[s];
-        for (int i = lo; i < hi; ++i) {
-            if (i >= 1 && i <= N - 1) run_s[s] += Ps[s * per_cta + (i - c_lo)];
-            Ps[s * per_cta + (i - c_lo)] = run_s[s];                    // P_s[i], P_s[0] = 0
-        }
-        for (int i = lo; i < hi; ++i) P.R[s][i] = 0ull;
+    const bool interior = own && i >= 1 && i <= N - 1;
+    // 2. local prefix p_s[i] (interior R from c_lo), its running sum e_s[i], slice moments
+    unsigned long long pv[2], ptot[4];
+    {
+        const unsigned long long v4[4] = {interior ? r[0] : 0ull, interior ? r[1] : 0ull, real ? r[0] : 0ull,
+                                          real ? r[1] : 0ull};
+        unsigned long long ex4[4];
+        block_exclusive_vec<unsigned long long, 4>(v4, ex4, ptot, ured);
+        pv[0] = ex4[0] + v4[0];                                    // p_s[i] (inclusive)
+        pv[1] = ex4[1] + v4[1];
     }
-    // 2. S_m = sum_s c_s P_s[m] + b m;  T_i = sum_{m<i} S_m
-    double b = P.bg_r;
-    if (P.periodic) {
-        double q = 0.0;
-        for (int s = 0; s < ns; ++s) q += P.cq[s] * (double)(long long)all_s[s];
-        b = -q / N;                                                      // neutralising part (bg cancels)
-    }
-    double segS = 0.0;
-    for (int i = lo; i < hi; ++i) {
-        double S = 0.0;
-        if (i < N) {
-            S = b * (double)i;
-            for (int s = 0; s < ns; ++s) S = fma(P.cq[s], (double)(long long)Ps[s * per_cta + (i - c_lo)], S);
-        }
-        T[i - c_lo] = S;
-        segS += S;
-    }
-    double ctaS;
-    double runT = block_exclusive_f64(segS, red, &ctaS);
-    if (tid == 0) x_S = ctaS;
-    cl.sync();
-    if (tid < 32) {                                                      // ranks' S totals, fixed order
-        double v = tid < kFieldCluster ? *cl.map_shared_rank(&x_S, tid) : 0.0;
-        double below = 0.0, all = 0.0;
-        for (int r = 0; r < kFieldCluster; ++r) {
-            const double y = __shfl_sync(0xffffffffu, v, r);
-            if (r < rank) below += y;
-            all += y;
-        }
-        if (tid == 0) { s_bcast[0] = below; s_bcast[1] = all; }
-    }
-    __syncthreads();
-    runT += s_bcast[0];
-    const double totS = s_bcast[1];
-    __syncthreads();
-    for (int i = lo; i < hi; ++i) {
-        const double S = T[i - c_lo];
-        T[i - c_lo] = runT;                                              // T_i
-        runT += S;
+    u128 e[2], qp_tot[2], qq_tot[2];
+    {
+        const u128 v2[2] = {own && i < N ? (u128)pv[0] : (u128)0, own && i < N ? (u128)pv[1] : (u128)0};
+        block_exclusive_vec<u128, 2>(v2, e, qp_tot, wred);          // e_s[i] = sum_{c_lo <= m < i} p_s[m]
+        const u128 w2[2] = {own && i < N ? e[0] : (u128)0, own && i < N ? e[1] : (u128)0};
+        u128 dummy[2];
+        block_exclusive_vec<u128, 2>(w2, dummy, qq_tot, wred);
     }
     if (tid == 0) {
-        double phi0 = 0.0;
-        if (!P.periodic) {
-            const double t = mode == 0 ? 0.0 : (double)(step + 1) * P.dt;
-            for (int h = 0; h < P.n_harm; ++h) phi0 += P.harm_a[h] * cos(2.0 * M_PI * P.harm_f[h] * t + P.harm_p[h]);
+        for (int s = 0; s < 2; ++s) {
+            const bool sp = s < ns;
+            pub.seg[s] = sp ? ptot[s] : 0ull;
+            pub.all[s] = sp ? ptot[2 + s] : 0ull;
+            pub.qp[s] = sp ? qp_tot[s] : (u128)0;
+            pub.qq[s] = sp ? qq_tot[s] : (u128)0;
         }
-        s_bcast[0] = phi0;
-        s_bcast[1] = (totS - phi0) / N;                                  // d_0 (T_N = sum of all S)
+    }
+    cl.sync();                                                      // the one exchange
+    // 3. warp 0: lane r takes rank r's moments; integer offsets; lane 0 the FP64 globals
+    if (tid < 32) {
+        const int lane = tid;
+        FieldPart q{};
+        if (lane < kFieldCluster) q = *cl.map_shared_rank(&pub, lane);
+        const int r_lo = min(lane * per_cta, N + 1), r_hi = min(r_lo + per_cta, N + 1);
+        const long long cnt = (lane < kFieldCluster && min(r_hi, N) > r_lo) ? min(r_hi, N) - r_lo : 0;
+        const u128 k1 = (u128)(cnt * (cnt - 1) / 2);                 // sum over slice i<N of (i - c_lo)
+        unsigned long long off[2], segtot[2], alltot[2];
+        u128 qoff[2], qn[2], sq[2];
+        for (int s = 0; s < 2; ++s) {
+            unsigned long long inc = q.seg[s], at = q.all[s];
+            const u128 A0 = q.qp[s];
+            for (int o = 1; o < kFieldCluster; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+                at += __shfl_xor_sync(0xffffffffu, at, o);
+            }
+            off[s] = inc - q.seg[s];
+            segtot[s] = __shfl_sync(0xffffffffu, inc, kFieldCluster - 1);
+            alltot[s] = __shfl_sync(0xffffffffu, at, 0);
+            const u128 A = (u128)cnt * off[s] + A0;                 // sum of P_s[m] over the slice's m < N
+            u128 ainc = A;
+            for (int o = 1; o < kFieldCluster; o <<= 1) {
+                const u128 y = shfl_up_u128(ainc, o);
+                if (lane >= o) ainc += y;
+            }
+            qoff[s] = ainc - A;                                     // Q_s[r_lo]
+            qn[s] = shfl_u128(ainc, kFieldCluster - 1);             // Q_s[N]
+            u128 B = (u128)cnt * qoff[s] + k1 * off[s] + q.qq[s];   // sum of Q_s[i] over the slice's i < N
+            for (int o = 1; o < kFieldCluster; o <<= 1) {
+                const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, (unsigned long long)B, o);
+                const unsigned long long hi2 = __shfl_xor_sync(0xffffffffu, (unsigned long long)(B >> 64), o);
+                B += ((u128)hi2 << 64) | lo2;
+            }
+            sq[s] = shfl_u128(B, 0);                                // sum_{i<N} Q_s[i]
+        }
+        const unsigned long long my_off0 = __shfl_sync(0xffffffffu, off[0], rank);
+        const unsigned long long my_off1 = __shfl_sync(0xffffffffu, off[1], rank);
+        const u128 my_q0 = shfl_u128(qoff[0], rank), my_q1 = shfl_u128(qoff[1], rank);
+        if (lane == 0) {
+            double phi0 = 0.0;                                      // electrode voltage at this solve's time
+            if (!P.periodic) {
+                if (mode == 0) phi0 = P.v_init;
+                else for (int h = 0; h < P.n_harm; ++h) phi0 = fma(P.harm_a[h], ctrl->drive_c[h], phi0);
+            }
+            double b = P.bg_r;
+            if (P.periodic) b = -(P.cq[0] * (double)(long long)alltot[0] + P.cq[1] * (double)(long long)alltot[1]) * P.inv_n;
+            const double Nd = (double)N;
+            const double TN = fma(P.cq[0], u128_to_double(qn[0]), fma(P.cq[1], u128_to_double(qn[1]), b * (0.5 * Nd * (Nd - 1.0))));
+            const double d0 = (TN - phi0) * P.inv_n;
+            double pm = 0.0;
+            if (P.periodic) {                                       // mean of phi_0 + i d_0 - T_i over i < N
+                const double sumT = fma(P.cq[0], u128_to_double(sq[0]),
+                                        fma(P.cq[1], u128_to_double(sq[1]), b * (Nd * (Nd - 1.0) * (Nd - 2.0) / 6.0)));
+                pm = (fma(d0, 0.5 * Nd * (Nd - 1.0), phi0 * Nd) - sumT) * P.inv_n;
+            }
+            g_off[0] = my_off0; g_off[1] = my_off1;
+            g_qoff[0] = my_q0; g_qoff[1] = my_q1;
+            g_seg[0] = segtot[0]; g_seg[1] = segtot[1];
+            g_b = b; g_d0 = d0; g_pm = pm; g_phi0 = phi0;
+        }
+    }
+    cl.barrier_arrive();                                          // done reading the other slices
+    __syncthreads();
+    if (real)
+        for (int s = 0; s < ns; ++s) P.R[s][i] = 0ull;             // every rank has read R
+    if (own && i == N)
+        for (int s = 0; s < ns; ++s) P.R[s][N] = 0ull;
+    const double b = g_b, d0 = g_d0, pm = g_pm, phi0 = g_phi0;
+    const double cq0 = P.cq[0], cq1 = ns > 1 ? P.cq[1] : 0.0;
+    // 4. S_i once per node (P_s[i] = O_s + p_s[i]); slot 0 holds S_{c_lo - 1} (P = O_s)
+    if (own) {
+        const double S = (i < N) ? fma(cq0, (double)(long long)(g_off[0] + pv[0]),
+                                       fma(cq1, (double)(long long)(g_off[1] + pv[1]), b * (double)i))
+                                 : 0.0;
+        Ssh[tid + 1] = S;
+    }
+    if (tid == 0) {
+        const int j = c_lo - 1;
+        double S = 0.0;
+        if (j >= 0) S = fma(cq0, (double)(long long)g_off[0], fma(cq1, (double)(long long)g_off[1], b * (double)j));
+        else if (P.periodic)                                        // left of node 0 is node N-1
+            S = fma(cq0, (double)(long long)g_seg[0], fma(cq1, (double)(long long)g_seg[1], b * (double)(N - 1)));
+        Ssh[0] = S;
     }
     __syncthreads();
-    const double phi0 = s_bcast[0], d0 = s_bcast[1];
-    double segT = 0.0;
-    for (int i = lo; i < hi; ++i) {
-        double v = fma((double)i, d0, phi0) - T[i - c_lo];
-        if (!P.periodic && i == N) v = 0.0;
-        phi[i - c_lo] = v;
-        if (i < N) segT += v;
-    }
-    if (P.periodic) {
-        double ctaT;
-        (void)block_exclusive_f64(segT, red, &ctaT);
-        if (tid == 0) x_phi = ctaT;
-        cl.sync();
-        if (tid < 32) {
-            double v = tid < kFieldCluster ? *cl.map_shared_rank(&x_phi, tid) : 0.0;
-            double all = 0.0;
-            for (int r = 0; r < kFieldCluster; ++r) all += __shfl_sync(0xffffffffu, v, r);
-            if (tid == 0) s_bcast[0] = all;
-        }
-        __syncthreads();
-        const double pm = s_bcast[0] / N;
-        for (int i = lo; i < hi; ++i) phi[i - c_lo] -= pm;
-    }
-    cl.sync();                                                           // every phi final and visible
-    // 3. node field (neighbours of the slice ends come from the owning CTA)
-    auto phi_at = [&](int j) -> double {
-        const int owner = j / per_cta;
-        if (owner == rank) return phi[j - c_lo];
-        return cl.map_shared_rank(phi, owner)[j - owner * per_cta];
-    };
-    double fe = 0.0;
-    int bad = 0;
-    for (int i = lo; i < hi && i < nn; ++i) {
+    // 5. node field, potential, FP32 copy for the gather, field energy (FP32), potential sum
+    float fe = 0.0f;
+    bool bad = false;
+    if (real) {
         double E;
-        const double ph = phi[i - c_lo];
-        if (P.periodic) {
-            const int ip = i + 1 == N ? 0 : i + 1, im = i == 0 ? N - 1 : i - 1;
-            E = (phi_at(im) - phi_at(ip)) * P.inv_2dx;
-            fe = fma(E, E, fe);
-        } else if (i == 0 || i == N) {
-            double rq = P.bg_charge;                                     // charge density of the wall node
-            for (int s = 0; s < ns; ++s) rq = fma(P.rho_wall[s], (double)(long long)R_last[s * nn + i], rq);
-            E = i == 0 ? (ph - phi_at(1)) * P.inv_dx - rq * P.half_dx_eps0
-                       : (phi_at(N - 1) - ph) * P.inv_dx + rq * P.half_dx_eps0;
-            fe = fma(0.5 * E, E, fe);
+        if (!P.periodic && (i == 0 || i == N)) {
+            double rq = P.bg_charge;                                // charge density of the wall node
+            for (int s = 0; s < ns; ++s) rq = fma(P.rho_wall[s], (double)(long long)r[s], rq);
+            E = i == 0 ? -d0 * P.inv_dx - rq * P.half_dx_eps0 : (Ssh[tid] - d0) * P.inv_dx + rq * P.half_dx_eps0;
+            fe = 0.5f * (float)E * (float)E;
         } else {
-            E = (phi_at(i - 1) - phi_at(i + 1)) * P.inv_2dx;
-            fe = fma(E, E, fe);
+            E = (Ssh[tid + 1] + Ssh[tid] - 2.0 * d0) * P.inv_2dx;
+            fe = (float)E * (float)E;
         }
+        // Q_s[i] = Q_s[c_lo] + (i - c_lo) O_s + e_s[i]
+        const unsigned long long k = (unsigned long long)tid;
+        double T = b * (0.5 * (double)i * (double)(i - 1));
+        T = fma(cq0, u128_to_double(g_qoff[0] + (u128)k * g_off[0] + e[0]), T);
+        if (ns > 1) T = fma(cq1, u128_to_double(g_qoff[1] + (u128)k * g_off[1] + e[1]), T);
+        double ph = fma((double)i, d0, phi0) - T - pm;
+        if (!P.periodic && i == N) ph = 0.0;
         P.E[i] = E;
         P.phi[i] = ph;
         P.E32[i] = (float)E;
         if (P.periodic && i == 0) P.E32[N] = (float)E;
         if (mode == 1) P.phi_sum[i] += ph;
-        bad |= !isfinite(ph) || !isfinite(E);
+        bad = !finite_bits(ph) || !finite_bits(E);
     }
-    fe = block_sum(fe, red);
-    bad = __syncthreads_or(bad);
-    if (tid == 0) { x_fe = fe; x_bad = bad; }
-    cl.sync();
-    if (rank == 0 && tid < 32) {
-        const double v = tid < kFieldCluster ? *cl.map_shared_rank(&x_fe, tid) : 0.0;
-        const int bv = tid < kFieldCluster ? *cl.map_shared_rank(&x_bad, tid) : 0;
-        double fe_all = 0.0;
-        for (int r = 0; r < kFieldCluster; ++r) fe_all += __shfl_sync(0xffffffffu, v, r);
-        const int bad_all = __any_sync(0xffffffffu, bv != 0);
-        if (tid == 0) {
-        if (bad_all) atomicOr(&ctrl->err, kErrNumeric);
-        if (mode == 1) {
-            P.fe_hist[ctrl->fe_n % (unsigned long long)P.fe_cap] = fe_all * P.fe_c;
-            ctrl->fe_n += 1;
-            ctrl->n_steps_acc += 1;
-            if (diag) ctrl->n_diag_acc += 1;
-            for (int s = 0; s < ns; ++s) {
-                unsigned long long nt = ctrl->n_total[s];
-                if (nt > P.cap[s]) nt = P.cap[s];
-                ctrl->n_total[s] = nt;
-                ctrl->n_active[s] = nt;
-            }
-            ctrl->step = step + 1;
-        }
-        }
+    for (int o = 16; o > 0; o >>= 1) fe += __shfl_xor_sync(0xffffffffu, fe, o);
+    if ((tid & 31) == 0) fred[tid >> 5] = fe;
+    const bool any_bad = __syncthreads_or(bad);
+    if (tid == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += fred[w];
+        if (any_bad) atomicOr(&ctrl->err, kErrNumeric);
+        if (mode == 1) P.fe_hist[(fe_n % (unsigned long long)P.fe_cap) * kFieldCluster + rank] = (double)t * P.fe_c;
     }
-    cl.sync();                                                           // no CTA leaves while read remotely
+    if (rank == 0 && tid == 0 && mode == 1) {
+        ctrl->fe_n = fe_n + 1;
+        ctrl->n_steps_acc += 1;
+        if (diag) ctrl->n_diag_acc += 1;
+        for (int s = 0; s < ns; ++s) {
+            unsigned long long nt = ctrl->n_total[s];
+            if (nt > P.cap[s]) nt = P.cap[s];
+            ctrl->n_total[s] = nt;
+            ctrl->n_active[s] = nt;
+        }
+        for (int h = 0; h < P.n_harm; ++h) {                      // advance each harmonic's phase by 2 pi f dt
+            const double c = ctrl->drive_c[h], sn = ctrl->drive_s[h];
+            ctrl->drive_c[h] = c * P.rot_c[h] - sn * P.rot_s[h];
+            ctrl->drive_s[h] = sn * P.rot_c[h] + c * P.rot_s[h];
+        }
+        ctrl->step = step + 1;
+    }
+    cl.barrier_wait();                                            // no CTA leaves while read remotely
 }
 
 // ---------------------------------------------------------------------------

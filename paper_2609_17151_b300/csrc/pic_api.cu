@@ -6,6 +6,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -56,6 +59,13 @@ struct pic_case {
     bool loaded[2] = {false, false};
     bool need_init = true;
     long long host_step = 0;
+    // sort interval: fixed by the descriptor, or chosen by the autotuner
+    bool autotune = false, tuned = false;
+    int sort_k = 16;
+    long long steps_since_sort = 0;
+    // CUDA graph of kGraphSteps steps (no sort), replayed by pic_step
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
     int step_grid[2] = {0, 0};
     unsigned step_smem[2] = {0, 0};
     unsigned field_smem = 0;
@@ -340,6 +350,163 @@ pic_status reset_moments(pic_case *c)
 
 } // namespace
 
+namespace {
+
+void drop_graph(pic_case *c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_steps = 0;
+}
+
+// The kernels of one step (both species, field solve), launched on the case stream.
+cudaError_t launch_one_step(pic_case *c)
+{
+    cudaError_t e = launch_step_sp<0>(c);
+    if (e == cudaSuccess && c->d.n_species > 1) e = launch_step_sp<1>(c);
+    if (e == cudaSuccess) e = launch_field(c, 1);
+    return e;
+}
+
+cudaError_t launch_sorts(pic_case *c)
+{
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < c->d.n_species && e == cudaSuccess; ++s) e = launch_sort(c, s);
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the sort interval K.  Right after a sort, the step time grows
+// as the particles lose their cell order (and, with electrodes, as absorbed
+// slots accumulate); a sort costs t_sort.  With t(k) ~ a + b k over the k-th
+// step after a sort, the mean cost per step of a period K is
+// a + b K / 2 + t_sort / K, minimised at K = sqrt(2 t_sort / b).  The tuner
+// times one sort and kTuneSteps steps with CUDA events, fits a and b by least
+// squares, and keeps K in [4, 1024] (1024 when the steps do not slow down).
+// Results are kept per case shape for the process, and in the file named by
+// PIC1D3V_TUNE_CACHE if that variable is set.
+// ---------------------------------------------------------------------------
+constexpr int kTuneSteps = 32;
+constexpr int kMaxSortInterval = 1024;
+
+std::mutex g_tune_mutex;
+std::map<std::string, int> g_tune_cache;
+bool g_tune_file_read = false;
+
+std::string tune_key(const pic_case *c)
+{
+    unsigned long long n = 0;
+    for (int s = 0; s < c->d.n_species; ++s) n += c->P.cap[s];
+    int lg = 0;
+    while ((1ull << (lg + 1)) <= n) ++lg;
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "p%d_c%d_n2^%d_m%d%d", c->d.periodic, c->d.n_cells, lg, c->P.sp[0].mcc,
+                  c->d.n_species > 1 ? c->P.sp[1].mcc : 0);
+    return buf;
+}
+
+int tune_lookup(const std::string &key)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    const char *path = std::getenv("PIC1D3V_TUNE_CACHE");
+    if (path && !g_tune_file_read) {
+        g_tune_file_read = true;
+        if (FILE *f = std::fopen(path, "r")) {
+            char k[128];
+            int v;
+            while (std::fscanf(f, "%127s %d", k, &v) == 2) g_tune_cache[k] = v;
+            std::fclose(f);
+        }
+    }
+    auto it = g_tune_cache.find(key);
+    return it == g_tune_cache.end() ? 0 : it->second;
+}
+
+void tune_store(const std::string &key, int k)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = k;
+    if (const char *path = std::getenv("PIC1D3V_TUNE_CACHE"))
+        if (FILE *f = std::fopen(path, "a")) {
+            std::fprintf(f, "%s %d\n", key.c_str(), k);
+            std::fclose(f);
+        }
+}
+
+pic_status autotune_sort_interval(pic_case *c, int64_t *left)
+{
+    const std::string key = tune_key(c);
+    if (int k = tune_lookup(key)) {
+        c->sort_k = k;
+        c->tuned = true;
+        return PIC_OK;
+    }
+    std::vector<cudaEvent_t> ev(2 * (kTuneSteps + 1));
+    for (auto &e : ev) CU(cudaEventCreate(&e));
+    CU(cudaEventRecord(ev[0], c->stream));
+    CU(launch_sorts(c));
+    CU(cudaEventRecord(ev[1], c->stream));
+    for (int k = 0; k < kTuneSteps; ++k) {
+        CU(cudaEventRecord(ev[2 + 2 * k], c->stream));
+        CU(launch_one_step(c));
+        CU(cudaEventRecord(ev[3 + 2 * k], c->stream));
+    }
+    CU(cudaStreamSynchronize(c->stream));
+    float ts = 0.f;
+    CU(cudaEventElapsedTime(&ts, ev[0], ev[1]));
+    double sx = 0, sy = 0, sxx = 0, sxy = 0;
+    for (int k = 0; k < kTuneSteps; ++k) {
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, ev[2 + 2 * k], ev[3 + 2 * k]));
+        const double x = k + 1;
+        sx += x; sy += t; sxx += x * x; sxy += x * t;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    const double n = kTuneSteps;
+    const double b = (n * sxy - sx * sy) / (n * sxx - sx * sx);
+    const double a = (sy - b * sx) / n;
+    int K = kMaxSortInterval;
+    if (b > 1e-4 * std::max(a, 1e-6)) K = (int)std::lround(std::sqrt(2.0 * ts / b));
+    K = std::max(4, std::min(kMaxSortInterval, K));
+    c->sort_k = K;
+    c->tuned = true;
+    c->host_step += kTuneSteps;
+    c->steps_since_sort = kTuneSteps;
+    *left -= kTuneSteps;
+    tune_store(key, K);
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graph of kGraphSteps steps.  Kernel arguments are captured by value,
+// so the graph is dropped whenever they change (load, tables).
+// ---------------------------------------------------------------------------
+constexpr int kGraphSteps = 16;
+
+pic_status build_graph(pic_case *c, int steps)
+{
+    drop_graph(c);
+    long long saved[pic_case::kClasses];
+    for (int k = 0; k < pic_case::kClasses; ++k) saved[k] = c->launches[k];
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < steps && e == cudaSuccess; ++i) e = launch_one_step(c);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    for (int k = 0; k < pic_case::kClasses; ++k) c->launches[k] = saved[k];
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(PIC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(PIC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    c->graph_steps = steps;
+    return PIC_OK;
+}
+
+} // namespace
+
 // Message for pic_last_error() from the other translation units of the library.
 namespace pic {
 void set_last_error(const std::string &msg) { g_err = msg; }
@@ -379,7 +546,8 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
         if (!(desc->mass_kg[s] > 0)) return fail(PIC_EINVAL, "species mass must be positive");
     pic_case *c = new pic_case();
     c->d = *desc;
-    if (c->d.sort_interval <= 0) c->d.sort_interval = 16;
+    c->autotune = c->d.sort_interval <= 0;
+    c->sort_k = c->autotune ? 16 : c->d.sort_interval;
     if (c->d.field_history <= 0) c->d.field_history = 65536;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -413,6 +581,13 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     P.inv_2dx = 0.5 / dx;
     P.half_dx_eps0 = 0.5 * dx / kEps0;
     P.fe_c = 0.5 * kEps0 * dx;
+    P.inv_n = 1.0 / N;
+    P.v_init = 0.0;
+    for (int h = 0; h < desc->n_harm; ++h) {
+        P.v_init += desc->harm_amp_v[h] * std::cos(desc->harm_phase_rad[h]);
+        P.rot_c[h] = std::cos(2.0 * M_PI * desc->harm_freq_hz[h] * desc->dt_s);
+        P.rot_s[h] = std::sin(2.0 * M_PI * desc->harm_freq_hz[h] * desc->dt_s);
+    }
     for (int s = 0; s < 2; ++s) {
         const double qw = s < desc->n_species ? desc->charge_C[s] * desc->weight_per_m2[s] / 4294967296.0 : 0.0;
         P.cq[s] = qw * dx / kEps0;
@@ -435,7 +610,7 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     P.pw_sum = (double *)c->dalloc(sizeof(double) * 2);
     P.eepf = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * kEepfBins);
     P.fe_cap = c->d.field_history;
-    P.fe_hist = (double *)c->dalloc(sizeof(double) * (size_t)P.fe_cap);
+    P.fe_hist = (double *)c->dalloc(sizeof(double) * (size_t)P.fe_cap * kFieldCluster);
     P.sort_count = (unsigned *)c->dalloc(sizeof(unsigned) * N);
     P.sort_cursor = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * (N + 1));
     if (!P.E32 || !P.E || !P.phi || !P.R[0] || !P.R[1] || !c->R_last || !P.ctrl || !P.Rsum || !P.Rdiag ||
@@ -447,7 +622,7 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), c->stream);
     cudaMemsetAsync(P.sort_count, 0, sizeof(unsigned) * N, c->stream);
     cudaMemsetAsync(c->R_last, 0, sizeof(unsigned long long) * 2 * nn, c->stream);
-    c->field_smem = (unsigned)(4 * ((N + 1 + kFieldCluster - 1) / kFieldCluster) * sizeof(double));
+    c->field_smem = (unsigned)((kFieldThreads + 1) * sizeof(double));
     if (cudaFuncSetAttribute(k_field, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->field_smem) != cudaSuccess) {
         pic_destroy(c);
         return fail(PIC_ECUDA, "field kernel shared memory attribute");
@@ -478,6 +653,7 @@ pic_status pic_load_xsec_table(pic_case *c, int species, int kind, double thr, c
         p.nu[i] = c->d.gas_density_m3 * sig * std::sqrt(2.0 * eps * kElem / mu);
     }
     c->proc[species].push_back(std::move(p));
+    drop_graph(c);
     fill_species(c, species);
     return upload_tables(c, species);
 }
@@ -527,6 +703,11 @@ pic_status pic_load_particles(pic_case *c, int sp, int64_t n, const int32_t *cel
     }
     Ctrl z;
     std::memset(&z, 0, sizeof(z));
+    for (int h = 0; h < c->d.n_harm; ++h) {                 // phases at the first step's field solve (t = dt)
+        const double ph = 2.0 * M_PI * c->d.harm_freq_hz[h] * c->d.dt_s + c->d.harm_phase_rad[h];
+        z.drive_c[h] = std::cos(ph);
+        z.drive_s[h] = std::sin(ph);
+    }
     for (int s = 0; s < 2; ++s) {
         const unsigned long long cnt = s == sp ? (unsigned long long)n : (c->loaded[s] ? h.n_total[s] : 0ull);
         z.n_total[s] = z.n_active[s] = cnt;
@@ -538,6 +719,8 @@ pic_status pic_load_particles(pic_case *c, int sp, int64_t n, const int32_t *cel
     c->loaded[sp] = true;
     c->need_init = true;
     c->host_step = 0;
+    c->steps_since_sort = 0;
+    drop_graph(c);
     return PIC_OK;
 }
 
@@ -550,13 +733,38 @@ pic_status pic_step(pic_case *c, int64_t n_steps)
         pic_status st = initialise(c);
         if (st != PIC_OK) return st;
     }
-    for (int64_t i = 0; i < n_steps; ++i) {
-        CU(launch_step_sp<0>(c));
-        if (c->d.n_species > 1) CU(launch_step_sp<1>(c));
-        CU(launch_field(c, 1));
-        c->host_step++;
-        if (c->host_step % c->d.sort_interval == 0)
-            for (int s = 0; s < c->d.n_species; ++s) CU(launch_sort(c, s));
+    int64_t left = n_steps;
+    while (left > 0) {
+        if (c->autotune && !c->tuned && c->host_step > 0 && left >= kTuneSteps) {
+            pic_status st = autotune_sort_interval(c, &left);
+            if (st != PIC_OK) return st;
+            continue;
+        }
+        const int K = c->sort_k;
+        const int G = std::min(kGraphSteps, K);
+        // replay the graph when G steps fit before the next sort (steps run
+        // directly while profiling, and for the first step after a load)
+        if (!c->prof && c->host_step > 0 && left >= G && c->steps_since_sort + G <= K) {
+            if (!c->graph || c->graph_steps != G) {
+                pic_status st = build_graph(c, G);
+                if (st != PIC_OK) return st;
+            }
+            CU(cudaGraphLaunch(c->graph, c->stream));
+            c->launches[KC_STEP] += (long long)G * c->d.n_species;
+            c->launches[KC_FIELD] += G;
+            c->host_step += G;
+            c->steps_since_sort += G;
+            left -= G;
+        } else {
+            CU(launch_one_step(c));
+            c->host_step++;
+            c->steps_since_sort++;
+            left--;
+        }
+        if (c->steps_since_sort >= K) {
+            CU(launch_sorts(c));
+            c->steps_since_sort = 0;
+        }
     }
     return PIC_OK;
 }
@@ -645,7 +853,7 @@ pic_status pic_read_moments(pic_case *c, pic_moments *m)
     if (m->en_sum) CU(cudaMemcpyAsync(m->en_sum, c->P.en_sum, ns * nn * 8, cudaMemcpyDeviceToHost, c->stream));
     std::vector<unsigned long long> ee(kEepfBins);
     CU(cudaMemcpyAsync(ee.data(), c->P.eepf, kEepfBins * 8, cudaMemcpyDeviceToHost, c->stream));
-    std::vector<double> fe((size_t)c->P.fe_cap);
+    std::vector<double> fe((size_t)c->P.fe_cap * kFieldCluster);
     CU(cudaMemcpyAsync(fe.data(), c->P.fe_hist, fe.size() * 8, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     m->n_nodes = (int32_t)nn;
@@ -669,6 +877,7 @@ pic_status pic_read_moments(pic_case *c, pic_moments *m)
             if (m->dens_sum) m->dens_sum[s * nn + i] = f * (double)rs[s * nn + i];
             if (m->dens_diag_sum) m->dens_diag_sum[s * nn + i] = f * (double)rd[s * nn + i];
         }
+    m->sort_interval = c->sort_k;
     m->see_emitted = (int64_t)h.see;
     m->ionizations = (int64_t)h.iz;
     if (m->eepf) for (int b = 0; b < kEepfBins; ++b) m->eepf[b] = (double)ee[b];
@@ -676,7 +885,10 @@ pic_status pic_read_moments(pic_case *c, pic_moments *m)
     long long want = m->field_energy ? std::min<long long>(have, m->field_energy_cap) : 0;
     for (long long i = 0; i < want; ++i) {
         const long long idx = (long long)h.fe_n - have + i;
-        m->field_energy[i] = fe[(size_t)(idx % c->P.fe_cap)];
+        const size_t e0 = (size_t)(idx % c->P.fe_cap) * kFieldCluster;
+        double v = 0.0;
+        for (int r = 0; r < kFieldCluster; ++r) v += fe[e0 + r];      // rank order
+        m->field_energy[i] = v;
     }
     m->field_energy_n = want;
     pic_status st = device_error(c);
@@ -729,6 +941,7 @@ pic_status pic_destroy(pic_case *c)
     if (!c) return PIC_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto &e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    drop_graph(c);
     while (!c->allocs.empty()) c->dfree(c->allocs.back().first);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

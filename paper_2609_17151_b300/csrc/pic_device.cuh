@@ -10,7 +10,7 @@ constexpr int kNGrid = 1000;            // cross-section grid, log-spaced on [1e
 constexpr float kGridEmin = 1e-3f;
 constexpr int kEepfBins = 240;          // 0..60 eV, 0.25 eV bins
 constexpr int kStepThreads = 512;
-constexpr int kFieldThreads = 256;
+constexpr int kFieldThreads = 576;      // >= nodes per CTA of the cluster (4097 / 8 = 513)
 constexpr int kFieldCluster = 8;       // CTAs (SMs) sharing one field solve
 
 // device error word bits
@@ -43,6 +43,7 @@ struct Ctrl {
     unsigned long long n_dead[2];       // absorbed slots not yet compacted
     unsigned long long fe_n;            // field-energy history entries written
     unsigned long long n_steps_acc, n_diag_acc;
+    double drive_c[4], drive_s[4];      // cos, sin of 2 pi f_h t + theta_h at the next field solve
 };
 
 struct SpConst {
@@ -93,9 +94,12 @@ struct StepConst {
     double rho_wall[2];                 // q_s w_s 2^-32 / (dx/2): charge density per raw unit at a wall node
     double bg_r;                        // bg dx^2 / eps0
     double inv_dx, inv_2dx, half_dx_eps0, fe_c;   // 1/dx, 1/(2dx), dx/(2 eps0), eps0 dx / 2
+    double inv_n;                       // 1 / n_cells
+    double v_init;                      // electrode voltage at t = 0
+    double rot_c[4], rot_s[4];          // cos, sin of 2 pi f_h dt (one step of each harmonic's phase)
     double *ke_sum, *pw_sum;            // [2]
     unsigned long long *eepf;           // [kEepfBins]
-    double *fe_hist;                    // [fe_cap]
+    double *fe_hist;                    // [fe_cap][kFieldCluster] partial field energies per cluster rank
     long long fe_cap;
     unsigned int *sort_count;           // [n_cells]
     unsigned long long *sort_cursor;    // [n_cells]

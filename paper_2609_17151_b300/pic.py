@@ -60,7 +60,7 @@ class Moments(C.Structure):
         ("dens_sum", C.c_void_p), ("phi_sum", C.c_void_p), ("en_sum", C.c_void_p),
         ("dens_diag_sum", C.c_void_p), ("eepf", C.c_void_p),
         ("field_energy", C.c_void_p), ("field_energy_cap", C.c_int64), ("field_energy_n", C.c_int64),
-        ("reset", C.c_int32),
+        ("reset", C.c_int32), ("sort_interval", C.c_int32),
     ]
 
 
@@ -264,7 +264,7 @@ def read_moments(h, n_nodes, n_species, reset=False, field_energy_cap=0) -> dict
                absorbed=np.array([[m.absorbed[s][w] for w in range(2)] for s in range(2)]),
                see_emitted=m.see_emitted, ionizations=m.ionizations, candidates=np.array(list(m.candidates)),
                collisions=np.array([[m.collisions[s][k] for k in range(MAX_PROC)] for s in range(2)]),
-               ke_sum=np.array(list(m.ke_sum)), pw_sum=np.array(list(m.pw_sum)))
+               ke_sum=np.array(list(m.ke_sum)), pw_sum=np.array(list(m.pw_sum)), sort_interval=m.sort_interval)
     return out
 
 

@@ -279,3 +279,24 @@ def test_sort_by_cell_matches_oracle(n_cells, n):
     oo = np.lexsort((src["id"][perm], cell[perm]))
     for kk in src:
         assert np.array_equal(got[kk][og], src[kk][perm][oo]), kk
+
+
+def test_autotuned_sort_interval_and_graph_replay_leave_results_unchanged():
+    """The autotuner picks K in [4, 1024]; replaying steps from a CUDA graph
+    and running them one launch at a time (profiling) give bit-identical
+    particles, and so does a run that never sorts."""
+    cfg, parts = small_ccp(seed=21, n=30001, ti_ev=400.0)
+    a = gpu_case(cfg, parts, sort_interval=0)
+    a.step(80)
+    k = a.moments()["sort_interval"]
+    assert 4 <= k <= 1024
+    b = gpu_case(cfg, parts, sort_interval=100000)
+    b.profile(True)                      # direct launches with events, no graph
+    b.step(80)
+    b.profile(False)
+    for s in range(2):
+        pa, pb = a.particles(s), b.particles(s)
+        ia, ib = np.argsort(pa["id"], kind="stable"), np.argsort(pb["id"], kind="stable")
+        for key in ("id", "cell", "off", "vx", "vy", "vz"):
+            assert np.array_equal(pa[key][ia], pb[key][ib]), (s, key)
+    a.close(); b.close()
