@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--sort-interval", type=int, default=0, help="0 = the library's autotuner")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="exb", choices=["exb", "batch"],
+                    help="exb: the 10.24M-particle E x B case (default); batch: the 256-case argon sweep")
+    ap.add_argument("--cases", type=int, default=256)
     return ap.parse_args()
 
 
@@ -156,6 +159,88 @@ def run_reference(args, rank):
     }), flush=True)
 
 
+# --------------------------------------------------------------------------- batched sweep
+def run_batch(args, torch):
+    """256 uneven argon cases: one batched launch per kernel per step against
+    the same cases stepped one case at a time (each case's kernels launched
+    on their own, then each case replaying its own CUDA graph)."""
+    from paper_2609_17151_b300 import pic
+    from paper_2609_17151_b300 import workloads as W
+    cfgs, counts = W.sweep_cases(args.cases)
+    stream = torch.cuda.Stream()
+
+    def load(view, cfg):
+        nn = cfg["n_cells"] + 1
+        L = cfg["load"]
+        view.load_profile(0, L["n"], np.full(nn, L["n0"]), np.full(nn, L["te_ev"]))
+        view.load_profile(1, L["n"], np.full(nn, L["n0"]), np.full(nn, L["ti_ev"]))
+
+    caps = [(4 * n, 4 * n) for n in counts]
+    b = pic.Batch(cfgs, stream=stream.cuda_stream, sort_interval=64, capacities=caps)
+    for v, cfg in zip(b.cases, cfgs):
+        load(v, cfg)
+    b.step(max(3, args.warmup))
+    b.sync()
+
+    def count_all(views):
+        return sum(sum(v.count()) for v in views)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = count_all(b.cases)
+    l0 = b.launches()
+    ev0.record(stream)
+    b.step(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_b = ev0.elapsed_time(ev1)
+    launches_b = b.launches() - l0
+    n1 = count_all(b.cases)
+    pps_b = 0.5 * (n0 + n1) * args.steps / (ms_b * 1e-3)
+    b.close()
+
+    # the same cases, one case at a time on the same stream
+    cases = []
+    for cfg, cap in zip(cfgs, caps):
+        c = pic.Case(cfg, stream=stream.cuda_stream, sort_interval=64, capacity=cap)
+        load(c, cfg)
+        cases.append(c)
+    for c in cases:
+        c.step(max(3, args.warmup))
+    torch.cuda.synchronize()
+    m0 = count_all(cases)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        for c in cases:
+            c.step(1)                       # every kernel of every case launched on its own
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_1 = ev0.elapsed_time(ev1)
+    ev0.record(stream)
+    for c in cases:
+        c.step(args.steps)                  # each case replays its own graph
+    ev1.record(stream)
+    ev1.synchronize()
+    ms_g = ev0.elapsed_time(ev1)
+    m1 = count_all(cases)
+    for c in cases:
+        c.close()
+    pps_1 = 0.5 * (m0 + m1) * args.steps / (ms_1 * 1e-3)
+    pps_g = 0.5 * (m0 + m1) * args.steps / (ms_g * 1e-3)
+    print(json.dumps({
+        "metric": METRIC, "value": pps_b, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"argon_ccp_sweep_{args.cases}_cases", "particles": int(n0),
+                   "cells_range": [min(c["n_cells"] for c in cfgs), max(c["n_cells"] for c in cfgs)],
+                   "sort_interval": 64, "parallelism": "batched cases, 1 GPU"},
+        "batched_vs_one_launch_per_case": pps_b / pps_1,
+        "batched_vs_per_case_graphs": pps_b / pps_g,
+        "one_launch_per_case": {"value": pps_1, "ms_per_step": ms_1 / args.steps},
+        "per_case_graphs": {"value": pps_g, "ms_per_step": ms_g / args.steps},
+        "gpu_launches": launches_b,
+    }), flush=True)
+
+
 # --------------------------------------------------------------------------- GPU leg
 def main():
     args = parse()
@@ -171,6 +256,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    if args.workload == "batch":
+        if rank == 0:
+            run_batch(args, torch)
+        return
     from paper_2609_17151_b300 import pic
     from paper_2609_17151_b300 import workloads as W
 

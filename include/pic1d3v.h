@@ -120,6 +120,22 @@ pic_status pic_load_particles(pic_case *c, int species, int64_t n, const int32_t
                               const float *offset, const float *vx, const float *vy,
                               const float *vz, const uint32_t *id, int on_device);
 
+/* Load n particles of one species sampled on the GPU from profiles at the
+ * nodes (n_nodes values each): number density (m^-3), giving the count per
+ * cell through the linear (CIC) density between nodes, and temperature (eV)
+ * of an isotropic Maxwellian, plus a drift velocity (m/s, may be NULL).  This
+ * is how a case starts from given profiles (a uniform plasma, or profiles
+ * predicted by the learned warm start).  Particle k gets id id_base + k and
+ * its draws come from Philox under the case seed, counter
+ * (id, 0xFFFFFFFF, species << 16 | 0x100 + j, 1), j = 0, 1: word 0 picks the
+ * cell (u <= cumulative mass, FP64), word 1 the offset (inverse of the linear
+ * density in the cell), words 2..5 three Gaussian components (Box-Muller).
+ * Replaces the species' particles, like pic_load_particles.  Scratch for the
+ * profile tables comes from the stream-ordered allocator.  Errors: PIC_EINVAL
+ * (negative profile, zero total density with n > 0), PIC_ECAPACITY. */
+pic_status pic_load_profile(pic_case *c, int species, int64_t n, const double *density,
+                            const double *temp_ev, const double drift_m_per_s[3], uint32_t id_base);
+
 /* Enqueue n_steps time steps (paper §1 scheme; step order in the design
  * notes) on the case stream.  Returns after enqueueing; steps are replayed
  * from a CUDA graph of up to 16 steps when no sort falls inside it.  With
@@ -236,6 +252,32 @@ pic_status pic_sort_by_cell(int32_t n_cells, int64_t n, const int32_t *cell, con
                             const float *vx, const float *vy, const float *vz, const uint32_t *id,
                             int32_t *cell_out, float *offset_out, float *vx_out, float *vy_out,
                             float *vz_out, uint32_t *id_out, int64_t *n_live, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched sweep: n independent cases (a parameter sweep of the paper's cases:
+ * different pressures, voltages, gaps, cell and particle counts) stepped
+ * together.  Each case is an ordinary pic_case created from descs[i] on the
+ * batch's stream (descs[0].stream, or one the batch creates); use
+ * pic_batch_case(b, i) with the per-case calls to load tables and particles
+ * and to read results.  pic_batch_step runs every case's steps with one
+ * persistent particle launch (work items: slices of ~131072 particles of any
+ * case and species, taken from an atomic counter) and one field launch (one
+ * 8-CTA cluster per case) per step, replayed from a CUDA graph between sorts;
+ * every sort_interval (descs[0].sort_interval, 0 = 64) steps each case is
+ * sorted.  All cases must share the boundary kind, the number of species and
+ * the collision model of each species (none, tables, or constant frequency
+ * for electrons).  Results equal stepping each case alone.
+ * Errors: PIC_EINVAL (mixed cases), PIC_ESTATE (a case without particles).
+ * ------------------------------------------------------------------------- */
+typedef struct pic_batch pic_batch;
+pic_status pic_batch_create(const pic_case_desc *descs, int n_cases, pic_batch **out);
+/* Borrowed handle of case i (owned by the batch; NULL if out of range). */
+pic_case *pic_batch_case(pic_batch *b, int i);
+pic_status pic_batch_step(pic_batch *b, int64_t n_steps);
+pic_status pic_batch_sync(pic_batch *b);
+/* Kernel launches the batch has enqueued (for launch accounting). */
+int64_t pic_batch_launches(const pic_batch *b);
+pic_status pic_batch_destroy(pic_batch *b);
 
 /* Allocation-free variant of pic_sort_by_cell.  The paper has no counterpart:
  * this entry point exists for callers that must not allocate device memory

@@ -75,6 +75,7 @@ def _load():
     lib.or_load_xsec.argtypes = [P, C.c_int, C.c_int, C.c_double, dp, dp, C.c_int]
     lib.or_load_particles.argtypes = [P, C.c_int, C.c_int64, dp, dp, dp, dp, C.POINTER(C.c_uint32)]
     lib.or_step.argtypes = [P, C.c_int64]
+    lib.or_load_profile.argtypes = [P, C.c_int, C.c_int64, dp, dp, dp, C.c_uint32]
     lib.or_count.restype = C.c_int64
     lib.or_count.argtypes = [P, C.c_int]
     lib.or_get_particles.argtypes = [P, C.c_int, dp, dp, dp, dp, C.POINTER(C.c_uint32), dp,
@@ -221,6 +222,11 @@ class Case:
                                     ids.ctypes.data_as(C.POINTER(C.c_uint32)))
         if rc != 0:
             raise ValueError(f"oracle rejected the particles ({rc})")
+
+    def load_profile(self, sp, n, density, temp_ev, drift=(0.0, 0.0, 0.0), id_base=0):
+        d = _f64(density); t = _f64(temp_ev); dr = _f64(drift)
+        if _lib.or_load_profile(self._h, sp, int(n), _d(d), _d(t), _d(dr), int(id_base) & 0xFFFFFFFF) != 0:
+            raise ValueError("oracle rejected the profile load")
 
     def step(self, n=1):
         if _lib.or_step(self._h, int(n)) != 0:

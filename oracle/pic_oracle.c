@@ -826,6 +826,59 @@ void or_reset_moments(or_case *c)
     c->cnt.step = step;
 }
 
+/* Loading from node profiles: n particles of species sp, ids id_base + k.
+ * Cell: the j with cdf[j] <= u < cdf[j+1], cdf the normalised cumulative mass
+ * (n_j + n_{j+1})/2 of the linear density between nodes (node N = node 0 when
+ * periodic).  Offset: inverse of the linear density a(1-d) + b d on [0, 1),
+ * d = u' (a+b) / (a + sqrt(a^2 + u' (b^2 - a^2))).  Velocity: isotropic
+ * Maxwellian at the linearly interpolated temperature plus the drift.
+ * Draws: Philox counter (id, 0xFFFFFFFF, sp << 16 | 0x100 + j, 1). */
+int or_load_profile(or_case *c, int sp, int64_t n, const double *density, const double *temp_ev,
+                    const double drift[3], uint32_t id_base)
+{
+    if (!c || sp < 0 || sp >= c->p.n_species || n < 0) return -1;
+    int N = c->p.n_cells;
+    double *cdf = calloc((size_t)N + 1, sizeof(double));
+    double *dn = malloc(sizeof(double) * ((size_t)N + 1)), *tn = malloc(sizeof(double) * ((size_t)N + 1));
+    for (int j = 0; j <= N; ++j) {
+        int jj = (c->p.periodic && j == N) ? 0 : j;
+        dn[j] = density[jj];
+        tn[j] = temp_ev[jj];
+    }
+    for (int j = 0; j < N; ++j) cdf[j + 1] = cdf[j] + 0.5 * (density[j] + density[(c->p.periodic && j + 1 == N) ? 0 : j + 1]);
+    double total = cdf[N];
+    for (int j = 1; j < N; ++j) cdf[j] /= total;
+    cdf[N] = 1.0;
+    uint32_t key[2] = { (uint32_t)c->p.seed, (uint32_t)(c->p.seed >> 32) };
+    species_t *s = &c->sp[sp];
+    s->n = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        uint32_t id = id_base + (uint32_t)k;
+        uint32_t ctr[4] = { id, 0xFFFFFFFFu, ((uint32_t)sp << 16) | 0x100u, 1u }, r[4], r2[4];
+        or_philox4x32_10(ctr, key, r);
+        ctr[2] = ((uint32_t)sp << 16) | 0x101u;
+        or_philox4x32_10(ctr, key, r2);
+        double u = or_uniform(r[0]);
+        int j = 0;
+        while (j + 1 < N && cdf[j + 1] <= u) ++j;
+        double a = dn[j], b = dn[j + 1], u2 = or_uniform(r[1]);
+        double den = a + sqrt(fmax(a * a + u2 * (b * b - a * a), 0.0));
+        double d = den > 0 ? u2 * (a + b) / den : u2;
+        double T = (1.0 - d) * tn[j] + d * tn[j + 1];
+        double vt = sqrt(fmax(T, 0.0) * ELEM / c->p.m[sp]);
+        double g0, g1, g2, g3;
+        box_muller(or_uniform(r[2]), or_uniform(r[3]), &g0, &g1);
+        box_muller(or_uniform(r2[0]), or_uniform(r2[1]), &g2, &g3);
+        double dr[3] = { drift ? drift[0] : 0, drift ? drift[1] : 0, drift ? drift[2] : 0 };
+        if (sp_push(s, j + d, vt * g0 + dr[0], vt * g1 + dr[1], vt * g2 + dr[2], id)) { free(cdf); free(dn); free(tn); return -3; }
+    }
+    free(cdf); free(dn); free(tn);
+    c->initialised = 0;
+    c->step = 0;
+    c->fe_n = 0;
+    return 0;
+}
+
 /* Counting sort by cell (the periodic reordering of the particle arrays):
  * the indices of the particles whose cell lies in [0, n_cells), grouped by
  * ascending cell and, inside a cell, in input order.  Returns how many. */

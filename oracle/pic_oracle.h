@@ -75,6 +75,8 @@ int  or_load_xsec(or_case *c, int sp, int kind, double threshold_ev,
 int  or_load_particles(or_case *c, int sp, int64_t n, const double *xi,
                        const double *vx, const double *vy, const double *vz,
                        const uint32_t *id);
+int  or_load_profile(or_case *c, int sp, int64_t n, const double *density, const double *temp_ev,
+                     const double drift[3], uint32_t id_base);
 int  or_step(or_case *c, int64_t n_steps);
 int64_t or_count(const or_case *c, int sp);
 /* margin/event: per particle, the smallest normalised distance of any

@@ -136,11 +136,11 @@ struct FieldPart {
     u128 qq[2];                         // sum over slice i < N of e_s[i] = sum_{c_lo <= m < i} p_s[m]
 };
 
-__global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldThreads)
-    k_field(const __grid_constant__ StepConst P, int mode, unsigned long long *R_last)
+__device__ __forceinline__ void field_solve(const StepConst &P, int mode)
 {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
+    unsigned long long *R_last = P.R_last;
     extern __shared__ __align__(16) double Ssh[];                    // [kFieldThreads + 1]: S at node c_lo - 1 + t
     __shared__ unsigned long long ured[kFieldThreads / 32][4];
     __shared__ u128 wred[kFieldThreads / 32][2];
@@ -351,6 +351,20 @@ __global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldTh
         ctrl->step = step + 1;
     }
     cl.barrier_wait();                                            // no CTA leaves while read remotely
+}
+
+__global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldThreads)
+    k_field(const __grid_constant__ StepConst P, int mode)
+{
+    field_solve(P, mode);
+}
+
+// One cluster per case; also resets the batch work-item counter for the next step.
+__global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldThreads)
+    k_batch_field(const StepConst *__restrict__ cases, int mode, unsigned *next_item)
+{
+    field_solve(cases[blockIdx.x / kFieldCluster], mode);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && next_item) *next_item = 0u;
 }
 
 // ---------------------------------------------------------------------------

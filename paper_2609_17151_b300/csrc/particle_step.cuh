@@ -50,13 +50,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity)
 // Bounded wait for the staging copy: gives up after a fixed number of polls,
 // raises kErrTimeout, then polls again (bounded) so no copy is left in
 // flight when the CTA returns.  Returns false if the data never arrived.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, Ctrl *ctrl)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, Ctrl *ctrl, unsigned parity)
 {
     for (int i = 0; i < (1 << 22); ++i)
-        if (mbar_try_wait(mbar, 0)) return true;
+        if (mbar_try_wait(mbar, parity)) return true;
     atomicOr(&ctrl->err, kErrTimeout);
     for (int i = 0; i < (1 << 22); ++i)
-        if (mbar_try_wait(mbar, 0)) return false;
+        if (mbar_try_wait(mbar, parity)) return false;
     return false;
 }
 
@@ -277,15 +277,22 @@ struct StepSmem {
     }
 };
 
-template <int SP, bool PERIODIC, int MCC>
-__global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_constant__ StepConst P)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ uint64_t mbar;
-    __shared__ unsigned s_cnt[2 + 2 * kMaxProc];        // candidates, per process, ionizations
-    __shared__ unsigned s_abs[2], s_see;
-    __shared__ float s_red[2][kStepThreads / 32];
+// Per-CTA shared state of the particle step besides the dynamic tables.
+struct StepShared {
+    uint64_t mbar;                                      // staging barrier (phase toggles per item)
+    unsigned s_cnt[2 + 2 * kMaxProc];                   // candidates, per process, ionizations
+    unsigned s_abs[2], s_see;
+    float s_red[2][kStepThreads / 32];
+};
 
+// One work item: chunks (4 particles) [beg, end) of the k-th of nk equal
+// slices of species SP of one case.  Stages the case's node field and the
+// species' table, processes the slice, flushes the deposit, the moments and
+// the counters.  `parity` is the staging barrier's phase, toggled per item.
+template <int SP, bool PERIODIC, int MCC>
+__device__ __forceinline__ void particle_item(const StepConst &P, unsigned char *smem, StepShared &sh,
+                                              unsigned &parity, long long k_item, long long n_items)
+{
     const SpConst &S = P.sp[SP];
     const int N = P.n_cells;
     const StepSmem L(N, MCC == 1 ? S.nproc : 0);
@@ -295,17 +302,25 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_
     float *nus = reinterpret_cast<float *>(smem + L.nu_off);
     float *hen = reinterpret_cast<float *>(smem + L.en_off);
     unsigned *heepf = reinterpret_cast<unsigned *>(smem + L.eepf_off);
+    unsigned *s_cnt = sh.s_cnt, *s_abs = sh.s_abs;
 
     Ctrl *ctrl = P.ctrl;
     const int tid = threadIdx.x;
+    const long long n = (long long)ctrl->n_active[SP];
+    const long long n_chunks = (n + 3) / 4;
+    long long per = (n_chunks + n_items - 1) / n_items;
+    per = (per + 31) & ~31ll;
+    const long long beg = k_item * per;
+    const long long end = min(beg + per, n_chunks);
+    if (beg >= end) return;                             // uniform over the CTA
+
     const unsigned e_bytes = align16((unsigned)(N + 1) * 4u);
     const unsigned nu_bytes = MCC == 1 ? (unsigned)S.nproc * kNGrid * 4u : 0u;
-    if (tid == 0) mbar_init(&mbar, 1);
-    __syncthreads();
     if (tid == 0) {
-        mbar_expect_tx(&mbar, e_bytes + nu_bytes);
-        bulk_g2s(Es, P.E32, e_bytes, &mbar);
-        if (MCC == 1) bulk_g2s(nus, P.nu_tab[SP], nu_bytes, &mbar);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // earlier reads before the async writes
+        mbar_expect_tx(&sh.mbar, e_bytes + nu_bytes);
+        bulk_g2s(Es, P.E32, e_bytes, &sh.mbar);
+        if (MCC == 1) bulk_g2s(nus, P.nu_tab[SP], nu_bytes, &sh.mbar);
     }
     const long long step_ll = ctrl->step;
     const uint32_t step = (uint32_t)step_ll;
@@ -315,21 +330,15 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_
     if (diag) for (int j = tid; j < kEepfBins; j += blockDim.x) heepf[j] = 0u;
     if (tid < 2 + 2 * kMaxProc) s_cnt[tid] = 0u;
     if (tid < 2) s_abs[tid] = 0u;
-    if (tid == 0) s_see = 0u;
-    const bool staged = mbar_wait_bounded(&mbar, ctrl);
-    __syncthreads();
+    if (tid == 0) sh.s_see = 0u;
+    const bool staged = mbar_wait_bounded(&sh.mbar, ctrl, parity);
+    parity ^= 1u;
     if (!__syncthreads_and(staged)) return;
 
     const int half = ctrl->cur[SP];
     const int half_e = ctrl->cur[0];
     const int half_i = P.n_species > 1 ? ctrl->cur[1] : 0;
     const SpeciesBufs B = P.buf[SP][half];
-    const long long n = (long long)ctrl->n_active[SP];
-    const long long n_chunks = (n + 3) / 4;
-    long long per = (n_chunks + gridDim.x - 1) / gridDim.x;
-    per = (per + 31) & ~31ll;
-    const long long beg = (long long)blockIdx.x * per;
-    const long long end = min(beg + per, n_chunks);
 
     const float dtdx = P.dtdx;
     const int lane = tid & 31, warp = tid >> 5;
@@ -394,7 +403,7 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_
                 // 4. electrode absorption (+ secondary emission by ions)
                 const int wall = c < 0 ? 0 : 1;
                 atomicAdd(&s_abs[wall], 1u);
-                if (SP == 1 && P.see_gamma > 0.0f) emit_secondary(P, ids[q], step, wall, half_e, diag, &s_see);
+                if (SP == 1 && P.see_gamma > 0.0f) emit_secondary(P, ids[q], step, wall, half_e, diag, &sh.s_see);
                 cc[q] = -1;
                 oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
                 continue;
@@ -485,11 +494,11 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_
             ke_acc += __shfl_xor_sync(0xffffffffu, ke_acc, o);
             pw_acc += __shfl_xor_sync(0xffffffffu, pw_acc, o);
         }
-        if (lane == 0) { s_red[0][warp] = ke_acc; s_red[1][warp] = pw_acc; }
+        if (lane == 0) { sh.s_red[0][warp] = ke_acc; sh.s_red[1][warp] = pw_acc; }
         __syncthreads();
         if (tid == 0) {
             double ke = 0, pw = 0;
-            for (int w = 0; w < (int)(blockDim.x / 32); ++w) { ke += s_red[0][w]; pw += s_red[1][w]; }
+            for (int w = 0; w < (int)(blockDim.x / 32); ++w) { ke += sh.s_red[0][w]; pw += sh.s_red[1][w]; }
             atomicAdd(&P.ke_sum[SP], 0.5 * S.m * S.w * ke);
             atomicAdd(&P.pw_sum[SP], S.q * S.w * pw);
         }
@@ -498,11 +507,53 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_
         if (s_abs[0]) { atomicAdd(&ctrl->absorbed[SP][0], (unsigned long long)s_abs[0]); }
         if (s_abs[1]) { atomicAdd(&ctrl->absorbed[SP][1], (unsigned long long)s_abs[1]); }
         if (s_abs[0] + s_abs[1]) atomicAdd(&ctrl->n_dead[SP], (unsigned long long)(s_abs[0] + s_abs[1]));
-        if (s_see) atomicAdd(&ctrl->see, (unsigned long long)s_see);
+        if (sh.s_see) atomicAdd(&ctrl->see, (unsigned long long)sh.s_see);
         if (s_cnt[0]) atomicAdd(&ctrl->cand[SP], (unsigned long long)s_cnt[0]);
         for (int k = 0; k < kMaxProc; ++k)
             if (s_cnt[1 + k]) atomicAdd(&ctrl->coll[SP][k], (unsigned long long)s_cnt[1 + k]);
         if (s_cnt[1 + kMaxProc]) atomicAdd(&ctrl->iz, (unsigned long long)s_cnt[1 + kMaxProc]);
+    }
+    __syncthreads();                                    // shared state free for the next item
+}
+
+// One case: CTA b takes the b-th of gridDim.x slices of the species.
+template <int SP, bool PERIODIC, int MCC>
+__global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_constant__ StepConst P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ StepShared sh;
+    if (threadIdx.x == 0) mbar_init(&sh.mbar, 1);
+    __syncthreads();
+    unsigned parity = 0;
+    particle_item<SP, PERIODIC, MCC>(P, smem, sh, parity, blockIdx.x, gridDim.x);
+}
+
+// Many cases in one persistent launch: CTAs take (case, species, slice) work
+// items from an atomic counter (reset by the batched field solve).
+struct BatchItem {
+    int case_idx, species, k, nk;
+};
+
+template <bool PERIODIC, int MCC0, int MCC1>
+__global__ void __launch_bounds__(kStepThreads, 2)
+    k_batch_particle_step(const StepConst *__restrict__ cases, const BatchItem *__restrict__ items, int n_items,
+                          unsigned *next_item)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ StepShared sh;
+    __shared__ int s_item;
+    if (threadIdx.x == 0) mbar_init(&sh.mbar, 1);
+    __syncthreads();
+    unsigned parity = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(next_item, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const BatchItem w = items[it];
+        if (w.species == 0) particle_item<0, PERIODIC, MCC0>(cases[w.case_idx], smem, sh, parity, w.k, w.nk);
+        else particle_item<1, PERIODIC, MCC1>(cases[w.case_idx], smem, sh, parity, w.k, w.nk);
     }
 }
 
@@ -531,6 +582,46 @@ __global__ void k_rewind(const __grid_constant__ StepConst P)
         B.vx[i] = vm.x + (vp.y * s2 - vp.z * s1) + hx;
         B.vy[i] = vm.y + (vp.z * s0 - vp.x * s2) + ey;
         B.vz[i] = vm.z + (vp.x * s1 - vp.y * s0) + ez;
+    }
+}
+
+// Particle loader: n particles of species sp sampled from node profiles.
+// Particle k has id = id_base + k and draws Philox counter
+// (id, 0xFFFFFFFF, sp << 16 | 0x100 + j, 1), j = 0, 1.  The cell is the j with
+// cdf[j] <= u < cdf[j+1] (FP64, cdf = cumulative CIC mass of the linear
+// density); the offset inverts the linear density inside the cell,
+// delta = u' (a+b) / (a + sqrt(a^2 + u' (b^2 - a^2))) with a, b the node
+// densities; the velocity is Maxwellian at the linearly interpolated
+// temperature plus a drift.
+__global__ void k_load_profile(SpeciesBufs B, long long n, int N, const double *__restrict__ cdf,
+                               const float *__restrict__ dens, const float *__restrict__ temp_ev, float vt_per_sqrt_ev,
+                               float drift_x, float drift_y, float drift_z, uint32_t id_base, int sp, uint32_t k0,
+                               uint32_t k1)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const uint32_t id = id_base + (uint32_t)k;
+        const uint4 r = philox4x32_10(make_uint4(id, 0xFFFFFFFFu, ((uint32_t)sp << 16) | 0x100u, 1u), k0, k1);
+        const uint4 r2 = philox4x32_10(make_uint4(id, 0xFFFFFFFFu, ((uint32_t)sp << 16) | 0x101u, 1u), k0, k1);
+        const double u = (double)u01(r.x);
+        int lo = 0, hi = N;                                  // cdf[lo] <= u < cdf[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (cdf[mid] <= u) lo = mid; else hi = mid;
+        }
+        const float a = dens[lo], b = dens[lo + 1], u2 = u01(r.y);
+        const float den = a + sqrtf(fmaxf(a * a + u2 * (b * b - a * a), 0.0f));
+        float o = den > 0.0f ? u2 * (a + b) / den : u2;
+        o = fminf(fmaxf(o, 0.0f), 0.99999994f);
+        const float T = (1.0f - o) * temp_ev[lo] + o * temp_ev[lo + 1];
+        const float vt = vt_per_sqrt_ev * sqrtf(fmaxf(T, 0.0f));
+        const float2 g01 = box_muller(u01(r.z), u01(r.w));
+        const float2 g23 = box_muller(u01(r2.x), u01(r2.y));
+        B.cell[k] = lo;
+        B.off[k] = o;
+        B.vx[k] = fmaf(vt, g01.x, drift_x);
+        B.vy[k] = fmaf(vt, g01.y, drift_y);
+        B.vz[k] = fmaf(vt, g23.x, drift_z);
+        B.id[k] = id;
     }
 }
 

@@ -247,7 +247,7 @@ cudaError_t launch_step_sp(pic_case *c)
 cudaError_t launch_field(pic_case *c, int mode)
 {
     Timed t(c, mode == 0 ? KC_INIT : KC_FIELD, 1);
-    k_field<<<kFieldCluster, kFieldThreads, c->field_smem, c->stream>>>(c->P, mode, c->R_last);
+    k_field<<<kFieldCluster, kFieldThreads, c->field_smem, c->stream>>>(c->P, mode);
     return cudaGetLastError();
 }
 
@@ -505,6 +505,59 @@ pic_status build_graph(pic_case *c, int steps)
     return PIC_OK;
 }
 
+// Common start of a load: buffers allocated, other species moved to half 0.
+pic_status load_begin(pic_case *c, int sp, int64_t n, Ctrl *h)
+{
+    CU(cudaStreamSynchronize(c->stream));
+    pic_status st = alloc_species(c, sp, n);
+    if (st != PIC_OK) return st;
+    for (int s = 0; s < c->d.n_species; ++s)
+        if (!c->P.buf[s][0].cell) {
+            st = alloc_species(c, s, 0);
+            if (st != PIC_OK) return st;
+        }
+    CU(cudaMemcpy(h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    // a load restarts the case: particles of the other species move back to half 0
+    for (int s = 0; s < c->d.n_species; ++s) {
+        if (s == sp || h->cur[s] == 0 || !c->loaded[s]) continue;
+        const SpeciesBufs &A = c->P.buf[s][1], &D = c->P.buf[s][0];
+        const size_t b = (size_t)h->n_total[s] * 4;
+        CU(cudaMemcpyAsync(D.cell, A.cell, b, cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(D.off, A.off, b, cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(D.vx, A.vx, b, cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(D.vy, A.vy, b, cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(D.vz, A.vz, b, cudaMemcpyDeviceToDevice, c->stream));
+        CU(cudaMemcpyAsync(D.id, A.id, b, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return PIC_OK;
+}
+
+// Common end of a load: counts, drive phases, moments reset, state restarts at step 0.
+pic_status load_finish(pic_case *c, int sp, int64_t n, const Ctrl &h)
+{
+    Ctrl z;
+    std::memset(&z, 0, sizeof(z));
+    for (int k = 0; k < c->d.n_harm; ++k) {                 // phases at the first step's field solve (t = dt)
+        const double ph = 2.0 * M_PI * c->d.harm_freq_hz[k] * c->d.dt_s + c->d.harm_phase_rad[k];
+        z.drive_c[k] = std::cos(ph);
+        z.drive_s[k] = std::sin(ph);
+    }
+    for (int s = 0; s < 2; ++s) {
+        const unsigned long long cnt = s == sp ? (unsigned long long)n : (c->loaded[s] ? h.n_total[s] : 0ull);
+        z.n_total[s] = z.n_active[s] = cnt;
+    }
+    CU(cudaMemcpyAsync(c->P.ctrl, &z, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
+    pic_status st = reset_moments(c);
+    if (st != PIC_OK) return st;
+    CU(cudaStreamSynchronize(c->stream));
+    c->loaded[sp] = true;
+    c->need_init = true;
+    c->host_step = 0;
+    c->steps_since_sort = 0;
+    drop_graph(c);
+    return PIC_OK;
+}
+
 } // namespace
 
 // Message for pic_last_error() from the other translation units of the library.
@@ -601,6 +654,7 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     P.phi = (double *)c->dalloc(sizeof(double) * nn);
     for (int s = 0; s < 2; ++s) P.R[s] = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * (N + 1));
     c->R_last = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * 2 * nn);
+    P.R_last = c->R_last;
     P.ctrl = (Ctrl *)c->dalloc(sizeof(Ctrl));
     P.Rsum = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * 2 * nn);
     P.Rdiag = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * 2 * nn);
@@ -663,28 +717,9 @@ pic_status pic_load_particles(pic_case *c, int sp, int64_t n, const int32_t *cel
 {
     if (!c || sp < 0 || sp >= c->d.n_species || n < 0) return fail(PIC_EINVAL, "bad load arguments");
     if (n > 0 && (!cell || !off || !vx || !vy || !vz)) return fail(PIC_EINVAL, "null particle array");
-    CU(cudaStreamSynchronize(c->stream));
-    pic_status st = alloc_species(c, sp, n);
-    if (st != PIC_OK) return st;
-    for (int s = 0; s < c->d.n_species; ++s)
-        if (!c->P.buf[s][0].cell) {
-            st = alloc_species(c, s, 0);
-            if (st != PIC_OK) return st;
-        }
     Ctrl h;
-    CU(cudaMemcpy(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
-    // a load restarts the case: particles of the other species move back to half 0
-    for (int s = 0; s < c->d.n_species; ++s) {
-        if (s == sp || h.cur[s] == 0 || !c->loaded[s]) continue;
-        const SpeciesBufs &A = c->P.buf[s][1], &D = c->P.buf[s][0];
-        const size_t b = (size_t)h.n_total[s] * 4;
-        CU(cudaMemcpyAsync(D.cell, A.cell, b, cudaMemcpyDeviceToDevice, c->stream));
-        CU(cudaMemcpyAsync(D.off, A.off, b, cudaMemcpyDeviceToDevice, c->stream));
-        CU(cudaMemcpyAsync(D.vx, A.vx, b, cudaMemcpyDeviceToDevice, c->stream));
-        CU(cudaMemcpyAsync(D.vy, A.vy, b, cudaMemcpyDeviceToDevice, c->stream));
-        CU(cudaMemcpyAsync(D.vz, A.vz, b, cudaMemcpyDeviceToDevice, c->stream));
-        CU(cudaMemcpyAsync(D.id, A.id, b, cudaMemcpyDeviceToDevice, c->stream));
-    }
+    pic_status st = load_begin(c, sp, n, &h);
+    if (st != PIC_OK) return st;
     const SpeciesBufs &B = c->P.buf[sp][0];
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (n > 0) {
@@ -701,27 +736,52 @@ pic_status pic_load_particles(pic_case *c, int sp, int64_t n, const int32_t *cel
         CU(cudaMemcpyAsync(B.id, seq.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
         CU(cudaStreamSynchronize(c->stream));
     }
-    Ctrl z;
-    std::memset(&z, 0, sizeof(z));
-    for (int h = 0; h < c->d.n_harm; ++h) {                 // phases at the first step's field solve (t = dt)
-        const double ph = 2.0 * M_PI * c->d.harm_freq_hz[h] * c->d.dt_s + c->d.harm_phase_rad[h];
-        z.drive_c[h] = std::cos(ph);
-        z.drive_s[h] = std::sin(ph);
+    return load_finish(c, sp, n, h);
+}
+
+pic_status pic_load_profile(pic_case *c, int sp, int64_t n, const double *density, const double *temp_ev,
+                            const double drift[3], uint32_t id_base)
+{
+    if (!c || sp < 0 || sp >= c->d.n_species || n < 0 || !density || !temp_ev) return fail(PIC_EINVAL, "bad profile load");
+    const int N = c->d.n_cells, nn = c->n_nodes;
+    // cumulative CIC mass per cell of the linear density between nodes (node N = node 0 when periodic)
+    std::vector<double> cdf(N + 1, 0.0);
+    std::vector<float> dn(N + 1), tn(N + 1);
+    for (int j = 0; j <= N; ++j) {
+        const int jj = (c->d.periodic && j == N) ? 0 : j;
+        if (!(density[jj] >= 0.0) || !(temp_ev[jj] >= 0.0)) return fail(PIC_EINVAL, "negative or NaN profile value");
+        dn[j] = (float)density[jj];
+        tn[j] = (float)temp_ev[jj];
     }
-    for (int s = 0; s < 2; ++s) {
-        const unsigned long long cnt = s == sp ? (unsigned long long)n : (c->loaded[s] ? h.n_total[s] : 0ull);
-        z.n_total[s] = z.n_active[s] = cnt;
-    }
-    CU(cudaMemcpyAsync(c->P.ctrl, &z, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
-    st = reset_moments(c);
+    for (int j = 0; j < N; ++j) cdf[j + 1] = cdf[j] + 0.5 * (density[j] + density[(c->d.periodic && j + 1 == N) ? 0 : j + 1]);
+    const double total = cdf[N];
+    if (n > 0 && !(total > 0.0)) return fail(PIC_EINVAL, "profile density integrates to zero");
+    for (int j = 1; j < N; ++j) cdf[j] /= total;
+    cdf[N] = 1.0;
+    (void)nn;
+    Ctrl h;
+    pic_status st = load_begin(c, sp, n, &h);
     if (st != PIC_OK) return st;
-    CU(cudaStreamSynchronize(c->stream));
-    c->loaded[sp] = true;
-    c->need_init = true;
-    c->host_step = 0;
-    c->steps_since_sort = 0;
-    drop_graph(c);
-    return PIC_OK;
+    if (n > 0) {
+        const size_t bytes = (N + 1) * (sizeof(double) + 2 * sizeof(float));
+        void *tmp = nullptr;
+        CU(cudaMallocAsync(&tmp, bytes, c->stream));
+        double *d_cdf = (double *)tmp;
+        float *d_dn = (float *)(d_cdf + (N + 1)), *d_tn = d_dn + (N + 1);
+        CU(cudaMemcpyAsync(d_cdf, cdf.data(), (N + 1) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CU(cudaMemcpyAsync(d_dn, dn.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CU(cudaMemcpyAsync(d_tn, tn.data(), (N + 1) * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        const float vt = (float)std::sqrt(kElem / c->d.mass_kg[sp]);
+        const double z3[3] = {0, 0, 0};
+        const double *dr = drift ? drift : z3;
+        const int grid = (int)std::min<long long>((n + 255) / 256, (long long)c->num_sms * 16);
+        k_load_profile<<<grid, 256, 0, c->stream>>>(c->P.buf[sp][0], n, N, d_cdf, d_dn, d_tn, vt, (float)dr[0],
+                                                    (float)dr[1], (float)dr[2], id_base, sp, c->P.key0, c->P.key1);
+        CU(cudaGetLastError());
+        CU(cudaFreeAsync(tmp, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return load_finish(c, sp, n, h);
 }
 
 pic_status pic_step(pic_case *c, int64_t n_steps)
@@ -1006,6 +1066,267 @@ pic_status pic_sort_by_cell(int32_t n_cells, int64_t n, const int32_t *cell, con
     }
     if (n_live) CU(cudaMemcpyAsync(n_live, cursor + N, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
     CU(cudaFreeAsync(scratch, st));
+    return PIC_OK;
+}
+
+} // extern "C"
+
+// ===========================================================================
+// Batched sweep: many independent cases stepped together.
+// ===========================================================================
+struct pic_batch {
+    std::vector<pic_case *> cases;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    StepConst *d_cases = nullptr;
+    BatchItem *d_items = nullptr;
+    unsigned *d_next = nullptr;
+    int n_items = 0;
+    bool planned = false;
+    int periodic = 0, mcc0 = 0, mcc1 = 0;
+    unsigned smem = 0;
+    int grid = 0;
+    int sort_k = 64;
+    long long host_step = 0, steps_since_sort = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    long long launches = 0;
+};
+
+namespace {
+
+constexpr long long kItemParticles = 131072;
+
+template <bool PER, int M0, int M1>
+cudaError_t batch_step_t(pic_batch *b)
+{
+    auto k = k_batch_particle_step<PER, M0, M1>;
+    if (b->grid == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kStepThreads, b->smem);
+        if (e != cudaSuccess) return e;
+        b->grid = std::max(1, occ) * b->cases[0]->num_sms;
+    }
+    k<<<b->grid, kStepThreads, b->smem, b->stream>>>(b->d_cases, b->d_items, b->n_items, b->d_next);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_particles(pic_batch *b)
+{
+    const int m = b->mcc0 * 3 + b->mcc1;
+    if (b->periodic) {
+        if (m == 0) return batch_step_t<true, 0, 0>(b);
+        if (m == 4) return batch_step_t<true, 1, 1>(b);
+        if (m == 6) return batch_step_t<true, 2, 0>(b);
+    } else {
+        if (m == 0) return batch_step_t<false, 0, 0>(b);
+        if (m == 4) return batch_step_t<false, 1, 1>(b);
+        if (m == 6) return batch_step_t<false, 2, 0>(b);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t batch_one_step(pic_batch *b)
+{
+    cudaError_t e = batch_particles(b);
+    if (e != cudaSuccess) return e;
+    k_batch_field<<<(unsigned)(kFieldCluster * b->cases.size()), kFieldThreads, b->cases[0]->field_smem, b->stream>>>(
+        b->d_cases, 1, b->d_next);
+    return cudaGetLastError();
+}
+
+void batch_drop_graph(pic_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_steps = 0;
+}
+
+pic_status batch_plan(pic_batch *b)
+{
+    const size_t nc = b->cases.size();
+    for (pic_case *c : b->cases) {
+        for (int s = 0; s < c->d.n_species; ++s)
+            if (!c->loaded[s] && !(s == 1 && c->loaded[0])) return fail(PIC_ESTATE, "a batch case has no particles");
+        if (c->need_init) {
+            pic_status st = initialise(c);
+            if (st != PIC_OK) return st;
+        }
+    }
+    const pic_case *c0 = b->cases[0];
+    b->periodic = c0->d.periodic;
+    b->mcc0 = c0->P.sp[0].mcc;
+    b->mcc1 = c0->d.n_species > 1 ? c0->P.sp[1].mcc : 0;
+    const int m = b->mcc0 * 3 + b->mcc1;
+    if (m != 0 && m != 4 && m != 6)
+        return fail(PIC_EINVAL, "batch supports: no collisions, tables for both species, or constant-frequency electrons");
+    unsigned smem = 0;
+    std::vector<BatchItem> items;
+    std::vector<StepConst> consts(nc);
+    for (size_t i = 0; i < nc; ++i) {
+        pic_case *c = b->cases[i];
+        if (c->d.periodic != b->periodic || c->P.sp[0].mcc != b->mcc0 ||
+            (c->d.n_species > 1 ? c->P.sp[1].mcc : 0) != b->mcc1)
+            return fail(PIC_EINVAL, "batch cases differ in boundary or collision model");
+        for (int s = 0; s < c->d.n_species; ++s)
+            smem = std::max(smem, StepSmem(c->d.n_cells, c->P.sp[s].mcc == 1 ? c->P.sp[s].nproc : 0).total);
+        Ctrl h;
+        CU(cudaMemcpyAsync(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+        CU(cudaStreamSynchronize(b->stream));
+        for (int s = 0; s < c->d.n_species; ++s) {
+            const long long n = (long long)h.n_active[s];
+            const int nk = (int)std::max<long long>(1, (n + kItemParticles - 1) / kItemParticles);
+            for (int k = 0; k < nk; ++k) items.push_back(BatchItem{(int)i, s, k, nk});
+        }
+        consts[i] = c->P;
+    }
+    if (b->d_cases) cudaFree(b->d_cases);
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_cases = nullptr;
+    b->d_items = nullptr;
+    CU(cudaMalloc(&b->d_cases, nc * sizeof(StepConst)));
+    CU(cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem)));
+    CU(cudaMemcpyAsync(b->d_cases, consts.data(), nc * sizeof(StepConst), cudaMemcpyHostToDevice, b->stream));
+    CU(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, b->stream));
+    CU(cudaMemsetAsync(b->d_next, 0, sizeof(unsigned), b->stream));
+    CU(cudaStreamSynchronize(b->stream));
+    b->n_items = (int)items.size();
+    if (smem != b->smem) b->grid = 0;
+    b->smem = smem;
+    b->planned = true;
+    batch_drop_graph(b);
+    return PIC_OK;
+}
+
+pic_status batch_build_graph(pic_batch *b, int steps)
+{
+    batch_drop_graph(b);
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < steps && e == cudaSuccess; ++i) e = batch_one_step(b);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(PIC_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(PIC_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    b->graph_steps = steps;
+    return PIC_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+pic_status pic_batch_create(const pic_case_desc *descs, int n_cases, pic_batch **out)
+{
+    if (!descs || !out || n_cases < 1) return fail(PIC_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    for (int i = 1; i < n_cases; ++i)
+        if (descs[i].periodic != descs[0].periodic || descs[i].n_species != descs[0].n_species)
+            return fail(PIC_EINVAL, "batch cases must share the boundary kind and the number of species");
+    pic_batch *b = new pic_batch();
+    if (descs[0].stream) b->stream = (cudaStream_t)descs[0].stream;
+    else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return fail(PIC_ECUDA, "stream creation failed");
+        }
+        b->own_stream = true;
+    }
+    b->sort_k = descs[0].sort_interval > 0 ? descs[0].sort_interval : 64;
+    for (int i = 0; i < n_cases; ++i) {
+        pic_case_desc d = descs[i];
+        d.stream = b->stream;                       // every case on the batch stream
+        pic_case *c = nullptr;
+        pic_status st = pic_create_case(&d, &c);
+        if (st != PIC_OK) {
+            pic_batch_destroy(b);
+            return st;
+        }
+        b->cases.push_back(c);
+    }
+    if (cudaMalloc(&b->d_next, sizeof(unsigned)) != cudaSuccess) {
+        pic_batch_destroy(b);
+        return fail(PIC_ENOMEM, "batch counter allocation failed");
+    }
+    *out = b;
+    return PIC_OK;
+}
+
+pic_case *pic_batch_case(pic_batch *b, int i)
+{
+    if (!b || i < 0 || i >= (int)b->cases.size()) return nullptr;
+    b->planned = false;                              // the caller may load or change this case
+    return b->cases[(size_t)i];
+}
+
+pic_status pic_batch_step(pic_batch *b, int64_t n_steps)
+{
+    if (!b || n_steps < 0) return fail(PIC_EINVAL, "bad batch step arguments");
+    if (!b->planned) {
+        pic_status st = batch_plan(b);
+        if (st != PIC_OK) return st;
+    }
+    int64_t left = n_steps;
+    while (left > 0) {
+        const int K = b->sort_k;
+        const int G = std::min(kGraphSteps, K);
+        if (b->host_step > 0 && left >= G && b->steps_since_sort + G <= K) {
+            if (!b->graph || b->graph_steps != G) {
+                pic_status st = batch_build_graph(b, G);
+                if (st != PIC_OK) return st;
+            }
+            CU(cudaGraphLaunch(b->graph, b->stream));
+            b->launches += 2LL * G;
+            b->host_step += G;
+            b->steps_since_sort += G;
+            left -= G;
+        } else {
+            CU(batch_one_step(b));
+            b->launches += 2;
+            b->host_step++;
+            b->steps_since_sort++;
+            left--;
+        }
+        if (b->steps_since_sort >= K) {
+            for (pic_case *c : b->cases) CU(launch_sorts(c));
+            b->launches += 4LL * b->cases.size() * b->cases[0]->d.n_species;
+            b->steps_since_sort = 0;
+        }
+    }
+    return PIC_OK;
+}
+
+pic_status pic_batch_sync(pic_batch *b)
+{
+    if (!b) return fail(PIC_EINVAL, "null batch");
+    CU(cudaStreamSynchronize(b->stream));
+    for (pic_case *c : b->cases) {
+        pic_status st = device_error(c);
+        if (st != PIC_OK) return st;
+    }
+    return PIC_OK;
+}
+
+int64_t pic_batch_launches(const pic_batch *b) { return b ? b->launches : 0; }
+
+pic_status pic_batch_destroy(pic_batch *b)
+{
+    if (!b) return PIC_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    for (pic_case *c : b->cases) pic_destroy(c);
+    if (b->d_cases) cudaFree(b->d_cases);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_next) cudaFree(b->d_next);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
     return PIC_OK;
 }
 

@@ -85,6 +85,7 @@ struct StepConst {
     float *E32;                         // [n_cells + 1 padded]: periodic ghost at n_cells
     double *E, *phi;                    // [n_nodes]
     unsigned long long *R[2];           // [n_cells + 1] raw fixed-point deposit
+    unsigned long long *R_last;         // [2][n_nodes] deposit of the last solve (read-back)
     SpeciesBufs buf[2][2];              // [species][half]
     unsigned long long cap[2];
     Ctrl *ctrl;

@@ -97,11 +97,21 @@ def _load_library():
     lib.pic_deposit.argtypes = [i32, i32, i64, vp, vp, vp, vp]
     lib.pic_sort_by_cell.argtypes = [i32, i64] + [vp] * 12 + [vp, vp]
     lib.pic_sort_by_cell_noalloc.argtypes = [i32, i64] + [vp] * 12 + [vp, vp]
+    lib.pic_load_profile.argtypes = [vp, C.c_int, i64, dp, dp, dp, C.c_uint32]
+    lib.pic_batch_create.argtypes = [C.POINTER(CaseDesc), C.c_int, C.POINTER(vp)]
+    lib.pic_batch_case.restype = vp
+    lib.pic_batch_case.argtypes = [vp, C.c_int]
+    lib.pic_batch_step.argtypes = [vp, i64]
+    lib.pic_batch_sync.argtypes = [vp]
+    lib.pic_batch_launches.restype = i64
+    lib.pic_batch_launches.argtypes = [vp]
+    lib.pic_batch_destroy.argtypes = [vp]
     lib.pic_profile.argtypes = [vp, C.c_int]
     lib.pic_profile_read.argtypes = [vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]
     for f in ("pic_create_case", "pic_load_xsec_table", "pic_load_particles", "pic_step", "pic_sync", "pic_count",
               "pic_read_particles", "pic_read_field", "pic_read_moments", "pic_destroy", "pic_philox", "pic_deposit",
-              "pic_profile", "pic_profile_read", "pic_sort_by_cell", "pic_sort_by_cell_noalloc"):
+              "pic_profile", "pic_profile_read", "pic_sort_by_cell", "pic_sort_by_cell_noalloc",
+              "pic_load_profile", "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -211,6 +221,15 @@ def load_particles(h, species, cell, offset, vx, vy, vz, ids=None, on_device=Fal
     check(lib.pic_load_particles(h, species, n, *args, int(bool(on_device))))
 
 
+def load_profile(h, species, n, density, temp_ev, drift=(0.0, 0.0, 0.0), id_base=0):
+    d = np.ascontiguousarray(density, dtype=np.float64)
+    t = np.ascontiguousarray(temp_ev, dtype=np.float64)
+    dr = np.ascontiguousarray(drift, dtype=np.float64)
+    dp_ = C.POINTER(C.c_double)
+    check(lib.pic_load_profile(h, species, int(n), d.ctypes.data_as(dp_), t.ctypes.data_as(dp_),
+                               dr.ctypes.data_as(dp_), int(id_base) & 0xFFFFFFFF))
+
+
 def step(h, n_steps=1):
     check(lib.pic_step(h, int(n_steps)))
 
@@ -307,6 +326,48 @@ def sort_by_cell_noalloc(n_cells, src: dict, dst: dict, n_live_dev=None, stream=
                                        *[_ptr(dst[k]) for k in keys], _ptr(n_live_dev), stream))
 
 
+class Batch:
+    """Many independent cases stepped together (``pic_batch_*``).  ``cases[i]``
+    is a borrowed :class:`Case` view for per-case loads and reads."""
+
+    def __init__(self, cfgs, *, stream=None, sort_interval=0, capacities=None):
+        descs = (CaseDesc * len(cfgs))()
+        for i, cfg in enumerate(cfgs):
+            cap = capacities[i] if capacities is not None else (0, 0)
+            descs[i] = make_desc(cfg, stream=stream, capacity=cap, sort_interval=sort_interval)
+        h = C.c_void_p()
+        check(lib.pic_batch_create(descs, len(cfgs), C.byref(h)))
+        self.h = h.value
+        self.cases = []
+        for i, cfg in enumerate(cfgs):
+            v = Case.__new__(Case)
+            v._view(cfg, lib.pic_batch_case(self.h, i))
+            for t in cfg.get("xsec", []):
+                if t["species"] < v.n_species:
+                    load_xsec_table(v.h, t["species"], t["kind"], t["threshold"], t["energy"], t["sigma"])
+            self.cases.append(v)
+
+    def step(self, n=1):
+        check(lib.pic_batch_step(self.h, int(n)))
+
+    def sync(self):
+        check(lib.pic_batch_sync(self.h))
+
+    def launches(self):
+        return int(lib.pic_batch_launches(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            check(lib.pic_batch_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Case:
     """A case on the current CUDA device: ``Case(cfg, parts)`` creates it, loads
     its tables and particles; ``step(n)``; ``particles(sp)``; ``moments()``."""
@@ -328,6 +389,19 @@ class Case:
         if parts is not None:
             for s, p in enumerate(parts):
                 self.load(s, p)
+
+    def _view(self, cfg, handle):
+        """Borrowed handle of a case owned by a batch (never destroyed here)."""
+        self.cfg = cfg
+        self.n_cells = int(cfg["n_cells"])
+        self.periodic = bool(cfg["periodic"])
+        self.n_nodes = self.n_cells if self.periodic else self.n_cells + 1
+        self.n_species = len(cfg["species"])
+        self.h = handle
+        self._borrowed = True
+
+    def load_profile(self, sp, n, density, temp_ev, drift=(0.0, 0.0, 0.0), id_base=0):
+        load_profile(self.h, sp, n, density, temp_ev, drift, id_base)
 
     def load(self, sp, p, on_device=False):
         load_particles(self.h, sp, p["cell"], p["off"], p["vx"], p["vy"], p["vz"], p.get("id"), on_device)
@@ -357,9 +431,9 @@ class Case:
         return profile_read(self.h)
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and not getattr(self, "_borrowed", False):
             destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

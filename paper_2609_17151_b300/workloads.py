@@ -172,3 +172,35 @@ def ecdi_case(seed: int = 1, n_cells: int = 2048, ppc: int = 2500, length: float
         seed=seed, diag_interval=0,
     )
     return cfg, [e, i]
+
+
+def sweep_cases(n_cases: int = 256, seed: int = 2609, freq: float = 13.56e6, n0: float = 2e14):
+    """Parameter sweep of argon CCPs (uneven sizes): pressure 10-300 mTorr,
+    voltage 100-500 V, gap 2-6 cm, 256-2048 cells, 5e4-1e6 particles per
+    species, drawn with numpy's Philox bit generator.  Returns the case
+    descriptions and, per case, the particle count per species; the
+    particles themselves are sampled on the device (uniform density n0,
+    electrons 2 eV, ions at 300 K).  The drive is V0 sin(2 pi f t): it starts
+    at zero, so the plasma shields the electrodes as the voltage rises
+    instead of meeting the full vacuum field at t = 0."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    cfgs, counts = [], []
+    tables = argon_tables()
+    for i in range(n_cases):
+        mtorr = rng.uniform(10.0, 300.0)
+        volts = rng.uniform(100.0, 500.0)
+        gap = rng.uniform(0.02, 0.06)
+        n_cells = int(rng.integers(256, 2049))
+        n = int(rng.uniform(5e4, 1e6))
+        tg = 300.0
+        cfg = dict(
+            name=f"sweep_{i}", periodic=0, n_cells=n_cells, length=gap, dt=1.0 / (freq * 400),
+            gas_density=mtorr * 1e-3 * TORR / (K_B * tg), gas_temp=tg, gas_mass=M_AR,
+            harmonics=[(freq, volts, -0.5 * math.pi)], see_gamma=0.1, see_temp_ev=1.0,
+            species=[dict(q=-E_CHARGE, m=M_E, w=n0 * gap / n), dict(q=E_CHARGE, m=M_AR, w=n0 * gap / n)],
+            xsec=tables, seed=seed * 1000 + i, diag_interval=0,
+            load=dict(n=n, n0=n0, te_ev=2.0, ti_ev=K_B * tg / E_CHARGE),
+        )
+        cfgs.append(cfg)
+        counts.append(n)
+    return cfgs, counts

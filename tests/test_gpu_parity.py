@@ -300,3 +300,73 @@ def test_autotuned_sort_interval_and_graph_replay_leave_results_unchanged():
         for key in ("id", "cell", "off", "vx", "vy", "vz"):
             assert np.array_equal(pa[key][ia], pb[key][ib]), (s, key)
     a.close(); b.close()
+
+
+# --------------------------------------------------------------------------- loader and batch
+def test_profile_loader_matches_oracle():
+    """Particles sampled on the GPU from node profiles: same ids and cells
+    (the cell is an FP64 decision on both sides), offsets and velocities to
+    FP32 rounding."""
+    cfg, _ = small_ccp(seed=41, n=10)
+    n_nodes = cfg["n_cells"] + 1
+    x = np.linspace(0, 1, n_nodes)
+    dens = 1e15 * (0.2 + np.sin(np.pi * x) ** 2)
+    temp = 1.0 + 4.0 * x
+    oc = oracle.Case(cfg)
+    oc.load_profile(0, 150_001, dens, temp, drift=(3e4, 0, 0), id_base=7)
+    gc = pic.Case(cfg)
+    gc.load_profile(0, 150_001, dens, temp, drift=(3e4, 0, 0), id_base=7)
+    g, o = gc.particles(0), oc.particles(0)
+    ig, io = np.argsort(g["id"]), np.argsort(o["id"])
+    assert np.array_equal(g["id"][ig], o["id"][io])
+    assert np.array_equal(g["cell"][ig], np.floor(o["xi"][io]).astype(np.int32))
+    off_o = o["xi"][io] - np.floor(o["xi"][io])
+    assert np.abs(g["off"][ig] - off_o).max() < 2e-6
+    vg = np.stack([g["vx"][ig], g["vy"][ig], g["vz"][ig]], 1)
+    vo = np.stack([o["vx"][io], o["vy"][io], o["vz"][io]], 1)
+    assert (np.linalg.norm(vg - vo, axis=1) / np.linalg.norm(vo, axis=1)).max() < 2e-5
+    gc.close()
+
+
+def _sweep_cfgs(n_cases, seed=5):
+    rng = np.random.default_rng(seed)
+    cfgs = []
+    for i in range(n_cases):
+        n_cells = int(rng.integers(32, 200))
+        cfg, _ = W.ccp_case(seed=100 + i, n_cells=n_cells, gap=n_cells * 5e-5, n_per_species=10,
+                            mtorr=float(rng.uniform(10, 300)), volts=float(rng.uniform(100, 500)), te_ev=20.0)
+        cfg["sort_interval"] = 8
+        cfgs.append(cfg)
+    return cfgs
+
+
+def test_batch_equals_cases_stepped_alone():
+    """Heterogeneous argon cases (cells, gap, pressure, voltage, particle
+    counts differ) stepped in one batch give bit-identical particles and
+    fields to each case stepped on its own."""
+    cfgs = _sweep_cfgs(5)
+    counts = [3000, 70_000, 150_000, 9_000, 260_001]
+    b = pic.Batch(cfgs, sort_interval=8)
+    singles = []
+    for cfg, n, view in zip(cfgs, counts, b.cases):
+        nn = cfg["n_cells"] + 1
+        for sp, T in ((0, 20.0), (1, 400.0)):
+            view.load_profile(sp, n, np.full(nn, 2e14), np.full(nn, T), id_base=0)
+        c = pic.Case(cfg, sort_interval=8)
+        for sp, T in ((0, 20.0), (1, 400.0)):
+            c.load_profile(sp, n, np.full(nn, 2e14), np.full(nn, T), id_base=0)
+        singles.append(c)
+    b.step(21)
+    b.sync()
+    for c in singles:
+        c.step(21)
+    for view, c in zip(b.cases, singles):
+        for s in range(2):
+            pa, pb = view.particles(s), c.particles(s)
+            ia, ib = np.argsort(pa["id"], kind="stable"), np.argsort(pb["id"], kind="stable")
+            for key in ("id", "cell", "off", "vx", "vy", "vz"):
+                assert np.array_equal(pa[key][ia], pb[key][ib]), (s, key)
+        assert np.array_equal(view.field()[1], c.field()[1])
+        c.close()
+    assert b.launches() > 0
+    b.close()

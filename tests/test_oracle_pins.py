@@ -521,3 +521,53 @@ def test_sort_by_cell_is_the_stable_sort_dropping_absorbed():
         keep = np.flatnonzero((cell >= 0) & (cell < n_cells))
         ref = keep[np.argsort(cell[keep], kind="stable")]
         assert np.array_equal(perm, ref)
+
+
+# --------------------------------------------------------------------------- loader
+def _loader_case(n_cells=50, periodic=0, seed=33):
+    cfg = dict(periodic=periodic, n_cells=n_cells, length=n_cells * 1e-4, dt=1e-12, gas_density=0.0, gas_temp=300.0,
+               gas_mass=W.M_AR, species=[dict(q=-E, m=W.M_E, w=1.0), dict(q=E, m=W.M_AR, w=1.0)], seed=seed)
+    return cfg, oracle.Case(cfg)
+
+
+def test_loader_uniform_density_fills_cells_evenly():
+    """Uniform density: cell counts are multinomial with equal probabilities
+    (chi-square), offsets uniform, the ids id_base + k."""
+    from scipy.stats import chi2, kstest
+    n_cells, n = 50, 200_000
+    cfg, c = _loader_case(n_cells)
+    c.load_profile(0, n, np.full(n_cells + 1, 1e15), np.full(n_cells + 1, 2.0), id_base=1000)
+    p = c.particles(0)
+    assert np.array_equal(np.sort(p["id"]), 1000 + np.arange(n, dtype=np.uint32))
+    cnt = np.bincount(np.floor(p["xi"]).astype(int), minlength=n_cells)
+    stat = ((cnt - n / n_cells) ** 2 / (n / n_cells)).sum()
+    assert stat < chi2.ppf(0.9999, n_cells - 1)
+    assert kstest(p["xi"] - np.floor(p["xi"]), "uniform").pvalue > 1e-4
+
+
+def test_loader_linear_density_and_temperature():
+    """A density ramp: offsets inside a cell follow the linear density
+    a(1-d) + b d (KS test against its CDF); velocities are Maxwellian at the
+    interpolated temperature (<v_i^2> = kT/m) around the drift."""
+    from scipy.stats import kstest
+    n_cells, n = 4, 400_000
+    cfg, c = _loader_case(n_cells)
+    dens = np.array([1.0, 1.0, 3.0, 3.0, 3.0]) * 1e15
+    temp = np.full(n_cells + 1, 5.0)
+    drift = (1e5, 0.0, -2e5)
+    c.load_profile(0, n, dens, temp, drift=drift)
+    p = c.particles(0)
+    xi = p["xi"]
+    cell = np.floor(xi).astype(int)
+    d = xi[cell == 1] - 1.0
+    a, b = 1.0, 3.0
+    cdf = lambda x: (a * x + (b - a) * x * x / 2) / ((a + b) / 2)
+    assert kstest(d, cdf).pvalue > 1e-4
+    masses = np.array([1.0, 2.0, 3.0, 3.0]) / 9.0
+    frac = np.bincount(cell, minlength=n_cells) / n
+    assert np.all(np.abs(frac - masses) < 5 * np.sqrt(masses / n))
+    vt2 = 5.0 * E / W.M_E
+    for k, (comp, dr) in enumerate(zip(("vx", "vy", "vz"), drift)):
+        v = p[comp]
+        assert abs(v.mean() - dr) < 5 * np.sqrt(vt2 / n)
+        assert abs(v.var() / vt2 - 1) < 0.02
