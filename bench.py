@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--workload", default="exb", choices=["exb", "batch"],
                     help="exb: the 10.24M-particle E x B case (default); batch: the 256-case argon sweep")
     ap.add_argument("--cases", type=int, default=256)
+    ap.add_argument("--small", action="store_true", help="batch: 5e3-5e4 particles per species per case")
     return ap.parse_args()
 
 
@@ -166,7 +167,7 @@ def run_batch(args, torch):
     on their own, then each case replaying its own CUDA graph)."""
     from paper_2609_17151_b300 import pic
     from paper_2609_17151_b300 import workloads as W
-    cfgs, counts = W.sweep_cases(args.cases)
+    cfgs, counts = W.sweep_cases(args.cases, n_range=(5e3, 5e4) if args.small else (5e4, 1e6))
     stream = torch.cuda.Stream()
 
     def load(view, cfg):
@@ -230,7 +231,8 @@ def run_batch(args, torch):
         "metric": METRIC, "value": pps_b, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"argon_ccp_sweep_{args.cases}_cases", "particles": int(n0),
+        "config": {"workload": f"argon_ccp_sweep_{args.cases}_cases" + ("_small" if args.small else ""),
+                   "particles": int(n0),
                    "cells_range": [min(c["n_cells"] for c in cfgs), max(c["n_cells"] for c in cfgs)],
                    "sort_interval": 64, "parallelism": "batched cases, 1 GPU"},
         "batched_vs_one_launch_per_case": pps_b / pps_1,

@@ -60,15 +60,35 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, Ctrl *ctrl, un
     return false;
 }
 
-// nu_k(eps): linear in ln(eps) between the grid energies; zero below threshold.
-__device__ __forceinline__ float nu_at(const float *tab, float eps, float thr, float inv_dlog)
+// Position of eps on the table grid (linear in ln eps), computed once per
+// collision candidate and shared by every process's table.
+struct GridPos {
+    int i;
+    float t;
+};
+__device__ __forceinline__ GridPos grid_pos(float eps, float inv_dlog)
 {
-    if (eps < thr) return 0.0f;
     float s = logf(eps * (1.0f / kGridEmin)) * inv_dlog;
     s = fminf(fmaxf(s, 0.0f), (float)(kNGrid - 1));
-    int i = min((int)s, kNGrid - 2);
-    const float t = s - (float)i;
-    return (1.0f - t) * tab[i] + t * tab[i + 1];
+    const int i = min((int)s, kNGrid - 2);
+    return GridPos{i, s - (float)i};
+}
+// nu_k(eps) between the grid energies; zero below the process threshold
+__device__ __forceinline__ float nu_at(const float *tab, GridPos g, float eps, float thr)
+{
+    if (eps < thr) return 0.0f;
+    return (1.0f - g.t) * tab[g.i] + g.t * tab[g.i + 1];
+}
+
+// Event counts of one thread over a work item (registers; reduced per warp
+// and added to the case's counters once per item).
+struct EvCount {
+    unsigned cand, coll[kMaxProc], iz, absorbed[2], see;
+};
+__device__ __forceinline__ void count_proc(EvCount &ev, int proc)
+{
+#pragma unroll
+    for (int k = 0; k < kMaxProc; ++k) ev.coll[k] += (k == proc) ? 1u : 0u;
 }
 
 struct Cell { int c; float o; };
@@ -112,12 +132,12 @@ __device__ void append_particle(const StepConst &P, int sp, int half, int c, flo
 // (-1: no real collision) and updates v.
 __device__ __forceinline__ void collide_electron(const StepConst &P, const float *nus, uint32_t id, uint32_t step,
                                                  int c, float o, float3 &v, int half_e, int half_i, bool diag,
-                                                 unsigned *s_cnt)
+                                                 EvCount &ev)
 {
     const SpConst &S = P.sp[0];
     const uint4 r = draw(P, id, step, 0, kBlkMcc);
     if (u01(r.x) >= S.pnull) return;
-    atomicAdd(&s_cnt[0], 1u);
+    ev.cand++;
     const float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
     const float eps = S.m_over_2e * v2;
     const float x = u01(r.y) * S.numax;
@@ -126,14 +146,15 @@ __device__ __forceinline__ void collide_electron(const StepConst &P, const float
     if (S.mcc == 2) {
         proc = 0;
     } else {
+        const GridPos g = grid_pos(eps, P.inv_dlog);
         float cum = 0.0f;
         for (int k = 0; k < S.nproc; ++k) {
-            cum += nu_at(nus + k * kNGrid, eps, S.thr[k], P.inv_dlog);
+            cum += nu_at(nus + k * kNGrid, g, eps, S.thr[k]);
             if (x < cum) { proc = k; kind = S.kind[k]; thr = S.thr[k]; break; }
         }
         if (proc < 0) return;
     }
-    atomicAdd(&s_cnt[1 + proc], 1u);
+    count_proc(ev, proc);
     const float3 n = iso_dir(u01(r.z), u01(r.w));
     if (kind == 0) {                                    // elastic, atom at rest
         const float speed = sqrtf(v2);
@@ -162,17 +183,17 @@ __device__ __forceinline__ void collide_electron(const StepConst &P, const float
             const float vt = S.vt_newion;
             append_particle(P, 1, half_i, c, o, vt * g01.x, vt * g01.y, vt * g23.x, ids.y, diag);
         }
-        atomicAdd(&s_cnt[1 + kMaxProc], 1u);
+        ev.iz++;
     }
 }
 
 __device__ __forceinline__ void collide_ion(const StepConst &P, const float *nus, uint32_t id, uint32_t step,
-                                            float3 &v, unsigned *s_cnt)
+                                            float3 &v, EvCount &ev)
 {
     const SpConst &S = P.sp[1];
     const uint4 r = draw(P, id, step, 1, kBlkMcc);
     if (u01(r.x) >= S.pnull) return;
-    atomicAdd(&s_cnt[0], 1u);
+    ev.cand++;
     const uint4 a = draw(P, id, step, 1, kBlkAux);
     const float2 g01 = box_muller(u01(a.x), u01(a.y));
     const float2 g23 = box_muller(u01(a.z), u01(a.w));
@@ -181,14 +202,15 @@ __device__ __forceinline__ void collide_ion(const StepConst &P, const float *nus
     const float g2 = g.x * g.x + g.y * g.y + g.z * g.z;
     const float eps = S.mu_over_2e * g2;
     const float x = u01(r.y) * S.numax;
+    const GridPos gp = grid_pos(eps, P.inv_dlog);
     float cum = 0.0f;
     int proc = -1, kind = 3;
     for (int k = 0; k < S.nproc; ++k) {
-        cum += nu_at(nus + k * kNGrid, eps, S.thr[k], P.inv_dlog);
+        cum += nu_at(nus + k * kNGrid, gp, eps, S.thr[k]);
         if (x < cum) { proc = k; kind = S.kind[k]; break; }
     }
     if (proc < 0) return;
-    atomicAdd(&s_cnt[1 + proc], 1u);
+    count_proc(ev, proc);
     if (kind == 4) {                                    // charge exchange
         v = vg;
     } else {                                            // isotropic in the centre-of-mass frame
@@ -201,7 +223,7 @@ __device__ __forceinline__ void collide_ion(const StepConst &P, const float *nus
 
 // Secondary electron from an ion that reached electrode `wall`.
 __device__ __forceinline__ void emit_secondary(const StepConst &P, uint32_t id, uint32_t step, int wall, int half_e,
-                                               bool diag, unsigned *s_see)
+                                               bool diag, EvCount &ev)
 {
     const uint4 r = draw(P, id, step, 1, kBlkSee);
     if (u01(r.x) >= P.see_gamma) return;
@@ -226,7 +248,7 @@ __device__ __forceinline__ void emit_secondary(const StepConst &P, uint32_t id, 
     if (c >= N) { c = N - 1; o = 0.99999994f; }
     const float vx = wall == 0 ? vn : -vn;
     append_particle(P, 0, half_e, c, o, vx, P.see_vth * t.x, P.see_vth * t.y, ids.x, diag);
-    atomicAdd(s_see, 1u);
+    ev.see++;
 }
 
 // Shared deposit histogram, per cell: particle count n and the sum of the
@@ -343,6 +365,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     const float dtdx = P.dtdx;
     const int lane = tid & 31, warp = tid >> 5;
     float ke_acc = 0.0f, pw_acc = 0.0f;
+    EvCount ev{};
 
     // at most kFlushParticles per flush of the histogram (counter range)
     for (long long sub = beg; sub < end; sub += kFlushParticles / 4) {
@@ -402,16 +425,16 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             } else if ((unsigned)c >= (unsigned)N) {
                 // 4. electrode absorption (+ secondary emission by ions)
                 const int wall = c < 0 ? 0 : 1;
-                atomicAdd(&s_abs[wall], 1u);
-                if (SP == 1 && P.see_gamma > 0.0f) emit_secondary(P, ids[q], step, wall, half_e, diag, &sh.s_see);
+                ev.absorbed[wall]++;
+                if (SP == 1 && P.see_gamma > 0.0f) emit_secondary(P, ids[q], step, wall, half_e, diag, ev);
                 cc[q] = -1;
                 oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
                 continue;
             }
             // 5-6. null-collision MCC with v^{n+1/2} at x^{n+1}; products appended
             if (MCC != 0) {
-                if (SP == 0) collide_electron(P, nus, ids[q], step, c, on, v, half_e, half_i, diag, s_cnt);
-                else collide_ion(P, nus, ids[q], step, v, s_cnt);
+                if (SP == 0) collide_electron(P, nus, ids[q], step, c, on, v, half_e, half_i, diag, ev);
+                else collide_ion(P, nus, ids[q], step, v, ev);
             }
             cc[q] = c; oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
             dc[q] = c;
@@ -474,7 +497,20 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         }
     }
     }
-    // CTA epilogue: flush the histogram and counters
+    // CTA epilogue: event counts (warp sums, one shared atomic per warp), histogram
+    {
+        unsigned vals[2 + 2 * kMaxProc] = {ev.cand, ev.coll[0], ev.coll[1], ev.coll[2], ev.coll[3], ev.iz,
+                                           ev.absorbed[0], ev.absorbed[1], ev.see, 0u};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const unsigned w = __reduce_add_sync(0xffffffffu, vals[k]);
+            if (lane == 0 && w) {
+                if (k < 6) atomicAdd(&s_cnt[k], w);
+                else if (k < 8) atomicAdd(&s_abs[k - 6], w);
+                else atomicAdd(&sh.s_see, w);
+            }
+        }
+    }
     hist_flush(hist, N, P.R[SP]);
     if (diag) {
         const int nn = P.n_nodes;
@@ -528,6 +564,15 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_
     particle_item<SP, PERIODIC, MCC>(P, smem, sh, parity, blockIdx.x, gridDim.x);
 }
 
+// Out-of-line item for the batch kernel: each species' body keeps its own
+// register allocation instead of the union of both.
+template <int SP, bool PERIODIC, int MCC>
+__device__ __noinline__ void particle_item_call(const StepConst &P, unsigned char *smem, StepShared &sh,
+                                               unsigned &parity, long long k_item, long long n_items)
+{
+    particle_item<SP, PERIODIC, MCC>(P, smem, sh, parity, k_item, n_items);
+}
+
 // Many cases in one persistent launch: CTAs take (case, species, slice) work
 // items from an atomic counter (reset by the batched field solve).
 struct BatchItem {
@@ -535,16 +580,18 @@ struct BatchItem {
 };
 
 template <bool PERIODIC, int MCC0, int MCC1>
-__global__ void __launch_bounds__(kStepThreads, 2)
+__global__ void __launch_bounds__(kStepThreads, 1)
     k_batch_particle_step(const StepConst *__restrict__ cases, const BatchItem *__restrict__ items, int n_items,
                           unsigned *next_item)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ StepShared sh;
     __shared__ int s_item;
+    __shared__ StepConst sP;                            // the item's case constants (read like parameters)
     if (threadIdx.x == 0) mbar_init(&sh.mbar, 1);
     __syncthreads();
     unsigned parity = 0;
+    int cur_case = -1;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(next_item, 1u);
         __syncthreads();
@@ -552,8 +599,15 @@ __global__ void __launch_bounds__(kStepThreads, 2)
         __syncthreads();
         if (it >= n_items) break;
         const BatchItem w = items[it];
-        if (w.species == 0) particle_item<0, PERIODIC, MCC0>(cases[w.case_idx], smem, sh, parity, w.k, w.nk);
-        else particle_item<1, PERIODIC, MCC1>(cases[w.case_idx], smem, sh, parity, w.k, w.nk);
+        if (w.case_idx != cur_case) {                   // copy the case's constants into shared memory
+            const int *src = reinterpret_cast<const int *>(&cases[w.case_idx]);
+            int *dst = reinterpret_cast<int *>(&sP);
+            for (int j = threadIdx.x; j < (int)(sizeof(StepConst) / sizeof(int)); j += blockDim.x) dst[j] = src[j];
+            cur_case = w.case_idx;
+            __syncthreads();
+        }
+        if (w.species == 0) particle_item_call<0, PERIODIC, MCC0>(sP, smem, sh, parity, w.k, w.nk);
+        else particle_item_call<1, PERIODIC, MCC1>(sP, smem, sh, parity, w.k, w.nk);
     }
 }
 

@@ -211,13 +211,27 @@ pic_status upload_tables(pic_case *c, int sp)
     return PIC_OK;
 }
 
+// The dynamic shared-memory cap is a property of the kernel, shared by every
+// case: set it once to the largest layout any case can need.
+const unsigned kMaxStepSmem = StepSmem(4096, kMaxProc).total;
+
+// One flag per kernel instantiation (the caller is itself a template).
+template <typename K>
+cudaError_t allow_max_step_smem(K k, std::once_flag &once, cudaError_t &err)
+{
+    std::call_once(once, [&] { err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxStepSmem); });
+    return err;
+}
+
 template <int SP, bool PER, int MCC>
 cudaError_t launch_step_t(pic_case *c)
 {
     auto k = k_particle_step<SP, PER, MCC>;
     const unsigned smem = StepSmem(c->d.n_cells, MCC == 1 ? c->P.sp[SP].nproc : 0).total;
     if (c->step_smem[SP] != smem || c->step_grid[SP] == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        static std::once_flag once;
+        static cudaError_t attr_err = cudaSuccess;
+        cudaError_t e = allow_max_step_smem(k, once, attr_err);
         if (e != cudaSuccess) return e;
         int occ = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kStepThreads, smem);
@@ -1102,7 +1116,9 @@ cudaError_t batch_step_t(pic_batch *b)
 {
     auto k = k_batch_particle_step<PER, M0, M1>;
     if (b->grid == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+        static std::once_flag once;
+        static cudaError_t attr_err = cudaSuccess;
+        cudaError_t e = allow_max_step_smem(k, once, attr_err);
         if (e != cudaSuccess) return e;
         int occ = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kStepThreads, b->smem);

@@ -174,7 +174,8 @@ def ecdi_case(seed: int = 1, n_cells: int = 2048, ppc: int = 2500, length: float
     return cfg, [e, i]
 
 
-def sweep_cases(n_cases: int = 256, seed: int = 2609, freq: float = 13.56e6, n0: float = 2e14):
+def sweep_cases(n_cases: int = 256, seed: int = 2609, freq: float = 13.56e6, n0: float = 2e14,
+                n_range=(5e4, 1e6)):
     """Parameter sweep of argon CCPs (uneven sizes): pressure 10-300 mTorr,
     voltage 100-500 V, gap 2-6 cm, 256-2048 cells, 5e4-1e6 particles per
     species, drawn with numpy's Philox bit generator.  Returns the case
@@ -191,7 +192,7 @@ def sweep_cases(n_cases: int = 256, seed: int = 2609, freq: float = 13.56e6, n0:
         volts = rng.uniform(100.0, 500.0)
         gap = rng.uniform(0.02, 0.06)
         n_cells = int(rng.integers(256, 2049))
-        n = int(rng.uniform(5e4, 1e6))
+        n = int(rng.uniform(*n_range))
         tg = 300.0
         cfg = dict(
             name=f"sweep_{i}", periodic=0, n_cells=n_cells, length=gap, dt=1.0 / (freq * 400),

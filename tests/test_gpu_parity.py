@@ -370,3 +370,23 @@ def test_batch_equals_cases_stepped_alone():
         c.close()
     assert b.launches() > 0
     b.close()
+
+
+def test_cases_of_different_sizes_interleave():
+    """Cases with different shared-memory layouts stepped in turn (the kernel's
+    dynamic shared-memory cap is shared by all of them)."""
+    big, _ = small_ccp(seed=51, n=5, n_cells=1500)
+    small, _ = small_ccp(seed=52, n=5, n_cells=40)
+    cs = []
+    for cfg in (big, small, big):
+        c = pic.Case(cfg)
+        nn = cfg["n_cells"] + 1
+        for sp in (0, 1):
+            c.load_profile(sp, 20_000, np.full(nn, 2e14), np.full(nn, 3.0))
+        cs.append(c)
+    for _ in range(3):
+        for c in cs:
+            c.step(1)
+    for c in cs:
+        c.sync()
+        c.close()
