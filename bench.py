@@ -41,8 +41,14 @@ def parse():
     ap.add_argument("--sort-interval", type=int, default=0, help="0 = the library's autotuner")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="exb", choices=["exb", "batch"],
-                    help="exb: the 10.24M-particle E x B case (default); batch: the 256-case argon sweep")
+    ap.add_argument("--workload", default="exb", choices=["exb", "batch", "warmstart"],
+                    help="exb: the 10.24M-particle E x B case (default); batch: the 256-case argon sweep; "
+                         "warmstart: RF cycles to steady state, cold start vs the learned warm start")
+    ap.add_argument("--train", type=int, default=64)
+    ap.add_argument("--test", type=int, default=16)
+    ap.add_argument("--max-cycles", type=int, default=1500)
+    ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--pilot", action="store_true")
     ap.add_argument("--cases", type=int, default=256)
     ap.add_argument("--small", action="store_true", help="batch: 5e3-5e4 particles per species per case")
     return ap.parse_args()
@@ -243,6 +249,123 @@ def run_batch(args, torch):
     }), flush=True)
 
 
+# --------------------------------------------------------------------------- learned warm start
+N_POINTS = 128          # profile points predicted by the network
+STEPS_PER_CYCLE = 400
+WINDOW = 10             # cycles per averaging window
+LAG = 10                # windows between the compared averages (100 cycles)
+
+
+def profiles_on_points(m, n_nodes):
+    """ne, ni, Te (eV) averaged over the window, at N_POINTS points on [0, L]."""
+    xs = np.linspace(0, n_nodes - 1, N_POINTS)
+    nodes = np.arange(n_nodes)
+    ne = m["dens_sum"][0] / max(m["n_steps"], 1)
+    ni = m["dens_sum"][1] / max(m["n_steps"], 1)
+    dd = m["dens_diag_sum"][0]
+    te = np.where(dd > 0, (2.0 / 3.0) * m["en_sum"][0] / np.maximum(dd, 1e-300), 0.0)
+    return (np.interp(xs, nodes, ne), np.interp(xs, nodes, ni), np.interp(xs, nodes, te))
+
+
+def run_to_steady_state(batch, max_cycles, log=None):
+    """Step a batch in windows of WINDOW cycles; a case reaches steady state at
+    the first window whose coarse (32-point) ion density differs from the one
+    LAG windows earlier by less than 1 % (relative L2)."""
+    n = len(batch.cases)
+    hist = [[] for _ in range(n)]
+    done = [None] * n
+    last = [None] * n
+    cycles = 0
+    while cycles < max_cycles and any(d is None for d in done):
+        batch.step(WINDOW * STEPS_PER_CYCLE)
+        cycles += WINDOW
+        for i, v in enumerate(batch.cases):
+            m = v.moments(reset=True)
+            prof = profiles_on_points(m, v.n_nodes)
+            last[i] = prof
+            coarse = prof[1].reshape(32, -1).mean(1)
+            hist[i].append(coarse)
+            if done[i] is None and len(hist[i]) > LAG:
+                ref = hist[i][-1 - LAG]
+                if np.linalg.norm(coarse - ref) < 0.01 * np.linalg.norm(coarse):
+                    done[i] = cycles
+        batch.replan()
+        if log:
+            log(cycles, done)
+    return done, last
+
+
+def run_warmstart(args, torch):
+    from paper_2609_17151_b300 import pic
+    from paper_2609_17151_b300 import workloads as W
+    n_train, n_test = (4, 4) if args.pilot else (args.train, args.test)
+    max_cycles = 60 if args.pilot else args.max_cycles
+    cfg_tr, par_tr = W.dual_frequency_family(n_train, seed=4)
+    cfg_te, par_te = W.dual_frequency_family(n_test, seed=5)
+    cfgs = cfg_tr + cfg_te
+    cap = (1_000_000, 1_000_000)
+    t0 = time.perf_counter()
+
+    def cold_load(v, cfg):
+        nn = cfg["n_cells"] + 1
+        L = cfg["load"]
+        v.load_profile(0, L["n"], np.full(nn, L["n0"]), np.full(nn, L["te_ev"]))
+        v.load_profile(1, L["n"], np.full(nn, L["n0"]), np.full(nn, L["ti_ev"]))
+
+    cold = pic.Batch(cfgs, sort_interval=64, capacities=[cap] * len(cfgs))
+    for v, cfg in zip(cold.cases, cfgs):
+        cold_load(v, cfg)
+    progress = []
+    cold_done, cold_prof = run_to_steady_state(
+        cold, max_cycles, log=lambda c, d: progress.append((c, sum(x is not None for x in d), [sum(v.count()) for v in cold.cases[:4]])))
+    t_cold = time.perf_counter() - t0
+    cold.close()
+    if args.pilot:
+        print(json.dumps({"pilot": True, "seconds": t_cold, "progress": progress[-6:]}), flush=True)
+        return
+    # training set: converged training cases
+    ok = [i for i in range(n_train) if cold_done[i] is not None]
+    X = par_tr[ok].astype(np.float32)
+    Y = np.stack([np.concatenate([np.log10(np.maximum(cold_prof[i][0], 1e6)), np.log10(np.maximum(cold_prof[i][1], 1e6)),
+                                  cold_prof[i][2]]) for i in ok]).astype(np.float32)
+    net = pic.MLP(4, 256, 3 * N_POINTS, seed=7)
+    lo, hi = np.array([10.0, 50.0, 50.0, 0.0]), np.array([100.0, 300.0, 300.0, 0.5 * np.pi])
+    net.set_normalization(lo, hi, Y.mean(0), Y.std(0) + 1e-3)
+    t1 = time.perf_counter()
+    curve = net.train(X, Y, epochs=args.epochs, lr=1e-3)
+    t_train = time.perf_counter() - t1
+    # warm start of the held-out cases
+    t2 = time.perf_counter()
+    warm = pic.Batch(cfg_te, sort_interval=64, capacities=[cap] * len(cfg_te))
+    for v, prm in zip(warm.cases, par_te):
+        v.warmstart_load(net, prm, N_POINTS, cfg_te[0]["load"]["ti_ev"], max_per_species=cap[0] // 2)
+    warm_done, warm_prof = run_to_steady_state(warm, max_cycles)
+    t_warm = time.perf_counter() - t2
+    warm.close()
+    net.close()
+    res = []
+    for j in range(n_test):
+        i = n_train + j
+        ref = cold_prof[i][1]
+        err = float(np.linalg.norm(warm_prof[j][1] - ref) / np.linalg.norm(ref))
+        res.append({"params": par_te[j].tolist(), "cold_cycles": cold_done[i], "warm_cycles": warm_done[j],
+                    "final_ni_rel_l2_diff": err})
+    both = [r for r in res if r["cold_cycles"] and r["warm_cycles"]]
+    ratio = float(np.mean([r["cold_cycles"] / r["warm_cycles"] for r in both])) if both else None
+    print(json.dumps({
+        "metric": "RF cycles to steady state, cold start / learned warm start (mean over held-out cases)",
+        "value": ratio, "unit": "ratio", "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": "dual_frequency_argon_ccp_family", "n_cells": cfg_te[0]["n_cells"], "gap_m": 0.03,
+                   "train_cases": n_train, "train_converged": len(ok), "test_cases": n_test,
+                   "criterion": "32-point ion density, 10-cycle averages 100 cycles apart, relative L2 < 1%",
+                   "max_cycles": max_cycles, "network": "4-256-256-384 GELU, BF16 tensor-core products",
+                   "epochs": args.epochs},
+        "train_loss_first_last": [float(curve[0]), float(curve[-1])],
+        "seconds": {"cold_runs": t_cold, "training": t_train, "warm_runs": t_warm},
+        "cases": res,
+    }), flush=True)
+
+
 # --------------------------------------------------------------------------- GPU leg
 def main():
     args = parse()
@@ -261,6 +384,10 @@ def main():
     if args.workload == "batch":
         if rank == 0:
             run_batch(args, torch)
+        return
+    if args.workload == "warmstart":
+        if rank == 0:
+            run_warmstart(args, torch)
         return
     from paper_2609_17151_b300 import pic
     from paper_2609_17151_b300 import workloads as W

@@ -279,6 +279,48 @@ pic_status pic_batch_sync(pic_batch *b);
 int64_t pic_batch_launches(const pic_batch *b);
 pic_status pic_batch_destroy(pic_batch *b);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start (a network that maps a case's parameters to initial
+ * profiles, so that a run starts near its steady state): a 3-layer MLP
+ * n_in -> n_hidden (GELU) -> n_hidden (GELU) -> n_out, trained and evaluated
+ * on the GPU.  Every product takes BF16-rounded operands on the tensor cores
+ * (mma m16n8k16) with FP32 accumulation; master weights, gradients and Adam
+ * moments are FP32.  Inputs are scaled to [-1, 1] by [in_lo, in_hi], outputs
+ * standardised by (out_mean, out_sd); the loss is the mean squared error of
+ * the standardised outputs.  Parameters are packed W1 (n_in x n_hidden,
+ * row-major), b1, W2, b2, W3, b3.  Host arrays are row-major, n rows.
+ * ------------------------------------------------------------------------- */
+typedef struct pic_mlp pic_mlp;
+/* Glorot-uniform weights from `seed`, zero biases, identity normalisation. */
+pic_status pic_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, pic_mlp **out);
+pic_status pic_mlp_set_normalization(pic_mlp *m, const float *in_lo, const float *in_hi,
+                                     const float *out_mean, const float *out_sd);
+int64_t pic_mlp_param_count(const pic_mlp *m);
+pic_status pic_mlp_get_params(pic_mlp *m, float *params);
+pic_status pic_mlp_set_params(pic_mlp *m, const float *params);   /* also clears the Adam state */
+/* Loss and its gradient (packed like the parameters) on n samples. */
+pic_status pic_mlp_gradients(pic_mlp *m, const float *X, const float *Y, int n, float *grads, float *loss);
+/* `epochs` full-batch Adam steps (lr; beta 0.9, 0.999; eps 1e-8); loss_curve
+ * (may be NULL) receives the loss before each step. */
+pic_status pic_mlp_train(pic_mlp *m, const float *X, const float *Y, int n, int epochs, float lr,
+                         float *loss_curve);
+/* Outputs in physical units (normalisation undone). */
+pic_status pic_mlp_predict(pic_mlp *m, const float *X, int n, float *Y);
+pic_status pic_mlp_destroy(pic_mlp *m);
+/* Warm start of a case from the network: predict, for the n_params case
+ * parameters, the profiles [log10 n_e (m^-3), log10 n_i (m^-3), T_e (eV)] at
+ * n_points points spanning [0, L] (n_out = 3 n_points), interpolate them
+ * linearly to the nodes, and load each species with pic_load_profile:
+ * count = integral of its density / its weight (capped at max_per_species when
+ * that is > 0), electrons at the predicted T_e, ions at ion_temp_ev. */
+pic_status pic_warmstart_load(pic_case *c, pic_mlp *m, const double *params, int n_params, int n_points,
+                              double ion_temp_ev, uint32_t id_base, int64_t max_per_species);
+/* The tensor-core product the MLP uses, on device FP32 arrays:
+ * C(i,j) = sum_k A(i,k) B(k,j), A(i,k) = A[i*ar + k*ac], B(k,j) = B[k*br + j*bc],
+ * C row-major with leading dimension ldc; operands rounded to BF16. */
+pic_status pic_gemm_bf16(const float *A, int ar, int ac, const float *B, int br, int bc, float *C, int ldc,
+                         int M, int N, int K, void *stream);
+
 /* Allocation-free variant of pic_sort_by_cell.  The paper has no counterpart:
  * this entry point exists for callers that must not allocate device memory
  * while they run (a fixed device-memory budget set at start-up, a plug-in

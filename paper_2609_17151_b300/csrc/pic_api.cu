@@ -798,6 +798,40 @@ pic_status pic_load_profile(pic_case *c, int sp, int64_t n, const double *densit
     return load_finish(c, sp, n, h);
 }
 
+pic_status pic_warmstart_load(pic_case *c, pic_mlp *m, const double *params, int n_params, int n_points,
+                              double ion_temp_ev, uint32_t id_base, int64_t max_per_species)
+{
+    if (!c || !m || !params || n_params < 1 || n_points < 2 || !(ion_temp_ev >= 0) || max_per_species < 0)
+        return fail(PIC_EINVAL, "bad warm-start arguments");
+    std::vector<float> x((size_t)n_params), y((size_t)3 * n_points);
+    for (int k = 0; k < n_params; ++k) x[(size_t)k] = (float)params[k];
+    pic_status st = pic_mlp_predict(m, x.data(), 1, y.data());
+    if (st != PIC_OK) return st;
+    const int N = c->d.n_cells, nn = c->n_nodes;
+    std::vector<double> ne(nn), ni(nn), te(nn), ti(nn, ion_temp_ev);
+    for (int i = 0; i < nn; ++i) {                      // the predicted points span [0, L] uniformly
+        const double s = (double)i / N * (n_points - 1);
+        const int k = std::min((int)s, n_points - 2);
+        const double t = s - k;
+        auto lerp = [&](int base) { return (1 - t) * y[(size_t)(base + k)] + t * y[(size_t)(base + k + 1)]; };
+        ne[i] = std::pow(10.0, lerp(0));
+        ni[i] = std::pow(10.0, lerp(n_points));
+        te[i] = std::max(0.0, lerp(2 * n_points));
+    }
+    const double dx = c->P.dx;
+    int64_t n_s[2] = {0, 0};
+    for (int s = 0; s < c->d.n_species && s < 2; ++s) {
+        const std::vector<double> &d = s == 0 ? ne : ni;
+        double integral = 0;                             // particles per area, trapezoid over the cells
+        for (int j = 0; j < N; ++j) integral += 0.5 * (d[j] + d[(c->d.periodic && j + 1 == N) ? 0 : j + 1]) * dx;
+        n_s[s] = (int64_t)std::llround(integral / c->d.weight_per_m2[s]);
+        if (max_per_species > 0) n_s[s] = std::min(n_s[s], max_per_species);
+    }
+    st = pic_load_profile(c, 0, n_s[0], ne.data(), te.data(), nullptr, id_base);
+    if (st != PIC_OK || c->d.n_species < 2) return st;
+    return pic_load_profile(c, 1, n_s[1], ni.data(), ti.data(), nullptr, id_base);
+}
+
 pic_status pic_step(pic_case *c, int64_t n_steps)
 {
     if (!c || n_steps < 0) return fail(PIC_EINVAL, "bad step arguments");

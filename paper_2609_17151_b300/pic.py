@@ -106,12 +106,28 @@ def _load_library():
     lib.pic_batch_launches.restype = i64
     lib.pic_batch_launches.argtypes = [vp]
     lib.pic_batch_destroy.argtypes = [vp]
+    fp = C.POINTER(C.c_float)
+    lib.pic_mlp_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(vp)]
+    lib.pic_mlp_set_normalization.argtypes = [vp, fp, fp, fp, fp]
+    lib.pic_mlp_param_count.restype = i64
+    lib.pic_mlp_param_count.argtypes = [vp]
+    lib.pic_mlp_get_params.argtypes = [vp, fp]
+    lib.pic_mlp_set_params.argtypes = [vp, fp]
+    lib.pic_mlp_gradients.argtypes = [vp, fp, fp, C.c_int, fp, fp]
+    lib.pic_mlp_train.argtypes = [vp, fp, fp, C.c_int, C.c_int, C.c_float, fp]
+    lib.pic_mlp_predict.argtypes = [vp, fp, C.c_int, fp]
+    lib.pic_mlp_destroy.argtypes = [vp]
+    lib.pic_gemm_bf16.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+    lib.pic_warmstart_load.argtypes = [vp, vp, dp, C.c_int, C.c_int, C.c_double, C.c_uint32, i64]
     lib.pic_profile.argtypes = [vp, C.c_int]
     lib.pic_profile_read.argtypes = [vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]
     for f in ("pic_create_case", "pic_load_xsec_table", "pic_load_particles", "pic_step", "pic_sync", "pic_count",
               "pic_read_particles", "pic_read_field", "pic_read_moments", "pic_destroy", "pic_philox", "pic_deposit",
               "pic_profile", "pic_profile_read", "pic_sort_by_cell", "pic_sort_by_cell_noalloc",
-              "pic_load_profile", "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy"):
+              "pic_load_profile", "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy",
+              "pic_mlp_create", "pic_mlp_set_normalization", "pic_mlp_get_params", "pic_mlp_set_params",
+              "pic_mlp_gradients", "pic_mlp_train", "pic_mlp_predict", "pic_mlp_destroy", "pic_gemm_bf16",
+              "pic_warmstart_load"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -326,6 +342,69 @@ def sort_by_cell_noalloc(n_cells, src: dict, dst: dict, n_live_dev=None, stream=
                                        *[_ptr(dst[k]) for k in keys], _ptr(n_live_dev), stream))
 
 
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class MLP:
+    """The warm-start network (``pic_mlp_*``): 3 layers, BF16 tensor-core products."""
+
+    def __init__(self, n_in, n_hidden, n_out, seed=0):
+        h = C.c_void_p()
+        check(lib.pic_mlp_create(n_in, n_hidden, n_out, int(seed), C.byref(h)))
+        self.h = h.value
+        self.n_in, self.n_hidden, self.n_out = n_in, n_hidden, n_out
+
+    def set_normalization(self, in_lo, in_hi, out_mean, out_sd):
+        arrs = [_f32(a) for a in (in_lo, in_hi, out_mean, out_sd)]
+        check(lib.pic_mlp_set_normalization(self.h, *[p for _, p in arrs]))
+
+    def params(self):
+        out = np.zeros(int(lib.pic_mlp_param_count(self.h)), np.float32)
+        check(lib.pic_mlp_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
+    def set_params(self, p):
+        a, ptr = _f32(p)
+        check(lib.pic_mlp_set_params(self.h, ptr))
+
+    def gradients(self, X, Y):
+        X, px = _f32(X); Y, py = _f32(Y)
+        g = np.zeros(int(lib.pic_mlp_param_count(self.h)), np.float32)
+        loss = C.c_float()
+        check(lib.pic_mlp_gradients(self.h, px, py, X.shape[0], g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)))
+        return float(loss.value), g
+
+    def train(self, X, Y, epochs, lr=1e-3, record=True):
+        X, px = _f32(X); Y, py = _f32(Y)
+        curve = np.zeros(epochs, np.float32)
+        check(lib.pic_mlp_train(self.h, px, py, X.shape[0], int(epochs), float(lr),
+                                curve.ctypes.data_as(C.POINTER(C.c_float)) if record else None))
+        return curve
+
+    def predict(self, X):
+        X, px = _f32(X)
+        Y = np.zeros((X.shape[0], self.n_out), np.float32)
+        check(lib.pic_mlp_predict(self.h, px, X.shape[0], Y.ctypes.data_as(C.POINTER(C.c_float))))
+        return Y
+
+    def close(self):
+        if getattr(self, "h", None):
+            check(lib.pic_mlp_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gemm_bf16(A, ar, ac, B, br, bc, Cm, ldc, M, N, K, stream=None):
+    check(lib.pic_gemm_bf16(_ptr(A), ar, ac, _ptr(B), br, bc, _ptr(Cm), ldc, M, N, K, stream))
+
+
 class Batch:
     """Many independent cases stepped together (``pic_batch_*``).  ``cases[i]``
     is a borrowed :class:`Case` view for per-case loads and reads."""
@@ -355,6 +434,10 @@ class Batch:
 
     def launches(self):
         return int(lib.pic_batch_launches(self.h))
+
+    def replan(self):
+        """Re-split the work items from the current particle counts before the next step."""
+        lib.pic_batch_case(self.h, 0)
 
     def close(self):
         if getattr(self, "h", None):
@@ -402,6 +485,11 @@ class Case:
 
     def load_profile(self, sp, n, density, temp_ev, drift=(0.0, 0.0, 0.0), id_base=0):
         load_profile(self.h, sp, n, density, temp_ev, drift, id_base)
+
+    def warmstart_load(self, mlp, params, n_points, ion_temp_ev, id_base=0, max_per_species=0):
+        prm = np.ascontiguousarray(params, dtype=np.float64)
+        check(lib.pic_warmstart_load(self.h, mlp.h, prm.ctypes.data_as(C.POINTER(C.c_double)), prm.size,
+                                     int(n_points), float(ion_temp_ev), int(id_base), int(max_per_species)))
 
     def load(self, sp, p, on_device=False):
         load_particles(self.h, sp, p["cell"], p["off"], p["vx"], p["vy"], p["vz"], p.get("id"), on_device)

@@ -205,3 +205,30 @@ def sweep_cases(n_cases: int = 256, seed: int = 2609, freq: float = 13.56e6, n0:
         cfgs.append(cfg)
         counts.append(n)
     return cfgs, counts
+
+
+def dual_frequency_family(n_cases: int, seed: int, n_cells: int = 256, gap: float = 0.03, n0: float = 1e14,
+                          n_init: int = 5000, freq: float = 13.56e6):
+    """Dual-frequency argon CCPs, V(t) = V1 cos(2 pi f t + theta) + V2 cos(4 pi f t)
+    (the two-harmonic waveform of the paper's §3.3), drawn with numpy's Philox:
+    p in [10, 100] mTorr, V1, V2 in [50, 300] V, theta in [0, 90 deg], 3 cm gap.
+    Returns (cfgs, params) with params[i] = (p_mTorr, V1, V2, theta)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    tables = argon_tables()
+    cfgs, params = [], []
+    tg = 300.0
+    w = n0 * gap / n_init
+    for i in range(n_cases):
+        mtorr = rng.uniform(10.0, 100.0)
+        v1, v2 = rng.uniform(50.0, 300.0), rng.uniform(50.0, 300.0)
+        theta = rng.uniform(0.0, 0.5 * math.pi)
+        cfgs.append(dict(
+            name=f"dual_freq_{seed}_{i}", periodic=0, n_cells=n_cells, length=gap, dt=1.0 / (freq * 400),
+            gas_density=mtorr * 1e-3 * TORR / (K_B * tg), gas_temp=tg, gas_mass=M_AR,
+            harmonics=[(freq, v1, theta), (2 * freq, v2, 0.0)], see_gamma=0.1, see_temp_ev=1.0,
+            species=[dict(q=-E_CHARGE, m=M_E, w=w), dict(q=E_CHARGE, m=M_AR, w=w)],
+            xsec=tables, seed=seed * 1000 + i, diag_interval=8,
+            load=dict(n=n_init, n0=n0, te_ev=2.0, ti_ev=K_B * tg / E_CHARGE),
+        ))
+        params.append((mtorr, v1, v2, theta))
+    return cfgs, np.array(params)

@@ -571,3 +571,30 @@ def test_loader_linear_density_and_temperature():
         v = p[comp]
         assert abs(v.mean() - dr) < 5 * np.sqrt(vt2 / n)
         assert abs(v.var() / vt2 - 1) < 0.02
+
+
+# --------------------------------------------------------------------------- MLP
+def test_mlp_gradient_matches_finite_differences():
+    """The oracle's backward pass against central differences of its loss
+    (FP64): a transposed product or a wrong GELU derivative fails."""
+    from oracle import mlp
+    rng = np.random.default_rng(8)
+    n_in, h, n_out, n = 4, 12, 9, 7
+    p = mlp.pack([rng.normal(0, 0.5, s) for s in mlp.sizes(n_in, h, n_out)])
+    X = rng.uniform(-1, 1, (n, n_in))
+    T = rng.normal(0, 1, (n, n_out))
+    loss, g = mlp.loss_and_grad(p, X, T, n_in, h, n_out)
+    idx = rng.choice(p.size, 60, replace=False)
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = 1e-6
+        fd = (mlp.loss_and_grad(p + e, X, T, n_in, h, n_out)[0] - mlp.loss_and_grad(p - e, X, T, n_in, h, n_out)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-8, (i, fd, g[i])
+
+
+def test_mlp_gelu_limits():
+    from oracle import mlp
+    x = np.array([-30.0, -1.0, 0.0, 1.0, 30.0])
+    y = mlp.gelu(x)
+    assert y[2] == 0.0 and abs(y[0]) < 1e-12 and abs(y[4] - 30.0) < 1e-12
+    assert abs(y[3] - 0.8413447460685429) < 1e-14          # Phi(1)
