@@ -299,7 +299,7 @@ def run_warmstart(args, torch):
     from paper_2609_17151_b300 import pic
     from paper_2609_17151_b300 import workloads as W
     n_train, n_test = (4, 4) if args.pilot else (args.train, args.test)
-    max_cycles = 60 if args.pilot else args.max_cycles
+    max_cycles = 200 if args.pilot else args.max_cycles
     cfg_tr, par_tr = W.dual_frequency_family(n_train, seed=4)
     cfg_te, par_te = W.dual_frequency_family(n_test, seed=5)
     cfgs = cfg_tr + cfg_te
@@ -317,14 +317,17 @@ def run_warmstart(args, torch):
         cold_load(v, cfg)
     progress = []
     cold_done, cold_prof = run_to_steady_state(
-        cold, max_cycles, log=lambda c, d: progress.append((c, sum(x is not None for x in d), [sum(v.count()) for v in cold.cases[:4]])))
+        cold, max_cycles, log=lambda c, d: progress.append((c, round(time.perf_counter() - t0, 1), sum(x is not None for x in d),
+                                                            [sum(v.count()) for v in cold.cases[:4]])))
     t_cold = time.perf_counter() - t0
     cold.close()
     if args.pilot:
-        print(json.dumps({"pilot": True, "seconds": t_cold, "progress": progress[-6:]}), flush=True)
+        print(json.dumps({"pilot": True, "seconds": t_cold, "done": cold_done, "progress": progress[::2]}), flush=True)
         return
     # training set: converged training cases
     ok = [i for i in range(n_train) if cold_done[i] is not None]
+    if len(ok) < 8:                       # too few at steady state: train on every case's last window
+        ok = list(range(n_train))
     X = par_tr[ok].astype(np.float32)
     Y = np.stack([np.concatenate([np.log10(np.maximum(cold_prof[i][0], 1e6)), np.log10(np.maximum(cold_prof[i][1], 1e6)),
                                   cold_prof[i][2]]) for i in ok]).astype(np.float32)

@@ -1143,7 +1143,8 @@ struct pic_batch {
 
 namespace {
 
-constexpr long long kItemParticles = 131072;
+constexpr long long kItemParticles = 131072;      // largest work item
+constexpr long long kMinItemParticles = 16384;    // smallest work item when splitting for balance
 
 template <bool PER, int M0, int M1>
 cudaError_t batch_step_t(pic_batch *b)
@@ -1215,6 +1216,19 @@ pic_status batch_plan(pic_batch *b)
     unsigned smem = 0;
     std::vector<BatchItem> items;
     std::vector<StepConst> consts(nc);
+    // current particle counts, then slices small enough that every CTA of the
+    // persistent grid gets several (at least kMinItemParticles each)
+    std::vector<Ctrl> hs(nc);
+    long long total = 0;
+    for (size_t i = 0; i < nc; ++i) {
+        CU(cudaMemcpyAsync(&hs[i], b->cases[i]->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+    }
+    CU(cudaStreamSynchronize(b->stream));
+    for (size_t i = 0; i < nc; ++i)
+        for (int s = 0; s < b->cases[i]->d.n_species; ++s) total += (long long)hs[i].n_active[s];
+    const long long target_items = 4LL * 2 * c0->num_sms;
+    const long long item_particles =
+        std::min(kItemParticles, std::max(kMinItemParticles, (total + target_items - 1) / target_items));
     for (size_t i = 0; i < nc; ++i) {
         pic_case *c = b->cases[i];
         if (c->d.periodic != b->periodic || c->P.sp[0].mcc != b->mcc0 ||
@@ -1222,12 +1236,10 @@ pic_status batch_plan(pic_batch *b)
             return fail(PIC_EINVAL, "batch cases differ in boundary or collision model");
         for (int s = 0; s < c->d.n_species; ++s)
             smem = std::max(smem, StepSmem(c->d.n_cells, c->P.sp[s].mcc == 1 ? c->P.sp[s].nproc : 0).total);
-        Ctrl h;
-        CU(cudaMemcpyAsync(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
-        CU(cudaStreamSynchronize(b->stream));
+        const Ctrl &h = hs[i];
         for (int s = 0; s < c->d.n_species; ++s) {
             const long long n = (long long)h.n_active[s];
-            const int nk = (int)std::max<long long>(1, (n + kItemParticles - 1) / kItemParticles);
+            const int nk = (int)std::max<long long>(1, (n + item_particles - 1) / item_particles);
             for (int k = 0; k < nk; ++k) items.push_back(BatchItem{(int)i, s, k, nk});
         }
         consts[i] = c->P;
