@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s on 1 B300 + % HBM roofline; batched & warm-start vs plain"
 UNIT = "particle-steps/s"
 ALGO_BYTES = 40          # per particle-step: cell, offset, vx, vy, vz read and written (4 B each)
+AUTOTUNE_STEPS = 51      # first step + the library autotuner's 50 (sort interval, launch shape)
 
 
 def parse():
@@ -267,14 +268,16 @@ def profiles_on_points(m, n_nodes):
     return (np.interp(xs, nodes, ne), np.interp(xs, nodes, ni), np.interp(xs, nodes, te))
 
 
-def run_to_steady_state(batch, max_cycles, log=None):
+def run_to_steady_state(batch, max_cycles, log=None, every=100):
     """Step a batch in windows of WINDOW cycles; a case reaches steady state at
     the first window whose coarse (32-point) ion density differs from the one
-    LAG windows earlier by less than 1 % (relative L2)."""
+    LAG windows earlier by less than 1 % (relative L2).  `log(cycles, done,
+    change, counts)` is called every `every` cycles."""
     n = len(batch.cases)
     hist = [[] for _ in range(n)]
     done = [None] * n
     last = [None] * n
+    change = [None] * n
     cycles = 0
     while cycles < max_cycles and any(d is None for d in done):
         batch.step(WINDOW * STEPS_PER_CYCLE)
@@ -285,13 +288,14 @@ def run_to_steady_state(batch, max_cycles, log=None):
             last[i] = prof
             coarse = prof[1].reshape(32, -1).mean(1)
             hist[i].append(coarse)
-            if done[i] is None and len(hist[i]) > LAG:
+            if len(hist[i]) > LAG:
                 ref = hist[i][-1 - LAG]
-                if np.linalg.norm(coarse - ref) < 0.01 * np.linalg.norm(coarse):
+                change[i] = float(np.linalg.norm(coarse - ref) / max(np.linalg.norm(coarse), 1e-300))
+                if done[i] is None and change[i] < 0.01:
                     done[i] = cycles
         batch.replan()
-        if log:
-            log(cycles, done)
+        if log and cycles % every == 0:
+            log(cycles, done, change, [int(sum(v.count())) for v in batch.cases])
     return done, last
 
 
@@ -299,12 +303,22 @@ def run_warmstart(args, torch):
     from paper_2609_17151_b300 import pic
     from paper_2609_17151_b300 import workloads as W
     n_train, n_test = (4, 4) if args.pilot else (args.train, args.test)
-    max_cycles = 200 if args.pilot else args.max_cycles
+    max_cycles = args.max_cycles
     cfg_tr, par_tr = W.dual_frequency_family(n_train, seed=4)
     cfg_te, par_te = W.dual_frequency_family(n_test, seed=5)
     cfgs = cfg_tr + cfg_te
-    cap = (1_000_000, 1_000_000)
+    cap = (2_000_000, 2_000_000)
     t0 = time.perf_counter()
+
+    def emit(obj):
+        print(json.dumps(obj), flush=True)
+
+    def progress(phase):
+        def log(c, done, change, counts):
+            emit({"phase": phase, "cycles": c, "seconds": round(time.perf_counter() - t0, 1),
+                  "n_done": sum(x is not None for x in done),
+                  "change": [None if x is None else round(x, 4) for x in change], "particles": counts})
+        return log
 
     def cold_load(v, cfg):
         nn = cfg["n_cells"] + 1
@@ -315,14 +329,11 @@ def run_warmstart(args, torch):
     cold = pic.Batch(cfgs, sort_interval=64, capacities=[cap] * len(cfgs))
     for v, cfg in zip(cold.cases, cfgs):
         cold_load(v, cfg)
-    progress = []
-    cold_done, cold_prof = run_to_steady_state(
-        cold, max_cycles, log=lambda c, d: progress.append((c, round(time.perf_counter() - t0, 1), sum(x is not None for x in d),
-                                                            [sum(v.count()) for v in cold.cases[:4]])))
+    cold_done, cold_prof = run_to_steady_state(cold, max_cycles, log=progress("cold"))
     t_cold = time.perf_counter() - t0
     cold.close()
+    emit({"phase": "cold_done", "seconds": round(t_cold, 1), "done": cold_done})
     if args.pilot:
-        print(json.dumps({"pilot": True, "seconds": t_cold, "done": cold_done, "progress": progress[::2]}), flush=True)
         return
     # training set: converged training cases
     ok = [i for i in range(n_train) if cold_done[i] is not None]
@@ -337,12 +348,14 @@ def run_warmstart(args, torch):
     t1 = time.perf_counter()
     curve = net.train(X, Y, epochs=args.epochs, lr=1e-3)
     t_train = time.perf_counter() - t1
+    emit({"phase": "trained", "seconds": round(t_train, 2), "loss_first_last": [float(curve[0]), float(curve[-1])]})
     # warm start of the held-out cases
     t2 = time.perf_counter()
     warm = pic.Batch(cfg_te, sort_interval=64, capacities=[cap] * len(cfg_te))
     for v, prm in zip(warm.cases, par_te):
         v.warmstart_load(net, prm, N_POINTS, cfg_te[0]["load"]["ti_ev"], max_per_species=cap[0] // 2)
-    warm_done, warm_prof = run_to_steady_state(warm, max_cycles)
+    emit({"phase": "warm_loaded", "particles": [int(sum(v.count())) for v in warm.cases]})
+    warm_done, warm_prof = run_to_steady_state(warm, max_cycles, log=progress("warm"))
     t_warm = time.perf_counter() - t2
     warm.close()
     net.close()
@@ -355,7 +368,7 @@ def run_warmstart(args, torch):
                     "final_ni_rel_l2_diff": err})
     both = [r for r in res if r["cold_cycles"] and r["warm_cycles"]]
     ratio = float(np.mean([r["cold_cycles"] / r["warm_cycles"] for r in both])) if both else None
-    print(json.dumps({
+    emit({
         "metric": "RF cycles to steady state, cold start / learned warm start (mean over held-out cases)",
         "value": ratio, "unit": "ratio", "higher_is_better": True, "data": "synthetic",
         "config": {"workload": "dual_frequency_argon_ccp_family", "n_cells": cfg_te[0]["n_cells"], "gap_m": 0.03,
@@ -366,7 +379,7 @@ def run_warmstart(args, torch):
         "train_loss_first_last": [float(curve[0]), float(curve[-1])],
         "seconds": {"cold_runs": t_cold, "training": t_train, "warm_runs": t_warm},
         "cases": res,
-    }), flush=True)
+    })
 
 
 # --------------------------------------------------------------------------- GPU leg
@@ -399,6 +412,9 @@ def main():
     n_particles = sum(p["id"].size for p in parts)
     stream = torch.cuda.Stream()
     case = pic.Case(cfg, parts, stream=stream.cuda_stream, sort_interval=args.sort_interval)
+    tune_steps = AUTOTUNE_STEPS if args.sort_interval == 0 else 0
+    if tune_steps:                        # the library's autotuner runs before the warm-up, untimed
+        case.step(tune_steps)
     case.step(max(3, args.warmup))
     case.sync()
 
@@ -430,7 +446,7 @@ def main():
     barrier()
     prof = case.profile_read()
     case.profile(False)
-    sort_k = case.moments()["sort_interval"]
+    tuning = case.tuning()
     n2 = sum(case.count())
     clk = clocks.stop()
     ms_t = torch.tensor([ms], device="cuda")
@@ -486,8 +502,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(args.ppc), "n_cells": 2048, "particles": n_particles,
-                       "particles_per_rank": n_particles, "dt_s": cfg["dt"], "sort_interval": sort_k,
+                       "particles_per_rank": n_particles, "dt_s": cfg["dt"],
+                       "sort_interval": list(tuning["sort_interval"]),
+                       "step_kernel_shape": {"threads": list(tuning["threads"]),
+                                             "tile_stages": list(tuning["stages"]),
+                                             "grid": list(tuning["grid"])},
                        "sort_interval_source": "autotuner" if args.sort_interval == 0 else "fixed",
+                       "autotune_steps_before_warmup": tune_steps,
                        "field": "f64 Poisson + field", "l2": "inputs larger than L2 (particle state "
                        f"{24 * n_particles / 1e6:.0f} MB)", "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

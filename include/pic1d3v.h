@@ -139,11 +139,14 @@ pic_status pic_load_profile(pic_case *c, int species, int64_t n, const double *d
 /* Enqueue n_steps time steps (paper §1 scheme; step order in the design
  * notes) on the case stream.  Returns after enqueueing; steps are replayed
  * from a CUDA graph of up to 16 steps when no sort falls inside it.  With
- * desc.sort_interval = 0, the first call that has 32 steps to run after the
- * first step times one sort and 32 steps (this call then synchronises once)
- * and picks the sort interval K minimising (sort time)/K + mean step time;
- * the choice is kept per case shape for the process and, if the environment
- * variable PIC1D3V_TUNE_CACHE names a file, in that file.  Errors:
+ * desc.sort_interval = 0, the first call that has 50 steps to run after the
+ * first step runs them as the autotuner (this call then synchronises once):
+ * one sort and 32 steps that fit the growth of the step time, giving per
+ * species the sort interval K minimising (sort time)/K + mean step time,
+ * then 18 steps that time six launch shapes of the step kernel per species
+ * (see pic_read_tuning).  The choice is kept per case shape for the process and,
+ * if the environment variable PIC1D3V_TUNE_CACHE names a file, in that file
+ * (one line per shape: key K0 K1 threads0 stages0 threads1 stages1).  Errors:
  * PIC_ESTATE (no particles loaded), PIC_ECUDA (launch failure). */
 pic_status pic_step(pic_case *c, int64_t n_steps);
 
@@ -196,6 +199,41 @@ typedef struct {
 } pic_moments;
 
 pic_status pic_read_moments(pic_case *c, pic_moments *out);
+
+/* Launch configuration in use, per species, and what the autotuner measured
+ * (no counterpart in the paper: a property of this implementation).  With
+ * desc.sort_interval = 0 the autotuner picks, per species, the sort interval
+ * and the step kernel's launch shape: CTA size (256, 512 or 1024 threads)
+ * and particle tiles in flight through shared memory (0 = each thread loads
+ * its own particles; 1 or 2 = bulk-copy pipeline); otherwise (1024, 0) and
+ * desc.sort_interval stand.  shape_ms[s][k] is the mean step-kernel time of
+ * candidate k = (1024,0), (512,0), (256,0), (1024,1), (512,1), (512,2); sort_ms
+ * the time of one sort; slope_ms the fitted growth of the step-kernel time
+ * per step since the last sort (all zero until the autotuner has run, and
+ * when its choice came from the cache).  `stages` reports the buffers in use
+ * (fewer than chosen when shared memory is short).  Does not synchronise.
+ * Errors: PIC_EINVAL (NULL argument or struct_size mismatch). */
+typedef struct {
+    uint32_t struct_size;          /* in: sizeof(pic_tuning) */
+    int32_t tuned;                 /* 1 once the autotuner (or its cache) has chosen */
+    int32_t sort_interval[2];
+    int32_t threads[2];
+    int32_t stages[2];
+    int32_t grid[2];               /* CTAs of the last step launch (0 before the first step) */
+    float shape_ms[2][6];
+    float sort_ms[2];
+    float slope_ms[2];
+} pic_tuning;
+
+pic_status pic_read_tuning(pic_case *c, pic_tuning *out);
+
+/* Set the step kernel's launch shape for one species by hand (no counterpart
+ * in the paper): threads = 256, 512 or 1024 per CTA, stages = particle tiles in
+ * flight through shared memory, 0 (each thread loads its own particles) to
+ * 4 (fewer are used when shared memory is short).  Results do not depend on
+ * the shape.  With desc.sort_interval = 0 an autotuner that has not run yet
+ * still chooses later.  Errors: PIC_EINVAL (bad species, threads or stages). */
+pic_status pic_set_step_shape(pic_case *c, int species, int threads, int stages);
 
 /* Free everything the case owns.  Safe on NULL. */
 pic_status pic_destroy(pic_case *c);
@@ -277,6 +315,11 @@ pic_status pic_batch_step(pic_batch *b, int64_t n_steps);
 pic_status pic_batch_sync(pic_batch *b);
 /* Kernel launches the batch has enqueued (for launch accounting). */
 int64_t pic_batch_launches(const pic_batch *b);
+/* Particle tiles the batch's step kernel keeps in flight through shared
+ * memory (0 = each thread loads its own particles, the default; 1-4 = bulk
+ * copies; fewer are used when shared memory is short).  Takes effect at the
+ * next pic_batch_step; results do not depend on it.  Errors: PIC_EINVAL. */
+pic_status pic_batch_set_stages(pic_batch *b, int stages);
 pic_status pic_batch_destroy(pic_batch *b);
 
 /* ---------------------------------------------------------------------------

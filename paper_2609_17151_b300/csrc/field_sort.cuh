@@ -165,8 +165,13 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
     const bool real = own && i < nn;
     if (real) {
         for (int s = 0; s < ns; ++s) {
-            r[s] = P.R[s][i];
-            if (P.periodic && i == 0) r[s] += P.R[s][N];
+            unsigned long long v[kDepositCopies];
+#pragma unroll
+            for (int k = 0; k < kDepositCopies; ++k) v[k] = P.R[s][k * P.r_stride + i];
+#pragma unroll
+            for (int k = 0; k < kDepositCopies; ++k) r[s] += v[k];
+            if (P.periodic && i == 0)
+                for (int k = 0; k < kDepositCopies; ++k) r[s] += P.R[s][k * P.r_stride + N];
             if (mode == 1) {
                 rs[s] = P.Rsum[s * nn + i];
                 if (diag) rd[s] = P.Rdiag[s * nn + i];
@@ -274,10 +279,12 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
     }
     cl.barrier_arrive();                                          // done reading the other slices
     __syncthreads();
-    if (real)
-        for (int s = 0; s < ns; ++s) P.R[s][i] = 0ull;             // every rank has read R
+    if (real)                                                     // every rank has read R
+        for (int s = 0; s < ns; ++s)
+            for (int k = 0; k < kDepositCopies; ++k) P.R[s][k * P.r_stride + i] = 0ull;
     if (own && i == N)
-        for (int s = 0; s < ns; ++s) P.R[s][N] = 0ull;
+        for (int s = 0; s < ns; ++s)
+            for (int k = 0; k < kDepositCopies; ++k) P.R[s][k * P.r_stride + N] = 0ull;
     const double b = g_b, d0 = g_d0, pm = g_pm, phi0 = g_phi0;
     const double cq0 = P.cq[0], cq1 = ns > 1 ? P.cq[1] : 0.0;
     // 4. S_i once per node (P_s[i] = O_s + p_s[i]); slot 0 holds S_{c_lo - 1} (P = O_s)

@@ -107,8 +107,9 @@ __device__ void append_particle(const StepConst &P, int sp, int half, int c, flo
     const SpeciesBufs &B = P.buf[sp][half];
     B.cell[slot] = c; B.off[slot] = o; B.vx[slot] = vx; B.vy[slot] = vy; B.vz[slot] = vz; B.id[slot] = id;
     const uint32_t f = __float2uint_rz(o * 4294967296.0f);
-    atomicAdd(&P.R[sp][c], (1ull << 32) - f);
-    atomicAdd(&P.R[sp][c + 1], (unsigned long long)f);
+    unsigned long long *R = P.R[sp] + (size_t)(blockIdx.x % kDepositCopies) * P.r_stride;
+    atomicAdd(&R[c], (1ull << 32) - f);
+    atomicAdd(&R[c + 1], (unsigned long long)f);
     if (diag) {
         const SpConst &S = P.sp[sp];
         const float v2 = vx * vx + vy * vy + vz * vz;
@@ -284,24 +285,39 @@ __device__ __forceinline__ void hist_flush(const DepHist &h, int N, unsigned lon
     __syncthreads();
 }
 
-// Shared memory layout of the step kernel (bytes, 16-aligned pieces).
+// Shared memory layout of the step kernel (bytes, 16-aligned pieces).  With
+// `stages` > 0 the particle tiles (one 4-particle chunk per thread, `narr`
+// arrays of 16 bytes per chunk) pass through `stages` buffers at the end.
 __host__ __device__ inline unsigned align16(unsigned x) { return (x + 15u) & ~15u; }
+__host__ __device__ inline unsigned align128(unsigned x) { return (x + 127u) & ~127u; }
 struct StepSmem {
-    unsigned e_off, h_off, nu_off, en_off, eepf_off, total;
-    __host__ __device__ StepSmem(int n_cells, int nproc)
+    unsigned e_off, h_off, nu_off, en_off, eepf_off, st_off, st_bytes, total;
+    __host__ __device__ StepSmem(int n_cells, int nproc, int threads = 0, int stages = 0, int narr = 0)
     {
         e_off = 0;
         h_off = align16(e_off + (unsigned)(n_cells + 1) * 4u);
         nu_off = align16(h_off + (unsigned)n_cells * 12u);
         en_off = align16(nu_off + (unsigned)nproc * kNGrid * 4u);
         eepf_off = align16(en_off + (unsigned)(n_cells + 1) * 4u);
-        total = align16(eepf_off + kEepfBins * 4u);
+        st_off = align128(eepf_off + kEepfBins * 4u);
+        st_bytes = (unsigned)threads * 16u * (unsigned)narr;      // one stage
+        total = stages > 0 ? st_off + (unsigned)stages * st_bytes : align16(eepf_off + kEepfBins * 4u);
     }
 };
+
+// Particle arrays a species' step reads: cell, off, vx, vy, vz, and id when
+// it draws random numbers (MCC, or secondary emission by ions).
+__host__ __device__ constexpr int step_arrays(int sp, bool periodic, int mcc)
+{
+    return (mcc != 0 || (sp == 1 && !periodic)) ? 6 : 5;
+}
 
 // Per-CTA shared state of the particle step besides the dynamic tables.
 struct StepShared {
     uint64_t mbar;                                      // staging barrier (phase toggles per item)
+    uint64_t full[kMaxStages];                          // particle-tile barriers (phase toggles per use)
+    unsigned tile_rel[kMaxStages];                      // warps done reading each buffer (running count)
+    unsigned tile_abort;                                // a tile wait gave up: stop streaming
     unsigned s_cnt[2 + 2 * kMaxProc];                   // candidates, per process, ionizations
     unsigned s_abs[2], s_see;
     float s_red[2][kStepThreads / 32];
@@ -310,14 +326,25 @@ struct StepShared {
 // One work item: chunks (4 particles) [beg, end) of the k-th of nk equal
 // slices of species SP of one case.  Stages the case's node field and the
 // species' table, processes the slice, flushes the deposit, the moments and
-// the counters.  `parity` is the staging barrier's phase, toggled per item.
-template <int SP, bool PERIODIC, int MCC>
+// the counters.  `parity` is the staging barrier's phase, toggled per item;
+// bit s of `tile_phase` is the phase of tile buffer s.
+//
+// The slice is processed in tiles of one chunk per thread.  Without STAGED
+// each thread loads its chunk from global memory itself; with STAGED and
+// S.stages = n > 0, n tiles stay in flight as bulk copies (global ->
+// shared, completion on a per-buffer mbarrier), so that HBM streams while
+// the warps compute, and the warps read their chunk from shared memory.
+// Results are written straight back to global memory.
+template <int SP, bool PERIODIC, int MCC, bool STAGED>
 __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char *smem, StepShared &sh,
-                                              unsigned &parity, long long k_item, long long n_items)
+                                              unsigned &parity, unsigned &tile_phase, long long k_item,
+                                              long long n_items)
 {
     const SpConst &S = P.sp[SP];
     const int N = P.n_cells;
-    const StepSmem L(N, MCC == 1 ? S.nproc : 0);
+    constexpr int kArr = step_arrays(SP, PERIODIC, MCC);
+    const int n_stages = STAGED ? S.stages : 0;
+    const StepSmem L(N, MCC == 1 ? S.nproc : 0, blockDim.x, n_stages, kArr);
     float *Es = reinterpret_cast<float *>(smem + L.e_off);
     const DepHist hist{reinterpret_cast<unsigned *>(smem + L.h_off), reinterpret_cast<unsigned *>(smem + L.h_off) + N,
                        reinterpret_cast<unsigned *>(smem + L.h_off) + 2 * N};
@@ -356,6 +383,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     const bool staged = mbar_wait_bounded(&sh.mbar, ctrl, parity);
     parity ^= 1u;
     if (!__syncthreads_and(staged)) return;
+    if (n_stages > 0 && sh.tile_abort) return;          // this CTA gave up on its tiles earlier
 
     const int half = ctrl->cur[SP];
     const int half_e = ctrl->cur[0];
@@ -367,24 +395,81 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     float ke_acc = 0.0f, pw_acc = 0.0f;
     EvCount ev{};
 
-    // at most kFlushParticles per flush of the histogram (counter range)
-    for (long long sub = beg; sub < end; sub += kFlushParticles / 4) {
-    const long long sub_end = min(sub + kFlushParticles / 4, end);
-    if (sub > beg) hist_flush(hist, N, P.R[SP]);
-    for (long long base = sub + warp * 32; base < sub_end; base += blockDim.x) {
-        const long long ch = base + lane;
-        const bool live_chunk = ch < sub_end;
+    unsigned long long *const R_cta = P.R[SP] + (size_t)(blockIdx.x % kDepositCopies) * P.r_stride;
+    const int T = blockDim.x;                           // chunks per tile
+    const int n_warps = T >> 5;
+    const int n_tiles = (int)((end - beg + T - 1) / T);
+    const int tiles_per_flush = max(1, (kFlushParticles / 4) / T);   // histogram counter range
+    unsigned char *const tiles = smem + L.st_off;
+    // tile k -> buffer b = k mod n_stages: one bulk copy per array, one mbarrier per buffer
+    auto issue_tile = [&](int k, int b) {
+        const long long c0 = beg + (long long)k * T;
+        const unsigned bytes = (unsigned)min((long long)T, end - c0) * 16u;
+        const void *src[6] = {B.cell, B.off, B.vx, B.vy, B.vz, B.id};
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // earlier reads of the buffer first
+        mbar_expect_tx(&sh.full[b], bytes * kArr);
+#pragma unroll
+        for (int a = 0; a < kArr; ++a)
+            bulk_g2s(tiles + ((size_t)(b * kArr + a) * T) * 16u, reinterpret_cast<const char *>(src[a]) + c0 * 16,
+                     bytes, &sh.full[b]);
+    };
+    if (n_stages > 0 && tid == 0)
+        for (int k = 0; k < n_tiles && k < n_stages; ++k) issue_tile(k, k);
+
+    int flush_left = tiles_per_flush, b = 0;
+    for (int k = 0; k < n_tiles; ++k) {
+        if (flush_left == 0) {
+            hist_flush(hist, N, R_cta);
+            flush_left = tiles_per_flush;
+        }
+        --flush_left;
+        const long long ch = beg + (long long)k * T + tid;
+        bool live_chunk = ch < end;
+        if (n_stages > 0) {
+            // skip the wait once any warp of the CTA has given up on a tile
+            const bool ok = !sh.tile_abort && mbar_wait_bounded(&sh.full[b], ctrl, (tile_phase >> b) & 1u);
+            tile_phase ^= 1u << b;
+            if (!ok) sh.tile_abort = 1u;
+            live_chunk = live_chunk && ok;
+        }
         const long long i0 = ch * 4;
         int4 c4 = make_int4(-1, -1, -1, -1);
         float4 o4 = make_float4(0, 0, 0, 0), x4 = o4, y4 = o4, z4 = o4;
         uint4 id4 = make_uint4(0, 0, 0, 0);
         if (live_chunk) {
-            c4 = *reinterpret_cast<const int4 *>(B.cell + i0);
-            o4 = *reinterpret_cast<const float4 *>(B.off + i0);
-            x4 = *reinterpret_cast<const float4 *>(B.vx + i0);
-            y4 = *reinterpret_cast<const float4 *>(B.vy + i0);
-            z4 = *reinterpret_cast<const float4 *>(B.vz + i0);
-            if (MCC != 0 || (SP == 1 && !PERIODIC)) id4 = *reinterpret_cast<const uint4 *>(B.id + i0);
+            if (n_stages > 0) {
+                const unsigned char *t = tiles + ((size_t)b * kArr * T + tid) * 16u;
+                const size_t stride = (size_t)T * 16u;
+                c4 = *reinterpret_cast<const int4 *>(t);
+                o4 = *reinterpret_cast<const float4 *>(t + stride);
+                x4 = *reinterpret_cast<const float4 *>(t + 2 * stride);
+                y4 = *reinterpret_cast<const float4 *>(t + 3 * stride);
+                z4 = *reinterpret_cast<const float4 *>(t + 4 * stride);
+                if (kArr == 6) id4 = *reinterpret_cast<const uint4 *>(t + 5 * stride);
+            } else {
+                c4 = *reinterpret_cast<const int4 *>(B.cell + i0);
+                o4 = *reinterpret_cast<const float4 *>(B.off + i0);
+                x4 = *reinterpret_cast<const float4 *>(B.vx + i0);
+                y4 = *reinterpret_cast<const float4 *>(B.vy + i0);
+                z4 = *reinterpret_cast<const float4 *>(B.vz + i0);
+                if (kArr == 6) id4 = *reinterpret_cast<const uint4 *>(B.id + i0);
+            }
+        }
+        if (n_stages > 0) {
+            // Release buffer b: the last warp of the CTA to have read its
+            // chunk of tile k refills it with tile k + n_stages (per-buffer
+            // arrival counter; block fences order every warp's reads before
+            // the bulk copy, which fence.proxy.async hands to the async proxy).
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                const unsigned arrived = atomicAdd(&sh.tile_rel[b], 1u) + 1u;
+                if (arrived % (unsigned)n_warps == 0u && !sh.tile_abort) {
+                    __threadfence_block();
+                    if (k + n_stages < n_tiles) issue_tile(k + n_stages, b);
+                }
+            }
+            b = (b + 1 == n_stages) ? 0 : b + 1;
         }
         int cc[4] = {c4.x, c4.y, c4.z, c4.w};
         float oo[4] = {o4.x, o4.y, o4.z, o4.w};
@@ -496,6 +581,16 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             hist_run(hist, acc_c, acc_n, acc_f);
         }
     }
+    if (n_stages > 0) {
+        __syncthreads();
+        if (sh.tile_abort) {
+            // a tile never arrived (kErrTimeout raised): the item is abandoned
+            // and the CTA streams no more tiles; wait, bounded, for every
+            // buffer's last copy once
+            if (tid == 0)
+                for (int j = 0; j < n_stages; ++j) mbar_wait_bounded(&sh.full[j], ctrl, (tile_phase >> j) & 1u);
+            return;
+        }
     }
     // CTA epilogue: event counts (warp sums, one shared atomic per warp), histogram
     {
@@ -511,7 +606,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             }
         }
     }
-    hist_flush(hist, N, P.R[SP]);
+    hist_flush(hist, N, R_cta);
     if (diag) {
         const int nn = P.n_nodes;
         for (int j = tid; j <= N; j += blockDim.x) {
@@ -553,24 +648,31 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
 }
 
 // One case: CTA b takes the b-th of gridDim.x slices of the species.
-template <int SP, bool PERIODIC, int MCC>
-__global__ void __launch_bounds__(kStepThreads, 2) k_particle_step(const __grid_constant__ StepConst P)
+template <int SP, bool PERIODIC, int MCC, bool STAGED>
+// launch bounds: up to 1024 threads, 64 registers (two 512-thread or four
+// 256-thread CTAs per SM when shared memory allows)
+__global__ void __launch_bounds__(kStepThreads, 1) k_particle_step(const __grid_constant__ StepConst P)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ StepShared sh;
-    if (threadIdx.x == 0) mbar_init(&sh.mbar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(&sh.mbar, 1);
+        for (int b = 0; b < kMaxStages; ++b) { mbar_init(&sh.full[b], 1); sh.tile_rel[b] = 0u; }
+        sh.tile_abort = 0u;
+    }
     __syncthreads();
-    unsigned parity = 0;
-    particle_item<SP, PERIODIC, MCC>(P, smem, sh, parity, blockIdx.x, gridDim.x);
+    unsigned parity = 0, tile_phase = 0;
+    particle_item<SP, PERIODIC, MCC, STAGED>(P, smem, sh, parity, tile_phase, blockIdx.x, gridDim.x);
 }
 
 // Out-of-line item for the batch kernel: each species' body keeps its own
 // register allocation instead of the union of both.
-template <int SP, bool PERIODIC, int MCC>
+template <int SP, bool PERIODIC, int MCC, bool STAGED>
 __device__ __noinline__ void particle_item_call(const StepConst &P, unsigned char *smem, StepShared &sh,
-                                               unsigned &parity, long long k_item, long long n_items)
+                                               unsigned &parity, unsigned &tile_phase, long long k_item,
+                                               long long n_items)
 {
-    particle_item<SP, PERIODIC, MCC>(P, smem, sh, parity, k_item, n_items);
+    particle_item<SP, PERIODIC, MCC, STAGED>(P, smem, sh, parity, tile_phase, k_item, n_items);
 }
 
 // Many cases in one persistent launch: CTAs take (case, species, slice) work
@@ -579,18 +681,22 @@ struct BatchItem {
     int case_idx, species, k, nk;
 };
 
-template <bool PERIODIC, int MCC0, int MCC1>
-__global__ void __launch_bounds__(kStepThreads, 1)
+template <bool PERIODIC, int MCC0, int MCC1, bool STAGED>
+__global__ void __launch_bounds__(kBatchThreads, 1)
     k_batch_particle_step(const StepConst *__restrict__ cases, const BatchItem *__restrict__ items, int n_items,
                           unsigned *next_item)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ StepShared sh;
     __shared__ int s_item;
     __shared__ StepConst sP;                            // the item's case constants (read like parameters)
-    if (threadIdx.x == 0) mbar_init(&sh.mbar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(&sh.mbar, 1);
+        for (int b = 0; b < kMaxStages; ++b) { mbar_init(&sh.full[b], 1); sh.tile_rel[b] = 0u; }
+        sh.tile_abort = 0u;
+    }
     __syncthreads();
-    unsigned parity = 0;
+    unsigned parity = 0, tile_phase = 0;
     int cur_case = -1;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(next_item, 1u);
@@ -606,8 +712,8 @@ __global__ void __launch_bounds__(kStepThreads, 1)
             cur_case = w.case_idx;
             __syncthreads();
         }
-        if (w.species == 0) particle_item_call<0, PERIODIC, MCC0>(sP, smem, sh, parity, w.k, w.nk);
-        else particle_item_call<1, PERIODIC, MCC1>(sP, smem, sh, parity, w.k, w.nk);
+        if (w.species == 0) particle_item_call<0, PERIODIC, MCC0, STAGED>(sP, smem, sh, parity, tile_phase, w.k, w.nk);
+        else particle_item_call<1, PERIODIC, MCC1, STAGED>(sP, smem, sh, parity, tile_phase, w.k, w.nk);
     }
 }
 
@@ -693,8 +799,9 @@ __global__ void k_deposit_species(const __grid_constant__ StepConst P, int sp)
         if (c >= N || !(o >= 0.0f && o < 1.0f)) { atomicOr(&P.ctrl->err, kErrLoad); B.cell[i] = -1; continue; }
         const uint32_t f = __float2uint_rz(o * 4294967296.0f);
         const int c1 = (P.periodic && c + 1 == N) ? 0 : c + 1;
-        atomicAdd(&P.R[sp][c], (1ull << 32) - f);
-        atomicAdd(&P.R[sp][c1], (unsigned long long)f);
+        unsigned long long *R = P.R[sp] + (size_t)(blockIdx.x % kDepositCopies) * P.r_stride;
+        atomicAdd(&R[c], (1ull << 32) - f);
+        atomicAdd(&R[c1], (unsigned long long)f);
     }
 }
 

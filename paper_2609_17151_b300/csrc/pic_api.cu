@@ -59,15 +59,21 @@ struct pic_case {
     bool loaded[2] = {false, false};
     bool need_init = true;
     long long host_step = 0;
-    // sort interval: fixed by the descriptor, or chosen by the autotuner
+    // per species: sort interval and launch shape of the step kernel, fixed
+    // (descriptor, defaults) or chosen by the autotuner
     bool autotune = false, tuned = false;
-    int sort_k = 16;
-    long long steps_since_sort = 0;
+    int sort_k[2] = {16, 16};
+    long long since_sort[2] = {0, 0};
+    int step_threads[2] = {1024, 1024};
+    int step_stages[2] = {0, 0};                // particle tiles in flight (0 = direct loads)
+    float tune_shape_ms[2][6] = {};             // autotuner measurements, reported by pic_read_tuning
+    float tune_sort_ms[2] = {}, tune_slope_ms[2] = {};
     // CUDA graph of kGraphSteps steps (no sort), replayed by pic_step
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     int step_grid[2] = {0, 0};
     unsigned step_smem[2] = {0, 0};
+    int step_grid_threads[2] = {0, 0}, step_grid_stages[2] = {-1, -1};   // shape the cached grid was computed for
     unsigned field_smem = 0;
     // profiling: per kernel class, launch counts and event pairs
     static constexpr int kClasses = 4;
@@ -211,37 +217,78 @@ pic_status upload_tables(pic_case *c, int sp)
     return PIC_OK;
 }
 
-// The dynamic shared-memory cap is a property of the kernel, shared by every
-// case: set it once to the largest layout any case can need.
-const unsigned kMaxStepSmem = StepSmem(4096, kMaxProc).total;
+// Dynamic shared memory a step kernel may use: the device's opt-in maximum
+// per block less a margin for the kernels' static shared memory (at most
+// StepShared + one StepConst).  The cap is a property of the kernel, shared
+// by every case: each instantiation sets it once.
+constexpr int kStaticSmemMargin = 4096;
+int step_smem_limit(int device)
+{
+    static std::once_flag once;
+    static int lim = 0;
+    std::call_once(once, [&] {
+        int optin = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) optin = 0;
+        lim = std::max(0, optin - kStaticSmemMargin);
+    });
+    return lim;
+}
 
 // One flag per kernel instantiation (the caller is itself a template).
 template <typename K>
-cudaError_t allow_max_step_smem(K k, std::once_flag &once, cudaError_t &err)
+cudaError_t allow_max_step_smem(K k, std::once_flag &once, cudaError_t &err, int device)
 {
-    std::call_once(once, [&] { err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxStepSmem); });
+    std::call_once(once, [&] {
+        err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, step_smem_limit(device));
+    });
     return err;
+}
+
+// Tile buffers that fit next to the tables: `want`, fewer if shared memory is short.
+int fit_stages(int n_cells, int nproc, int threads, int want, int narr, int limit)
+{
+    int st = std::max(0, std::min(want, kMaxStages));
+    while (st > 0 && StepSmem(n_cells, nproc, threads, st, narr).total > (unsigned)limit) --st;
+    return st;
+}
+
+// The two variants (direct loads, bulk-copy tiles) are separate kernels, so
+// that the direct one carries no pipeline state.
+template <int SP, bool PER, int MCC, bool STAGED>
+cudaError_t launch_step_k(pic_case *c, int stages)
+{
+    auto k = k_particle_step<SP, PER, MCC, STAGED>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    cudaError_t e = allow_max_step_smem(k, once, attr_err, c->device);
+    if (e != cudaSuccess) return e;
+    const int nproc = MCC == 1 ? c->P.sp[SP].nproc : 0;
+    constexpr int narr = step_arrays(SP, PER, MCC);
+    const int threads = c->step_threads[SP];
+    const unsigned smem = StepSmem(c->d.n_cells, nproc, threads, stages, narr).total;
+    if (c->step_smem[SP] != smem || c->step_grid[SP] == 0 || c->step_grid_threads[SP] != threads ||
+        c->step_grid_stages[SP] != stages) {
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, smem);
+        if (e != cudaSuccess) return e;
+        c->step_grid[SP] = std::max(1, occ) * c->num_sms;
+        c->step_smem[SP] = smem;
+        c->step_grid_threads[SP] = threads;
+        c->step_grid_stages[SP] = stages;
+    }
+    c->P.sp[SP].stages = stages;
+    Timed t(c, KC_STEP, 1);
+    k<<<c->step_grid[SP], threads, smem, c->stream>>>(c->P);
+    return cudaGetLastError();
 }
 
 template <int SP, bool PER, int MCC>
 cudaError_t launch_step_t(pic_case *c)
 {
-    auto k = k_particle_step<SP, PER, MCC>;
-    const unsigned smem = StepSmem(c->d.n_cells, MCC == 1 ? c->P.sp[SP].nproc : 0).total;
-    if (c->step_smem[SP] != smem || c->step_grid[SP] == 0) {
-        static std::once_flag once;
-        static cudaError_t attr_err = cudaSuccess;
-        cudaError_t e = allow_max_step_smem(k, once, attr_err);
-        if (e != cudaSuccess) return e;
-        int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kStepThreads, smem);
-        if (e != cudaSuccess) return e;
-        c->step_grid[SP] = std::max(1, occ) * c->num_sms;
-        c->step_smem[SP] = smem;
-    }
-    Timed t(c, KC_STEP, 1);
-    k<<<c->step_grid[SP], kStepThreads, smem, c->stream>>>(c->P);
-    return cudaGetLastError();
+    const int nproc = MCC == 1 ? c->P.sp[SP].nproc : 0;
+    const int stages = fit_stages(c->d.n_cells, nproc, c->step_threads[SP], c->step_stages[SP],
+                                  step_arrays(SP, PER, MCC), step_smem_limit(c->device));
+    return stages > 0 ? launch_step_k<SP, PER, MCC, true>(c, stages) : launch_step_k<SP, PER, MCC, false>(c, 0);
 }
 
 template <int SP>
@@ -318,9 +365,8 @@ pic_status alloc_species(pic_case *c, int sp, long long need)
 pic_status initialise(pic_case *c)
 {
     for (int s = 0; s < c->d.n_species; ++s) fill_species(c, s);
-    const int N = c->d.n_cells;
     for (int s = 0; s < c->d.n_species; ++s)
-        CU(cudaMemsetAsync(c->P.R[s], 0, sizeof(unsigned long long) * (N + 1), c->stream));
+        CU(cudaMemsetAsync(c->P.R[s], 0, sizeof(unsigned long long) * kDepositCopies * c->P.r_stride, c->stream));
     Timed t(c, KC_INIT, c->d.n_species * (c->d.rewind ? 2 : 1));
     for (int s = 0; s < c->d.n_species; ++s) {
         k_deposit_species<<<c->num_sms * 4, 256, 0, c->stream>>>(c->P, s);
@@ -390,104 +436,195 @@ cudaError_t launch_sorts(pic_case *c)
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner of the sort interval K.  Right after a sort, the step time grows
-// as the particles lose their cell order (and, with electrodes, as absorbed
-// slots accumulate); a sort costs t_sort.  With t(k) ~ a + b k over the k-th
-// step after a sort, the mean cost per step of a period K is
-// a + b K / 2 + t_sort / K, minimised at K = sqrt(2 t_sort / b).  The tuner
-// times one sort and kTuneSteps steps with CUDA events, fits a and b by least
-// squares, and keeps K in [4, 1024] (1024 when the steps do not slow down).
-// Results are kept per case shape for the process, and in the file named by
-// PIC1D3V_TUNE_CACHE if that variable is set.
+// Autotuner, per species, of the sort interval K and of the step kernel's
+// launch shape.
+//  1. Sort interval: right after a sort, the step time grows as particles
+//     lose their cell order (and, with electrodes, as absorbed slots
+//     accumulate); a sort costs t_sort.  With t(k) ~ a + b k over the k-th
+//     step after a sort, the mean cost per step of a period K is
+//     a + b K / 2 + t_sort / K, minimised at K = sqrt(2 t_sort / b).  The
+//     tuner times one sort and kTuneSteps steps per species (default shape),
+//     fits a and b by least squares and keeps K in [4, 1024] (1024 when the
+//     steps do not slow down).
+//  2. Launch shape: CTA size (256, 512 or 1024 threads) and particle tiles
+//     in flight through shared memory (0 = each thread loads its own chunk;
+//     1 or 2 = bulk-copy pipeline).  Fewer, larger CTAs flush fewer copies
+//     of the shared deposit histogram, which matters once the particles have
+//     lost their cell order.  Continuing from the state step 1 left
+//     (the particle order of the middle of a sort period), the candidates
+//     take turns, one step each, for kShapeRounds rounds; each species keeps
+//     the candidate with the least summed kernel time.
+// Particle results do not depend on any of these choices (the deposit is
+// exact integer arithmetic); only FP32/FP64 moment sums may change in their
+// last bits with the launch shape.  Results are kept per case shape for the
+// process, and in the file named by PIC1D3V_TUNE_CACHE if that variable is set.
 // ---------------------------------------------------------------------------
 constexpr int kTuneSteps = 32;
+constexpr int kShapeRounds = 3;
+constexpr int kShapes = 6;
+constexpr int kShapeThreads[kShapes] = {1024, 512, 256, 1024, 512, 512};
+constexpr int kShapeStages[kShapes] = {0, 0, 0, 1, 1, 2};
+constexpr int kTuneTotalSteps = kTuneSteps + kShapeRounds * kShapes;
 constexpr int kMaxSortInterval = 1024;
 
+struct TuneResult {
+    int K[2], threads[2], stages[2];
+};
+
 std::mutex g_tune_mutex;
-std::map<std::string, int> g_tune_cache;
+std::map<std::string, TuneResult> g_tune_cache;
 bool g_tune_file_read = false;
 
 std::string tune_key(const pic_case *c)
 {
-    unsigned long long n = 0;
-    for (int s = 0; s < c->d.n_species; ++s) n += c->P.cap[s];
-    int lg = 0;
-    while ((1ull << (lg + 1)) <= n) ++lg;
-    char buf[128];
-    std::snprintf(buf, sizeof buf, "p%d_c%d_n2^%d_m%d%d", c->d.periodic, c->d.n_cells, lg, c->P.sp[0].mcc,
-                  c->d.n_species > 1 ? c->P.sp[1].mcc : 0);
+    char buf[160];
+    int lg[2] = {0, 0};
+    for (int s = 0; s < c->d.n_species; ++s)
+        while ((1ull << (lg[s] + 1)) <= c->P.cap[s]) ++lg[s];
+    std::snprintf(buf, sizeof buf, "p%d_c%d_n2^%d_2^%d_m%d%d", c->d.periodic, c->d.n_cells, lg[0], lg[1],
+                  c->P.sp[0].mcc, c->d.n_species > 1 ? c->P.sp[1].mcc : 0);
     return buf;
 }
 
-int tune_lookup(const std::string &key)
+bool tune_lookup(const std::string &key, TuneResult *out)
 {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     const char *path = std::getenv("PIC1D3V_TUNE_CACHE");
     if (path && !g_tune_file_read) {
         g_tune_file_read = true;
         if (FILE *f = std::fopen(path, "r")) {
-            char k[128];
-            int v;
-            while (std::fscanf(f, "%127s %d", k, &v) == 2) g_tune_cache[k] = v;
+            char line[256], k[160];
+            TuneResult r;
+            while (std::fgets(line, sizeof line, f))
+                if (std::sscanf(line, "%159s %d %d %d %d %d %d", k, &r.K[0], &r.K[1], &r.threads[0], &r.stages[0],
+                                &r.threads[1], &r.stages[1]) == 7) {
+                    bool ok = true;
+                    for (int s = 0; s < 2; ++s)
+                        ok = ok && r.K[s] >= 1 && r.K[s] <= kMaxSortInterval &&
+                             (r.threads[s] == 256 || r.threads[s] == 512 || r.threads[s] == 1024) &&
+                             r.stages[s] >= 0 && r.stages[s] <= kMaxStages;
+                    if (ok) g_tune_cache[k] = r;                     // malformed lines are ignored
+                }
             std::fclose(f);
         }
     }
     auto it = g_tune_cache.find(key);
-    return it == g_tune_cache.end() ? 0 : it->second;
+    if (it == g_tune_cache.end()) return false;
+    *out = it->second;
+    return true;
 }
 
-void tune_store(const std::string &key, int k)
+void tune_store(const std::string &key, const TuneResult &r)
 {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = k;
+    g_tune_cache[key] = r;
     if (const char *path = std::getenv("PIC1D3V_TUNE_CACHE"))
         if (FILE *f = std::fopen(path, "a")) {
-            std::fprintf(f, "%s %d\n", key.c_str(), k);
+            std::fprintf(f, "%s %d %d %d %d %d %d\n", key.c_str(), r.K[0], r.K[1], r.threads[0], r.stages[0],
+                         r.threads[1], r.stages[1]);
             std::fclose(f);
         }
 }
 
-pic_status autotune_sort_interval(pic_case *c, int64_t *left)
+void apply_tuning(pic_case *c, const TuneResult &r)
+{
+    for (int s = 0; s < 2; ++s) {
+        c->sort_k[s] = r.K[s];
+        c->step_threads[s] = r.threads[s];
+        c->step_stages[s] = r.stages[s];
+    }
+    c->tuned = true;
+    drop_graph(c);                                   // captured launches carry the old shape
+}
+
+// One step with events around each species' step kernel (ev[2 * s], ev[2 * s + 1]).
+cudaError_t launch_one_step_timed(pic_case *c, const cudaEvent_t *ev)
+{
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < c->d.n_species && e == cudaSuccess; ++s) {
+        e = cudaEventRecord(ev[2 * s], c->stream);
+        if (e == cudaSuccess) e = s == 0 ? launch_step_sp<0>(c) : launch_step_sp<1>(c);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * s + 1], c->stream);
+    }
+    if (e == cudaSuccess) e = launch_field(c, 1);
+    return e;
+}
+
+pic_status autotune(pic_case *c, int64_t *left)
 {
     const std::string key = tune_key(c);
-    if (int k = tune_lookup(key)) {
-        c->sort_k = k;
-        c->tuned = true;
+    TuneResult r{};
+    if (tune_lookup(key, &r)) {
+        apply_tuning(c, r);
         return PIC_OK;
     }
-    std::vector<cudaEvent_t> ev(2 * (kTuneSteps + 1));
-    for (auto &e : ev) CU(cudaEventCreate(&e));
-    CU(cudaEventRecord(ev[0], c->stream));
-    CU(launch_sorts(c));
-    CU(cudaEventRecord(ev[1], c->stream));
-    for (int k = 0; k < kTuneSteps; ++k) {
-        CU(cudaEventRecord(ev[2 + 2 * k], c->stream));
-        CU(launch_one_step(c));
-        CU(cudaEventRecord(ev[3 + 2 * k], c->stream));
+    const int ns = c->d.n_species;
+    drop_graph(c);
+    struct Events {                                  // destroyed on every return path
+        std::vector<cudaEvent_t> v;
+        ~Events() { for (auto e : v) cudaEventDestroy(e); }
+    } ev;
+    ev.v.resize(4 + 4 * kTuneSteps + 4 * kShapeRounds * kShapes, nullptr);
+    for (auto &e : ev.v) CU(cudaEventCreate(&e));
+    cudaEvent_t *sev = ev.v.data();                  // sorts
+    cudaEvent_t *tev = sev + 4;                      // steps after the sort
+    cudaEvent_t *shev = tev + 4 * kTuneSteps;        // shape rounds
+    // 1. sort interval with the default shape
+    for (int s = 0; s < 2; ++s) { c->step_threads[s] = kShapeThreads[0]; c->step_stages[s] = kShapeStages[0]; }
+    for (int s = 0; s < ns; ++s) {
+        CU(cudaEventRecord(sev[2 * s], c->stream));
+        CU(launch_sort(c, s));
+        CU(cudaEventRecord(sev[2 * s + 1], c->stream));
     }
+    for (int k = 0; k < kTuneSteps; ++k) CU(launch_one_step_timed(c, &tev[4 * k]));
+    // 2. launch shapes, interleaved
+    for (int rnd = 0; rnd < kShapeRounds; ++rnd)
+        for (int k = 0; k < kShapes; ++k) {
+            for (int s = 0; s < 2; ++s) { c->step_threads[s] = kShapeThreads[k]; c->step_stages[s] = kShapeStages[k]; }
+            CU(launch_one_step_timed(c, &shev[4 * (rnd * kShapes + k)]));
+        }
     CU(cudaStreamSynchronize(c->stream));
-    float ts = 0.f;
-    CU(cudaEventElapsedTime(&ts, ev[0], ev[1]));
-    double sx = 0, sy = 0, sxx = 0, sxy = 0;
-    for (int k = 0; k < kTuneSteps; ++k) {
-        float t = 0.f;
-        CU(cudaEventElapsedTime(&t, ev[2 + 2 * k], ev[3 + 2 * k]));
-        const double x = k + 1;
-        sx += x; sy += t; sxx += x * x; sxy += x * t;
+    for (int s = 0; s < 2; ++s) {
+        r.K[s] = kMaxSortInterval;
+        r.threads[s] = kShapeThreads[0];
+        r.stages[s] = kShapeStages[0];
+        for (int k = 0; k < kShapes; ++k) c->tune_shape_ms[s][k] = 0.f;
+        if (s >= ns) continue;
+        float ts = 0.f;
+        CU(cudaEventElapsedTime(&ts, sev[2 * s], sev[2 * s + 1]));
+        double sx = 0, sy = 0, sxx = 0, sxy = 0;
+        for (int k = 0; k < kTuneSteps; ++k) {
+            float t = 0.f;
+            CU(cudaEventElapsedTime(&t, tev[4 * k + 2 * s], tev[4 * k + 2 * s + 1]));
+            const double x = k + 1;
+            sx += x; sy += t; sxx += x * x; sxy += x * t;
+        }
+        const double n = kTuneSteps;
+        const double b = (n * sxy - sx * sy) / (n * sxx - sx * sx);
+        const double a = (sy - b * sx) / n;
+        if (b > 1e-4 * std::max(a, 1e-6)) r.K[s] = (int)std::lround(std::sqrt(2.0 * ts / b));
+        r.K[s] = std::max(4, std::min(kMaxSortInterval, r.K[s]));
+        c->tune_sort_ms[s] = ts;
+        c->tune_slope_ms[s] = (float)b;
+        float shape_ms[kShapes] = {};
+        for (int rnd = 0; rnd < kShapeRounds; ++rnd)
+            for (int k = 0; k < kShapes; ++k) {
+                float t = 0.f;
+                CU(cudaEventElapsedTime(&t, shev[4 * (rnd * kShapes + k) + 2 * s], shev[4 * (rnd * kShapes + k) + 2 * s + 1]));
+                shape_ms[k] += t / kShapeRounds;
+            }
+        int best = 0;
+        for (int k = 1; k < kShapes; ++k)
+            if (shape_ms[k] < shape_ms[best]) best = k;
+        r.threads[s] = kShapeThreads[best];
+        r.stages[s] = kShapeStages[best];
+        for (int k = 0; k < kShapes; ++k) c->tune_shape_ms[s][k] = shape_ms[k];
     }
-    for (auto &e : ev) cudaEventDestroy(e);
-    const double n = kTuneSteps;
-    const double b = (n * sxy - sx * sy) / (n * sxx - sx * sx);
-    const double a = (sy - b * sx) / n;
-    int K = kMaxSortInterval;
-    if (b > 1e-4 * std::max(a, 1e-6)) K = (int)std::lround(std::sqrt(2.0 * ts / b));
-    K = std::max(4, std::min(kMaxSortInterval, K));
-    c->sort_k = K;
-    c->tuned = true;
-    c->host_step += kTuneSteps;
-    c->steps_since_sort = kTuneSteps;
-    *left -= kTuneSteps;
-    tune_store(key, K);
+    apply_tuning(c, r);
+    c->host_step += kTuneTotalSteps;
+    c->since_sort[0] = c->since_sort[1] = kTuneTotalSteps;
+    *left -= kTuneTotalSteps;
+    tune_store(key, r);
     return PIC_OK;
 }
 
@@ -567,7 +704,7 @@ pic_status load_finish(pic_case *c, int sp, int64_t n, const Ctrl &h)
     c->loaded[sp] = true;
     c->need_init = true;
     c->host_step = 0;
-    c->steps_since_sort = 0;
+    c->since_sort[0] = c->since_sort[1] = 0;
     drop_graph(c);
     return PIC_OK;
 }
@@ -614,7 +751,7 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     pic_case *c = new pic_case();
     c->d = *desc;
     c->autotune = c->d.sort_interval <= 0;
-    c->sort_k = c->autotune ? 16 : c->d.sort_interval;
+    c->sort_k[0] = c->sort_k[1] = c->autotune ? 16 : c->d.sort_interval;
     if (c->d.field_history <= 0) c->d.field_history = 65536;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -666,7 +803,9 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     P.E32 = (float *)c->dalloc(sizeof(float) * (((N + 1) + 3) / 4 * 4));
     P.E = (double *)c->dalloc(sizeof(double) * nn);
     P.phi = (double *)c->dalloc(sizeof(double) * nn);
-    for (int s = 0; s < 2; ++s) P.R[s] = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * (N + 1));
+    P.r_stride = (N + 1 + 15) / 16 * 16;
+    for (int s = 0; s < 2; ++s)
+        P.R[s] = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * kDepositCopies * P.r_stride);
     c->R_last = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * 2 * nn);
     P.R_last = c->R_last;
     P.ctrl = (Ctrl *)c->dalloc(sizeof(Ctrl));
@@ -843,16 +982,21 @@ pic_status pic_step(pic_case *c, int64_t n_steps)
     }
     int64_t left = n_steps;
     while (left > 0) {
-        if (c->autotune && !c->tuned && c->host_step > 0 && left >= kTuneSteps) {
-            pic_status st = autotune_sort_interval(c, &left);
+        if (c->autotune && !c->tuned && c->host_step > 0 && left >= kTuneTotalSteps) {
+            pic_status st = autotune(c, &left);
             if (st != PIC_OK) return st;
             continue;
         }
-        const int K = c->sort_k;
-        const int G = std::min(kGraphSteps, K);
+        // steps before the next sort of any species
+        long long room = kGraphSteps;
+        int G = kGraphSteps;
+        for (int s = 0; s < c->d.n_species; ++s) {
+            room = std::min(room, c->sort_k[s] - c->since_sort[s]);
+            G = std::min(G, c->sort_k[s]);
+        }
         // replay the graph when G steps fit before the next sort (steps run
         // directly while profiling, and for the first step after a load)
-        if (!c->prof && c->host_step > 0 && left >= G && c->steps_since_sort + G <= K) {
+        if (!c->prof && c->host_step > 0 && left >= G && G <= room) {
             if (!c->graph || c->graph_steps != G) {
                 pic_status st = build_graph(c, G);
                 if (st != PIC_OK) return st;
@@ -861,18 +1005,19 @@ pic_status pic_step(pic_case *c, int64_t n_steps)
             c->launches[KC_STEP] += (long long)G * c->d.n_species;
             c->launches[KC_FIELD] += G;
             c->host_step += G;
-            c->steps_since_sort += G;
+            for (int s = 0; s < 2; ++s) c->since_sort[s] += G;
             left -= G;
         } else {
             CU(launch_one_step(c));
             c->host_step++;
-            c->steps_since_sort++;
+            for (int s = 0; s < 2; ++s) c->since_sort[s]++;
             left--;
         }
-        if (c->steps_since_sort >= K) {
-            CU(launch_sorts(c));
-            c->steps_since_sort = 0;
-        }
+        for (int s = 0; s < c->d.n_species; ++s)
+            if (c->since_sort[s] >= c->sort_k[s]) {
+                CU(launch_sort(c, s));
+                c->since_sort[s] = 0;
+            }
     }
     return PIC_OK;
 }
@@ -944,6 +1089,35 @@ pic_status pic_read_field(pic_case *c, double *phi, double *E, int64_t *rho_raw)
     return device_error(c);
 }
 
+pic_status pic_set_step_shape(pic_case *c, int species, int threads, int stages)
+{
+    if (!c) return fail(PIC_EINVAL, "null case");
+    if (species < 0 || species >= c->d.n_species) return fail(PIC_EINVAL, "bad species");
+    if (threads != 256 && threads != 512 && threads != 1024) return fail(PIC_EINVAL, "threads must be 256, 512 or 1024");
+    if (stages < 0 || stages > kMaxStages) return fail(PIC_EINVAL, "stages must be in [0, 4]");
+    c->step_threads[species] = threads;
+    c->step_stages[species] = stages;
+    drop_graph(c);
+    return PIC_OK;
+}
+
+pic_status pic_read_tuning(pic_case *c, pic_tuning *t)
+{
+    if (!c || !t) return fail(PIC_EINVAL, "null argument");
+    if (t->struct_size != sizeof(pic_tuning)) return fail(PIC_EINVAL, "pic_tuning size mismatch");
+    t->tuned = c->tuned ? 1 : 0;
+    for (int s = 0; s < 2; ++s) {
+        t->sort_interval[s] = c->sort_k[s];
+        t->threads[s] = c->step_threads[s];
+        t->stages[s] = c->step_grid_stages[s] >= 0 ? c->step_grid_stages[s] : c->step_stages[s];
+        t->grid[s] = c->step_grid[s];
+        for (int k = 0; k < 6; ++k) t->shape_ms[s][k] = c->tune_shape_ms[s][k];
+        t->sort_ms[s] = c->tune_sort_ms[s];
+        t->slope_ms[s] = c->tune_slope_ms[s];
+    }
+    return PIC_OK;
+}
+
 pic_status pic_read_moments(pic_case *c, pic_moments *m)
 {
     if (!c || !m || m->struct_size != sizeof(pic_moments)) return fail(PIC_EINVAL, "bad moments struct");
@@ -985,7 +1159,7 @@ pic_status pic_read_moments(pic_case *c, pic_moments *m)
             if (m->dens_sum) m->dens_sum[s * nn + i] = f * (double)rs[s * nn + i];
             if (m->dens_diag_sum) m->dens_diag_sum[s * nn + i] = f * (double)rd[s * nn + i];
         }
-    m->sort_interval = c->sort_k;
+    m->sort_interval = c->d.n_species > 1 ? std::min(c->sort_k[0], c->sort_k[1]) : c->sort_k[0];
     m->see_emitted = (int64_t)h.see;
     m->ionizations = (int64_t)h.iz;
     if (m->eepf) for (int b = 0; b < kEepfBins; ++b) m->eepf[b] = (double)ee[b];
@@ -1132,6 +1306,8 @@ struct pic_batch {
     int n_items = 0;
     bool planned = false;
     int periodic = 0, mcc0 = 0, mcc1 = 0;
+    int stages = 0;                 // particle tiles in flight per CTA requested (0 = direct loads)
+    int run_stages = 0;             // in use (fewer if shared memory is short)
     unsigned smem = 0;
     int grid = 0;
     int sort_k = 64;
@@ -1146,22 +1322,28 @@ namespace {
 constexpr long long kItemParticles = 131072;      // largest work item
 constexpr long long kMinItemParticles = 16384;    // smallest work item when splitting for balance
 
-template <bool PER, int M0, int M1>
-cudaError_t batch_step_t(pic_batch *b)
+template <bool PER, int M0, int M1, bool STAGED>
+cudaError_t batch_step_k(pic_batch *b)
 {
-    auto k = k_batch_particle_step<PER, M0, M1>;
+    auto k = k_batch_particle_step<PER, M0, M1, STAGED>;
     if (b->grid == 0) {
         static std::once_flag once;
         static cudaError_t attr_err = cudaSuccess;
-        cudaError_t e = allow_max_step_smem(k, once, attr_err);
+        cudaError_t e = allow_max_step_smem(k, once, attr_err, b->cases[0]->device);
         if (e != cudaSuccess) return e;
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kStepThreads, b->smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kBatchThreads, b->smem);
         if (e != cudaSuccess) return e;
         b->grid = std::max(1, occ) * b->cases[0]->num_sms;
     }
-    k<<<b->grid, kStepThreads, b->smem, b->stream>>>(b->d_cases, b->d_items, b->n_items, b->d_next);
+    k<<<b->grid, kBatchThreads, b->smem, b->stream>>>(b->d_cases, b->d_items, b->n_items, b->d_next);
     return cudaGetLastError();
+}
+
+template <bool PER, int M0, int M1>
+cudaError_t batch_step_t(pic_batch *b)
+{
+    return b->run_stages > 0 ? batch_step_k<PER, M0, M1, true>(b) : batch_step_k<PER, M0, M1, false>(b);
 }
 
 cudaError_t batch_particles(pic_batch *b)
@@ -1234,8 +1416,6 @@ pic_status batch_plan(pic_batch *b)
         if (c->d.periodic != b->periodic || c->P.sp[0].mcc != b->mcc0 ||
             (c->d.n_species > 1 ? c->P.sp[1].mcc : 0) != b->mcc1)
             return fail(PIC_EINVAL, "batch cases differ in boundary or collision model");
-        for (int s = 0; s < c->d.n_species; ++s)
-            smem = std::max(smem, StepSmem(c->d.n_cells, c->P.sp[s].mcc == 1 ? c->P.sp[s].nproc : 0).total);
         const Ctrl &h = hs[i];
         for (int s = 0; s < c->d.n_species; ++s) {
             const long long n = (long long)h.n_active[s];
@@ -1244,6 +1424,27 @@ pic_status batch_plan(pic_batch *b)
         }
         consts[i] = c->P;
     }
+    // tile buffers: as many as the largest case leaves room for (same for all cases)
+    int stages = b->stages;
+    for (size_t i = 0; i < nc; ++i) {
+        const pic_case *c = b->cases[i];
+        for (int s = 0; s < c->d.n_species; ++s) {
+            const int np = c->P.sp[s].mcc == 1 ? c->P.sp[s].nproc : 0;
+            const int narr = step_arrays(s, b->periodic != 0, c->P.sp[s].mcc);
+            stages = std::min(stages, fit_stages(c->d.n_cells, np, kBatchThreads, stages, narr, step_smem_limit(c->device)));
+        }
+    }
+    for (size_t i = 0; i < nc; ++i) {
+        const pic_case *c = b->cases[i];
+        for (int s = 0; s < c->d.n_species; ++s) {
+            const int np = c->P.sp[s].mcc == 1 ? c->P.sp[s].nproc : 0;
+            const int narr = step_arrays(s, b->periodic != 0, c->P.sp[s].mcc);
+            smem = std::max(smem, StepSmem(c->d.n_cells, np, kBatchThreads, stages, narr).total);
+            consts[i].sp[s].stages = stages;
+        }
+    }
+    if (stages != b->run_stages) b->grid = 0;
+    b->run_stages = stages;
     if (b->d_cases) cudaFree(b->d_cases);
     if (b->d_items) cudaFree(b->d_items);
     b->d_cases = nullptr;
@@ -1377,6 +1578,15 @@ pic_status pic_batch_sync(pic_batch *b)
 }
 
 int64_t pic_batch_launches(const pic_batch *b) { return b ? b->launches : 0; }
+
+pic_status pic_batch_set_stages(pic_batch *b, int stages)
+{
+    if (!b || stages < 0 || stages > kMaxStages) return fail(PIC_EINVAL, "stages must be in [0, 4]");
+    b->stages = stages;
+    b->planned = false;                              // re-planned (and the graph rebuilt) at the next step
+    batch_drop_graph(b);
+    return PIC_OK;
+}
 
 pic_status pic_batch_destroy(pic_batch *b)
 {

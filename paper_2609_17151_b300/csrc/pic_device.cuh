@@ -9,7 +9,13 @@ constexpr int kMaxProc = 4;
 constexpr int kNGrid = 1000;            // cross-section grid, log-spaced on [1e-3, 1e3] eV
 constexpr float kGridEmin = 1e-3f;
 constexpr int kEepfBins = 240;          // 0..60 eV, 0.25 eV bins
-constexpr int kStepThreads = 512;
+constexpr int kStepThreads = 1024;     // largest CTA of the particle step
+constexpr int kBatchThreads = 512;     // CTA of the batched (many-case) particle step
+constexpr int kMaxStages = 4;          // particle tiles in flight per CTA (bulk-copy pipeline)
+// Copies of each species' raw deposit: CTA b adds its histogram into copy
+// b mod kDepositCopies, spreading the int64 atomics of hundreds of CTAs over
+// more L2 lines; the field solve sums the copies (exact: integers).
+constexpr int kDepositCopies = 8;
 constexpr int kFieldThreads = 576;      // >= nodes per CTA of the cluster (4097 / 8 = 513)
 constexpr int kFieldCluster = 8;       // CTAs (SMs) sharing one field solve
 
@@ -64,6 +70,7 @@ struct SpConst {
     float vt_newion;                    // sqrt(k T_gas / m_ion)
     double q, m, w;
     int mcc;                            // 0 none, 1 tables, 2 constant frequency
+    int stages;                         // particle tiles in flight through shared memory (0 = direct loads)
 };
 
 struct StepConst {
@@ -84,7 +91,8 @@ struct StepConst {
     const float *nu_tab[2];             // [nproc][kNGrid] per species
     float *E32;                         // [n_cells + 1 padded]: periodic ghost at n_cells
     double *E, *phi;                    // [n_nodes]
-    unsigned long long *R[2];           // [n_cells + 1] raw fixed-point deposit
+    unsigned long long *R[2];           // [kDepositCopies][r_stride] raw fixed-point deposit (copies summed)
+    int r_stride;                       // words between copies (n_cells + 1 rounded up to 16)
     unsigned long long *R_last;         // [2][n_nodes] deposit of the last solve (read-back)
     SpeciesBufs buf[2][2];              // [species][half]
     unsigned long long cap[2];

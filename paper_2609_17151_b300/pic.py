@@ -64,6 +64,14 @@ class Moments(C.Structure):
     ]
 
 
+class Tuning(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("tuned", C.c_int32), ("sort_interval", C.c_int32 * 2),
+        ("threads", C.c_int32 * 2), ("stages", C.c_int32 * 2), ("grid", C.c_int32 * 2),
+        ("shape_ms", (C.c_float * 6) * 2), ("sort_ms", C.c_float * 2), ("slope_ms", C.c_float * 2),
+    ]
+
+
 class KernelStat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("timed", C.c_int64), ("total_ms", C.c_double)]
 
@@ -89,6 +97,8 @@ def _load_library():
     lib.pic_read_particles.argtypes = [vp, C.c_int, i64, C.POINTER(i64), vp, vp, vp, vp, vp, vp]
     lib.pic_read_field.argtypes = [vp, vp, vp, vp]
     lib.pic_read_moments.argtypes = [vp, C.POINTER(Moments)]
+    lib.pic_read_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    lib.pic_set_step_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     lib.pic_destroy.argtypes = [vp]
     lib.pic_status_str.restype = C.c_char_p
     lib.pic_status_str.argtypes = [C.c_int]
@@ -106,6 +116,7 @@ def _load_library():
     lib.pic_batch_launches.restype = i64
     lib.pic_batch_launches.argtypes = [vp]
     lib.pic_batch_destroy.argtypes = [vp]
+    lib.pic_batch_set_stages.argtypes = [vp, C.c_int]
     fp = C.POINTER(C.c_float)
     lib.pic_mlp_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(vp)]
     lib.pic_mlp_set_normalization.argtypes = [vp, fp, fp, fp, fp]
@@ -122,9 +133,10 @@ def _load_library():
     lib.pic_profile.argtypes = [vp, C.c_int]
     lib.pic_profile_read.argtypes = [vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]
     for f in ("pic_create_case", "pic_load_xsec_table", "pic_load_particles", "pic_step", "pic_sync", "pic_count",
-              "pic_read_particles", "pic_read_field", "pic_read_moments", "pic_destroy", "pic_philox", "pic_deposit",
+              "pic_read_particles", "pic_read_field", "pic_read_moments", "pic_read_tuning", "pic_set_step_shape", "pic_destroy", "pic_philox", "pic_deposit",
               "pic_profile", "pic_profile_read", "pic_sort_by_cell", "pic_sort_by_cell_noalloc",
               "pic_load_profile", "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy",
+              "pic_batch_set_stages",
               "pic_mlp_create", "pic_mlp_set_normalization", "pic_mlp_get_params", "pic_mlp_set_params",
               "pic_mlp_gradients", "pic_mlp_train", "pic_mlp_predict", "pic_mlp_destroy", "pic_gemm_bf16",
               "pic_warmstart_load"):
@@ -303,6 +315,16 @@ def read_moments(h, n_nodes, n_species, reset=False, field_energy_cap=0) -> dict
     return out
 
 
+def read_tuning(h) -> dict:
+    t = Tuning()
+    t.struct_size = C.sizeof(Tuning)
+    check(lib.pic_read_tuning(h, C.byref(t)))
+    return dict(tuned=bool(t.tuned), sort_interval=tuple(t.sort_interval), threads=tuple(t.threads),
+                stages=tuple(t.stages), grid=tuple(t.grid),
+                shape_ms=[list(t.shape_ms[s]) for s in range(2)], sort_ms=tuple(t.sort_ms),
+                slope_ms=tuple(t.slope_ms))
+
+
 def profile(h, enable=True):
     check(lib.pic_profile(h, int(bool(enable))))
 
@@ -435,6 +457,9 @@ class Batch:
     def launches(self):
         return int(lib.pic_batch_launches(self.h))
 
+    def set_stages(self, stages):
+        check(lib.pic_batch_set_stages(self.h, int(stages)))
+
     def replan(self):
         """Re-split the work items from the current particle counts before the next step."""
         lib.pic_batch_case(self.h, 0)
@@ -511,6 +536,12 @@ class Case:
 
     def moments(self, reset=False, field_energy_cap=0):
         return read_moments(self.h, self.n_nodes, self.n_species, reset=reset, field_energy_cap=field_energy_cap)
+
+    def tuning(self):
+        return read_tuning(self.h)
+
+    def set_step_shape(self, species, threads, stages):
+        check(lib.pic_set_step_shape(self.h, species, threads, stages))
 
     def profile(self, enable=True):
         profile(self.h, enable)

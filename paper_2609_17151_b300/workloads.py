@@ -207,7 +207,7 @@ def sweep_cases(n_cases: int = 256, seed: int = 2609, freq: float = 13.56e6, n0:
     return cfgs, counts
 
 
-def dual_frequency_family(n_cases: int, seed: int, n_cells: int = 256, gap: float = 0.03, n0: float = 1e14,
+def dual_frequency_family(n_cases: int, seed: int, n_cells: int = 256, gap: float = 0.03, n0: float = 2e14,
                           n_init: int = 5000, freq: float = 13.56e6):
     """Dual-frequency argon CCPs, V(t) = V1 cos(2 pi f t + theta) + V2 cos(4 pi f t)
     (the two-harmonic waveform of the paper's §3.3), drawn with numpy's Philox:

@@ -134,13 +134,18 @@ def test_full_size_ccp_one_step():
     gc.close()
 
 
-def test_full_size_exb_one_step():
+@pytest.mark.parametrize("shape", [(512, 0), (1024, 0), (512, 1), (1024, 1), (256, 2)])
+def test_full_size_exb_one_step(shape):
     """The 1.02e7-particle E x B workload (2048 cells, 2500 per cell per species)
-    at full size, one step, every particle, in the bench's launch configuration."""
+    at full size, one step, every particle, in each launch shape the bench's
+    autotuner may pick: direct loads, and particle tiles streamed through
+    shared memory by bulk copies (several histogram flushes per CTA)."""
     cfg, parts = W.ecdi_case(seed=1)
     oc = oracle_case(cfg, parts)
     oc.step(1)
-    gc = gpu_case(cfg, parts)
+    gc = gpu_case(cfg, parts, sort_interval=64)
+    for s in range(2):
+        gc.set_step_shape(s, *shape)
     gc.step(1)
     st = compare_all(cfg, gc, oc)
     phi_g, E_g, R_g = gc.field()
@@ -151,6 +156,38 @@ def test_full_size_exb_one_step():
 
 
 # --------------------------------------------------------------------------- properties
+@pytest.mark.parametrize("shape", [(256, 0), (1024, 0), (512, 1), (1024, 1), (512, 2), (256, 2), (512, 3), (256, 4)])
+def test_launch_shapes_give_identical_particles(shape):
+    """Every launch shape of the step kernel (CTA size; particle tiles loaded
+    directly or streamed through 1-4 shared-memory buffers by bulk copies)
+    gives bit-identical particles and field: bounded argon case with
+    ionization, SEE appends, absorption and a ragged last tile."""
+    cfg, parts = small_ccp(seed=31, n=30001, ti_ev=400.0)
+    ref = gpu_case(cfg, parts, sort_interval=8)
+    ref.step(20)
+    got = gpu_case(cfg, parts, sort_interval=8)
+    for s in range(2):
+        got.set_step_shape(s, *shape)
+    got.step(20)
+    t = got.tuning()
+    assert t["threads"] == (shape[0], shape[0]) and t["stages"] == (shape[1], shape[1])
+    for s in range(2):
+        pa, pb = ref.particles(s), got.particles(s)
+        assert pa["id"].size == pb["id"].size and pa["id"].size > 0
+        ia, ib = np.argsort(pa["id"], kind="stable"), np.argsort(pb["id"], kind="stable")
+        for key in ("id", "cell", "off", "vx", "vy", "vz"):
+            assert np.array_equal(pa[key][ia], pb[key][ib]), (s, key)
+    for x, y in zip(ref.field(), got.field()):
+        assert np.array_equal(x, y)
+    with pytest.raises(pic.PicError):
+        got.set_step_shape(0, 384, 0)
+    with pytest.raises(pic.PicError):
+        got.set_step_shape(0, 2048, 0)
+    with pytest.raises(pic.PicError):
+        got.set_step_shape(0, 512, 5)
+    ref.close(); got.close()
+
+
 def test_sort_interval_does_not_change_results():
     """Reordering particles (counting sort every step) leaves every particle
     bit-identical: the update of a particle depends only on its own state, the
@@ -290,6 +327,17 @@ def test_autotuned_sort_interval_and_graph_replay_leave_results_unchanged():
     a.step(80)
     k = a.moments()["sort_interval"]
     assert 4 <= k <= 1024
+    t = a.tuning()
+    assert t["tuned"]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for s in range(2):                   # per species: sort interval and launch shape
+        assert 4 <= t["sort_interval"][s] <= 1024
+        assert t["threads"][s] in (256, 512, 1024) and t["stages"][s] in (0, 1, 2)
+        assert t["grid"][s] > 0 and t["grid"][s] % sms == 0
+        assert all(x > 0 for x in t["shape_ms"][s]) and t["sort_ms"][s] > 0
+        best = min(range(6), key=lambda j: t["shape_ms"][s][j])
+        assert (t["threads"][s], t["stages"][s]) == ((1024, 512, 256, 1024, 512, 512)[best], (0, 0, 0, 1, 1, 2)[best])
+    assert k == min(t["sort_interval"])
     b = gpu_case(cfg, parts, sort_interval=100000)
     b.profile(True)                      # direct launches with events, no graph
     b.step(80)
@@ -300,6 +348,45 @@ def test_autotuned_sort_interval_and_graph_replay_leave_results_unchanged():
         for key in ("id", "cell", "off", "vx", "vy", "vz"):
             assert np.array_equal(pa[key][ia], pb[key][ib]), (s, key)
     a.close(); b.close()
+
+
+_TUNE_SCRIPT = """
+import json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2609_17151_b300 import pic, workloads as W
+cfg, parts = W.ccp_case(seed=5, n_cells=128, n_per_species=40000)
+c = pic.Case(cfg, parts, sort_interval=0)
+c.step(60)
+c.sync()
+print(json.dumps(c.tuning()))
+c.close()
+"""
+
+
+def test_tune_cache_file_round_trip(tmp_path):
+    """The autotuner's per-species choice goes to the file named by
+    PIC1D3V_TUNE_CACHE; a fresh process with the same case shape reads it
+    back and skips the timing runs (its measurements stay zero)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PIC1D3V_TUNE_CACHE=str(tmp_path / "tune.txt"))
+    runs = []
+    for _ in range(2):
+        out = subprocess.run([sys.executable, "-c", _TUNE_SCRIPT, root], env=env, capture_output=True, text=True,
+                             timeout=600)
+        assert out.returncode == 0, out.stderr[-2000:]
+        runs.append(json.loads(out.stdout.strip().splitlines()[-1]))
+    first, second = runs
+    assert first["tuned"] and second["tuned"]
+    lines = (tmp_path / "tune.txt").read_text().split("\n")
+    lines = [ln for ln in lines if ln.strip()]
+    assert len(lines) == 1 and len(lines[0].split()) == 7
+    for k in ("sort_interval", "threads", "stages"):
+        assert first[k] == second[k], k
+    assert all(x > 0 for x in first["shape_ms"][0]) and all(x == 0 for x in second["shape_ms"][0])
 
 
 # --------------------------------------------------------------------------- loader and batch
@@ -340,13 +427,16 @@ def _sweep_cfgs(n_cases, seed=5):
     return cfgs
 
 
-def test_batch_equals_cases_stepped_alone():
+@pytest.mark.parametrize("stages", [0, 1, 2])
+def test_batch_equals_cases_stepped_alone(stages):
     """Heterogeneous argon cases (cells, gap, pressure, voltage, particle
     counts differ) stepped in one batch give bit-identical particles and
-    fields to each case stepped on its own."""
+    fields to each case stepped on its own; the batch kernel loads its
+    particles directly (0) or through 1-2 bulk-copy tile buffers."""
     cfgs = _sweep_cfgs(5)
     counts = [3000, 70_000, 150_000, 9_000, 260_001]
     b = pic.Batch(cfgs, sort_interval=8)
+    b.set_stages(stages)
     singles = []
     for cfg, n, view in zip(cfgs, counts, b.cases):
         nn = cfg["n_cells"] + 1
