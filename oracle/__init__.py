@@ -25,6 +25,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 NGRID = 1000
 EEPF_BINS = 240
+IFEDF_BINS = 256
 ELASTIC, EXCITATION, IONIZATION, ISO, CX = 0, 1, 2, 3, 4
 
 
@@ -53,6 +54,7 @@ class Params(C.Structure):
         ("q", C.c_double * 2), ("m", C.c_double * 2), ("w", C.c_double * 2),
         ("seed", C.c_uint64),
         ("diag_interval", C.c_int32), ("rewind", C.c_int32),
+        ("circuit", C.c_int32), ("cap", C.c_double), ("ifedf_emax_ev", C.c_double),
     ]
 
 
@@ -87,6 +89,9 @@ def _load():
     lib.or_get_counters.argtypes = [P, C.POINTER(Counters)]
     lib.or_get_moments.argtypes = [P, dp, dp, dp, dp, dp, dp, dp]
     lib.or_reset_moments.argtypes = [P]
+    lib.or_get_ifedf.argtypes = [P, dp]
+    lib.or_get_electrode_charge.restype = C.c_double
+    lib.or_get_electrode_charge.argtypes = [P]
     lib.or_get_field_energy.restype = C.c_int64
     lib.or_get_field_energy.argtypes = [P, dp, C.c_int64]
     lib.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
@@ -186,6 +191,9 @@ def make_params(cfg: dict) -> Params:
     p.seed = int(cfg.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
     p.diag_interval = int(cfg.get("diag_interval", 0))
     p.rewind = int(cfg.get("rewind", 1))
+    p.circuit = 1 if cfg.get("circuit", "voltage") == "capacitor" else 0
+    p.cap = float(cfg.get("blocking_cap", 0.0))
+    p.ifedf_emax_ev = float(cfg.get("ifedf_emax_ev", 0.0))
     return p
 
 
@@ -288,6 +296,16 @@ class Case:
 
     def reset_moments(self):
         _lib.or_reset_moments(self._h)
+
+    def ifedf(self) -> np.ndarray:
+        """Ion energy histogram at each electrode, shape (2, IFEDF_BINS)."""
+        out = np.zeros(2 * IFEDF_BINS)
+        _lib.or_get_ifedf(self._h, _d(out))
+        return out.reshape(2, IFEDF_BINS)
+
+    def electrode_charge(self) -> float:
+        """Charge per area of electrode 0 with its capacitor plate (C/m^2)."""
+        return float(_lib.or_get_electrode_charge(self._h))
 
     def field_energy(self) -> np.ndarray:
         n = int(_lib.or_get_field_energy(self._h, None, 0))

@@ -103,6 +103,10 @@ struct or_case {
     or_counters cnt;
     double *dens, *phi_sum, *en, *dens_diag, eepf[OR_EEPF_BINS], ke[OR_MAX_SPECIES], pw[OR_MAX_SPECIES];
     double *fe_hist; int64_t fe_n, fe_cap;
+    double q_el;                      /* series-capacitor circuit: charge of electrode 0 + plate, C/m^2 */
+    int64_t st_abs0[OR_MAX_SPECIES];  /* this step: particles absorbed at x = 0 */
+    int64_t st_see0;                  /* this step: secondary electrons emitted at x = 0 */
+    double ifedf[2 * OR_IFEDF_BINS];
 };
 
 static void draw(const or_case *c, uint32_t id, int64_t n, int sp, uint32_t blk, uint32_t out[4])
@@ -143,6 +147,8 @@ static void sp_free(species_t *s)
 or_case *or_create(const or_params *p)
 {
     if (!p || p->n_cells < 2 || p->n_species < 1 || p->n_species > OR_MAX_SPECIES || p->dt <= 0 || p->length <= 0)
+        return NULL;
+    if (p->circuit < 0 || p->circuit > 1 || (p->circuit == 1 && (p->periodic || !(p->cap >= 0))))
         return NULL;
     or_case *c = calloc(1, sizeof(*c));
     if (!c) return NULL;
@@ -370,10 +376,30 @@ static double drive_voltage(const or_case *c, double t)
     return v;
 }
 
+/* Series blocking capacitor (reading; paper §3.3 reports the DC self-bias
+ * such a capacitor develops).  A capacitor of `cap` F/m^2 sits between the
+ * source V(t) and the electrode at x = 0.  Electrode and capacitor plate form
+ * one isolated conductor whose charge Q per area changes only by the charge
+ * of the particles it absorbs and of the secondary electrons it emits.  The
+ * plate carries cap (phi_0 - V) and the electrode surface sigma = eps0 E_0,
+ * E_0 being the electrode field of Gauss's law over the half cell, so
+ *   Q = eps0 E_0 + cap (phi_0 - V).
+ * Poisson's solution with phi_N = 0 is linear in phi_0: phi = phi_p + phi_0
+ * (1 - i/N), phi_p solving it for phi_0 = 0.  With E_0 = -(phi_1 - phi_0)/dx
+ * - rho_0 dx / (2 eps0) this gives
+ *   phi_0 (cap + eps0/L) = Q + cap V + (eps0/dx) phi_p[1] + rho_0 dx/2.
+ * cap -> infinity is the voltage drive, cap = 0 a floating electrode.  At
+ * load the capacitor is uncharged: phi_0 = V(0) and Q = eps0 E_0. */
+static double circuit_phi0(const or_case *c, double V)
+{
+    double L = c->p.length, dx = c->dx;
+    return (c->q_el + c->p.cap * V + (EPS0 / dx) * c->phi[1] + 0.5 * c->rho[0] * dx) / (c->p.cap + EPS0 / L);
+}
+
 /* deposit every species, form rho, solve for phi and E at time t */
 static void solve_field(or_case *c, double t)
 {
-    int nn = c->n_nodes;
+    int nn = c->n_nodes, N = c->p.n_cells;
     for (int s = 0; s < c->p.n_species; ++s) {
         memset(c->R[s], 0, sizeof(int64_t) * nn);
         or_deposit(c->p.n_cells, c->p.periodic, c->sp[s].n, c->sp[s].xi, c->R[s]);
@@ -384,8 +410,17 @@ static void solve_field(or_case *c, double t)
             r += c->p.q[s] * c->p.w[s] * ((double)c->R[s][i] / TWO32) / node_vol(c, i);
         c->rho[i] = r;
     }
-    or_poisson(c->p.n_cells, c->p.periodic, c->dx, c->rho, c->p.periodic ? 0.0 : drive_voltage(c, t), c->phi);
+    if (!c->p.periodic && c->p.circuit == 1 && c->initialised) {
+        or_poisson(N, 0, c->dx, c->rho, 0.0, c->phi);            /* phi_p */
+        double phi0 = circuit_phi0(c, drive_voltage(c, t));
+        for (int i = 0; i <= N; ++i) c->phi[i] += phi0 * (1.0 - (double)i / N);
+        c->phi[0] = phi0;
+        c->phi[N] = 0.0;
+    } else {
+        or_poisson(c->p.n_cells, c->p.periodic, c->dx, c->rho, c->p.periodic ? 0.0 : drive_voltage(c, t), c->phi);
+    }
     field_from_phi(c);
+    if (!c->p.periodic && c->p.circuit == 1 && !c->initialised) c->q_el = EPS0 * c->E[0];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -589,6 +624,7 @@ static void emit_secondary(or_case *c, uint32_t ion_id, int wall, double *margin
     double vx = wall == 0 ? vn : -vn;
     sp_push(&c->pend[0], xi, vx, vth * t0, vth * t1, ids[0]);
     c->cnt.see_emitted++;
+    if (wall == 0) c->st_see0++;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -671,6 +707,12 @@ static int one_step(or_case *c)
                 c->pw[s] += p->q[s] * p->w[s] * v[0] * (E[0] - p->E_ext[0]);
             if (absorbed >= 0) {                                     /* 4 */
                 c->cnt.absorbed[s][absorbed]++;
+                if (absorbed == 0) c->st_abs0[s]++;
+                if (s == 1 && p->ifedf_emax_ev > 0) {                /* ion energy at the electrode */
+                    double eps = 0.5 * p->m[1] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / ELEM;
+                    double b = floor(eps / p->ifedf_emax_ev * OR_IFEDF_BINS);
+                    if (b >= 0 && b < OR_IFEDF_BINS) c->ifedf[absorbed * OR_IFEDF_BINS + (int)b] += 1.0;
+                }
                 if (s == 1 && p->see_gamma > 0) emit_secondary(c, sp->id[k], absorbed, &margin);
                 continue;
             }
@@ -692,6 +734,14 @@ static int one_step(or_case *c)
         for (int64_t k = 0; k < pd->n; ++k)
             if (sp_push(&c->sp[s], pd->xi[k], pd->vx[k], pd->vy[k], pd->vz[k], pd->id[k])) return -1;
     }
+    if (p->circuit == 1) {                                           /* charge reaching electrode 0 */
+        double dq = p->q[0] * p->w[0] * (double)c->st_abs0[0];
+        if (p->n_species > 1) dq += p->q[1] * p->w[1] * (double)c->st_abs0[1];
+        dq -= p->q[0] * p->w[0] * (double)c->st_see0;                 /* an emitted electron leaves it */
+        c->q_el += dq;
+    }
+    c->st_abs0[0] = c->st_abs0[1] = 0;
+    c->st_see0 = 0;
     solve_field(c, (double)(c->step + 1) * p->dt);                    /* 7, 8, 9 */
     /* 10: moments.  Every step: density and potential.  Diagnostic steps:
      * energy moment, EEPF, kinetic energy over every particle alive after
@@ -819,6 +869,7 @@ void or_reset_moments(or_case *c)
     memset(c->en, 0, sizeof(double) * nn * OR_MAX_SPECIES);
     memset(c->dens_diag, 0, sizeof(double) * nn * OR_MAX_SPECIES);
     memset(c->eepf, 0, sizeof(c->eepf));
+    memset(c->ifedf, 0, sizeof(c->ifedf));
     memset(c->ke, 0, sizeof(c->ke));
     memset(c->pw, 0, sizeof(c->pw));
     int64_t step = c->cnt.step;
@@ -895,6 +946,15 @@ int64_t or_sort_by_cell(int n_cells, int64_t n, const int32_t *cell, int64_t *pe
     free(start);
     return kept;
 }
+
+int or_get_ifedf(const or_case *c, double *out)
+{
+    if (!c || !out) return -1;
+    memcpy(out, c->ifedf, sizeof(c->ifedf));
+    return 0;
+}
+
+double or_get_electrode_charge(const or_case *c) { return c ? c->q_el : 0.0; }
 
 int64_t or_get_field_energy(const or_case *c, double *out, int64_t max_n)
 {

@@ -26,6 +26,7 @@
 #define OR_MAX_PROC 4
 #define OR_NGRID 1000          /* cross-section grid: 1000 log points (1e-3..1e3 eV) */
 #define OR_EEPF_BINS 240       /* 0..60 eV in 0.25 eV bins */
+#define OR_IFEDF_BINS 256      /* ion energy at the electrodes: 256 bins on [0, ifedf_emax_ev) */
 
 enum { OR_ELASTIC = 0, OR_EXCITATION = 1, OR_IONIZATION = 2, OR_ISO = 3, OR_CX = 4 };
 
@@ -50,6 +51,9 @@ typedef struct {
     uint64_t seed;
     int32_t diag_interval;     /* energy moments / EEPF every diag_interval steps (0 = never) */
     int32_t rewind;            /* 1 = velocities loaded at t=0 are pushed back dt/2 before the first step */
+    int32_t circuit;           /* electrode at x = 0: 0 = driven by V(t), 1 = V(t) through a series capacitor */
+    double cap;                /* that capacitor, F/m^2 (0 = floating electrode) */
+    double ifedf_emax_ev;      /* > 0: histogram the energy of ions reaching each electrode */
 } or_params;
 
 typedef struct or_case or_case;
@@ -101,6 +105,12 @@ void or_get_counters(const or_case *c, or_counters *out);
 int  or_get_moments(const or_case *c, double *dens, double *phi_sum, double *en,
                     double *dens_diag, double *eepf, double *ke, double *pw);
 void or_reset_moments(or_case *c);
+/* ion energy histogram at each electrode since the last reset:
+ * out[wall * OR_IFEDF_BINS + b], b = floor(eps / ifedf_emax_ev * OR_IFEDF_BINS) */
+int  or_get_ifedf(const or_case *c, double *out);
+/* charge per area of the electrode at x = 0 with its capacitor plate (series
+ * capacitor circuit), C/m^2 */
+double or_get_electrode_charge(const or_case *c);
 /* field energy per area (J/m^2) after each step since load, n_out values */
 int64_t or_get_field_energy(const or_case *c, double *out, int64_t max_n);
 

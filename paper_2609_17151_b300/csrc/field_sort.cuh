@@ -340,6 +340,9 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
         if (any_bad) atomicOr(&ctrl->err, kErrNumeric);
         if (mode == 1) P.fe_hist[(fe_n % (unsigned long long)P.fe_cap) * kFieldCluster + rank] = (double)t * P.fe_c;
     }
+    cl.barrier_wait();                                            // no CTA leaves while read remotely
+    // Every rank has read the drive phases and counts (its global terms come
+    // before its barrier arrival): rank 0 advances them for the next step.
     if (rank == 0 && tid == 0 && mode == 1) {
         ctrl->fe_n = fe_n + 1;
         ctrl->n_steps_acc += 1;
@@ -357,7 +360,6 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
         }
         ctrl->step = step + 1;
     }
-    cl.barrier_wait();                                            // no CTA leaves while read remotely
 }
 
 __global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldThreads)

@@ -479,6 +479,100 @@ def test_secondary_emission_is_binomial_and_inward():
     assert abs(np.abs(e["vx"]).mean() / (vth * math.sqrt(np.pi / 2)) - 1) < 0.02
 
 
+# --------------------------------------------------------------------------- electrode circuit, IFEDF
+EPS0 = 8.8541878128e-12
+
+
+def _circuit_cfg(cap, harmonics, *, n_cells=40, L=0.02, see=0.0, w=1e10, ifedf=0.0, dt=1e-10):
+    return dict(periodic=0, n_cells=n_cells, length=L, dt=dt, gas_density=0.0, gas_temp=300.0,
+                gas_mass=W.M_AR, harmonics=harmonics, see_gamma=see, see_temp_ev=1.0,
+                species=[dict(q=-E, m=W.M_E, w=w), dict(q=E, m=W.M_AR, w=w)], seed=8, rewind=0,
+                circuit="capacitor", blocking_cap=cap, ifedf_emax_ev=ifedf)
+
+
+def _empty(c):
+    z = np.zeros(0)
+    for sp in (0, 1):
+        c.load_particles(sp, z, z, z, z, np.zeros(0, dtype=np.uint32))
+
+
+@pytest.mark.parametrize("cap", [0.0, 3e-10, 1e-8])
+def test_capacitor_in_series_with_vacuum_gap_is_a_divider(cap):
+    """Empty gap: the capacitor (cap) and the gap (eps0/L) divide every change
+    of the source from its value at load, phi_0(t) = (eps0 V(0)/L + cap V(t)) /
+    (cap + eps0/L), and the potential is linear across the gap."""
+    f, V0, L, N = 13.56e6, 100.0, 0.02, 40
+    cfg = _circuit_cfg(cap, [(f, V0, 0.3)], n_cells=N, L=L)
+    c = oracle.Case(cfg)
+    _empty(c)
+    for k in (1, 7, 20):
+        c.step(k - (0 if k == 1 else {7: 1, 20: 7}[k]))
+        t = k * cfg["dt"]
+        V = V0 * math.cos(2 * math.pi * f * t + 0.3)
+        expect = (EPS0 * V0 * math.cos(0.3) / L + cap * V) / (cap + EPS0 / L)
+        phi, Ef = c.field()
+        assert abs(phi[0] - expect) < 1e-12 * V0
+        assert np.allclose(phi, phi[0] * (1 - np.arange(N + 1) / N), atol=1e-12 * V0)
+        q0 = EPS0 * V0 * math.cos(0.3) / L
+        assert abs(c.electrode_charge() - q0) < 1e-12 * q0
+
+
+def test_capacitor_charge_follows_absorbed_and_emitted_particles():
+    """An ion reaches electrode 0 and releases an electron (gamma = 1): the
+    electrode's charge grows by q_i w - q_e w.  Without emission the gap is
+    then empty and phi_0 = (Q + cap V) / (cap + eps0/L)."""
+    cap, w, L, N = 2e-9, 1e9, 0.02, 40
+    z = np.zeros(0)
+    out = []
+    for see in (1.0, 0.0):
+        c = oracle.Case(_circuit_cfg(cap, [(0.0, 50.0, 0.0)], n_cells=N, L=L, see=see, w=w, dt=1e-10))
+        c.load_particles(0, z, z, z, z, np.zeros(0, dtype=np.uint32))
+        c.load_particles(1, np.array([0.3]), np.array([-2e6]), np.zeros(1), np.zeros(1),
+                         np.array([5], dtype=np.uint32))
+        c.step(0)                                                   # the field at load fixes Q
+        q0 = c.electrode_charge()
+        c.step(1)
+        assert c.counters()["absorbed"][1][0] == 1 and c.counters()["see_emitted"] == int(see)
+        out.append((c, q0))
+    (c1, q1), (c2, q2) = out
+    assert abs(c1.electrode_charge() - (q1 + E * w + E * w)) < 1e-14 * abs(q1)
+    Q = c2.electrode_charge()
+    assert abs(Q - (q2 + E * w)) < 1e-14 * abs(q2)
+    phi, _ = c2.field()
+    assert abs(phi[0] - (Q + cap * 50.0) / (cap + EPS0 / L)) < 1e-12 * 50.0
+
+
+def test_large_capacitor_is_the_voltage_drive():
+    """cap -> infinity: the series circuit reproduces the voltage-driven case."""
+    cfg, parts = W.ccp_case(seed=3, n_cells=64, gap=0.003, n_per_species=3000, te_ev=20.0)
+    ref = oracle.Case(cfg)
+    big = oracle.Case(dict(cfg, circuit="capacitor", blocking_cap=1e6))
+    for c in (ref, big):
+        for sp, p in enumerate(parts):
+            c.load_particles(sp, W.as_xi(p), p["vx"], p["vy"], p["vz"], p["id"])
+        c.step(3)
+    pa, pb = ref.field()[0], big.field()[0]
+    assert np.abs(pa - pb).max() < 1e-9 * np.abs(pa).max()
+
+
+def test_ion_energy_histogram_of_a_monoenergetic_beam():
+    """Ions of 51.3 eV all reaching electrode 0 in one step land in bin
+    floor(51.3 / 100 * 256) = 131 of its histogram (negligible space charge)."""
+    n = 500
+    cfg = _circuit_cfg(1e6, [], n_cells=20, L=0.002, w=1e-6, ifedf=100.0, dt=1e-9)
+    c = oracle.Case(cfg)
+    v = math.sqrt(2 * 51.3 * E / W.M_AR)
+    rng = np.random.default_rng(2)
+    z = np.zeros(0)
+    c.load_particles(0, z, z, z, z, np.zeros(0, dtype=np.uint32))
+    c.load_particles(1, rng.uniform(0.0, 0.1, n), np.full(n, -v), np.zeros(n), np.zeros(n),
+                     np.arange(n, dtype=np.uint32))
+    c.step(1)
+    h = c.ifedf()
+    assert h.shape == (2, oracle.IFEDF_BINS)
+    assert h[0][131] == n and h.sum() == n
+
+
 # --------------------------------------------------------------------------- moments
 def test_uniform_plasma_density_moment_including_half_wall_cells():
     """A uniform load between electrodes gives the loaded density at every node,
