@@ -49,10 +49,11 @@ typedef enum {
 /* collision process kinds (cumulative sums follow the load order) */
 enum { PIC_ELASTIC = 0, PIC_EXCITATION = 1, PIC_IONIZATION = 2, PIC_ISO = 3, PIC_CX = 4 };
 
-#define PIC_DESC_VERSION 1u
+#define PIC_DESC_VERSION 2u
 #define PIC_MAX_PROC 4
 #define PIC_NGRID 1000          /* cross-section grid: 1000 energies log-spaced on [1e-3, 1e3] eV */
 #define PIC_EEPF_BINS 240       /* 0..60 eV in 0.25 eV bins */
+#define PIC_IFEDF_BINS 256      /* ion energy at each electrode: bins of ifedf_emax_ev / 256 */
 
 /* Case descriptor: versioned plain data, SI units (paper §1's dialog). */
 typedef struct {
@@ -83,6 +84,23 @@ typedef struct {
     int32_t rewind;               /* 1: velocities given to pic_load_particles are at t = 0 and are
                                      pushed back by dt/2 before the first step (leapfrog start) */
     int32_t field_history;        /* field-energy history length kept on the device; 0 = 65536 */
+    int32_t circuit;              /* electrode at x = 0: 0 = held at V(t); 1 = V(t) through a series
+                                     blocking capacitor (bounded cases).  Electrode and capacitor plate
+                                     form one conductor whose charge Q changes only by the particles it
+                                     absorbs and the secondary electrons it emits; each step
+                                     phi_0 (C + eps0/L) = Q + C V + (eps0/dx) phi_p(1) + rho_0 dx/2, phi_p
+                                     the potential for phi_0 = 0 (paper §3.3 reports the DC self-bias such
+                                     a capacitor develops).  At load the capacitor is uncharged. */
+                                  /* 2 = the current density J(t) is imposed on it instead (the harmonics
+                                     read as A/m^2, into the electrode; paper §3.2 drives Godyak's
+                                     discharges this way): Q also gains J(t^{n+1}) dt each step and
+                                     phi_0 eps0/L = Q + (eps0/dx) phi_p(1) + rho_0 dx/2; phi_0 = 0 at load. */
+    double blocking_cap_F_per_m2; /* C of circuit 1 (0 = floating electrode) */
+    double ifedf_emax_ev;         /* > 0: histogram the energy of the ions reaching each electrode,
+                                     PIC_IFEDF_BINS bins on [0, ifedf_emax_ev) (paper §3.3's ion
+                                     flux-energy distributions); energies beyond are not counted */
+    int32_t no_field;             /* 1: no Poisson solve, the particles feel only E_ext (swarm runs of the
+                                     paper's §4); densities and counters are still accumulated */
     void *stream;                 /* cudaStream_t to enqueue on; NULL = a stream owned by the case */
     /* optional device allocator (e.g. a framework's caching allocator); NULL = cudaMalloc */
     void *(*alloc)(size_t bytes, void *ctx);
@@ -196,6 +214,10 @@ typedef struct {
     int32_t reset;                 /* in: nonzero = clear the sums after reading */
     int32_t sort_interval;         /* out: steps between sorts in use (chosen by the autotuner when
                                       desc.sort_interval = 0) */
+    double *ifedf;                 /* [2 * PIC_IFEDF_BINS] ion counts per energy bin, electrode x = 0 then
+                                      x = L (desc.ifedf_emax_ev > 0) */
+    double electrode_charge;       /* out: charge per area of the electrode at x = 0 and its capacitor
+                                      plate (circuit 1), C/m^2 */
 } pic_moments;
 
 pic_status pic_read_moments(pic_case *c, pic_moments *out);
@@ -234,6 +256,24 @@ pic_status pic_read_tuning(pic_case *c, pic_tuning *out);
  * the shape.  With desc.sort_interval = 0 an autotuner that has not run yet
  * still chooses later.  Errors: PIC_EINVAL (bad species, threads or stages). */
 pic_status pic_set_step_shape(pic_case *c, int species, int threads, int stages);
+
+/* Checkpoint and resume (paper §1: the program saves a run and resumes it).
+ * The state between two steps (particles of both species including slots of
+ * absorbed particles not yet compacted, the control block with the step
+ * counter, drive phases and circuit charge, the field, the moment sums and
+ * the sort and launch settings) goes into one caller-owned host buffer.
+ * Random numbers are drawn from (id, step) counters, so a case restored into
+ * a case created from the same descriptor continues bit-identically to an
+ * uninterrupted run.
+ *   pic_checkpoint_size: bytes needed now.
+ *   pic_checkpoint_save: synchronises, writes the state (bytes >= size).
+ *   pic_checkpoint_load: restores into c; c's descriptor must match the saved
+ *   one in cells, species, charges, masses, weights, dt, length and seed.
+ * Errors: PIC_EINVAL (NULL, buffer too small, not a checkpoint, descriptor
+ * mismatch), PIC_ECAPACITY (saved particles exceed c's capacity), PIC_ECUDA. */
+pic_status pic_checkpoint_size(pic_case *c, uint64_t *bytes);
+pic_status pic_checkpoint_save(pic_case *c, void *host, uint64_t bytes);
+pic_status pic_checkpoint_load(pic_case *c, const void *host, uint64_t bytes);
 
 /* Free everything the case owns.  Safe on NULL. */
 pic_status pic_destroy(pic_case *c);

@@ -55,6 +55,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64),
         ("diag_interval", C.c_int32), ("rewind", C.c_int32),
         ("circuit", C.c_int32), ("cap", C.c_double), ("ifedf_emax_ev", C.c_double),
+        ("no_field", C.c_int32),
     ]
 
 
@@ -191,9 +192,10 @@ def make_params(cfg: dict) -> Params:
     p.seed = int(cfg.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
     p.diag_interval = int(cfg.get("diag_interval", 0))
     p.rewind = int(cfg.get("rewind", 1))
-    p.circuit = 1 if cfg.get("circuit", "voltage") == "capacitor" else 0
+    p.circuit = {"voltage": 0, "capacitor": 1, "current": 2}[cfg.get("circuit", "voltage")]
     p.cap = float(cfg.get("blocking_cap", 0.0))
     p.ifedf_emax_ev = float(cfg.get("ifedf_emax_ev", 0.0))
+    p.no_field = int(bool(cfg.get("no_field", False)))
     return p
 
 

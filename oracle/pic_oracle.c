@@ -148,7 +148,7 @@ or_case *or_create(const or_params *p)
 {
     if (!p || p->n_cells < 2 || p->n_species < 1 || p->n_species > OR_MAX_SPECIES || p->dt <= 0 || p->length <= 0)
         return NULL;
-    if (p->circuit < 0 || p->circuit > 1 || (p->circuit == 1 && (p->periodic || !(p->cap >= 0))))
+    if (p->circuit < 0 || p->circuit > 2 || (p->circuit >= 1 && (p->periodic || !(p->cap >= 0))))
         return NULL;
     or_case *c = calloc(1, sizeof(*c));
     if (!c) return NULL;
@@ -396,6 +396,15 @@ static double circuit_phi0(const or_case *c, double V)
     return (c->q_el + c->p.cap * V + (EPS0 / dx) * c->phi[1] + 0.5 * c->rho[0] * dx) / (c->p.cap + EPS0 / L);
 }
 
+/* Current-source drive (reading; paper §3.2 runs Godyak's discharges with the
+ * current imposed): circuit 2 imposes J(t) = sum_h A_h cos(2 pi f_h t +
+ * theta_h) (A/m^2, into the electrode) on the electrode at x = 0.  Its charge
+ * then changes by J(t^{n+1}) dt each step besides the absorbed and emitted
+ * particles, and phi_0 follows from the relation above with no capacitor
+ * (cap = 0): phi_0 eps0/L = Q + (eps0/dx) phi_p[1] + rho_0 dx/2.  At load the
+ * electrode is at phi_0 = 0 and Q = eps0 E_0. */
+static double drive_current(const or_case *c, double t) { return drive_voltage(c, t); }
+
 /* deposit every species, form rho, solve for phi and E at time t */
 static void solve_field(or_case *c, double t)
 {
@@ -410,17 +419,23 @@ static void solve_field(or_case *c, double t)
             r += c->p.q[s] * c->p.w[s] * ((double)c->R[s][i] / TWO32) / node_vol(c, i);
         c->rho[i] = r;
     }
-    if (!c->p.periodic && c->p.circuit == 1 && c->initialised) {
+    if (c->p.no_field) {                                         /* swarm: only the imposed field */
+        memset(c->phi, 0, sizeof(double) * nn);
+        memset(c->E, 0, sizeof(double) * nn);
+        return;
+    }
+    if (!c->p.periodic && c->p.circuit >= 1 && c->initialised) {
         or_poisson(N, 0, c->dx, c->rho, 0.0, c->phi);            /* phi_p */
-        double phi0 = circuit_phi0(c, drive_voltage(c, t));
+        double phi0 = circuit_phi0(c, c->p.circuit == 1 ? drive_voltage(c, t) : 0.0);
         for (int i = 0; i <= N; ++i) c->phi[i] += phi0 * (1.0 - (double)i / N);
         c->phi[0] = phi0;
         c->phi[N] = 0.0;
     } else {
-        or_poisson(c->p.n_cells, c->p.periodic, c->dx, c->rho, c->p.periodic ? 0.0 : drive_voltage(c, t), c->phi);
+        double phi_left = (c->p.periodic || c->p.circuit == 2) ? 0.0 : drive_voltage(c, t);
+        or_poisson(c->p.n_cells, c->p.periodic, c->dx, c->rho, phi_left, c->phi);
     }
     field_from_phi(c);
-    if (!c->p.periodic && c->p.circuit == 1 && !c->initialised) c->q_el = EPS0 * c->E[0];
+    if (!c->p.periodic && c->p.circuit >= 1 && !c->initialised) c->q_el = EPS0 * c->E[0];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -734,10 +749,11 @@ static int one_step(or_case *c)
         for (int64_t k = 0; k < pd->n; ++k)
             if (sp_push(&c->sp[s], pd->xi[k], pd->vx[k], pd->vy[k], pd->vz[k], pd->id[k])) return -1;
     }
-    if (p->circuit == 1) {                                           /* charge reaching electrode 0 */
+    if (p->circuit >= 1) {                                           /* charge reaching electrode 0 */
         double dq = p->q[0] * p->w[0] * (double)c->st_abs0[0];
         if (p->n_species > 1) dq += p->q[1] * p->w[1] * (double)c->st_abs0[1];
         dq -= p->q[0] * p->w[0] * (double)c->st_see0;                 /* an emitted electron leaves it */
+        if (p->circuit == 2) dq += p->dt * drive_current(c, (double)(c->step + 1) * p->dt);
         c->q_el += dq;
     }
     c->st_abs0[0] = c->st_abs0[1] = 0;

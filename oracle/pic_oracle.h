@@ -51,9 +51,11 @@ typedef struct {
     uint64_t seed;
     int32_t diag_interval;     /* energy moments / EEPF every diag_interval steps (0 = never) */
     int32_t rewind;            /* 1 = velocities loaded at t=0 are pushed back dt/2 before the first step */
-    int32_t circuit;           /* electrode at x = 0: 0 = driven by V(t), 1 = V(t) through a series capacitor */
+    int32_t circuit;           /* electrode at x = 0: 0 = driven by V(t), 1 = V(t) through a series capacitor,
+                                  2 = driven by the current density J(t) (the harmonics in A/m^2) */
     double cap;                /* that capacitor, F/m^2 (0 = floating electrode) */
     double ifedf_emax_ev;      /* > 0: histogram the energy of ions reaching each electrode */
+    int32_t no_field;          /* 1: no Poisson solve; the particles feel only E_ext (swarm runs) */
 } or_params;
 
 typedef struct or_case or_case;

@@ -134,6 +134,7 @@ struct FieldPart {
     unsigned long long seg[2], all[2];  // interior / all-node raw charge of the slice
     u128 qp[2];                         // sum over slice m < N of the local prefix p_s[m]
     u128 qq[2];                         // sum over slice i < N of e_s[i] = sum_{c_lo <= m < i} p_s[m]
+    unsigned long long r0[2];           // rank 0: raw deposit of node 0 (series-capacitor circuit)
 };
 
 __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
@@ -148,7 +149,7 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
     __shared__ FieldPart pub;                                       // this CTA's published moments
     __shared__ unsigned long long g_off[2], g_seg[2];               // slice prefix offset O_s, total interior charge
     __shared__ u128 g_qoff[2];                                      // Q_s[c_lo]
-    __shared__ double g_b, g_d0, g_pm, g_phi0;
+    __shared__ double g_b, g_d0, g_pm, g_phi0, g_qel;
     const int rank = (int)cl.block_rank();
     const int N = P.n_cells, nn = P.n_nodes, tid = threadIdx.x, ns = P.n_species;
     const int per_cta = (N + 1 + kFieldCluster - 1) / kFieldCluster;   // <= kFieldThreads (n_cells <= 4096)
@@ -211,6 +212,7 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
             pub.all[s] = sp ? ptot[2 + s] : 0ull;
             pub.qp[s] = sp ? qp_tot[s] : (u128)0;
             pub.qq[s] = sp ? qq_tot[s] : (u128)0;
+            pub.r0[s] = sp ? r[s] : 0ull;
         }
     }
     cl.sync();                                                      // the one exchange
@@ -264,6 +266,22 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
             if (P.periodic) b = -(P.cq[0] * (double)(long long)alltot[0] + P.cq[1] * (double)(long long)alltot[1]) * P.inv_n;
             const double Nd = (double)N;
             const double TN = fma(P.cq[0], u128_to_double(qn[0]), fma(P.cq[1], u128_to_double(qn[1]), b * (0.5 * Nd * (Nd - 1.0))));
+            double q_el = 0.0;
+            if (P.circuit && mode == 1) {
+                // (circuit 2: phi0 holds J(t^{n+1}) and c_blk = 0)
+                // series capacitor: the electrode's charge takes this step's
+                // absorbed and emitted particles; then phi_0 (C + eps0/L) =
+                // Q + C V + (eps0/L) T_N + rho_0 dx/2, with (eps0/L) T_N the
+                // (eps0/dx) phi_1 of the solution for phi_0 = 0
+                double dq = P.qw[0] * (double)ctrl->st_abs0[0];
+                if (ns > 1) dq += P.qw[1] * (double)ctrl->st_abs0[1];
+                dq -= P.qw[0] * (double)ctrl->st_see0;
+                if (P.circuit == 2) dq += P.dt * phi0;
+                q_el = ctrl->q_el + dq;
+                const double rho0_half =
+                    fma(P.r0c[0], (double)(long long)q.r0[0], fma(P.r0c[1], (double)(long long)q.r0[1], P.bg_half));
+                phi0 = (q_el + P.c_blk * phi0 + P.eps0_L * TN + rho0_half) * P.inv_cap_eps0_L;
+            }
             const double d0 = (TN - phi0) * P.inv_n;
             double pm = 0.0;
             if (P.periodic) {                                       // mean of phi_0 + i d_0 - T_i over i < N
@@ -274,7 +292,7 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
             g_off[0] = my_off0; g_off[1] = my_off1;
             g_qoff[0] = my_q0; g_qoff[1] = my_q1;
             g_seg[0] = segtot[0]; g_seg[1] = segtot[1];
-            g_b = b; g_d0 = d0; g_pm = pm; g_phi0 = phi0;
+            g_b = b; g_d0 = d0; g_pm = pm; g_phi0 = phi0; g_qel = q_el;
         }
     }
     cl.barrier_arrive();                                          // done reading the other slices
@@ -312,6 +330,11 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
             double rq = P.bg_charge;                                // charge density of the wall node
             for (int s = 0; s < ns; ++s) rq = fma(P.rho_wall[s], (double)(long long)r[s], rq);
             E = i == 0 ? -d0 * P.inv_dx - rq * P.half_dx_eps0 : (Ssh[tid] - d0) * P.inv_dx + rq * P.half_dx_eps0;
+            if (mode == 0 && P.circuit && i == 0) {                // at load the capacitor is uncharged
+                ctrl->q_el = P.eps0 * E;
+                ctrl->st_abs0[0] = ctrl->st_abs0[1] = 0ull;
+                ctrl->st_see0 = 0ull;
+            }
             fe = 0.5f * (float)E * (float)E;
         } else {
             E = (Ssh[tid + 1] + Ssh[tid] - 2.0 * d0) * P.inv_2dx;
@@ -324,6 +347,7 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
         if (ns > 1) T = fma(cq1, u128_to_double(g_qoff[1] + (u128)k * g_off[1] + e[1]), T);
         double ph = fma((double)i, d0, phi0) - T - pm;
         if (!P.periodic && i == N) ph = 0.0;
+        if (P.no_field) { E = 0.0; ph = 0.0; fe = 0.0f; }    // swarm: only the imposed field acts
         P.E[i] = E;
         P.phi[i] = ph;
         P.E32[i] = (float)E;
@@ -359,12 +383,21 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
             ctrl->drive_s[h] = sn * P.rot_c[h] + c * P.rot_s[h];
         }
         ctrl->step = step + 1;
+        if (P.circuit) {
+            ctrl->q_el = g_qel;
+            ctrl->st_abs0[0] = ctrl->st_abs0[1] = 0ull;
+            ctrl->st_see0 = 0ull;
+        }
     }
 }
 
+// Waits for the step's particle kernels (programmatic launch), then lets the
+// next step's electron kernel start its prologue on the other SMs.
 __global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldThreads)
     k_field(const __grid_constant__ StepConst P, int mode)
 {
+    grid_dep_wait();
+    grid_dep_launch();
     field_solve(P, mode);
 }
 

@@ -83,7 +83,7 @@ __device__ __forceinline__ float nu_at(const float *tab, GridPos g, float eps, f
 // Event counts of one thread over a work item (registers; reduced per warp
 // and added to the case's counters once per item).
 struct EvCount {
-    unsigned cand, coll[kMaxProc], iz, absorbed[2], see;
+    unsigned cand, coll[kMaxProc], iz, absorbed[2], see, see0;
 };
 __device__ __forceinline__ void count_proc(EvCount &ev, int proc)
 {
@@ -250,6 +250,7 @@ __device__ __forceinline__ void emit_secondary(const StepConst &P, uint32_t id, 
     const float vx = wall == 0 ? vn : -vn;
     append_particle(P, 0, half_e, c, o, vx, P.see_vth * t.x, P.see_vth * t.y, ids.x, diag);
     ev.see++;
+    if (wall == 0) ev.see0++;
 }
 
 // Shared deposit histogram, per cell: particle count n and the sum of the
@@ -319,7 +320,7 @@ struct StepShared {
     unsigned tile_rel[kMaxStages];                      // warps done reading each buffer (running count)
     unsigned tile_abort;                                // a tile wait gave up: stop streaming
     unsigned s_cnt[2 + 2 * kMaxProc];                   // candidates, per process, ionizations
-    unsigned s_abs[2], s_see;
+    unsigned s_abs[2], s_see, s_see0;
     float s_red[2][kStepThreads / 32];
 };
 
@@ -379,7 +380,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     if (diag) for (int j = tid; j < kEepfBins; j += blockDim.x) heepf[j] = 0u;
     if (tid < 2 + 2 * kMaxProc) s_cnt[tid] = 0u;
     if (tid < 2) s_abs[tid] = 0u;
-    if (tid == 0) sh.s_see = 0u;
+    if (tid == 0) { sh.s_see = 0u; sh.s_see0 = 0u; }
     const bool staged = mbar_wait_bounded(&sh.mbar, ctrl, parity);
     parity ^= 1u;
     if (!__syncthreads_and(staged)) return;
@@ -511,6 +512,10 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
                 // 4. electrode absorption (+ secondary emission by ions)
                 const int wall = c < 0 ? 0 : 1;
                 ev.absorbed[wall]++;
+                if (SP == 1 && P.ifedf_scale > 0.0f) {        // ion energy at the electrode
+                    const int bin = (int)(S.m_over_2e * (v.x * v.x + v.y * v.y + v.z * v.z) * P.ifedf_scale);
+                    if (bin >= 0 && bin < kIfedfBins) atomicAdd(&P.ifedf[wall * kIfedfBins + bin], 1ull);
+                }
                 if (SP == 1 && P.see_gamma > 0.0f) emit_secondary(P, ids[q], step, wall, half_e, diag, ev);
                 cc[q] = -1;
                 oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
@@ -595,14 +600,15 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     // CTA epilogue: event counts (warp sums, one shared atomic per warp), histogram
     {
         unsigned vals[2 + 2 * kMaxProc] = {ev.cand, ev.coll[0], ev.coll[1], ev.coll[2], ev.coll[3], ev.iz,
-                                           ev.absorbed[0], ev.absorbed[1], ev.see, 0u};
+                                           ev.absorbed[0], ev.absorbed[1], ev.see, ev.see0};
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
+        for (int k = 0; k < 10; ++k) {
             const unsigned w = __reduce_add_sync(0xffffffffu, vals[k]);
             if (lane == 0 && w) {
                 if (k < 6) atomicAdd(&s_cnt[k], w);
                 else if (k < 8) atomicAdd(&s_abs[k - 6], w);
-                else atomicAdd(&sh.s_see, w);
+                else if (k == 8) atomicAdd(&sh.s_see, w);
+                else atomicAdd(&sh.s_see0, w);
             }
         }
     }
@@ -638,6 +644,8 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         if (s_abs[0]) { atomicAdd(&ctrl->absorbed[SP][0], (unsigned long long)s_abs[0]); }
         if (s_abs[1]) { atomicAdd(&ctrl->absorbed[SP][1], (unsigned long long)s_abs[1]); }
         if (s_abs[0] + s_abs[1]) atomicAdd(&ctrl->n_dead[SP], (unsigned long long)(s_abs[0] + s_abs[1]));
+        if (P.circuit && s_abs[0]) atomicAdd(&ctrl->st_abs0[SP], (unsigned long long)s_abs[0]);
+        if (P.circuit && sh.s_see0) atomicAdd(&ctrl->st_see0, (unsigned long long)sh.s_see0);
         if (sh.s_see) atomicAdd(&ctrl->see, (unsigned long long)sh.s_see);
         if (s_cnt[0]) atomicAdd(&ctrl->cand[SP], (unsigned long long)s_cnt[0]);
         for (int k = 0; k < kMaxProc; ++k)
@@ -648,6 +656,13 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
 }
 
 // One case: CTA b takes the b-th of gridDim.x slices of the species.
+// Launch chain of a step (programmatic dependent launches): the electron
+// kernel waits for the previous field solve, then lets the ion kernel launch;
+// the ion kernel reads nothing the electron kernel writes (each species
+// processes its own first n_active slots, appends go beyond them, deposits
+// and counters are atomic), so it runs into the electron kernel's tail and
+// waits for it only before exiting, which keeps the field solve (launched
+// after it, waiting for it) behind both.
 template <int SP, bool PERIODIC, int MCC, bool STAGED>
 // launch bounds: up to 1024 threads, 64 registers (two 512-thread or four
 // 256-thread CTAs per SM when shared memory allows)
@@ -661,8 +676,16 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_particle_step(const __grid_
         sh.tile_abort = 0u;
     }
     __syncthreads();
+    if (SP == 0) {
+        grid_dep_wait();
+        grid_dep_launch();
+    }
     unsigned parity = 0, tile_phase = 0;
     particle_item<SP, PERIODIC, MCC, STAGED>(P, smem, sh, parity, tile_phase, blockIdx.x, gridDim.x);
+    if (SP == 1) {
+        grid_dep_launch();
+        grid_dep_wait();
+    }
 }
 
 // Out-of-line item for the batch kernel: each species' body keeps its own

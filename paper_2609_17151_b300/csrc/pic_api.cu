@@ -217,6 +217,26 @@ pic_status upload_tables(pic_case *c, int sp)
     return PIC_OK;
 }
 
+// Launch with programmatic stream serialization: the kernel may begin while
+// the stream's previous kernel finishes (it orders itself with
+// griddepcontrol; see k_particle_step and k_field).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_programmatic(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Dynamic shared memory a step kernel may use: the device's opt-in maximum
 // per block less a margin for the kernels' static shared memory (at most
 // StepShared + one StepConst).  The cap is a property of the kernel, shared
@@ -278,7 +298,8 @@ cudaError_t launch_step_k(pic_case *c, int stages)
     }
     c->P.sp[SP].stages = stages;
     Timed t(c, KC_STEP, 1);
-    k<<<c->step_grid[SP], threads, smem, c->stream>>>(c->P);
+    e = launch_programmatic(k, dim3(c->step_grid[SP]), dim3(threads), smem, c->stream, c->P);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -308,7 +329,9 @@ cudaError_t launch_step_sp(pic_case *c)
 cudaError_t launch_field(pic_case *c, int mode)
 {
     Timed t(c, mode == 0 ? KC_INIT : KC_FIELD, 1);
-    k_field<<<kFieldCluster, kFieldThreads, c->field_smem, c->stream>>>(c->P, mode);
+    cudaError_t e = launch_programmatic(k_field, dim3(kFieldCluster), dim3(kFieldThreads), c->field_smem, c->stream,
+                                        c->P, mode);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -403,6 +426,7 @@ pic_status reset_moments(pic_case *c)
     CU(cudaMemsetAsync(c->P.ke_sum, 0, sizeof(double) * 2, c->stream));
     CU(cudaMemsetAsync(c->P.pw_sum, 0, sizeof(double) * 2, c->stream));
     CU(cudaMemsetAsync(c->P.eepf, 0, sizeof(unsigned long long) * kEepfBins, c->stream));
+    CU(cudaMemsetAsync(c->P.ifedf, 0, sizeof(unsigned long long) * 2 * kIfedfBins, c->stream));
     k_reset_counters<<<1, 1, 0, c->stream>>>(c->P.ctrl);
     CU(cudaGetLastError());
     return PIC_OK;
@@ -746,6 +770,11 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     if (desc->n_species < 1 || desc->n_species > 2) return fail(PIC_EINVAL, "n_species must be 1 or 2");
     if (!(desc->dt_s > 0) || !(desc->length_m > 0)) return fail(PIC_EINVAL, "dt and length must be positive");
     if (desc->n_harm < 0 || desc->n_harm > 4) return fail(PIC_EINVAL, "n_harm must be in [0, 4]");
+    if (desc->circuit < 0 || desc->circuit > 2) return fail(PIC_EINVAL, "circuit must be 0, 1 or 2");
+    if (desc->circuit >= 1 && desc->periodic) return fail(PIC_EINVAL, "an electrode circuit needs electrodes");
+    if (desc->circuit == 1 && (!(desc->blocking_cap_F_per_m2 >= 0) || !std::isfinite(desc->blocking_cap_F_per_m2)))
+        return fail(PIC_EINVAL, "a series capacitor needs a finite capacitance >= 0");
+    if (!(desc->ifedf_emax_ev >= 0)) return fail(PIC_EINVAL, "ifedf_emax_ev must be >= 0");
     for (int s = 0; s < desc->n_species; ++s)
         if (!(desc->mass_kg[s] > 0)) return fail(PIC_EINVAL, "species mass must be positive");
     pic_case *c = new pic_case();
@@ -792,11 +821,23 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
         P.rot_c[h] = std::cos(2.0 * M_PI * desc->harm_freq_hz[h] * desc->dt_s);
         P.rot_s[h] = std::sin(2.0 * M_PI * desc->harm_freq_hz[h] * desc->dt_s);
     }
+    if (desc->circuit == 2) P.v_init = 0.0;                  // current drive: electrode at 0 V at load
     for (int s = 0; s < 2; ++s) {
         const double qw = s < desc->n_species ? desc->charge_C[s] * desc->weight_per_m2[s] / 4294967296.0 : 0.0;
         P.cq[s] = qw * dx / kEps0;
         P.rho_wall[s] = qw / (0.5 * dx);
     }
+    P.circuit = desc->circuit;
+    P.c_blk = desc->circuit == 1 ? desc->blocking_cap_F_per_m2 : 0.0;
+    P.no_field = desc->no_field ? 1 : 0;
+    P.eps0_L = kEps0 / desc->length_m;
+    P.inv_cap_eps0_L = 1.0 / (P.c_blk + P.eps0_L);
+    for (int s = 0; s < 2; ++s) {
+        P.qw[s] = s < desc->n_species ? desc->charge_C[s] * desc->weight_per_m2[s] : 0.0;
+        P.r0c[s] = P.qw[s] / 4294967296.0;
+    }
+    P.bg_half = P.bg_charge * 0.5 * dx;
+    P.ifedf_scale = desc->ifedf_emax_ev > 0 ? (float)(kIfedfBins / desc->ifedf_emax_ev) : 0.0f;
     P.n_harm = desc->n_harm;
     for (int h = 0; h < 4; ++h) { P.harm_f[h] = desc->harm_freq_hz[h]; P.harm_a[h] = desc->harm_amp_v[h]; P.harm_p[h] = desc->harm_phase_rad[h]; }
     const size_t nn = (size_t)c->n_nodes;
@@ -820,7 +861,8 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     P.fe_hist = (double *)c->dalloc(sizeof(double) * (size_t)P.fe_cap * kFieldCluster);
     P.sort_count = (unsigned *)c->dalloc(sizeof(unsigned) * N);
     P.sort_cursor = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * (N + 1));
-    if (!P.E32 || !P.E || !P.phi || !P.R[0] || !P.R[1] || !c->R_last || !P.ctrl || !P.Rsum || !P.Rdiag ||
+    P.ifedf = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * 2 * kIfedfBins);
+    if (!P.ifedf || !P.E32 || !P.E || !P.phi || !P.R[0] || !P.R[1] || !c->R_last || !P.ctrl || !P.Rsum || !P.Rdiag ||
         !P.en_sum || !P.phi_sum || !P.ke_sum || !P.pw_sum || !P.eepf || !P.fe_hist || !P.sort_count || !P.sort_cursor) {
         pic_destroy(c);
         return fail(PIC_ENOMEM, "device allocation failed");
@@ -1133,8 +1175,9 @@ pic_status pic_read_moments(pic_case *c, pic_moments *m)
     CU(cudaMemcpyAsync(rd.data(), c->P.Rdiag, 2 * nn * 8, cudaMemcpyDeviceToHost, c->stream));
     if (m->phi_sum) CU(cudaMemcpyAsync(m->phi_sum, c->P.phi_sum, nn * 8, cudaMemcpyDeviceToHost, c->stream));
     if (m->en_sum) CU(cudaMemcpyAsync(m->en_sum, c->P.en_sum, ns * nn * 8, cudaMemcpyDeviceToHost, c->stream));
-    std::vector<unsigned long long> ee(kEepfBins);
+    std::vector<unsigned long long> ee(kEepfBins), ifd(2 * kIfedfBins);
     CU(cudaMemcpyAsync(ee.data(), c->P.eepf, kEepfBins * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(ifd.data(), c->P.ifedf, 2 * kIfedfBins * 8, cudaMemcpyDeviceToHost, c->stream));
     std::vector<double> fe((size_t)c->P.fe_cap * kFieldCluster);
     CU(cudaMemcpyAsync(fe.data(), c->P.fe_hist, fe.size() * 8, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
@@ -1163,6 +1206,8 @@ pic_status pic_read_moments(pic_case *c, pic_moments *m)
     m->see_emitted = (int64_t)h.see;
     m->ionizations = (int64_t)h.iz;
     if (m->eepf) for (int b = 0; b < kEepfBins; ++b) m->eepf[b] = (double)ee[b];
+    if (m->ifedf) for (int b = 0; b < 2 * kIfedfBins; ++b) m->ifedf[b] = (double)ifd[b];
+    m->electrode_charge = h.q_el;
     const long long have = std::min<long long>((long long)h.fe_n, c->P.fe_cap);
     long long want = m->field_energy ? std::min<long long>(have, m->field_energy_cap) : 0;
     for (long long i = 0; i < want; ++i) {
@@ -1217,6 +1262,171 @@ pic_status pic_profile_read(pic_case *c, pic_kernel_stat *out, int max_entries, 
     if (n_out) *n_out = n;
     return PIC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Checkpoint: header, control block, particles of the current halves, then
+// fixed-size device arrays, in this order.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char kCkptMagic[8] = {'P', 'I', 'C', '1', 'D', '3', 'V', 'C'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    int32_t n_cells, n_species, n_nodes, r_stride, deposit_copies, need_init;
+    int64_t fe_cap, host_step, since_sort[2];
+    int32_t sort_k[2], threads[2], stages[2], tuned, autotune;
+    double dt, length, q[2], m[2], w[2];
+    uint64_t seed;
+    uint64_t n_slots[2];           // particle slots saved per species
+};
+
+// The device arrays after the particles: (pointer, bytes) in save order.
+std::vector<std::pair<void *, size_t>> ckpt_arrays(const pic_case *c)
+{
+    const StepConst &P = c->P;
+    const size_t nn = (size_t)c->n_nodes, N = (size_t)c->d.n_cells;
+    return {
+        {P.E32, sizeof(float) * ((N + 1 + 3) / 4 * 4)}, {P.E, 8 * nn}, {P.phi, 8 * nn},
+        {P.R[0], 8 * (size_t)kDepositCopies * P.r_stride}, {P.R[1], 8 * (size_t)kDepositCopies * P.r_stride},
+        {c->R_last, 8 * 2 * nn}, {P.Rsum, 8 * 2 * nn}, {P.Rdiag, 8 * 2 * nn}, {P.en_sum, 8 * 2 * nn},
+        {P.phi_sum, 8 * nn}, {P.ke_sum, 16}, {P.pw_sum, 16}, {P.eepf, 8 * (size_t)kEepfBins},
+        {P.ifedf, 8 * 2 * (size_t)kIfedfBins}, {P.fe_hist, 8 * (size_t)P.fe_cap * kFieldCluster},
+    };
+}
+
+pic_status ckpt_layout(pic_case *c, Ctrl *h, uint64_t *total)
+{
+    CU(cudaMemcpyAsync(h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    uint64_t b = sizeof(CkptHeader) + sizeof(Ctrl);
+    for (int s = 0; s < c->d.n_species; ++s)
+        if (c->loaded[s] || (s == 1 && c->loaded[0])) b += 24ull * h->n_total[s];
+    for (auto &a : ckpt_arrays(c)) b += a.second;
+    *total = b;
+    return PIC_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+pic_status pic_checkpoint_size(pic_case *c, uint64_t *bytes)
+{
+    if (!c || !bytes) return fail(PIC_EINVAL, "null argument");
+    Ctrl h;
+    return ckpt_layout(c, &h, bytes);
+}
+
+pic_status pic_checkpoint_save(pic_case *c, void *host, uint64_t bytes)
+{
+    if (!c || !host) return fail(PIC_EINVAL, "null argument");
+    Ctrl h;
+    uint64_t need = 0;
+    pic_status st = ckpt_layout(c, &h, &need);
+    if (st != PIC_OK) return st;
+    if (bytes < need) return fail(PIC_EINVAL, "checkpoint buffer too small");
+    st = device_error(c);
+    if (st != PIC_OK) return st;
+    CkptHeader hd{};
+    std::memcpy(hd.magic, kCkptMagic, 8);
+    hd.version = kCkptVersion;
+    hd.header_bytes = sizeof(CkptHeader);
+    hd.n_cells = c->d.n_cells; hd.n_species = c->d.n_species; hd.n_nodes = c->n_nodes;
+    hd.r_stride = c->P.r_stride; hd.deposit_copies = kDepositCopies; hd.need_init = c->need_init ? 1 : 0;
+    hd.fe_cap = c->P.fe_cap; hd.host_step = c->host_step;
+    hd.tuned = c->tuned ? 1 : 0; hd.autotune = c->autotune ? 1 : 0;
+    for (int s = 0; s < 2; ++s) {
+        hd.since_sort[s] = c->since_sort[s]; hd.sort_k[s] = c->sort_k[s];
+        hd.threads[s] = c->step_threads[s]; hd.stages[s] = c->step_stages[s];
+        hd.q[s] = c->d.charge_C[s]; hd.m[s] = c->d.mass_kg[s]; hd.w[s] = c->d.weight_per_m2[s];
+        hd.n_slots[s] = (s < c->d.n_species && (c->loaded[s] || (s == 1 && c->loaded[0]))) ? h.n_total[s] : 0;
+    }
+    hd.dt = c->d.dt_s; hd.length = c->d.length_m; hd.seed = c->d.seed;
+    char *p = static_cast<char *>(host);
+    std::memcpy(p, &hd, sizeof hd); p += sizeof hd;
+    std::memcpy(p, &h, sizeof h); p += sizeof h;
+    for (int s = 0; s < 2; ++s) {
+        const size_t n = hd.n_slots[s];
+        if (!n) continue;
+        const SpeciesBufs &B = c->P.buf[s][h.cur[s]];
+        const void *src[6] = {B.cell, B.off, B.vx, B.vy, B.vz, B.id};
+        for (int a = 0; a < 6; ++a) {
+            CU(cudaMemcpyAsync(p, src[a], 4 * n, cudaMemcpyDeviceToHost, c->stream));
+            p += 4 * n;
+        }
+    }
+    for (auto &a : ckpt_arrays(c)) {
+        CU(cudaMemcpyAsync(p, a.first, a.second, cudaMemcpyDeviceToHost, c->stream));
+        p += a.second;
+    }
+    CU(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+pic_status pic_checkpoint_load(pic_case *c, const void *host, uint64_t bytes)
+{
+    if (!c || !host) return fail(PIC_EINVAL, "null argument");
+    if (bytes < sizeof(CkptHeader) + sizeof(Ctrl)) return fail(PIC_EINVAL, "checkpoint buffer too small");
+    CkptHeader hd;
+    const char *p = static_cast<const char *>(host);
+    std::memcpy(&hd, p, sizeof hd);
+    if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != kCkptVersion || hd.header_bytes != sizeof hd)
+        return fail(PIC_EINVAL, "not a checkpoint of this library version");
+    bool same = hd.n_cells == c->d.n_cells && hd.n_species == c->d.n_species && hd.n_nodes == c->n_nodes &&
+                hd.r_stride == c->P.r_stride && hd.deposit_copies == kDepositCopies && hd.fe_cap == c->P.fe_cap &&
+                hd.dt == c->d.dt_s && hd.length == c->d.length_m && hd.seed == c->d.seed;
+    for (int s = 0; s < c->d.n_species; ++s)
+        same = same && hd.q[s] == c->d.charge_C[s] && hd.m[s] == c->d.mass_kg[s] && hd.w[s] == c->d.weight_per_m2[s];
+    if (!same) return fail(PIC_EINVAL, "checkpoint of a different case descriptor");
+    uint64_t need = sizeof hd + sizeof(Ctrl) + 24ull * (hd.n_slots[0] + hd.n_slots[1]);
+    for (auto &a : ckpt_arrays(c)) need += a.second;
+    if (bytes < need) return fail(PIC_EINVAL, "checkpoint buffer too small");
+    CU(cudaStreamSynchronize(c->stream));
+    for (int s = 0; s < c->d.n_species; ++s) {
+        pic_status st = alloc_species(c, s, (long long)hd.n_slots[s]);
+        if (st != PIC_OK) return st;
+    }
+    Ctrl h;
+    std::memcpy(&h, p + sizeof hd, sizeof h);
+    p += sizeof hd + sizeof h;
+    for (int s = 0; s < 2; ++s) {
+        const size_t n = hd.n_slots[s];
+        h.cur[s] = 0;                                  // particles go to half 0
+        if (!n) continue;
+        const SpeciesBufs &B = c->P.buf[s][0];
+        void *dst[6] = {B.cell, B.off, B.vx, B.vy, B.vz, B.id};
+        for (int a = 0; a < 6; ++a) {
+            CU(cudaMemcpyAsync(dst[a], p, 4 * n, cudaMemcpyHostToDevice, c->stream));
+            p += 4 * n;
+        }
+    }
+    CU(cudaMemcpyAsync(c->P.ctrl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+    for (auto &a : ckpt_arrays(c)) {
+        CU(cudaMemcpyAsync(a.first, p, a.second, cudaMemcpyHostToDevice, c->stream));
+        p += a.second;
+    }
+    CU(cudaStreamSynchronize(c->stream));
+    for (int s = 0; s < c->d.n_species; ++s) {
+        fill_species(c, s);                            // tables and constants of the descriptor
+        c->loaded[s] = hd.n_slots[s] > 0 || s == 0;
+    }
+    c->need_init = hd.need_init != 0;
+    c->host_step = hd.host_step;
+    c->tuned = hd.tuned != 0;
+    for (int s = 0; s < 2; ++s) {
+        c->since_sort[s] = hd.since_sort[s];
+        c->sort_k[s] = hd.sort_k[s];
+        c->step_threads[s] = hd.threads[s];
+        c->step_stages[s] = hd.stages[s];
+    }
+    drop_graph(c);
+    return PIC_OK;
+}
+
+} // extern "C"
 
 pic_status pic_destroy(pic_case *c)
 {

@@ -9,6 +9,7 @@ constexpr int kMaxProc = 4;
 constexpr int kNGrid = 1000;            // cross-section grid, log-spaced on [1e-3, 1e3] eV
 constexpr float kGridEmin = 1e-3f;
 constexpr int kEepfBins = 240;          // 0..60 eV, 0.25 eV bins
+constexpr int kIfedfBins = 256;         // ion energy at each electrode
 constexpr int kStepThreads = 1024;     // largest CTA of the particle step
 constexpr int kBatchThreads = 512;     // CTA of the batched (many-case) particle step
 constexpr int kMaxStages = 4;          // particle tiles in flight per CTA (bulk-copy pipeline)
@@ -50,6 +51,9 @@ struct Ctrl {
     unsigned long long fe_n;            // field-energy history entries written
     unsigned long long n_steps_acc, n_diag_acc;
     double drive_c[4], drive_s[4];      // cos, sin of 2 pi f_h t + theta_h at the next field solve
+    double q_el;                        // series capacitor: charge per area of electrode 0 + plate
+    unsigned long long st_abs0[2];      // this step: particles absorbed at x = 0 per species
+    unsigned long long st_see0;         // this step: secondary electrons emitted at x = 0
 };
 
 struct SpConst {
@@ -112,7 +116,23 @@ struct StepConst {
     long long fe_cap;
     unsigned int *sort_count;           // [n_cells]
     unsigned long long *sort_cursor;    // [n_cells]
+    // electrode circuit (series capacitor) and ion energy histograms
+    int circuit;                        // 0 = electrode 0 at V(t), 1 = V(t) through a capacitor, 2 = J(t)
+    int no_field;                       // 1: E = 0 on the mesh (only E_ext acts)
+    double c_blk, eps0_L, inv_cap_eps0_L; // blocking capacitance C, eps0/L, 1/(C + eps0/L)
+    double qw[2];                       // q_s w_s: charge per area of one particle
+    double r0c[2], bg_half;             // rho_0 dx/2 = sum r0c_s R_s[0] + bg_half
+    float ifedf_scale;                  // bins per eV (0 = no histogram)
+    unsigned long long *ifedf;          // [2][kIfedfBins]
 };
+
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may start while the previous kernel of the stream runs;
+// grid_dep_wait() blocks until that kernel has completed and its writes are
+// visible, grid_dep_launch() lets the next kernel start launching.  Both are
+// no-ops for a kernel launched the ordinary way.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Ten rounds; each forms

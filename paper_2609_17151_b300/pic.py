@@ -18,7 +18,8 @@ ELASTIC, EXCITATION, IONIZATION, ISO, CX = 0, 1, 2, 3, 4
 NGRID = 1000
 EEPF_BINS = 240
 MAX_PROC = 4
-DESC_VERSION = 1
+DESC_VERSION = 2
+IFEDF_BINS = 256
 
 STATUS = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ENOMEM", 3: "PIC_ECUDA", 4: "PIC_ECAPACITY",
           5: "PIC_ENUMERIC", 6: "PIC_ETIMEOUT", 7: "PIC_ESTATE"}
@@ -44,6 +45,8 @@ class CaseDesc(C.Structure):
         ("seed", C.c_uint64),
         ("sort_interval", C.c_int32), ("diag_interval", C.c_int32), ("rewind", C.c_int32),
         ("field_history", C.c_int32),
+        ("circuit", C.c_int32), ("blocking_cap_F_per_m2", C.c_double), ("ifedf_emax_ev", C.c_double),
+        ("no_field", C.c_int32),
         ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]
@@ -61,6 +64,7 @@ class Moments(C.Structure):
         ("dens_diag_sum", C.c_void_p), ("eepf", C.c_void_p),
         ("field_energy", C.c_void_p), ("field_energy_cap", C.c_int64), ("field_energy_n", C.c_int64),
         ("reset", C.c_int32), ("sort_interval", C.c_int32),
+        ("ifedf", C.c_void_p), ("electrode_charge", C.c_double),
     ]
 
 
@@ -99,6 +103,9 @@ def _load_library():
     lib.pic_read_moments.argtypes = [vp, C.POINTER(Moments)]
     lib.pic_read_tuning.argtypes = [vp, C.POINTER(Tuning)]
     lib.pic_set_step_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+    lib.pic_checkpoint_size.argtypes = [vp, C.POINTER(C.c_uint64)]
+    lib.pic_checkpoint_save.argtypes = [vp, vp, C.c_uint64]
+    lib.pic_checkpoint_load.argtypes = [vp, vp, C.c_uint64]
     lib.pic_destroy.argtypes = [vp]
     lib.pic_status_str.restype = C.c_char_p
     lib.pic_status_str.argtypes = [C.c_int]
@@ -133,7 +140,8 @@ def _load_library():
     lib.pic_profile.argtypes = [vp, C.c_int]
     lib.pic_profile_read.argtypes = [vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]
     for f in ("pic_create_case", "pic_load_xsec_table", "pic_load_particles", "pic_step", "pic_sync", "pic_count",
-              "pic_read_particles", "pic_read_field", "pic_read_moments", "pic_read_tuning", "pic_set_step_shape", "pic_destroy", "pic_philox", "pic_deposit",
+              "pic_read_particles", "pic_read_field", "pic_read_moments", "pic_read_tuning", "pic_set_step_shape", "pic_checkpoint_size",
+              "pic_checkpoint_save", "pic_checkpoint_load", "pic_destroy", "pic_philox", "pic_deposit",
               "pic_profile", "pic_profile_read", "pic_sort_by_cell", "pic_sort_by_cell_noalloc",
               "pic_load_profile", "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy",
               "pic_batch_set_stages",
@@ -216,6 +224,10 @@ def make_desc(cfg: dict, *, stream=None, allocator: TorchAllocator | None = None
     d.diag_interval = int(cfg.get("diag_interval", 0))
     d.rewind = int(cfg.get("rewind", 1))
     d.field_history = int(field_history)
+    d.circuit = {"voltage": 0, "capacitor": 1, "current": 2}[cfg.get("circuit", "voltage")]
+    d.no_field = int(bool(cfg.get("no_field", False)))
+    d.blocking_cap_F_per_m2 = float(cfg.get("blocking_cap", 0.0))
+    d.ifedf_emax_ev = float(cfg.get("ifedf_emax_ev", 0.0))
     d.stream = stream
     if allocator is not None:
         d.alloc, d.free = allocator._alloc, allocator._free
@@ -297,7 +309,8 @@ def read_moments(h, n_nodes, n_species, reset=False, field_energy_cap=0) -> dict
     m.struct_size = C.sizeof(Moments)
     bufs = {"dens_sum": np.zeros(n_species * n_nodes), "phi_sum": np.zeros(n_nodes),
             "en_sum": np.zeros(n_species * n_nodes), "dens_diag_sum": np.zeros(n_species * n_nodes),
-            "eepf": np.zeros(EEPF_BINS), "field_energy": np.zeros(max(1, field_energy_cap))}
+            "eepf": np.zeros(EEPF_BINS), "field_energy": np.zeros(max(1, field_energy_cap)),
+            "ifedf": np.zeros(2 * IFEDF_BINS)}
     for k, v in bufs.items():
         setattr(m, k, v.ctypes.data)
     m.field_energy_cap = field_energy_cap
@@ -306,6 +319,8 @@ def read_moments(h, n_nodes, n_species, reset=False, field_energy_cap=0) -> dict
     out = {k: v for k, v in bufs.items()}
     for k in ("dens_sum", "en_sum", "dens_diag_sum"):
         out[k] = out[k].reshape(n_species, n_nodes)
+    out["ifedf"] = out["ifedf"].reshape(2, IFEDF_BINS)
+    out["electrode_charge"] = m.electrode_charge
     out["field_energy"] = out["field_energy"][: m.field_energy_n]
     out.update(step=m.step, n_steps=m.n_steps, n_diag=m.n_diag, n_alive=tuple(m.n_alive),
                absorbed=np.array([[m.absorbed[s][w] for w in range(2)] for s in range(2)]),
@@ -542,6 +557,19 @@ class Case:
 
     def set_step_shape(self, species, threads, stages):
         check(lib.pic_set_step_shape(self.h, species, threads, stages))
+
+    def checkpoint(self) -> bytes:
+        """The case's state between steps (pic_checkpoint_save) as bytes."""
+        n = C.c_uint64()
+        check(lib.pic_checkpoint_size(self.h, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        check(lib.pic_checkpoint_save(self.h, buf, n.value))
+        return buf.raw
+
+    def restore(self, data: bytes):
+        """Continue from a checkpoint taken from a case of the same descriptor."""
+        buf = C.create_string_buffer(data, len(data))
+        check(lib.pic_checkpoint_load(self.h, buf, len(data)))
 
     def profile(self, enable=True):
         profile(self.h, enable)

@@ -208,10 +208,13 @@ def sweep_cases(n_cases: int = 256, seed: int = 2609, freq: float = 13.56e6, n0:
 
 
 def dual_frequency_family(n_cases: int, seed: int, n_cells: int = 256, gap: float = 0.03, n0: float = 2e14,
-                          n_init: int = 5000, freq: float = 13.56e6):
+                          n_init: int = 2500, freq: float = 13.56e6, steps_per_cycle: int = 1600):
     """Dual-frequency argon CCPs, V(t) = V1 cos(2 pi f t + theta) + V2 cos(4 pi f t)
     (the two-harmonic waveform of the paper's §3.3), drawn with numpy's Philox:
     p in [10, 100] mTorr, V1, V2 in [50, 300] V, theta in [0, 90 deg], 3 cm gap.
+    These discharges reach 1e16 - 2e16 m^-3 with the synthetic tables, so the
+    step is 1/1600 of the period (omega_pe dt <= 0.4 there; 400 steps per
+    period would put omega_pe dt near the leapfrog limit of 2).
     Returns (cfgs, params) with params[i] = (p_mTorr, V1, V2, theta)."""
     rng = np.random.Generator(np.random.Philox(seed))
     tables = argon_tables()
@@ -223,7 +226,7 @@ def dual_frequency_family(n_cases: int, seed: int, n_cells: int = 256, gap: floa
         v1, v2 = rng.uniform(50.0, 300.0), rng.uniform(50.0, 300.0)
         theta = rng.uniform(0.0, 0.5 * math.pi)
         cfgs.append(dict(
-            name=f"dual_freq_{seed}_{i}", periodic=0, n_cells=n_cells, length=gap, dt=1.0 / (freq * 400),
+            name=f"dual_freq_{seed}_{i}", periodic=0, n_cells=n_cells, length=gap, dt=1.0 / (freq * steps_per_cycle),
             gas_density=mtorr * 1e-3 * TORR / (K_B * tg), gas_temp=tg, gas_mass=M_AR,
             harmonics=[(freq, v1, theta), (2 * freq, v2, 0.0)], see_gamma=0.1, see_temp_ev=1.0,
             species=[dict(q=-E_CHARGE, m=M_E, w=w), dict(q=E_CHARGE, m=M_AR, w=w)],

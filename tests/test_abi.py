@@ -41,11 +41,27 @@ def test_status_strings_and_null_handling_without_gpu():
 
 
 def test_descriptor_layout_matches_header():
-    """The ctypes mirror of pic_case_desc / pic_moments has the C sizes."""
+    """The ctypes mirrors of pic_case_desc, pic_moments and pic_tuning have the
+    sizes and field offsets the C compiler gives the header's structs."""
+    import subprocess
+    import tempfile
     import paper_2609_17151_b300.pic as pic
     src = open(os.path.join(ROOT, "include", "pic1d3v.h")).read()
-    assert "PIC_DESC_VERSION 1u" in src
-    # 8-byte aligned structs with the documented field counts
-    assert ctypes.sizeof(pic.CaseDesc) % 8 == 0
-    assert ctypes.sizeof(pic.Moments) % 8 == 0
-    assert [f[0] for f in pic.CaseDesc._fields_][:4] == ["struct_size", "version", "periodic", "n_cells"]
+    assert f"PIC_DESC_VERSION {pic.DESC_VERSION}u" in src
+    mirrors = {"pic_case_desc": pic.CaseDesc, "pic_moments": pic.Moments, "pic_tuning": pic.Tuning}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pic1d3v.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines.append("return 0; }")
+    with tempfile.TemporaryDirectory() as d:
+        c_file, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(c_file, "w").write("\n".join(lines))
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c_file, "-o", exe])
+        out = subprocess.check_output([exe], text=True).split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])

@@ -155,6 +155,195 @@ def test_full_size_exb_one_step(shape):
     gc.close()
 
 
+# --------------------------------------------------------------------------- electrode circuit
+EPS0 = 8.8541878128e-12
+
+
+@pytest.mark.parametrize("steps", [1, 4])
+@pytest.mark.parametrize("cap_over_gap", [3.0, 0.0])
+def test_series_capacitor_and_ion_energy_histograms_match_oracle(steps, cap_over_gap):
+    """Electrode 0 driven through a series capacitor (3x the gap's eps0/L, or
+    0 = floating), ion energies histogrammed at both electrodes: particles,
+    the electrode's charge, phi_0 and the histograms agree with the oracle
+    (counts up to the rare FP32-vs-FP64 decisions the comparison reports)."""
+    cfg, parts = small_ccp(ti_ev=400.0)
+    cfg = dict(cfg, circuit="capacitor", blocking_cap=cap_over_gap * EPS0 / cfg["length"], ifedf_emax_ev=2000.0)
+    oc = oracle_case(cfg, parts)
+    oc.step(steps)
+    gc = gpu_case(cfg, parts)
+    gc.step(steps)
+    st = compare_all(cfg, gc, oc, steps=steps)
+    flips = st[0]["flips"] + st[1]["flips"]
+    m = gc.moments()
+    co = oc.counters()
+    qo = oc.electrode_charge()
+    w = cfg["species"][0]["w"]
+    q_part = 1.602176634e-19 * w
+    assert abs(m["electrode_charge"] - qo) <= 1e-9 * abs(qo) + 2 * flips * q_part
+    phi_g, phi_o = gc.field()[0], oc.field()[0]
+    assert abs(phi_g[0] - phi_o[0]) <= 1e-5 * np.abs(phi_o).max() + 0.0
+    assert np.allclose(phi_g, phi_o, rtol=0, atol=1e-5 * np.abs(phi_o).max())
+    h_g, h_o = m["ifedf"], oc.ifedf()
+    assert h_o.sum() > 0 and h_o.sum() <= co["absorbed"][1].sum()
+    for wall in range(2):
+        assert abs(h_g[wall].sum() - h_o[wall].sum()) <= max(2, flips)
+    assert np.abs(h_g - h_o).sum() <= 2 * max(2, flips)
+    gc.close()
+
+
+def test_batch_with_series_capacitor_equals_cases_alone():
+    """The batched step carries each case's circuit and histograms: particles,
+    field, electrode charge and ion energy histograms bit-identical to the
+    cases stepped alone."""
+    cfgs = _sweep_cfgs(3)
+    for c in cfgs:
+        c.update(circuit="capacitor", blocking_cap=1e-9, ifedf_emax_ev=500.0)
+    b = pic.Batch(cfgs, sort_interval=8)
+    singles = []
+    for cfg, view in zip(cfgs, b.cases):
+        nn = cfg["n_cells"] + 1
+        c = pic.Case(cfg, sort_interval=8)
+        for tgt in (view, c):
+            for sp, T in ((0, 20.0), (1, 400.0)):
+                tgt.load_profile(sp, 40_000, np.full(nn, 2e14), np.full(nn, T), id_base=0)
+        singles.append(c)
+    b.step(13)
+    b.sync()
+    for c in singles:
+        c.step(13)
+    for view, c in zip(b.cases, singles):
+        for s in range(2):
+            pa, pb = view.particles(s), c.particles(s)
+            ia, ib = np.argsort(pa["id"], kind="stable"), np.argsort(pb["id"], kind="stable")
+            for key in ("id", "cell", "off", "vx", "vy", "vz"):
+                assert np.array_equal(pa[key][ia], pb[key][ib]), (s, key)
+        assert np.array_equal(view.field()[0], c.field()[0])
+        ma, mb = view.moments(), c.moments()
+        assert ma["electrode_charge"] == mb["electrode_charge"]
+        assert np.array_equal(ma["ifedf"], mb["ifedf"]) and ma["ifedf"].sum() > 0
+        c.close()
+    b.close()
+
+
+@pytest.mark.parametrize("steps", [1, 4])
+def test_current_drive_matches_oracle(steps):
+    """Imposed current density on electrode 0 (circuit 2): particles, the
+    electrode's charge and the potential agree with the oracle."""
+    cfg, parts = small_ccp(ti_ev=400.0)
+    cfg = dict(cfg, circuit="current", harmonics=[(13.56e6, 40.0, 0.2)])
+    oc = oracle_case(cfg, parts)
+    oc.step(steps)
+    gc = gpu_case(cfg, parts)
+    gc.step(steps)
+    st = compare_all(cfg, gc, oc, steps=steps)
+    flips = st[0]["flips"] + st[1]["flips"]
+    qo = oc.electrode_charge()
+    q_part = 1.602176634e-19 * cfg["species"][0]["w"]
+    assert abs(gc.moments()["electrode_charge"] - qo) <= 1e-9 * abs(qo) + 2 * flips * q_part
+    phi_g, phi_o = gc.field()[0], oc.field()[0]
+    assert np.allclose(phi_g, phi_o, rtol=0, atol=1e-5 * np.abs(phi_o).max())
+    gc.close()
+
+
+def _swarm_case(n, nu, Ex, seed=12):
+    cfg = dict(periodic=1, n_cells=64, length=64e-4, dt=1e-11, gas_density=0.0, gas_temp=300.0,
+               gas_mass=W.M_AR, const_nu_e=nu, E_ext=(Ex, 0.0, 0.0), no_field=True,
+               species=[dict(q=-1.602176634e-19, m=W.M_E, w=1e6)], seed=seed, rewind=0)
+    rng = np.random.default_rng(seed)
+    xi = rng.uniform(0, 64, n)
+    cell = np.floor(xi).astype(np.int32)
+    off = (xi - cell).astype(np.float32)
+    off[off >= 1] = 0
+    z = np.zeros(n, dtype=np.float32)
+    return cfg, [dict(cell=cell, off=off, vx=z.copy(), vy=z.copy(), vz=z.copy(), id=np.arange(n, dtype=np.uint32))]
+
+
+def test_swarm_mode_matches_oracle_and_drift_velocity():
+    """No Poisson solve (swarm runs): a few steps agree with the oracle particle
+    by particle, and 1e6 electrons with a constant collision frequency drift at
+    q E / (m nu) (1 - e^{-nu t})."""
+    cfg, parts = _swarm_case(30_001, 1e9, 100.0)
+    oc = oracle_case(cfg, parts)
+    oc.step(5)
+    gc = gpu_case(cfg, parts)
+    gc.step(5)
+    compare_all(cfg, gc, oc, steps=5)
+    assert np.all(gc.field()[1] == 0)
+    gc.close()
+    nu, Ex, steps = 1e9, 100.0, 300
+    cfg, parts = _swarm_case(1_000_000, nu, Ex, seed=13)
+    gc = gpu_case(cfg, parts)
+    gc.step(steps)
+    vd = -1.602176634e-19 * Ex / (W.M_E * nu) * (1 - math.exp(-nu * steps * cfg["dt"]))
+    assert abs(gc.particles(0)["vx"].mean() / vd - 1) < 0.01
+    gc.close()
+
+
+def test_checkpoint_resume_is_bit_identical():
+    """A run saved after 12 steps and restored into a fresh case continues
+    bit-identically to an uninterrupted 30-step run: particles, field, moment
+    sums, histograms, counters and the series-capacitor charge."""
+    cfg, parts = small_ccp(ti_ev=400.0)
+    cfg = dict(cfg, circuit="capacitor", blocking_cap=1e-9, ifedf_emax_ev=2000.0, diag_interval=4)
+    a = gpu_case(cfg, parts, sort_interval=8)
+    a.step(30)
+    b = gpu_case(cfg, parts, sort_interval=8)
+    b.step(12)
+    blob = b.checkpoint()
+    b.close()
+    c = pic.Case(cfg, sort_interval=8)
+    c.restore(blob)
+    c.step(18)
+    for s in range(2):
+        pa, pc = a.particles(s), c.particles(s)
+        ia, ic = np.argsort(pa["id"], kind="stable"), np.argsort(pc["id"], kind="stable")
+        for key in ("id", "cell", "off", "vx", "vy", "vz"):
+            assert np.array_equal(pa[key][ia], pc[key][ic]), (s, key)
+    for x, y in zip(a.field(), c.field()):
+        assert np.array_equal(x, y)
+    ma, mc = a.moments(), c.moments()
+    for key in ("dens_sum", "phi_sum", "eepf", "ifedf", "absorbed", "collisions", "candidates"):
+        assert np.array_equal(ma[key], mc[key]), key
+    assert np.allclose(ma["en_sum"], mc["en_sum"], rtol=1e-12, atol=0)   # FP64 atomics: order may differ
+    for key in ("step", "n_steps", "n_diag", "see_emitted", "ionizations", "electrode_charge"):
+        assert ma[key] == mc[key], key
+    # a checkpoint fits only a case of the same descriptor, and must be whole
+    other, _ = small_ccp(n_cells=80)
+    d = pic.Case(other)
+    with pytest.raises(pic.PicError):
+        d.restore(blob)
+    with pytest.raises(pic.PicError):
+        c.restore(blob[: len(blob) // 2])
+    a.close(); c.close(); d.close()
+
+
+@pytest.mark.slow
+def test_electrical_asymmetry_reverses_the_self_bias():
+    """Paper §3.3: with V(t) = V0 [cos(2 pi f t + theta) + cos(4 pi f t)] on a
+    series capacitor, the DC self-bias of the powered electrode is negative at
+    theta = 0 and positive at theta = 90 deg in a geometrically symmetric
+    discharge (synthetic argon, 3 cm, 200 cycles, bias averaged over the last 50)."""
+    f, V0 = 13.56e6, 150.0
+    bias = {}
+    for theta in (0.0, 0.5 * math.pi):
+        cfgs, _ = W.dual_frequency_family(1, seed=6)
+        cfg = dict(cfgs[0], harmonics=[(f, V0, theta), (2 * f, V0, 0.0)], circuit="capacitor",
+                   blocking_cap=1e-6, gas_density=50e-3 * W.TORR / (W.K_B * 300.0))
+        c = pic.Case(cfg, sort_interval=64, capacity=(2_000_000, 2_000_000))
+        nn = cfg["n_cells"] + 1
+        L = cfg["load"]
+        spc = int(round(1.0 / (f * cfg["dt"])))                 # steps per RF period
+        c.load_profile(0, 20_000, np.full(nn, 2e15), np.full(nn, 2.0))
+        c.load_profile(1, 20_000, np.full(nn, 2e15), np.full(nn, L["ti_ev"]))
+        c.step(150 * spc)
+        c.moments(reset=True)
+        c.step(50 * spc)
+        m = c.moments()
+        bias[theta] = m["phi_sum"][0] / m["n_steps"]
+        c.close()
+    assert bias[0.0] < -5.0 and bias[0.5 * math.pi] > 5.0, bias
+
+
 # --------------------------------------------------------------------------- properties
 @pytest.mark.parametrize("shape", [(256, 0), (1024, 0), (512, 1), (1024, 1), (512, 2), (256, 2), (512, 3), (256, 4)])
 def test_launch_shapes_give_identical_particles(shape):

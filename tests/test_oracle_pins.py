@@ -573,6 +573,41 @@ def test_ion_energy_histogram_of_a_monoenergetic_beam():
     assert h[0][131] == n and h.sum() == n
 
 
+def test_current_drive_charges_an_empty_gap():
+    """Imposed current J(t) on electrode 0 of an empty gap: its charge is the
+    running sum of J(t_k) dt and phi_0 = Q L / eps0 (the gap is a capacitor)."""
+    f, J0, th, L, N = 13.56e6, 5.0, 0.4, 0.02, 40
+    cfg = dict(_circuit_cfg(0.0, [(f, J0, th)], n_cells=N, L=L), circuit="current")
+    c = oracle.Case(cfg)
+    _empty(c)
+    c.step(0)
+    assert c.electrode_charge() == 0.0 and c.field()[0][0] == 0.0
+    q = 0.0
+    for k in range(1, 31):
+        c.step(1)
+        q += cfg["dt"] * J0 * math.cos(2 * math.pi * f * k * cfg["dt"] + th)
+        phi, _ = c.field()
+        assert abs(c.electrode_charge() - q) <= 1e-12 * J0 * cfg["dt"] * k
+        assert abs(phi[0] - q * L / EPS0) <= 1e-9 * abs(J0 * cfg["dt"] * L / EPS0)
+
+
+def test_swarm_drift_velocity_of_maxwell_molecules():
+    """Field solve off, electrons in a uniform imposed field with a constant
+    collision frequency: the mean velocity relaxes as q E / (m nu) (1 - e^{-nu t})
+    (momentum balance of Maxwell molecules), whatever the energy distribution."""
+    n, nu, Ex, dt, steps = 20_000, 1e9, 100.0, 1e-11, 300
+    cfg, (xi, vx, vy, vz, ids) = _beam_case(n, 1e-6, const_nu=nu, tables=False, dt=dt)
+    cfg = dict(cfg, E_ext=(Ex, 0.0, 0.0), no_field=True)
+    c = oracle.Case(cfg)
+    c.load_particles(0, xi, np.zeros(n), np.zeros(n), np.zeros(n), ids)
+    c.step(steps)
+    t = steps * dt
+    vd = -E * Ex / (W.M_E * nu) * (1 - math.exp(-nu * t))
+    got = c.particles(0)["vx"].mean()
+    assert abs(got / vd - 1) < 0.03
+    assert np.all(c.field()[0] == 0) and np.all(c.field()[1] == 0)
+
+
 # --------------------------------------------------------------------------- moments
 def test_uniform_plasma_density_moment_including_half_wall_cells():
     """A uniform load between electrodes gives the loaded density at every node,
