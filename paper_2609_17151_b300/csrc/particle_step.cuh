@@ -480,12 +480,13 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         const uint32_t ids[4] = {id4.x, id4.y, id4.z, id4.w};
         int dc[4];
         uint32_t df[4];
+        const int n_valid = live_chunk ? (int)min(4ll, n - i0) : 0;   // particles of the chunk below n
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             dc[q] = -1;
             df[q] = 0;
             int c = cc[q];
-            if (!live_chunk || i0 + q >= n || c < 0) continue;
+            if (q >= n_valid || c < 0) continue;
             float o = oo[q];
             // 1. gather E^n (linear weights), plus the imposed field
             const float e_mesh = (1.0f - o) * Es[c] + o * Es[c + 1];
@@ -493,12 +494,20 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             // 2. Boris: half kick, rotation, half kick
             const float hx = S.c_e * ex;
             float3 vm = make_float3(vx[q] + hx, vy[q] + S.cEy, vz[q] + S.cEz);
-            const float3 vp = make_float3(vm.x + (vm.y * S.tB[2] - vm.z * S.tB[1]),
-                                          vm.y + (vm.z * S.tB[0] - vm.x * S.tB[2]),
-                                          vm.z + (vm.x * S.tB[1] - vm.y * S.tB[0]));
-            float3 v = make_float3(vm.x + (vp.y * S.sB[2] - vp.z * S.sB[1]) + hx,
-                                   vm.y + (vp.z * S.sB[0] - vp.x * S.sB[2]) + S.cEy,
-                                   vm.z + (vp.x * S.sB[1] - vp.y * S.sB[0]) + S.cEz);
+            float3 v;
+            if (S.rot == 0) {                               // no magnetic field: two half kicks
+                v = make_float3(vm.x + hx, vm.y + S.cEy, vm.z + S.cEz);
+            } else if (S.rot == 1) {                        // B along y: rotation in the x-z plane
+                const float vpx = vm.x - vm.z * S.tB[1], vpz = vm.z + vm.x * S.tB[1];
+                v = make_float3(vm.x - vpz * S.sB[1] + hx, vm.y + S.cEy, vm.z + vpx * S.sB[1] + S.cEz);
+            } else {
+                const float3 vp = make_float3(vm.x + (vm.y * S.tB[2] - vm.z * S.tB[1]),
+                                              vm.y + (vm.z * S.tB[0] - vm.x * S.tB[2]),
+                                              vm.z + (vm.x * S.tB[1] - vm.y * S.tB[0]));
+                v = make_float3(vm.x + (vp.y * S.sB[2] - vp.z * S.sB[1]) + hx,
+                                vm.y + (vp.z * S.sB[0] - vp.x * S.sB[2]) + S.cEy,
+                                vm.z + (vp.x * S.sB[1] - vp.y * S.sB[0]) + S.cEz);
+            }
             if (diag) pw_acc += v.x * e_mesh;
             // 3. move
             float on = fmaf(v.x, dtdx, o);

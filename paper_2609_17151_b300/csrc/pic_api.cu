@@ -164,6 +164,9 @@ void fill_species(pic_case *c, int sp)
     for (int k = 0; k < 3; ++k) { t[k] = ce * d.B_T[k]; tt += t[k] * t[k]; }
     S.c_e = (float)ce;
     for (int k = 0; k < 3; ++k) { S.tB[k] = (float)t[k]; S.sB[k] = (float)(2.0 * t[k] / (1.0 + tt)); }
+    S.rot = (S.tB[0] == 0.0f && S.tB[1] == 0.0f && S.tB[2] == 0.0f) ? 0
+            : (S.tB[0] == 0.0f && S.tB[2] == 0.0f)                  ? 1
+                                                                    : 2;
     S.cEy = (float)(ce * d.E_ext_V_per_m[1]);
     S.cEz = (float)(ce * d.E_ext_V_per_m[2]);
     S.m_over_2e = (float)(m / (2.0 * kElem));

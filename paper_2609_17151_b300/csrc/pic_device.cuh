@@ -59,6 +59,7 @@ struct Ctrl {
 struct SpConst {
     float c_e;                          // q dt / (2 m): half electric kick per V/m
     float tB[3], sB[3];                 // Boris rotation vectors t = (q dt / 2m) B, s = 2t/(1+t^2)
+    int rot;                            // 0: B = 0 (no rotation), 1: B along y only, 2: general B
     float cEy, cEz;                     // c_e * E_ext_y, c_e * E_ext_z
     float m_over_2e;                    // eps[eV] = m/(2e) |v|^2
     float v_of_sqrt_eps;                // |v| = sqrt(2e/m) sqrt(eps)

@@ -304,7 +304,8 @@ def test_checkpoint_resume_is_bit_identical():
     ma, mc = a.moments(), c.moments()
     for key in ("dens_sum", "phi_sum", "eepf", "ifedf", "absorbed", "collisions", "candidates"):
         assert np.array_equal(ma[key], mc[key]), key
-    assert np.allclose(ma["en_sum"], mc["en_sum"], rtol=1e-12, atol=0)   # FP64 atomics: order may differ
+    # the energy moment is summed per CTA with FP32 shared atomics: order-dependent at FP32 rounding
+    assert np.allclose(ma["en_sum"], mc["en_sum"], rtol=1e-6, atol=0)
     for key in ("step", "n_steps", "n_diag", "see_emitted", "ionizations", "electrode_charge"):
         assert ma[key] == mc[key], key
     # a checkpoint fits only a case of the same descriptor, and must be whole
