@@ -27,6 +27,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s on 1 B300 + % HBM roofline; batched & warm-start vs plain"
+
+
+def job_throughput(p_steps: float, ms: float, dist=None, device="cpu"):
+    """Whole-job particle-steps/s over N replicas: the particle-steps of all
+    ranks over the slowest rank's time (ms).  Returns (value, max ms)."""
+    import torch
+    s = torch.tensor([float(p_steps)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(s.item()) / (float(m.item()) * 1e-3), float(m.item())
 UNIT = "particle-steps/s"
 ALGO_BYTES = 40          # per particle-step: cell, offset, vx, vy, vz read and written (4 B each)
 AUTOTUNE_STEPS = 51      # first step + the library autotuner's 50 (sort interval, launch shape)
@@ -455,13 +467,9 @@ def main():
     tuning = case.tuning()
     n2 = sum(case.count())
     clk = clocks.stop()
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
     p_steps = 0.5 * (n0 + n1) * args.steps
     p_steps2 = 0.5 * (n1 + n2) * args.steps
-    value = p_steps * world / (ms_max * 1e-3)
+    value, ms_max = job_throughput(p_steps, ms, dist, device="cuda")
 
     ps = prof["particle_step"]
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
