@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--workload", default="exb", choices=["exb", "batch", "warmstart"],
                     help="exb: the 10.24M-particle E x B case (default); batch: the 256-case argon sweep; "
                          "warmstart: RF cycles to steady state, cold start vs the learned warm start")
-    ap.add_argument("--train", type=int, default=24)
+    ap.add_argument("--train", type=int, default=40)
     ap.add_argument("--test", type=int, default=8)
     ap.add_argument("--max-cycles", type=int, default=1500)
     ap.add_argument("--epochs", type=int, default=3000)
@@ -195,7 +195,10 @@ def run_batch(args, torch):
         view.load_profile(0, L["n"], np.full(nn, L["n0"]), np.full(nn, L["te_ev"]))
         view.load_profile(1, L["n"], np.full(nn, L["n0"]), np.full(nn, L["ti_ev"]))
 
-    caps = [(4 * n, 4 * n) for n in counts]
+    # room for the growth of the densest (ionizing) cases over warm-up plus
+    # the two per-case timings (2 x steps); small cases grow relatively more
+    grow = 16 if args.small else 4
+    caps = [(grow * n, grow * n) for n in counts]
     b = pic.Batch(cfgs, stream=stream.cuda_stream, sort_interval=64, capacities=caps)
     for v, cfg in zip(b.cases, cfgs):
         load(v, cfg)
@@ -354,13 +357,33 @@ def run_warmstart(args, torch):
     X = par_tr[ok].astype(np.float32)
     Y = np.stack([np.concatenate([np.log10(np.maximum(cold_prof[i][0], 1e6)), np.log10(np.maximum(cold_prof[i][1], 1e6)),
                                   cold_prof[i][2]]) for i in ok]).astype(np.float32)
-    net = pic.MLP(4, 256, 3 * N_POINTS, seed=7)
     lo, hi = np.array([10.0, 50.0, 50.0, 0.0]), np.array([100.0, 300.0, 300.0, 0.5 * np.pi])
-    net.set_normalization(lo, hi, Y.mean(0), Y.std(0) + 1e-3)
+    y_mean, y_sd = Y.mean(0), Y.std(0) + 1e-3
+
+    def new_net():
+        n = pic.MLP(4, 256, 3 * N_POINTS, seed=7)
+        n.set_normalization(lo, hi, y_mean, y_sd)
+        return n
+
     t1 = time.perf_counter()
-    curve = net.train(X, Y, epochs=args.epochs, lr=1e-3)
+    # epochs chosen on a quarter of the training cases held out, then the
+    # network is trained on all of them for that many epochs
+    perm = np.random.default_rng(11).permutation(len(ok))
+    n_val = max(2, len(ok) // 4)
+    val, fit = perm[:n_val], perm[n_val:]
+    probe = new_net()
+    best_err, epochs = np.inf, 100
+    for k in range(1, args.epochs // 100 + 1):
+        probe.train(X[fit], Y[fit], 100, lr=1e-3, record=False)
+        err = float(np.mean(((probe.predict(X[val]) - Y[val]) / y_sd) ** 2))
+        if err < best_err:
+            best_err, epochs = err, 100 * k
+    probe.close()
+    net = new_net()
+    curve = net.train(X, Y, epochs=epochs, lr=1e-3)
     t_train = time.perf_counter() - t1
-    emit({"phase": "trained", "seconds": round(t_train, 2), "loss_first_last": [float(curve[0]), float(curve[-1])]})
+    emit({"phase": "trained", "seconds": round(t_train, 2), "epochs": epochs, "validation_nmse": best_err,
+          "loss_first_last": [float(curve[0]), float(curve[-1])]})
     # warm start of the held-out cases
     t2 = time.perf_counter()
     warm = pic.Batch(cfg_te, sort_interval=64, capacities=[cap] * len(cfg_te))
@@ -393,8 +416,9 @@ def run_warmstart(args, torch):
                    "train_cases": n_train, "train_converged": len(ok), "test_cases": n_test,
                    "criterion": "32-point ion density, 10-cycle averages 100 cycles apart, relative L2 < 1%",
                    "max_cycles": max_cycles, "network": "4-256-256-384 GELU, BF16 tensor-core products",
-                   "epochs": args.epochs},
+                   "max_epochs": args.epochs},
         "train_loss_first_last": [float(curve[0]), float(curve[-1])],
+        "epochs_chosen": epochs, "validation_nmse": best_err,
         "seconds": {"cold_runs": t_cold, "training": t_train, "warm_runs": t_warm},
         "cases": res,
     })

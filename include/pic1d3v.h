@@ -356,10 +356,16 @@ pic_status pic_batch_sync(pic_batch *b);
 /* Kernel launches the batch has enqueued (for launch accounting). */
 int64_t pic_batch_launches(const pic_batch *b);
 /* Particle tiles the batch's step kernel keeps in flight through shared
- * memory (0 = each thread loads its own particles, the default; 1-4 = bulk
- * copies; fewer are used when shared memory is short).  Takes effect at the
+ * memory (0 = each thread loads its own particles; 1-4 = bulk copies, 2 by
+ * default; fewer are used when shared memory is short).  Takes effect at the
  * next pic_batch_step; results do not depend on it.  Errors: PIC_EINVAL. */
 pic_status pic_batch_set_stages(pic_batch *b, int stages);
+/* Cases with at least `particles` live particles (both species, counted when
+ * the batch plans its step) run the single-case step kernels inside the
+ * batch's graph instead of the shared persistent kernel; every case's field
+ * solve stays in the one batched launch.  0 = every case in the persistent
+ * kernel.  Default 2^19.  Results do not depend on it.  Errors: PIC_EINVAL. */
+pic_status pic_batch_set_own_threshold(pic_batch *b, int64_t particles);
 pic_status pic_batch_destroy(pic_batch *b);
 
 /* ---------------------------------------------------------------------------

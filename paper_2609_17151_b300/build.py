@@ -36,7 +36,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+    cmd = [NVCC, *ARCH, "-O3", "-fmad=false", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
            "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64",
            "-I", INCLUDE, "-I", CSRC, "-o", tmp, *sources()]
     if verbose:

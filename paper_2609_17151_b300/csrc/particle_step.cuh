@@ -488,8 +488,11 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             int c = cc[q];
             if (q >= n_valid || c < 0) continue;
             float o = oo[q];
-            // 1. gather E^n (linear weights), plus the imposed field
-            const float e_mesh = (1.0f - o) * Es[c] + o * Es[c + 1];
+            // 1. gather E^n (linear weights), plus the imposed field.  The
+            // library is built without implicit multiply-add contraction and
+            // every FMA of the push is written out, so that each kernel
+            // variant (direct, staged, batched) rounds identically.
+            const float e_mesh = fmaf(o, Es[c + 1], (1.0f - o) * Es[c]);
             const float ex = e_mesh + P.Ex_ext;
             // 2. Boris: half kick, rotation, half kick
             const float hx = S.c_e * ex;
@@ -498,15 +501,15 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             if (S.rot == 0) {                               // no magnetic field: two half kicks
                 v = make_float3(vm.x + hx, vm.y + S.cEy, vm.z + S.cEz);
             } else if (S.rot == 1) {                        // B along y: rotation in the x-z plane
-                const float vpx = vm.x - vm.z * S.tB[1], vpz = vm.z + vm.x * S.tB[1];
-                v = make_float3(vm.x - vpz * S.sB[1] + hx, vm.y + S.cEy, vm.z + vpx * S.sB[1] + S.cEz);
-            } else {
-                const float3 vp = make_float3(vm.x + (vm.y * S.tB[2] - vm.z * S.tB[1]),
-                                              vm.y + (vm.z * S.tB[0] - vm.x * S.tB[2]),
-                                              vm.z + (vm.x * S.tB[1] - vm.y * S.tB[0]));
-                v = make_float3(vm.x + (vp.y * S.sB[2] - vp.z * S.sB[1]) + hx,
-                                vm.y + (vp.z * S.sB[0] - vp.x * S.sB[2]) + S.cEy,
-                                vm.z + (vp.x * S.sB[1] - vp.y * S.sB[0]) + S.cEz);
+                const float vpx = fmaf(-vm.z, S.tB[1], vm.x), vpz = fmaf(vm.x, S.tB[1], vm.z);
+                v = make_float3(fmaf(-vpz, S.sB[1], vm.x) + hx, vm.y + S.cEy, fmaf(vpx, S.sB[1], vm.z) + S.cEz);
+            } else {                                        // v- + v- x t, then v- + v' x s
+                const float3 vp = make_float3(vm.x + fmaf(vm.y, S.tB[2], -(vm.z * S.tB[1])),
+                                              vm.y + fmaf(vm.z, S.tB[0], -(vm.x * S.tB[2])),
+                                              vm.z + fmaf(vm.x, S.tB[1], -(vm.y * S.tB[0])));
+                v = make_float3(vm.x + fmaf(vp.y, S.sB[2], -(vp.z * S.sB[1])) + hx,
+                                vm.y + fmaf(vp.z, S.sB[0], -(vp.x * S.sB[2])) + S.cEy,
+                                vm.z + fmaf(vp.x, S.sB[1], -(vp.y * S.sB[0])) + S.cEz);
             }
             if (diag) pw_acc += v.x * e_mesh;
             // 3. move

@@ -1519,8 +1519,15 @@ struct pic_batch {
     int n_items = 0;
     bool planned = false;
     int periodic = 0, mcc0 = 0, mcc1 = 0;
-    int stages = 0;                 // particle tiles in flight per CTA requested (0 = direct loads)
+    int stages = 2;                 // particle tiles in flight per CTA requested (0 = direct loads):
+                                    // the batched kernel runs one 512-thread CTA per SM, and the
+                                    // bulk-copy tiles keep HBM busy where its 16 warps cannot
     int run_stages = 0;             // in use (fewer if shared memory is short)
+    // cases with at least own_threshold particles run their own step kernels
+    // (single-case kernels, 1024-thread CTAs) inside the batch's graph; the
+    // rest share the persistent kernel; all field solves share one launch
+    long long own_threshold = 1LL << 19;
+    std::vector<int> own;
     unsigned smem = 0;
     int grid = 0;
     int sort_k = 64;
@@ -1574,9 +1581,19 @@ cudaError_t batch_particles(pic_batch *b)
     return cudaErrorInvalidValue;
 }
 
+int batch_launches_per_step(const pic_batch *b)
+{
+    return (b->n_items > 0 ? 1 : 0) + 1 + (int)b->own.size() * b->cases[0]->d.n_species;
+}
+
 cudaError_t batch_one_step(pic_batch *b)
 {
-    cudaError_t e = batch_particles(b);
+    cudaError_t e = b->n_items > 0 ? batch_particles(b) : cudaSuccess;
+    for (int i : b->own) {
+        pic_case *c = b->cases[(size_t)i];
+        if (e == cudaSuccess) e = launch_step_sp<0>(c);
+        if (e == cudaSuccess && c->d.n_species > 1) e = launch_step_sp<1>(c);
+    }
     if (e != cudaSuccess) return e;
     k_batch_field<<<(unsigned)(kFieldCluster * b->cases.size()), kFieldThreads, b->cases[0]->field_smem, b->stream>>>(
         b->d_cases, 1, b->d_next);
@@ -1621,21 +1638,35 @@ pic_status batch_plan(pic_batch *b)
     CU(cudaStreamSynchronize(b->stream));
     for (size_t i = 0; i < nc; ++i)
         for (int s = 0; s < b->cases[i]->d.n_species; ++s) total += (long long)hs[i].n_active[s];
+    b->own.clear();
+    long long shared_total = 0;
+    for (size_t i = 0; i < nc; ++i) {
+        long long n = 0;
+        for (int s = 0; s < b->cases[i]->d.n_species; ++s) n += (long long)hs[i].n_active[s];
+        if (b->own_threshold > 0 && n >= b->own_threshold) b->own.push_back((int)i);
+        else shared_total += n;
+    }
+    (void)total;
     const long long target_items = 4LL * 2 * c0->num_sms;
     const long long item_particles =
-        std::min(kItemParticles, std::max(kMinItemParticles, (total + target_items - 1) / target_items));
+        std::min(kItemParticles, std::max(kMinItemParticles, (shared_total + target_items - 1) / target_items));
+    size_t next_own = 0;
     for (size_t i = 0; i < nc; ++i) {
         pic_case *c = b->cases[i];
         if (c->d.periodic != b->periodic || c->P.sp[0].mcc != b->mcc0 ||
             (c->d.n_species > 1 ? c->P.sp[1].mcc : 0) != b->mcc1)
             return fail(PIC_EINVAL, "batch cases differ in boundary or collision model");
+        consts[i] = c->P;
+        if (next_own < b->own.size() && b->own[next_own] == (int)i) {   // stepped by its own kernels
+            ++next_own;
+            continue;
+        }
         const Ctrl &h = hs[i];
         for (int s = 0; s < c->d.n_species; ++s) {
             const long long n = (long long)h.n_active[s];
             const int nk = (int)std::max<long long>(1, (n + item_particles - 1) / item_particles);
             for (int k = 0; k < nk; ++k) items.push_back(BatchItem{(int)i, s, k, nk});
         }
-        consts[i] = c->P;
     }
     // tile buffers: as many as the largest case leaves room for (same for all cases)
     int stages = b->stages;
@@ -1663,9 +1694,10 @@ pic_status batch_plan(pic_batch *b)
     b->d_cases = nullptr;
     b->d_items = nullptr;
     CU(cudaMalloc(&b->d_cases, nc * sizeof(StepConst)));
-    CU(cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem)));
+    CU(cudaMalloc(&b->d_items, std::max<size_t>(1, items.size()) * sizeof(BatchItem)));
     CU(cudaMemcpyAsync(b->d_cases, consts.data(), nc * sizeof(StepConst), cudaMemcpyHostToDevice, b->stream));
-    CU(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, b->stream));
+    if (!items.empty())
+        CU(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, b->stream));
     CU(cudaMemsetAsync(b->d_next, 0, sizeof(unsigned), b->stream));
     CU(cudaStreamSynchronize(b->stream));
     b->n_items = (int)items.size();
@@ -1759,13 +1791,13 @@ pic_status pic_batch_step(pic_batch *b, int64_t n_steps)
                 if (st != PIC_OK) return st;
             }
             CU(cudaGraphLaunch(b->graph, b->stream));
-            b->launches += 2LL * G;
+            b->launches += (long long)batch_launches_per_step(b) * G;
             b->host_step += G;
             b->steps_since_sort += G;
             left -= G;
         } else {
             CU(batch_one_step(b));
-            b->launches += 2;
+            b->launches += batch_launches_per_step(b);
             b->host_step++;
             b->steps_since_sort++;
             left--;
@@ -1791,6 +1823,15 @@ pic_status pic_batch_sync(pic_batch *b)
 }
 
 int64_t pic_batch_launches(const pic_batch *b) { return b ? b->launches : 0; }
+
+pic_status pic_batch_set_own_threshold(pic_batch *b, int64_t particles)
+{
+    if (!b || particles < 0) return fail(PIC_EINVAL, "threshold must be >= 0");
+    b->own_threshold = particles;
+    b->planned = false;
+    batch_drop_graph(b);
+    return PIC_OK;
+}
 
 pic_status pic_batch_set_stages(pic_batch *b, int stages)
 {

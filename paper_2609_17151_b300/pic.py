@@ -124,6 +124,7 @@ def _load_library():
     lib.pic_batch_launches.argtypes = [vp]
     lib.pic_batch_destroy.argtypes = [vp]
     lib.pic_batch_set_stages.argtypes = [vp, C.c_int]
+    lib.pic_batch_set_own_threshold.argtypes = [vp, i64]
     fp = C.POINTER(C.c_float)
     lib.pic_mlp_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(vp)]
     lib.pic_mlp_set_normalization.argtypes = [vp, fp, fp, fp, fp]
@@ -144,7 +145,7 @@ def _load_library():
               "pic_checkpoint_save", "pic_checkpoint_load", "pic_destroy", "pic_philox", "pic_deposit",
               "pic_profile", "pic_profile_read", "pic_sort_by_cell", "pic_sort_by_cell_noalloc",
               "pic_load_profile", "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy",
-              "pic_batch_set_stages",
+              "pic_batch_set_stages", "pic_batch_set_own_threshold",
               "pic_mlp_create", "pic_mlp_set_normalization", "pic_mlp_get_params", "pic_mlp_set_params",
               "pic_mlp_gradients", "pic_mlp_train", "pic_mlp_predict", "pic_mlp_destroy", "pic_gemm_bf16",
               "pic_warmstart_load"):
@@ -474,6 +475,9 @@ class Batch:
 
     def set_stages(self, stages):
         check(lib.pic_batch_set_stages(self.h, int(stages)))
+
+    def set_own_threshold(self, particles):
+        check(lib.pic_batch_set_own_threshold(self.h, int(particles)))
 
     def replan(self):
         """Re-split the work items from the current particle counts before the next step."""

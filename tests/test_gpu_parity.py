@@ -617,16 +617,19 @@ def _sweep_cfgs(n_cases, seed=5):
     return cfgs
 
 
-@pytest.mark.parametrize("stages", [0, 1, 2])
-def test_batch_equals_cases_stepped_alone(stages):
+@pytest.mark.parametrize("stages,own", [(0, 0), (1, 0), (2, 0), (0, 100_000), (0, 1)])
+def test_batch_equals_cases_stepped_alone(stages, own):
     """Heterogeneous argon cases (cells, gap, pressure, voltage, particle
     counts differ) stepped in one batch give bit-identical particles and
     fields to each case stepped on its own; the batch kernel loads its
-    particles directly (0) or through 1-2 bulk-copy tile buffers."""
+    particles directly (0) or through 1-2 bulk-copy tile buffers, and cases
+    above `own` particles run the single-case kernels inside the batch
+    (own = 1: every case; 0: none)."""
     cfgs = _sweep_cfgs(5)
     counts = [3000, 70_000, 150_000, 9_000, 260_001]
     b = pic.Batch(cfgs, sort_interval=8)
     b.set_stages(stages)
+    b.set_own_threshold(own)
     singles = []
     for cfg, n, view in zip(cfgs, counts, b.cases):
         nn = cfg["n_cells"] + 1
