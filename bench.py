@@ -502,9 +502,12 @@ def main():
     achieved = ALGO_BYTES * p_steps2 / (ps["total_ms"] * 1e-3) / 1e9 if ps["total_ms"] > 0 else None
     launches = sum(v["launches"] for v in prof.values())
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    tpath = os.path.join(ROOT, "profiles", "traffic.txt")
     if os.path.exists(tpath):
-        traffic = json.load(open(tpath)).get("particle_step_bytes_per_launch")
+        for line in open(tpath):
+            f = line.split()
+            if len(f) == 2 and f[0] == "particle_step_bytes_per_launch":
+                traffic = float(f[1])
 
     e2e = None
     if not args.no_e2e:
