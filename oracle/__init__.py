@@ -56,6 +56,7 @@ class Params(C.Structure):
         ("diag_interval", C.c_int32), ("rewind", C.c_int32),
         ("circuit", C.c_int32), ("cap", C.c_double), ("ifedf_emax_ev", C.c_double),
         ("no_field", C.c_int32),
+        ("axial_len", C.c_double), ("renew_temp_ev", C.c_double * 2), ("renew_drift", (C.c_double * 3) * 2),
     ]
 
 
@@ -64,7 +65,7 @@ class Counters(C.Structure):
         ("n_steps", C.c_int64), ("n_diag", C.c_int64),
         ("absorbed", (C.c_int64 * 2) * 2), ("see_emitted", C.c_int64),
         ("candidates", C.c_int64 * 2), ("collisions", (C.c_int64 * 4) * 2),
-        ("ionizations", C.c_int64), ("step", C.c_int64),
+        ("ionizations", C.c_int64), ("step", C.c_int64), ("renewed", C.c_int64 * 2),
     ]
 
 
@@ -84,6 +85,7 @@ def _load():
     lib.or_get_particles.argtypes = [P, C.c_int, dp, dp, dp, dp, C.POINTER(C.c_uint32), dp,
                                      C.POINTER(C.c_int32)]
     lib.or_get_field.argtypes = [P, dp, dp]
+    lib.or_get_axial.argtypes = [P, C.c_int, dp]
     lib.or_get_deposit.argtypes = [P, C.c_int, C.POINTER(C.c_int64)]
     lib.or_get_numax.argtypes = [P, C.c_int, dp]
     lib.or_get_nu_table.argtypes = [P, C.c_int, C.c_int, dp]
@@ -196,6 +198,11 @@ def make_params(cfg: dict) -> Params:
     p.cap = float(cfg.get("blocking_cap", 0.0))
     p.ifedf_emax_ev = float(cfg.get("ifedf_emax_ev", 0.0))
     p.no_field = int(bool(cfg.get("no_field", False)))
+    p.axial_len = float(cfg.get("axial_length", 0.0))
+    for i, s in enumerate(sp):
+        p.renew_temp_ev[i] = float(s.get("renew_temp_ev", 0.0))
+        for k in range(3):
+            p.renew_drift[i][k] = float(s.get("renew_drift", (0.0, 0.0, 0.0))[k])
     return p
 
 
@@ -255,6 +262,12 @@ class Case:
                               out["event"].ctypes.data_as(C.POINTER(C.c_int32)))
         return out
 
+    def axial(self, sp) -> np.ndarray:
+        """Axial excursion z (m) of each particle, in the order of ``particles``."""
+        z = np.zeros(self.count(sp))
+        _lib.or_get_axial(self._h, sp, _d(z))
+        return z
+
     def field(self):
         phi = np.zeros(self.n_nodes); E = np.zeros(self.n_nodes)
         _lib.or_get_field(self._h, _d(phi), _d(E))
@@ -285,7 +298,7 @@ class Case:
             "see_emitted": c.see_emitted,
             "candidates": np.array([c.candidates[s] for s in range(2)]),
             "collisions": np.array([[c.collisions[s][k] for k in range(4)] for s in range(2)]),
-            "ionizations": c.ionizations, "step": c.step,
+            "ionizations": c.ionizations, "step": c.step, "renewed": np.array(list(c.renewed)),
         }
 
     def moments(self) -> dict:

@@ -70,7 +70,7 @@ double or_uniform(uint32_t r) { return ((double)(r >> 9) + 0.5) * (1.0 / 8388608
  * counter (id, n, sp<<16 | blk, 0), key (seed_lo, seed_hi). */
 static void draw(const or_case *c, uint32_t id, int64_t n, int sp, uint32_t blk, uint32_t out[4]);
 
-enum { BLK_MCC = 0, BLK_AUX = 1, BLK_NEWION = 2, BLK_SEE = 3, BLK_SEE_V = 4, BLK_CHILD = 0xFFFF };
+enum { BLK_MCC = 0, BLK_AUX = 1, BLK_NEWION = 2, BLK_SEE = 3, BLK_SEE_V = 4, BLK_RENEW = 5, BLK_CHILD = 0xFFFF };
 
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -79,6 +79,7 @@ typedef struct {
     uint32_t *id;
     double *margin;
     int32_t *event;
+    double *z;                 /* axial excursion (m), used with axial renewal */
 } species_t;
 
 typedef struct {
@@ -123,7 +124,7 @@ static int sp_reserve(species_t *s, int64_t cap)
     while (nc < cap) nc *= 2;
 #define GROW(f, T) do { void *q = realloc(s->f, (size_t)nc * sizeof(T)); if (!q) return -1; s->f = q; } while (0)
     GROW(xi, double); GROW(vx, double); GROW(vy, double); GROW(vz, double);
-    GROW(id, uint32_t); GROW(margin, double); GROW(event, int32_t);
+    GROW(id, uint32_t); GROW(margin, double); GROW(event, int32_t); GROW(z, double);
 #undef GROW
     s->cap = nc;
     return 0;
@@ -134,13 +135,13 @@ static int sp_push(species_t *s, double xi, double vx, double vy, double vz, uin
     if (sp_reserve(s, s->n + 1)) return -1;
     int64_t k = s->n++;
     s->xi[k] = xi; s->vx[k] = vx; s->vy[k] = vy; s->vz[k] = vz; s->id[k] = id;
-    s->margin[k] = INFINITY; s->event[k] = 0;
+    s->margin[k] = INFINITY; s->event[k] = 0; s->z[k] = 0.0;
     return 0;
 }
 
 static void sp_free(species_t *s)
 {
-    free(s->xi); free(s->vx); free(s->vy); free(s->vz); free(s->id); free(s->margin); free(s->event);
+    free(s->xi); free(s->vx); free(s->vy); free(s->vz); free(s->id); free(s->margin); free(s->event); free(s->z);
     memset(s, 0, sizeof(*s));
 }
 
@@ -642,6 +643,29 @@ static void emit_secondary(or_case *c, uint32_t ion_id, int wall, double *margin
     if (wall == 0) c->st_see0++;
 }
 
+/* Axial renewal (paper §3.6: a periodic azimuthal box holds the ECDI only if
+ * particles are renewed after a virtual axial transit, the method of
+ * Lafleur, Baalrud and Chabert).  Reading: each particle carries its axial
+ * excursion z, advanced by v_z dt after the push; when |z| reaches
+ * axial_len the particle keeps its azimuthal position and gets a new
+ * velocity from the species' renewal Maxwellian (temperature and drift), and
+ * z = 0.  It happens before the collision test of the step.  Draws: Philox
+ * block BLK_RENEW, words 0-1 and 2-3 through Box-Muller (x, y; z). */
+static void renew(or_case *c, int s, int64_t k)
+{
+    species_t *sp = &c->sp[s];
+    uint32_t r[4];
+    draw(c, sp->id[k], c->step, s, BLK_RENEW, r);
+    double g0, g1, g2, g3;
+    box_muller(or_uniform(r[0]), or_uniform(r[1]), &g0, &g1);
+    box_muller(or_uniform(r[2]), or_uniform(r[3]), &g2, &g3);
+    double vt = sqrt(c->p.renew_temp_ev[s] * ELEM / c->p.m[s]);
+    sp->vx[k] = c->p.renew_drift[s][0] + vt * g0;
+    sp->vy[k] = c->p.renew_drift[s][1] + vt * g1;
+    sp->vz[k] = c->p.renew_drift[s][2] + vt * g2;
+    c->cnt.renewed[s]++;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Leapfrog start (reading): the first step solves the field of the loaded     */
 /* state at t = 0 and pushes the velocities back by dt/2 with a Boris step.   */
@@ -732,13 +756,23 @@ static int one_step(or_case *c)
                 continue;
             }
             sp->xi[k] = xn;
+            if (p->axial_len > 0) {                                  /* axial renewal */
+                double zn = sp->z[k] + v[2] * p->dt;
+                margin = fminabs(margin, (fabs(zn) - p->axial_len) / p->axial_len);
+                if (fabs(zn) >= p->axial_len) {
+                    renew(c, s, k);
+                    zn = 0.0;
+                    event = -2;
+                }
+                sp->z[k] = zn;
+            }
             if (c->numax[s] > 0) {                                   /* 5, 6 */
                 if (s == 0) event = collide_electron(c, k, &margin);
                 else event = collide_ion(c, k, &margin);
             }
             /* compact in place */
             sp->xi[keep] = sp->xi[k]; sp->vx[keep] = sp->vx[k]; sp->vy[keep] = sp->vy[k];
-            sp->vz[keep] = sp->vz[k]; sp->id[keep] = sp->id[k];
+            sp->vz[keep] = sp->vz[k]; sp->id[keep] = sp->id[k]; sp->z[keep] = sp->z[k];
             sp->margin[keep] = margin; sp->event[keep] = event;
             ++keep;
         }
@@ -828,6 +862,13 @@ int or_get_particles(const or_case *c, int sp, double *xi, double *vx, double *v
     if (id) memcpy(id, s->id, n * sizeof(uint32_t));
     if (margin) memcpy(margin, s->margin, n * sizeof(double));
     if (event) memcpy(event, s->event, n * sizeof(int32_t));
+    return 0;
+}
+
+int or_get_axial(const or_case *c, int sp, double *z)
+{
+    if (!c || sp < 0 || sp >= c->p.n_species || !z) return -1;
+    memcpy(z, c->sp[sp].z, (size_t)c->sp[sp].n * sizeof(double));
     return 0;
 }
 

@@ -56,6 +56,10 @@ typedef struct {
     double cap;                /* that capacitor, F/m^2 (0 = floating electrode) */
     double ifedf_emax_ev;      /* > 0: histogram the energy of ions reaching each electrode */
     int32_t no_field;          /* 1: no Poisson solve; the particles feel only E_ext (swarm runs) */
+    double axial_len;          /* > 0: virtual axial length (m); a particle whose axial excursion reaches it
+                                  is renewed (paper §3.6, after Lafleur, Baalrud and Chabert) */
+    double renew_temp_ev[OR_MAX_SPECIES];      /* Maxwellian of the renewed particles */
+    double renew_drift[OR_MAX_SPECIES][3];     /* and its drift, m/s */
 } or_params;
 
 typedef struct or_case or_case;
@@ -70,6 +74,7 @@ typedef struct {
     int64_t collisions[OR_MAX_SPECIES][OR_MAX_PROC];
     int64_t ionizations;
     int64_t step;              /* completed steps since load */
+    int64_t renewed[OR_MAX_SPECIES];   /* axial renewals */
 } or_counters;
 
 or_case *or_create(const or_params *p);
@@ -90,6 +95,8 @@ int64_t or_count(const or_case *c, int sp);
  * (0 none, 1 null candidate, 2+k process k, -1 absorbed).  Either may be NULL. */
 int  or_get_particles(const or_case *c, int sp, double *xi, double *vx, double *vy,
                       double *vz, uint32_t *id, double *margin, int32_t *event);
+/* axial excursion z (m) of each particle, same order as or_get_particles */
+int  or_get_axial(const or_case *c, int sp, double *z);
 /* phi, E: n_nodes; R: n_nodes int64 raw deposit of species sp */
 int  or_get_field(const or_case *c, double *phi, double *E);
 int  or_get_deposit(const or_case *c, int sp, int64_t *R);

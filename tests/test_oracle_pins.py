@@ -608,6 +608,61 @@ def test_swarm_drift_velocity_of_maxwell_molecules():
     assert np.all(c.field()[0] == 0) and np.all(c.field()[1] == 0)
 
 
+# --------------------------------------------------------------------------- axial renewal
+def _axial_cfg(n_sp, L_ax, temps, drifts, E_ext=(0.0, 0.0, 0.0), dt=1e-11):
+    sp = [dict(q=-E, m=W.M_E, w=1e-6, renew_temp_ev=temps[0], renew_drift=drifts[0]),
+          dict(q=E, m=W.M_XE, w=1e-6, renew_temp_ev=temps[1], renew_drift=drifts[1])][:n_sp]
+    return dict(periodic=1, n_cells=32, length=32e-5, dt=dt, gas_density=0.0, gas_temp=300.0, gas_mass=W.M_XE,
+                E_ext=E_ext, no_field=True, species=sp, seed=21, rewind=0, axial_length=L_ax)
+
+
+def test_axial_renewal_after_a_free_transit():
+    """Free electrons with axial speed u are renewed at the first step n with
+    n u dt >= L (z advanced by v_z dt per step); the renewed velocities follow
+    the renewal Maxwellian (mean = drift, variance = kT/m per component)."""
+    n, u, dt, L = 40_000, 1.3e5, 1e-11, 1e-5            # u dt = 1.3e-6: renewal at step 8
+    T, drift = 4.0, (-1e6, 2e5, 0.0)
+    cfg = _axial_cfg(1, L, (T, 0.0), (drift, (0, 0, 0)), dt=dt)
+    rng = np.random.default_rng(5)
+    c = oracle.Case(cfg)
+    c.load_particles(0, rng.uniform(0, 32, n), np.zeros(n), np.zeros(n), np.full(n, u),
+                     np.arange(n, dtype=np.uint32))
+    c.step(7)
+    assert c.counters()["renewed"][0] == 0
+    assert np.allclose(c.axial(0), 7 * u * dt, rtol=1e-12)
+    c.step(1)
+    assert c.counters()["renewed"][0] == n
+    assert np.all(c.axial(0) == 0.0)
+    p = c.particles(0)
+    vt = math.sqrt(T * E / W.M_E)
+    for k, key in enumerate(("vx", "vy", "vz")):
+        v = p[key]
+        assert abs(v.mean() - drift[k]) < 5 * vt / math.sqrt(n)
+        assert abs(v.var() / vt**2 - 1) < 5 * math.sqrt(2.0 / n)
+
+
+def test_axial_renewal_of_ions_accelerated_from_rest():
+    """Ions at rest in an axial field E_z: after n steps v_z = n a dt and
+    z = a dt^2 n (n + 1) / 2, so they are renewed at the first n where that
+    reaches L."""
+    Ez, dt, L = 2e4, 1e-10, 3e-4
+    a = E * Ez / W.M_XE
+    n_star = next(k for k in range(1, 10_000) if a * dt * dt * k * (k + 1) / 2 >= L)
+    cfg = _axial_cfg(2, L, (1.0, 0.05), ((0, 0, 0), (0, 0, 0)), E_ext=(0.0, 0.0, Ez), dt=dt)
+    c = oracle.Case(cfg)
+    z = np.zeros(0)
+    c.load_particles(0, z, z, z, z, np.zeros(0, dtype=np.uint32))
+    c.load_particles(1, np.array([3.5, 17.25]), np.zeros(2), np.zeros(2), np.zeros(2), np.array([1, 2], dtype=np.uint32))
+    c.step(n_star - 1)
+    k = n_star - 1
+    assert c.counters()["renewed"][1] == 0
+    assert np.allclose(c.axial(1), a * dt * dt * k * (k + 1) / 2, rtol=1e-9)
+    assert np.allclose(c.particles(1)["vz"], k * a * dt, rtol=1e-9)
+    c.step(1)
+    assert c.counters()["renewed"][1] == 2 and np.all(c.axial(1) == 0.0)
+    assert np.allclose(c.particles(1)["xi"], [3.5, 17.25])          # the azimuthal position is kept
+
+
 # --------------------------------------------------------------------------- moments
 def test_uniform_plasma_density_moment_including_half_wall_cells():
     """A uniform load between electrodes gives the loaded density at every node,
