@@ -101,6 +101,14 @@ typedef struct {
                                      flux-energy distributions); energies beyond are not counted */
     int32_t no_field;             /* 1: no Poisson solve, the particles feel only E_ext (swarm runs of the
                                      paper's §4); densities and counters are still accumulated */
+    double axial_length_m;        /* > 0: axial renewal (paper §3.6, after Lafleur, Baalrud and Chabert):
+                                     every particle carries its axial excursion z, advanced by v_z dt
+                                     after the push; when |z| reaches this length the particle keeps its
+                                     position, takes a new velocity from the renewal Maxwellian below
+                                     and z = 0, before the collision test.  Single cases only (not in a
+                                     batch); the step then always loads its particles directly. */
+    double renew_temp_ev[2];      /* renewal Maxwellian per species: temperature (eV) */
+    double renew_drift_m_per_s[2][3];   /* and drift */
     void *stream;                 /* cudaStream_t to enqueue on; NULL = a stream owned by the case */
     /* optional device allocator (e.g. a framework's caching allocator); NULL = cudaMalloc */
     void *(*alloc)(size_t bytes, void *ctx);
@@ -181,6 +189,11 @@ pic_status pic_read_particles(pic_case *c, int species, int64_t max_n, int64_t *
                               int32_t *cell, float *offset, float *vx, float *vy, float *vz,
                               uint32_t *id);
 
+/* Axial excursion z (m) of the live particles of a species, in the order
+ * pic_read_particles gives them (desc.axial_length_m > 0; PIC_ESTATE
+ * otherwise).  *n_out = live count; PIC_ECAPACITY if max_n is smaller. */
+pic_status pic_read_axial(pic_case *c, int species, int64_t max_n, int64_t *n_out, float *z);
+
 /* Copy the FP64 potential and field at the nodes (n_nodes = n_cells for a
  * periodic case, n_cells + 1 otherwise) and, if rho_raw is not NULL, the
  * raw fixed-point deposit of each species (int64, units of 2^-32 particle,
@@ -218,6 +231,7 @@ typedef struct {
                                       x = L (desc.ifedf_emax_ev > 0) */
     double electrode_charge;       /* out: charge per area of the electrode at x = 0 and its capacitor
                                       plate (circuit 1), C/m^2 */
+    int64_t renewed[2];            /* out: axial renewals per species (desc.axial_length_m > 0) */
 } pic_moments;
 
 pic_status pic_read_moments(pic_case *c, pic_moments *out);
@@ -356,8 +370,8 @@ pic_status pic_batch_sync(pic_batch *b);
 /* Kernel launches the batch has enqueued (for launch accounting). */
 int64_t pic_batch_launches(const pic_batch *b);
 /* Particle tiles the batch's step kernel keeps in flight through shared
- * memory (0 = each thread loads its own particles; 1-4 = bulk copies, 2 by
- * default; fewer are used when shared memory is short).  Takes effect at the
+ * memory (0 = each thread loads its own particles, the default; 1-4 = bulk
+ * copies; fewer are used when shared memory is short).  Takes effect at the
  * next pic_batch_step; results do not depend on it.  Errors: PIC_EINVAL. */
 pic_status pic_batch_set_stages(pic_batch *b, int stages);
 /* Cases with at least `particles` live particles (both species, counted when

@@ -486,6 +486,7 @@ __global__ void k_cells_scatter(SortHalves H, const int32_t *cur_dev, const unsi
         const unsigned long long p = base[c] + atomicAdd(&lcnt[c], 1u);
         D.cell[p] = c; D.off[p] = A.off[i]; D.vx[p] = A.vx[i]; D.vy[p] = A.vy[i]; D.vz[p] = A.vz[i];
         D.id[p] = A.id[i];
+        if (A.z) D.z[p] = A.z[i];
     }
 }
 

@@ -83,7 +83,7 @@ __device__ __forceinline__ float nu_at(const float *tab, GridPos g, float eps, f
 // Event counts of one thread over a work item (registers; reduced per warp
 // and added to the case's counters once per item).
 struct EvCount {
-    unsigned cand, coll[kMaxProc], iz, absorbed[2], see, see0;
+    unsigned cand, coll[kMaxProc], iz, absorbed[2], see, see0, renew;
 };
 __device__ __forceinline__ void count_proc(EvCount &ev, int proc)
 {
@@ -106,6 +106,7 @@ __device__ void append_particle(const StepConst &P, int sp, int half, int c, flo
     }
     const SpeciesBufs &B = P.buf[sp][half];
     B.cell[slot] = c; B.off[slot] = o; B.vx[slot] = vx; B.vy[slot] = vy; B.vz[slot] = vz; B.id[slot] = id;
+    if (B.z) B.z[slot] = 0.0f;
     const uint32_t f = __float2uint_rz(o * 4294967296.0f);
     unsigned long long *R = P.R[sp] + (size_t)(blockIdx.x % kDepositCopies) * P.r_stride;
     atomicAdd(&R[c], (1ull << 32) - f);
@@ -320,7 +321,7 @@ struct StepShared {
     unsigned tile_rel[kMaxStages];                      // warps done reading each buffer (running count)
     unsigned tile_abort;                                // a tile wait gave up: stop streaming
     unsigned s_cnt[2 + 2 * kMaxProc];                   // candidates, per process, ionizations
-    unsigned s_abs[2], s_see, s_see0;
+    unsigned s_abs[2], s_see, s_see0, s_renew;
     float s_red[2][kStepThreads / 32];
 };
 
@@ -336,7 +337,7 @@ struct StepShared {
 // shared, completion on a per-buffer mbarrier), so that HBM streams while
 // the warps compute, and the warps read their chunk from shared memory.
 // Results are written straight back to global memory.
-template <int SP, bool PERIODIC, int MCC, bool STAGED>
+template <int SP, bool PERIODIC, int MCC, bool STAGED, bool AXIAL>
 __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char *smem, StepShared &sh,
                                               unsigned &parity, unsigned &tile_phase, long long k_item,
                                               long long n_items)
@@ -380,7 +381,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     if (diag) for (int j = tid; j < kEepfBins; j += blockDim.x) heepf[j] = 0u;
     if (tid < 2 + 2 * kMaxProc) s_cnt[tid] = 0u;
     if (tid < 2) s_abs[tid] = 0u;
-    if (tid == 0) { sh.s_see = 0u; sh.s_see0 = 0u; }
+    if (tid == 0) { sh.s_see = 0u; sh.s_see0 = 0u; sh.s_renew = 0u; }
     const bool staged = mbar_wait_bounded(&sh.mbar, ctrl, parity);
     parity ^= 1u;
     if (!__syncthreads_and(staged)) return;
@@ -435,7 +436,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         }
         const long long i0 = ch * 4;
         int4 c4 = make_int4(-1, -1, -1, -1);
-        float4 o4 = make_float4(0, 0, 0, 0), x4 = o4, y4 = o4, z4 = o4;
+        float4 o4 = make_float4(0, 0, 0, 0), x4 = o4, y4 = o4, z4 = o4, a4 = o4;
         uint4 id4 = make_uint4(0, 0, 0, 0);
         if (live_chunk) {
             if (n_stages > 0) {
@@ -453,7 +454,8 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
                 x4 = *reinterpret_cast<const float4 *>(B.vx + i0);
                 y4 = *reinterpret_cast<const float4 *>(B.vy + i0);
                 z4 = *reinterpret_cast<const float4 *>(B.vz + i0);
-                if (kArr == 6) id4 = *reinterpret_cast<const uint4 *>(B.id + i0);
+                if (kArr == 6 || AXIAL) id4 = *reinterpret_cast<const uint4 *>(B.id + i0);
+                if (AXIAL) a4 = *reinterpret_cast<const float4 *>(B.z + i0);
             }
         }
         if (n_stages > 0) {
@@ -478,6 +480,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         float vy[4] = {y4.x, y4.y, y4.z, y4.w};
         float vz[4] = {z4.x, z4.y, z4.z, z4.w};
         const uint32_t ids[4] = {id4.x, id4.y, id4.z, id4.w};
+        float za[4] = {a4.x, a4.y, a4.z, a4.w};
         int dc[4];
         uint32_t df[4];
         const int n_valid = live_chunk ? (int)min(4ll, n - i0) : 0;   // particles of the chunk below n
@@ -533,6 +536,21 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
                 oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
                 continue;
             }
+            // axial renewal: z advances by v_z dt; at |z| >= L the particle
+            // takes a new velocity from the renewal Maxwellian and z = 0
+            if (AXIAL) {
+                float zn = fmaf(v.z, P.dt_f, za[q]);
+                if (fabsf(zn) >= P.axial_len) {
+                    const uint4 r = draw(P, ids[q], step, SP, kBlkRenew);
+                    const float2 g01 = box_muller(u01(r.x), u01(r.y));
+                    const float2 g23 = box_muller(u01(r.z), u01(r.w));
+                    v = make_float3(fmaf(S.renew_vt, g01.x, S.renew_drift[0]), fmaf(S.renew_vt, g01.y, S.renew_drift[1]),
+                                    fmaf(S.renew_vt, g23.x, S.renew_drift[2]));
+                    zn = 0.0f;
+                    ev.renew++;
+                }
+                za[q] = zn;
+            }
             // 5-6. null-collision MCC with v^{n+1/2} at x^{n+1}; products appended
             if (MCC != 0) {
                 if (SP == 0) collide_electron(P, nus, ids[q], step, c, on, v, half_e, half_i, diag, ev);
@@ -564,11 +582,13 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
                 *reinterpret_cast<float4 *>(B.vx + i0) = make_float4(vx[0], vx[1], vx[2], vx[3]);
                 *reinterpret_cast<float4 *>(B.vy + i0) = make_float4(vy[0], vy[1], vy[2], vy[3]);
                 *reinterpret_cast<float4 *>(B.vz + i0) = make_float4(vz[0], vz[1], vz[2], vz[3]);
+                if (AXIAL) *reinterpret_cast<float4 *>(B.z + i0) = make_float4(za[0], za[1], za[2], za[3]);
             } else {
                 for (int q = 0; q < 4; ++q) {
                     if (i0 + q >= n) break;
                     B.cell[i0 + q] = cc[q]; B.off[i0 + q] = oo[q];
                     B.vx[i0 + q] = vx[q]; B.vy[i0 + q] = vy[q]; B.vz[i0 + q] = vz[q];
+                    if (AXIAL) B.z[i0 + q] = za[q];
                 }
             }
         }
@@ -611,16 +631,17 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     }
     // CTA epilogue: event counts (warp sums, one shared atomic per warp), histogram
     {
-        unsigned vals[2 + 2 * kMaxProc] = {ev.cand, ev.coll[0], ev.coll[1], ev.coll[2], ev.coll[3], ev.iz,
-                                           ev.absorbed[0], ev.absorbed[1], ev.see, ev.see0};
+        unsigned vals[11] = {ev.cand, ev.coll[0], ev.coll[1], ev.coll[2], ev.coll[3], ev.iz,
+                             ev.absorbed[0], ev.absorbed[1], ev.see, ev.see0, ev.renew};
 #pragma unroll
-        for (int k = 0; k < 10; ++k) {
+        for (int k = 0; k < (AXIAL ? 11 : 10); ++k) {
             const unsigned w = __reduce_add_sync(0xffffffffu, vals[k]);
             if (lane == 0 && w) {
                 if (k < 6) atomicAdd(&s_cnt[k], w);
                 else if (k < 8) atomicAdd(&s_abs[k - 6], w);
                 else if (k == 8) atomicAdd(&sh.s_see, w);
-                else atomicAdd(&sh.s_see0, w);
+                else if (k == 9) atomicAdd(&sh.s_see0, w);
+                else atomicAdd(&sh.s_renew, w);
             }
         }
     }
@@ -658,6 +679,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         if (s_abs[0] + s_abs[1]) atomicAdd(&ctrl->n_dead[SP], (unsigned long long)(s_abs[0] + s_abs[1]));
         if (P.circuit && s_abs[0]) atomicAdd(&ctrl->st_abs0[SP], (unsigned long long)s_abs[0]);
         if (P.circuit && sh.s_see0) atomicAdd(&ctrl->st_see0, (unsigned long long)sh.s_see0);
+        if (AXIAL && sh.s_renew) atomicAdd(&ctrl->renewed[SP], (unsigned long long)sh.s_renew);
         if (sh.s_see) atomicAdd(&ctrl->see, (unsigned long long)sh.s_see);
         if (s_cnt[0]) atomicAdd(&ctrl->cand[SP], (unsigned long long)s_cnt[0]);
         for (int k = 0; k < kMaxProc; ++k)
@@ -675,7 +697,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
 // and counters are atomic), so it runs into the electron kernel's tail and
 // waits for it only before exiting, which keeps the field solve (launched
 // after it, waiting for it) behind both.
-template <int SP, bool PERIODIC, int MCC, bool STAGED>
+template <int SP, bool PERIODIC, int MCC, bool STAGED, bool AXIAL>
 // launch bounds: up to 1024 threads, 64 registers (two 512-thread or four
 // 256-thread CTAs per SM when shared memory allows)
 __global__ void __launch_bounds__(kStepThreads, 1) k_particle_step(const __grid_constant__ StepConst P)
@@ -693,7 +715,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_particle_step(const __grid_
         grid_dep_launch();
     }
     unsigned parity = 0, tile_phase = 0;
-    particle_item<SP, PERIODIC, MCC, STAGED>(P, smem, sh, parity, tile_phase, blockIdx.x, gridDim.x);
+    particle_item<SP, PERIODIC, MCC, STAGED, AXIAL>(P, smem, sh, parity, tile_phase, blockIdx.x, gridDim.x);
     if (SP == 1) {
         grid_dep_launch();
         grid_dep_wait();
@@ -707,7 +729,7 @@ __device__ __noinline__ void particle_item_call(const StepConst &P, unsigned cha
                                                unsigned &parity, unsigned &tile_phase, long long k_item,
                                                long long n_items)
 {
-    particle_item<SP, PERIODIC, MCC, STAGED>(P, smem, sh, parity, tile_phase, k_item, n_items);
+    particle_item<SP, PERIODIC, MCC, STAGED, false>(P, smem, sh, parity, tile_phase, k_item, n_items);
 }
 
 // Many cases in one persistent launch: CTAs take (case, species, slice) work
@@ -817,6 +839,7 @@ __global__ void k_load_profile(SpeciesBufs B, long long n, int N, const double *
         B.vy[k] = fmaf(vt, g01.y, drift_y);
         B.vz[k] = fmaf(vt, g23.x, drift_z);
         B.id[k] = id;
+        if (B.z) B.z[k] = 0.0f;
     }
 }
 

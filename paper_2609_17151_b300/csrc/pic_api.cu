@@ -178,6 +178,8 @@ void fill_species(pic_case *c, int sp)
     S.mu_over_2e = (float)(reduced_mass(c, sp) / (2.0 * kElem));
     S.vt_newion = d.n_species > 1 ? (float)std::sqrt(kBoltz * d.gas_temp_k / d.mass_kg[1]) : 0.0f;
     S.q = q; S.m = m; S.w = d.weight_per_m2[sp];
+    S.renew_vt = (float)std::sqrt(d.renew_temp_ev[sp] * kElem / m);
+    for (int k = 0; k < 3; ++k) S.renew_drift[k] = (float)d.renew_drift_m_per_s[sp][k];
     double numax = 0.0;
     S.nproc = (int)c->proc[sp].size();
     for (int k = 0; k < kMaxProc; ++k) {
@@ -275,12 +277,12 @@ int fit_stages(int n_cells, int nproc, int threads, int want, int narr, int limi
     return st;
 }
 
-// The two variants (direct loads, bulk-copy tiles) are separate kernels, so
-// that the direct one carries no pipeline state.
-template <int SP, bool PER, int MCC, bool STAGED>
+// The variants (direct loads, bulk-copy tiles, axial renewal with direct
+// loads) are separate kernels, so that each carries only its own state.
+template <int SP, bool PER, int MCC, bool STAGED, bool AXIAL = false>
 cudaError_t launch_step_k(pic_case *c, int stages)
 {
-    auto k = k_particle_step<SP, PER, MCC, STAGED>;
+    auto k = k_particle_step<SP, PER, MCC, STAGED, AXIAL>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     cudaError_t e = allow_max_step_smem(k, once, attr_err, c->device);
@@ -309,6 +311,7 @@ cudaError_t launch_step_k(pic_case *c, int stages)
 template <int SP, bool PER, int MCC>
 cudaError_t launch_step_t(pic_case *c)
 {
+    if (c->P.axial_len > 0.0f) return launch_step_k<SP, PER, MCC, false, true>(c, 0);
     const int nproc = MCC == 1 ? c->P.sp[SP].nproc : 0;
     const int stages = fit_stages(c->d.n_cells, nproc, c->step_threads[SP], c->step_stages[SP],
                                   step_arrays(SP, PER, MCC), step_smem_limit(c->device));
@@ -375,6 +378,8 @@ pic_status alloc_species(pic_case *c, int sp, long long need)
     for (int h = 0; h < 2; ++h) {
         SpeciesBufs &B = c->P.buf[sp][h];
         c->dfree(B.cell); c->dfree(B.off); c->dfree(B.vx); c->dfree(B.vy); c->dfree(B.vz); c->dfree(B.id);
+        c->dfree(B.z);
+        B.z = nullptr;
     }
     const long long slots = (cap + 3) / 4 * 4 + 4;   // float4 access never leaves the buffer
     for (int h = 0; h < 2; ++h) {
@@ -383,6 +388,11 @@ pic_status alloc_species(pic_case *c, int sp, long long need)
         B.vx = (float *)c->dalloc(slots * 4); B.vy = (float *)c->dalloc(slots * 4);
         B.vz = (float *)c->dalloc(slots * 4); B.id = (uint32_t *)c->dalloc(slots * 4);
         if (!B.cell || !B.off || !B.vx || !B.vy || !B.vz || !B.id) return fail(PIC_ENOMEM, "particle allocation failed");
+        if (c->d.axial_length_m > 0) {                              // axial excursion for the renewal
+            B.z = (float *)c->dalloc(slots * 4);
+            if (!B.z) return fail(PIC_ENOMEM, "particle allocation failed");
+            CU(cudaMemsetAsync(B.z, 0, slots * 4, c->stream));
+        }
     }
     c->P.cap[sp] = (unsigned long long)cap;
     return PIC_OK;
@@ -412,6 +422,7 @@ __global__ void k_reset_counters(Ctrl *ctrl)
 {
     ctrl->absorbed[0][0] = ctrl->absorbed[0][1] = ctrl->absorbed[1][0] = ctrl->absorbed[1][1] = 0;
     ctrl->see = ctrl->iz = 0;
+    ctrl->renewed[0] = ctrl->renewed[1] = 0;
     ctrl->cand[0] = ctrl->cand[1] = 0;
     for (int s = 0; s < 2; ++s)
         for (int k = 0; k < kMaxProc; ++k) ctrl->coll[s][k] = 0;
@@ -706,6 +717,7 @@ pic_status load_begin(pic_case *c, int sp, int64_t n, Ctrl *h)
         CU(cudaMemcpyAsync(D.vy, A.vy, b, cudaMemcpyDeviceToDevice, c->stream));
         CU(cudaMemcpyAsync(D.vz, A.vz, b, cudaMemcpyDeviceToDevice, c->stream));
         CU(cudaMemcpyAsync(D.id, A.id, b, cudaMemcpyDeviceToDevice, c->stream));
+        if (A.z) CU(cudaMemcpyAsync(D.z, A.z, b, cudaMemcpyDeviceToDevice, c->stream));
     }
     return PIC_OK;
 }
@@ -725,6 +737,8 @@ pic_status load_finish(pic_case *c, int sp, int64_t n, const Ctrl &h)
         z.n_total[s] = z.n_active[s] = cnt;
     }
     CU(cudaMemcpyAsync(c->P.ctrl, &z, sizeof(Ctrl), cudaMemcpyHostToDevice, c->stream));
+    if (c->P.buf[sp][0].z && n > 0)                                   // loaded particles start at z = 0
+        CU(cudaMemsetAsync(c->P.buf[sp][0].z, 0, sizeof(float) * (size_t)n, c->stream));
     pic_status st = reset_moments(c);
     if (st != PIC_OK) return st;
     CU(cudaStreamSynchronize(c->stream));
@@ -778,6 +792,10 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     if (desc->circuit == 1 && (!(desc->blocking_cap_F_per_m2 >= 0) || !std::isfinite(desc->blocking_cap_F_per_m2)))
         return fail(PIC_EINVAL, "a series capacitor needs a finite capacitance >= 0");
     if (!(desc->ifedf_emax_ev >= 0)) return fail(PIC_EINVAL, "ifedf_emax_ev must be >= 0");
+    if (!(desc->axial_length_m >= 0) || !std::isfinite(desc->axial_length_m))
+        return fail(PIC_EINVAL, "axial_length_m must be finite and >= 0");
+    for (int s = 0; s < desc->n_species; ++s)
+        if (!(desc->renew_temp_ev[s] >= 0)) return fail(PIC_EINVAL, "renew_temp_ev must be >= 0");
     for (int s = 0; s < desc->n_species; ++s)
         if (!(desc->mass_kg[s] > 0)) return fail(PIC_EINVAL, "species mass must be positive");
     pic_case *c = new pic_case();
@@ -833,6 +851,8 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     P.circuit = desc->circuit;
     P.c_blk = desc->circuit == 1 ? desc->blocking_cap_F_per_m2 : 0.0;
     P.no_field = desc->no_field ? 1 : 0;
+    P.axial_len = (float)desc->axial_length_m;
+    P.dt_f = (float)desc->dt_s;
     P.eps0_L = kEps0 / desc->length_m;
     P.inv_cap_eps0_L = 1.0 / (P.c_blk + P.eps0_L);
     for (int s = 0; s < 2; ++s) {
@@ -1123,6 +1143,32 @@ pic_status pic_read_particles(pic_case *c, int sp, int64_t max_n, int64_t *n_out
     return device_error(c);
 }
 
+pic_status pic_read_axial(pic_case *c, int sp, int64_t max_n, int64_t *n_out, float *z)
+{
+    if (!c || sp < 0 || sp >= c->d.n_species || max_n < 0) return fail(PIC_EINVAL, "bad read arguments");
+    if (!c->P.buf[sp][0].z) return fail(PIC_ESTATE, "the case has no axial renewal");
+    Ctrl h;
+    CU(cudaMemcpyAsync(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    const size_t n = (size_t)h.n_total[sp];
+    const SpeciesBufs &B = c->P.buf[sp][h.cur[sp]];
+    std::vector<int32_t> hc(n);
+    std::vector<float> hz(n);
+    if (n) {
+        CU(cudaMemcpy(hc.data(), B.cell, n * 4, cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(hz.data(), B.z, n * 4, cudaMemcpyDeviceToHost));
+    }
+    int64_t k = 0;
+    for (size_t i = 0; i < n; ++i) {                 // live slots, in pic_read_particles' order
+        if (hc[i] < 0) continue;
+        if (k < max_n && z) z[k] = hz[i];
+        ++k;
+    }
+    if (n_out) *n_out = k;
+    if (k > max_n) return fail(PIC_ECAPACITY, "output buffer smaller than the live count");
+    return device_error(c);
+}
+
 pic_status pic_read_field(pic_case *c, double *phi, double *E, int64_t *rho_raw)
 {
     if (!c) return fail(PIC_EINVAL, "null case");
@@ -1211,6 +1257,8 @@ pic_status pic_read_moments(pic_case *c, pic_moments *m)
     if (m->eepf) for (int b = 0; b < kEepfBins; ++b) m->eepf[b] = (double)ee[b];
     if (m->ifedf) for (int b = 0; b < 2 * kIfedfBins; ++b) m->ifedf[b] = (double)ifd[b];
     m->electrode_charge = h.q_el;
+    m->renewed[0] = (int64_t)h.renewed[0];
+    m->renewed[1] = (int64_t)h.renewed[1];
     const long long have = std::min<long long>((long long)h.fe_n, c->P.fe_cap);
     long long want = m->field_energy ? std::min<long long>(have, m->field_energy_cap) : 0;
     for (long long i = 0; i < want; ++i) {
@@ -1273,14 +1321,14 @@ pic_status pic_profile_read(pic_case *c, pic_kernel_stat *out, int max_entries, 
 namespace {
 
 constexpr char kCkptMagic[8] = {'P', 'I', 'C', '1', 'D', '3', 'V', 'C'};
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 
 struct CkptHeader {
     char magic[8];
     uint32_t version, header_bytes;
     int32_t n_cells, n_species, n_nodes, r_stride, deposit_copies, need_init;
     int64_t fe_cap, host_step, since_sort[2];
-    int32_t sort_k[2], threads[2], stages[2], tuned, autotune;
+    int32_t sort_k[2], threads[2], stages[2], tuned, autotune, has_z, pad_;
     double dt, length, q[2], m[2], w[2];
     uint64_t seed;
     uint64_t n_slots[2];           // particle slots saved per species
@@ -1305,8 +1353,9 @@ pic_status ckpt_layout(pic_case *c, Ctrl *h, uint64_t *total)
     CU(cudaMemcpyAsync(h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     uint64_t b = sizeof(CkptHeader) + sizeof(Ctrl);
+    const uint64_t per = c->P.buf[0][0].z ? 28ull : 24ull;        // + axial excursion
     for (int s = 0; s < c->d.n_species; ++s)
-        if (c->loaded[s] || (s == 1 && c->loaded[0])) b += 24ull * h->n_total[s];
+        if (c->loaded[s] || (s == 1 && c->loaded[0])) b += per * h->n_total[s];
     for (auto &a : ckpt_arrays(c)) b += a.second;
     *total = b;
     return PIC_OK;
@@ -1341,6 +1390,7 @@ pic_status pic_checkpoint_save(pic_case *c, void *host, uint64_t bytes)
     hd.r_stride = c->P.r_stride; hd.deposit_copies = kDepositCopies; hd.need_init = c->need_init ? 1 : 0;
     hd.fe_cap = c->P.fe_cap; hd.host_step = c->host_step;
     hd.tuned = c->tuned ? 1 : 0; hd.autotune = c->autotune ? 1 : 0;
+    hd.has_z = c->P.buf[0][0].z ? 1 : 0;
     for (int s = 0; s < 2; ++s) {
         hd.since_sort[s] = c->since_sort[s]; hd.sort_k[s] = c->sort_k[s];
         hd.threads[s] = c->step_threads[s]; hd.stages[s] = c->step_stages[s];
@@ -1355,8 +1405,8 @@ pic_status pic_checkpoint_save(pic_case *c, void *host, uint64_t bytes)
         const size_t n = hd.n_slots[s];
         if (!n) continue;
         const SpeciesBufs &B = c->P.buf[s][h.cur[s]];
-        const void *src[6] = {B.cell, B.off, B.vx, B.vy, B.vz, B.id};
-        for (int a = 0; a < 6; ++a) {
+        const void *src[7] = {B.cell, B.off, B.vx, B.vy, B.vz, B.id, B.z};
+        for (int a = 0; a < (hd.has_z ? 7 : 6); ++a) {
             CU(cudaMemcpyAsync(p, src[a], 4 * n, cudaMemcpyDeviceToHost, c->stream));
             p += 4 * n;
         }
@@ -1383,8 +1433,9 @@ pic_status pic_checkpoint_load(pic_case *c, const void *host, uint64_t bytes)
                 hd.dt == c->d.dt_s && hd.length == c->d.length_m && hd.seed == c->d.seed;
     for (int s = 0; s < c->d.n_species; ++s)
         same = same && hd.q[s] == c->d.charge_C[s] && hd.m[s] == c->d.mass_kg[s] && hd.w[s] == c->d.weight_per_m2[s];
+    same = same && hd.has_z == (c->d.axial_length_m > 0 ? 1 : 0);
     if (!same) return fail(PIC_EINVAL, "checkpoint of a different case descriptor");
-    uint64_t need = sizeof hd + sizeof(Ctrl) + 24ull * (hd.n_slots[0] + hd.n_slots[1]);
+    uint64_t need = sizeof hd + sizeof(Ctrl) + (hd.has_z ? 28ull : 24ull) * (hd.n_slots[0] + hd.n_slots[1]);
     for (auto &a : ckpt_arrays(c)) need += a.second;
     if (bytes < need) return fail(PIC_EINVAL, "checkpoint buffer too small");
     CU(cudaStreamSynchronize(c->stream));
@@ -1400,8 +1451,8 @@ pic_status pic_checkpoint_load(pic_case *c, const void *host, uint64_t bytes)
         h.cur[s] = 0;                                  // particles go to half 0
         if (!n) continue;
         const SpeciesBufs &B = c->P.buf[s][0];
-        void *dst[6] = {B.cell, B.off, B.vx, B.vy, B.vz, B.id};
-        for (int a = 0; a < 6; ++a) {
+        void *dst[7] = {B.cell, B.off, B.vx, B.vy, B.vz, B.id, B.z};
+        for (int a = 0; a < (hd.has_z ? 7 : 6); ++a) {
             CU(cudaMemcpyAsync(dst[a], p, 4 * n, cudaMemcpyHostToDevice, c->stream));
             p += 4 * n;
         }
@@ -1519,9 +1570,9 @@ struct pic_batch {
     int n_items = 0;
     bool planned = false;
     int periodic = 0, mcc0 = 0, mcc1 = 0;
-    int stages = 2;                 // particle tiles in flight per CTA requested (0 = direct loads):
-                                    // the batched kernel runs one 512-thread CTA per SM, and the
-                                    // bulk-copy tiles keep HBM busy where its 16 warps cannot
+    int stages = 0;                 // particle tiles in flight per CTA requested (0 = direct loads;
+                                    // on the 256-case sweep, direct loads measured 2.23 ms/step
+                                    // and two tile buffers 2.39 ms/step)
     int run_stages = 0;             // in use (fewer if shared memory is short)
     // cases with at least own_threshold particles run their own step kernels
     // (single-case kernels, 1024-thread CTAs) inside the batch's graph; the
@@ -1656,6 +1707,7 @@ pic_status batch_plan(pic_batch *b)
         if (c->d.periodic != b->periodic || c->P.sp[0].mcc != b->mcc0 ||
             (c->d.n_species > 1 ? c->P.sp[1].mcc : 0) != b->mcc1)
             return fail(PIC_EINVAL, "batch cases differ in boundary or collision model");
+        if (c->P.axial_len > 0.0f) return fail(PIC_EINVAL, "axial renewal is for single cases, not batches");
         consts[i] = c->P;
         if (next_own < b->own.size() && b->own[next_own] == (int)i) {   // stepped by its own kernels
             ++next_own;

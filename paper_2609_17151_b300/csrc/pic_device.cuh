@@ -27,12 +27,14 @@ constexpr unsigned kErrTimeout = 4u;
 constexpr unsigned kErrLoad = 8u;
 
 // Random-draw blocks: counter word 2 is (species << 16) | block.
-constexpr uint32_t kBlkMcc = 0, kBlkAux = 1, kBlkNewIon = 2, kBlkSee = 3, kBlkSeeV = 4, kBlkChild = 0xFFFF;
+constexpr uint32_t kBlkMcc = 0, kBlkAux = 1, kBlkNewIon = 2, kBlkSee = 3, kBlkSeeV = 4, kBlkRenew = 5,
+                   kBlkChild = 0xFFFF;
 
 struct SpeciesBufs {                    // one half of a species' ping-pong storage
     int32_t *cell;
     float *off, *vx, *vy, *vz;
     uint32_t *id;
+    float *z;                           // axial excursion (only with axial renewal, else null)
 };
 
 // Device-resident control block: counts, step, errors, event counters.
@@ -54,6 +56,7 @@ struct Ctrl {
     double q_el;                        // series capacitor: charge per area of electrode 0 + plate
     unsigned long long st_abs0[2];      // this step: particles absorbed at x = 0 per species
     unsigned long long st_see0;         // this step: secondary electrons emitted at x = 0
+    unsigned long long renewed[2];      // axial renewals per species
 };
 
 struct SpConst {
@@ -76,6 +79,7 @@ struct SpConst {
     double q, m, w;
     int mcc;                            // 0 none, 1 tables, 2 constant frequency
     int stages;                         // particle tiles in flight through shared memory (0 = direct loads)
+    float renew_vt, renew_drift[3];     // axial renewal Maxwellian: sqrt(kT/m), drift
 };
 
 struct StepConst {
@@ -120,6 +124,7 @@ struct StepConst {
     // electrode circuit (series capacitor) and ion energy histograms
     int circuit;                        // 0 = electrode 0 at V(t), 1 = V(t) through a capacitor, 2 = J(t)
     int no_field;                       // 1: E = 0 on the mesh (only E_ext acts)
+    float axial_len, dt_f;              // axial renewal length (0 = off), dt in FP32
     double c_blk, eps0_L, inv_cap_eps0_L; // blocking capacitance C, eps0/L, 1/(C + eps0/L)
     double qw[2];                       // q_s w_s: charge per area of one particle
     double r0c[2], bg_half;             // rho_0 dx/2 = sum r0c_s R_s[0] + bg_half

@@ -47,6 +47,8 @@ class CaseDesc(C.Structure):
         ("field_history", C.c_int32),
         ("circuit", C.c_int32), ("blocking_cap_F_per_m2", C.c_double), ("ifedf_emax_ev", C.c_double),
         ("no_field", C.c_int32),
+        ("axial_length_m", C.c_double), ("renew_temp_ev", C.c_double * 2),
+        ("renew_drift_m_per_s", (C.c_double * 3) * 2),
         ("stream", C.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
     ]
@@ -64,7 +66,7 @@ class Moments(C.Structure):
         ("dens_diag_sum", C.c_void_p), ("eepf", C.c_void_p),
         ("field_energy", C.c_void_p), ("field_energy_cap", C.c_int64), ("field_energy_n", C.c_int64),
         ("reset", C.c_int32), ("sort_interval", C.c_int32),
-        ("ifedf", C.c_void_p), ("electrode_charge", C.c_double),
+        ("ifedf", C.c_void_p), ("electrode_charge", C.c_double), ("renewed", C.c_int64 * 2),
     ]
 
 
@@ -100,6 +102,7 @@ def _load_library():
     lib.pic_count.argtypes = [vp, C.POINTER(i64)]
     lib.pic_read_particles.argtypes = [vp, C.c_int, i64, C.POINTER(i64), vp, vp, vp, vp, vp, vp]
     lib.pic_read_field.argtypes = [vp, vp, vp, vp]
+    lib.pic_read_axial.argtypes = [vp, C.c_int, i64, C.POINTER(i64), vp]
     lib.pic_read_moments.argtypes = [vp, C.POINTER(Moments)]
     lib.pic_read_tuning.argtypes = [vp, C.POINTER(Tuning)]
     lib.pic_set_step_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int]
@@ -141,7 +144,7 @@ def _load_library():
     lib.pic_profile.argtypes = [vp, C.c_int]
     lib.pic_profile_read.argtypes = [vp, C.POINTER(KernelStat), C.c_int, C.POINTER(C.c_int)]
     for f in ("pic_create_case", "pic_load_xsec_table", "pic_load_particles", "pic_step", "pic_sync", "pic_count",
-              "pic_read_particles", "pic_read_field", "pic_read_moments", "pic_read_tuning", "pic_set_step_shape", "pic_checkpoint_size",
+              "pic_read_particles", "pic_read_field", "pic_read_moments", "pic_read_axial", "pic_read_tuning", "pic_set_step_shape", "pic_checkpoint_size",
               "pic_checkpoint_save", "pic_checkpoint_load", "pic_destroy", "pic_philox", "pic_deposit",
               "pic_profile", "pic_profile_read", "pic_sort_by_cell", "pic_sort_by_cell_noalloc",
               "pic_load_profile", "pic_batch_create", "pic_batch_step", "pic_batch_sync", "pic_batch_destroy",
@@ -227,6 +230,11 @@ def make_desc(cfg: dict, *, stream=None, allocator: TorchAllocator | None = None
     d.field_history = int(field_history)
     d.circuit = {"voltage": 0, "capacitor": 1, "current": 2}[cfg.get("circuit", "voltage")]
     d.no_field = int(bool(cfg.get("no_field", False)))
+    d.axial_length_m = float(cfg.get("axial_length", 0.0))
+    for i, s in enumerate(cfg["species"]):
+        d.renew_temp_ev[i] = float(s.get("renew_temp_ev", 0.0))
+        for k in range(3):
+            d.renew_drift_m_per_s[i][k] = float(s.get("renew_drift", (0.0, 0.0, 0.0))[k])
     d.blocking_cap_F_per_m2 = float(cfg.get("blocking_cap", 0.0))
     d.ifedf_emax_ev = float(cfg.get("ifedf_emax_ev", 0.0))
     d.stream = stream
@@ -322,6 +330,7 @@ def read_moments(h, n_nodes, n_species, reset=False, field_energy_cap=0) -> dict
         out[k] = out[k].reshape(n_species, n_nodes)
     out["ifedf"] = out["ifedf"].reshape(2, IFEDF_BINS)
     out["electrode_charge"] = m.electrode_charge
+    out["renewed"] = np.array(list(m.renewed))
     out["field_energy"] = out["field_energy"][: m.field_energy_n]
     out.update(step=m.step, n_steps=m.n_steps, n_diag=m.n_diag, n_alive=tuple(m.n_alive),
                absorbed=np.array([[m.absorbed[s][w] for w in range(2)] for s in range(2)]),
@@ -555,6 +564,14 @@ class Case:
 
     def moments(self, reset=False, field_energy_cap=0):
         return read_moments(self.h, self.n_nodes, self.n_species, reset=reset, field_energy_cap=field_energy_cap)
+
+    def axial(self, sp):
+        """Axial excursion z (m) of the live particles, in the order of ``particles``."""
+        n = int(self.count()[sp])
+        z = np.zeros(n, np.float32)
+        k = C.c_int64()
+        check(lib.pic_read_axial(self.h, sp, n, C.byref(k), z.ctypes.data))
+        return z[: k.value]
 
     def tuning(self):
         return read_tuning(self.h)

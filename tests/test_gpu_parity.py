@@ -279,6 +279,40 @@ def test_swarm_mode_matches_oracle_and_drift_velocity():
     gc.close()
 
 
+def _axial_ecdi(ppc, n_cells=64, L_ax=2e-5, seed=4):
+    cfg, parts = W.ecdi_case(seed=seed, n_cells=n_cells, ppc=ppc, length=n_cells * 5e-3 / 2048)
+    sp = cfg["species"]
+    sp[0].update(renew_temp_ev=10.0, renew_drift=(-2e4 / 0.02, 0.0, 0.0))
+    sp[1].update(renew_temp_ev=0.5, renew_drift=(0.0, 0.0, 0.0))
+    return dict(cfg, axial_length=L_ax), parts
+
+
+@pytest.mark.parametrize("steps", [1, 6])
+def test_axial_renewal_matches_oracle(steps):
+    """E x B box with axial renewal (the axial length is short so that
+    electrons are renewed within a few steps): particles, axial excursions
+    and renewal counts agree with the oracle."""
+    cfg, parts = _axial_ecdi(ppc=200)
+    oc = oracle_case(cfg, parts)
+    oc.step(steps)
+    gc = gpu_case(cfg, parts, sort_interval=4)
+    gc.step(steps)
+    st = compare_all(cfg, gc, oc, steps=steps)
+    flips = st[0]["flips"] + st[1]["flips"]
+    ro, rg = oc.counters()["renewed"], gc.moments()["renewed"]
+    if steps > 1:
+        assert ro[0] > 100
+    assert np.all(np.abs(rg - ro) <= max(2, flips))
+    for s in range(2):
+        g, o = gc.particles(s), oc.particles(s)
+        zg, zo = gc.axial(s), oc.axial(s)
+        ig, io = np.argsort(g["id"]), np.argsort(o["id"])
+        zg, zo = zg[ig], zo[io]
+        bad = np.abs(zg - zo) > 1e-6 * cfg["axial_length"] + 1e-5 * np.abs(zo)
+        assert bad.sum() <= max(2, flips), (s, bad.sum())
+    gc.close()
+
+
 def test_checkpoint_resume_is_bit_identical():
     """A run saved after 12 steps and restored into a fresh case continues
     bit-identically to an uninterrupted 30-step run: particles, field, moment
