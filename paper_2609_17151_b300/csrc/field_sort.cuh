@@ -165,19 +165,25 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
     unsigned long long r[2] = {0ull, 0ull}, rs[2] = {0ull, 0ull}, rd[2] = {0ull, 0ull};
     const bool real = own && i < nn;
     if (real) {
-        for (int s = 0; s < ns; ++s) {
-            unsigned long long v[kDepositCopies];
+        unsigned long long v[2][kDepositCopies];
 #pragma unroll
-            for (int k = 0; k < kDepositCopies; ++k) v[k] = P.R[s][k * P.r_stride + i];
+        for (int s = 0; s < 2; ++s)
 #pragma unroll
-            for (int k = 0; k < kDepositCopies; ++k) r[s] += v[k];
-            if (P.periodic && i == 0)
+            for (int k = 0; k < kDepositCopies; ++k) v[s][k] = s < ns ? P.R[s][k * P.r_stride + i] : 0ull;
+        if (mode == 1)
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+                if (s < ns) {
+                    rs[s] = P.Rsum[s * nn + i];
+                    if (diag) rd[s] = P.Rdiag[s * nn + i];
+                }
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int k = 0; k < kDepositCopies; ++k) r[s] += v[s][k];
+        if (P.periodic && i == 0)
+            for (int s = 0; s < ns; ++s)
                 for (int k = 0; k < kDepositCopies; ++k) r[s] += P.R[s][k * P.r_stride + N];
-            if (mode == 1) {
-                rs[s] = P.Rsum[s * nn + i];
-                if (diag) rd[s] = P.Rdiag[s * nn + i];
-            }
-        }
         for (int s = 0; s < ns; ++s) {
             R_last[s * nn + i] = r[s];
             if (mode == 1) {

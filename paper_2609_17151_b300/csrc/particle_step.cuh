@@ -3,7 +3,9 @@
 // One persistent launch per species per step.  Each CTA stages the FP32 node
 // field and the species' collision-frequency table into shared memory with a
 // bulk asynchronous copy, then streams a contiguous range of particles in
-// chunks of four (int4/float4 loads and stores), doing for each particle:
+// chunks of two (vector loads and stores; each thread's loads of its next
+// chunk are in flight while it computes the current one), doing for each
+// particle:
 //   gather E^n (linear)  ->  Boris v^{n-1/2} -> v^{n+1/2}  ->  x^{n+1}
 //   -> electrode absorption (+ secondary emission)  ->  null-collision MCC
 //   -> append of the ionization products  ->  fixed-point CIC deposit of
@@ -314,6 +316,60 @@ __host__ __device__ constexpr int step_arrays(int sp, bool periodic, int mcc)
     return (mcc != 0 || (sp == 1 && !periodic)) ? 6 : 5;
 }
 
+// Direct-load path: particles per chunk, and how many chunks ahead of the one
+// being computed each thread keeps its loads in flight (register double
+// buffering; 0 = none).  Within 64 registers a thread, chunks of two with one
+// chunk ahead measured fastest on the E x B box: chunks of one with two to
+// four ahead, chunks of two with two ahead, and chunks of four without any
+// were slower.  The staged path always moves chunks of four.
+constexpr int kDirectChunk = 2;
+constexpr int kDirectDepth = 1;
+constexpr bool kDirectPipeline = kDirectDepth > 0;
+
+// One chunk of CH consecutive particles of a species, in registers.
+template <int CH> struct VecOf;
+template <> struct VecOf<4> { typedef int4 I; typedef float4 F; typedef uint4 U; };
+template <> struct VecOf<2> { typedef int2 I; typedef float2 F; typedef uint2 U; };
+template <> struct VecOf<1> { typedef int I; typedef float F; typedef uint32_t U; };
+template <int CH> struct Chunk {
+    int c[CH];
+    float o[CH], vx[CH], vy[CH], vz[CH], z[CH];
+    uint32_t id[CH];
+};
+// vector load / store of CH elements (address aligned to CH elements)
+template <class V, int CH, class T>
+__device__ __forceinline__ void vload(T (&d)[CH], const T *src)
+{
+    const V v = *reinterpret_cast<const V *>(src);
+    const T *e = reinterpret_cast<const T *>(&v);
+#pragma unroll
+    for (int q = 0; q < CH; ++q) d[q] = e[q];
+}
+template <class V, int CH, class T>
+__device__ __forceinline__ void vstore(T *dst, const T (&s)[CH])
+{
+    V v;
+    T *e = reinterpret_cast<T *>(&v);
+#pragma unroll
+    for (int q = 0; q < CH; ++q) e[q] = s[q];
+    *reinterpret_cast<V *>(dst) = v;
+}
+// Chunk starting at slot i0 of arrays `src` (cell, off, vx, vy, vz, id, z);
+// `stride` elements between arrays when they are consecutive tiles in
+// shared memory.
+template <int CH, bool ID, bool Z>
+__device__ __forceinline__ void load_chunk(Chunk<CH> &t, const SpeciesBufs &B, long long i0)
+{
+    typedef VecOf<CH> V;
+    vload<typename V::I>(t.c, B.cell + i0);
+    vload<typename V::F>(t.o, B.off + i0);
+    vload<typename V::F>(t.vx, B.vx + i0);
+    vload<typename V::F>(t.vy, B.vy + i0);
+    vload<typename V::F>(t.vz, B.vz + i0);
+    if (ID) vload<typename V::U>(t.id, B.id + i0);
+    if (Z) vload<typename V::F>(t.z, B.z + i0);
+}
+
 // Per-CTA shared state of the particle step besides the dynamic tables.
 struct StepShared {
     uint64_t mbar;                                      // staging barrier (phase toggles per item)
@@ -325,14 +381,15 @@ struct StepShared {
     float s_red[2][kStepThreads / 32];
 };
 
-// One work item: chunks (4 particles) [beg, end) of the k-th of nk equal
+// One work item: chunks (CH particles) [beg, end) of the k-th of nk equal
 // slices of species SP of one case.  Stages the case's node field and the
 // species' table, processes the slice, flushes the deposit, the moments and
 // the counters.  `parity` is the staging barrier's phase, toggled per item;
 // bit s of `tile_phase` is the phase of tile buffer s.
 //
 // The slice is processed in tiles of one chunk per thread.  Without STAGED
-// each thread loads its chunk from global memory itself; with STAGED and
+// each thread loads its chunks from global memory itself, issuing the loads of
+// chunk k + kDirectDepth before it computes chunk k; with STAGED and
 // S.stages = n > 0, n tiles stay in flight as bulk copies (global ->
 // shared, completion on a per-buffer mbarrier), so that HBM streams while
 // the warps compute, and the warps read their chunk from shared memory.
@@ -358,7 +415,10 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     Ctrl *ctrl = P.ctrl;
     const int tid = threadIdx.x;
     const long long n = (long long)ctrl->n_active[SP];
-    const long long n_chunks = (n + 3) / 4;
+    constexpr int CH = STAGED ? 4 : kDirectChunk;        // particles per chunk
+    constexpr bool PIPE = !STAGED && kDirectPipeline;
+    constexpr bool LOAD_ID = kArr == 6 || AXIAL;
+    const long long n_chunks = (n + CH - 1) / CH;
     long long per = (n_chunks + n_items - 1) / n_items;
     per = (per + 31) & ~31ll;
     const long long beg = k_item * per;
@@ -419,6 +479,13 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         for (int k = 0; k < n_tiles && k < n_stages; ++k) issue_tile(k, k);
 
     int flush_left = tiles_per_flush, b = 0;
+    constexpr int D = PIPE ? kDirectDepth : 1;
+    Chunk<CH> nx[D] = {};                               // PIPE: the next D chunks, loads in flight
+    if (PIPE) {
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+            if (beg + d * T + tid < end) load_chunk<CH, LOAD_ID, AXIAL>(nx[d], B, (beg + d * T + tid) * CH);
+    }
     for (int k = 0; k < n_tiles; ++k) {
         if (flush_left == 0) {
             hist_flush(hist, N, R_cta);
@@ -434,28 +501,25 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             if (!ok) sh.tile_abort = 1u;
             live_chunk = live_chunk && ok;
         }
-        const long long i0 = ch * 4;
-        int4 c4 = make_int4(-1, -1, -1, -1);
-        float4 o4 = make_float4(0, 0, 0, 0), x4 = o4, y4 = o4, z4 = o4, a4 = o4;
-        uint4 id4 = make_uint4(0, 0, 0, 0);
-        if (live_chunk) {
+        const long long i0 = ch * CH;
+        Chunk<CH> t;
+        if (PIPE) {
+            t = nx[0];
+#pragma unroll
+            for (int d = 0; d + 1 < D; ++d) nx[d] = nx[d + 1];
+            if (ch + (long long)D * T < end) load_chunk<CH, LOAD_ID, AXIAL>(nx[D - 1], B, (ch + (long long)D * T) * CH);
+        } else if (live_chunk) {
             if (n_stages > 0) {
-                const unsigned char *t = tiles + ((size_t)b * kArr * T + tid) * 16u;
+                const unsigned char *tl = tiles + ((size_t)b * kArr * T + tid) * 16u;
                 const size_t stride = (size_t)T * 16u;
-                c4 = *reinterpret_cast<const int4 *>(t);
-                o4 = *reinterpret_cast<const float4 *>(t + stride);
-                x4 = *reinterpret_cast<const float4 *>(t + 2 * stride);
-                y4 = *reinterpret_cast<const float4 *>(t + 3 * stride);
-                z4 = *reinterpret_cast<const float4 *>(t + 4 * stride);
-                if (kArr == 6) id4 = *reinterpret_cast<const uint4 *>(t + 5 * stride);
+                vload<int4>(t.c, reinterpret_cast<const int *>(tl));
+                vload<float4>(t.o, reinterpret_cast<const float *>(tl + stride));
+                vload<float4>(t.vx, reinterpret_cast<const float *>(tl + 2 * stride));
+                vload<float4>(t.vy, reinterpret_cast<const float *>(tl + 3 * stride));
+                vload<float4>(t.vz, reinterpret_cast<const float *>(tl + 4 * stride));
+                if (kArr == 6) vload<uint4>(t.id, reinterpret_cast<const uint32_t *>(tl + 5 * stride));
             } else {
-                c4 = *reinterpret_cast<const int4 *>(B.cell + i0);
-                o4 = *reinterpret_cast<const float4 *>(B.off + i0);
-                x4 = *reinterpret_cast<const float4 *>(B.vx + i0);
-                y4 = *reinterpret_cast<const float4 *>(B.vy + i0);
-                z4 = *reinterpret_cast<const float4 *>(B.vz + i0);
-                if (kArr == 6 || AXIAL) id4 = *reinterpret_cast<const uint4 *>(B.id + i0);
-                if (AXIAL) a4 = *reinterpret_cast<const float4 *>(B.z + i0);
+                load_chunk<CH, LOAD_ID, AXIAL>(t, B, i0);
             }
         }
         if (n_stages > 0) {
@@ -474,18 +538,18 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             }
             b = (b + 1 == n_stages) ? 0 : b + 1;
         }
-        int cc[4] = {c4.x, c4.y, c4.z, c4.w};
-        float oo[4] = {o4.x, o4.y, o4.z, o4.w};
-        float vx[4] = {x4.x, x4.y, x4.z, x4.w};
-        float vy[4] = {y4.x, y4.y, y4.z, y4.w};
-        float vz[4] = {z4.x, z4.y, z4.z, z4.w};
-        const uint32_t ids[4] = {id4.x, id4.y, id4.z, id4.w};
-        float za[4] = {a4.x, a4.y, a4.z, a4.w};
-        int dc[4];
-        uint32_t df[4];
-        const int n_valid = live_chunk ? (int)min(4ll, n - i0) : 0;   // particles of the chunk below n
+        int (&cc)[CH] = t.c;
+        float (&oo)[CH] = t.o;
+        float (&vx)[CH] = t.vx;
+        float (&vy)[CH] = t.vy;
+        float (&vz)[CH] = t.vz;
+        const uint32_t (&ids)[CH] = t.id;
+        float (&za)[CH] = t.z;
+        int dc[CH];
+        uint32_t df[CH];
+        const int n_valid = live_chunk ? (int)min((long long)CH, n - i0) : 0;   // particles of the chunk below n
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < CH; ++q) {
             dc[q] = -1;
             df[q] = 0;
             int c = cc[q];
@@ -576,15 +640,16 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         }
         // write back (never past n: slots beyond belong to this step's appends)
         if (live_chunk) {
-            if (i0 + 4 <= n) {
-                *reinterpret_cast<int4 *>(B.cell + i0) = make_int4(cc[0], cc[1], cc[2], cc[3]);
-                *reinterpret_cast<float4 *>(B.off + i0) = make_float4(oo[0], oo[1], oo[2], oo[3]);
-                *reinterpret_cast<float4 *>(B.vx + i0) = make_float4(vx[0], vx[1], vx[2], vx[3]);
-                *reinterpret_cast<float4 *>(B.vy + i0) = make_float4(vy[0], vy[1], vy[2], vy[3]);
-                *reinterpret_cast<float4 *>(B.vz + i0) = make_float4(vz[0], vz[1], vz[2], vz[3]);
-                if (AXIAL) *reinterpret_cast<float4 *>(B.z + i0) = make_float4(za[0], za[1], za[2], za[3]);
+            if (i0 + CH <= n) {
+                typedef VecOf<CH> V;
+                vstore<typename V::I>(B.cell + i0, cc);
+                vstore<typename V::F>(B.off + i0, oo);
+                vstore<typename V::F>(B.vx + i0, vx);
+                vstore<typename V::F>(B.vy + i0, vy);
+                vstore<typename V::F>(B.vz + i0, vz);
+                if (AXIAL) vstore<typename V::F>(B.z + i0, za);
             } else {
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < CH; ++q) {
                     if (i0 + q >= n) break;
                     B.cell[i0 + q] = cc[q]; B.off[i0 + q] = oo[q];
                     B.vx[i0 + q] = vx[q]; B.vy[i0 + q] = vy[q]; B.vz[i0 + q] = vz[q];
@@ -599,7 +664,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         unsigned long long acc_f = 0;
         bool split = false;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < CH; ++q) {
             if (dc[q] < 0) continue;
             if (dc[q] == acc_c) { acc_n++; acc_f += df[q]; }
             else {
