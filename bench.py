@@ -550,6 +550,9 @@ def main():
                                              "grid": list(tuning["grid"])},
                        "sort_interval_source": "autotuner" if args.sort_interval == 0 else "fixed",
                        "autotune_steps_before_warmup": tune_steps,
+                       "tuner_ms": {"sort": [round(x, 4) for x in tuning["sort_ms"]],
+                                    "slope_per_step": [round(x, 6) for x in tuning["slope_ms"]],
+                                    "shapes": [[round(x, 4) for x in row] for row in tuning["shape_ms"]]},
                        "field": "f64 Poisson + field", "l2": "inputs larger than L2 (particle state "
                        f"{24 * n_particles / 1e6:.0f} MB)", "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

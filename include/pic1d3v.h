@@ -244,8 +244,10 @@ pic_status pic_read_moments(pic_case *c, pic_moments *out);
  * its own particles; 1 or 2 = bulk-copy pipeline); otherwise (1024, 0) and
  * desc.sort_interval stand.  shape_ms[s][k] is the mean step-kernel time of
  * candidate k = (1024,0), (512,0), (256,0), (1024,1), (512,1), (512,2); sort_ms
- * the time of one sort; slope_ms the fitted growth of the step-kernel time
- * per step since the last sort (all zero until the autotuner has run, and
+ * the time of one sort; slope_ms the growth of the step-kernel time per step
+ * that the tuner extends beyond its timing window (the fitted slope of the
+ * window's second half less two standard errors, not below zero; all zero
+ * until the autotuner has run, and
  * when its choice came from the cache).  `stages` reports the buffers in use
  * (fewer than chosen when shared memory is short).  Does not synchronise.
  * Errors: PIC_EINVAL (NULL argument or struct_size mismatch). */

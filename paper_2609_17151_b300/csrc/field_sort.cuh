@@ -430,6 +430,32 @@ __device__ __forceinline__ long long sort_count_of(const unsigned long long *n_d
     return n_dev ? (long long)*n_dev : n_host;
 }
 
+// Warp-aggregated increment of the shared counter cnt[c]: each run of
+// consecutive lanes holding the same cell shares one atomic (sorted or nearly
+// sorted particles would otherwise serialise 32 atomics on one address).  A
+// cell that appears in several runs of the warp gets one reservation per run,
+// so the ranks stay unique for any input.  Every lane of the warp calls it;
+// lanes with `active` false take no part.  Returns the counter's old value plus
+// the lane's rank within its run.
+__device__ __forceinline__ unsigned warp_agg_inc(unsigned *cnt, int c, bool active)
+{
+    const int lane = threadIdx.x & 31;
+    const int key = active ? c : -1;
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || key != prev);
+    const int s0 = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));      // this lane's run start
+    const unsigned above = lane == 31 ? 0u : starts & (0xffffffffu << (lane + 1));
+    const int e0 = above ? __ffs(above) - 1 : 32;                         // its end
+    unsigned old = 0u;
+    if (active && lane == s0) old = atomicAdd(&cnt[c], (unsigned)(e0 - s0));
+    old = __shfl_sync(0xffffffffu, old, s0);
+    return old + (unsigned)(lane - s0);
+}
+
+// Loops below advance whole warps together (blockDim a multiple of 32), so
+// that every lane reaches the warp-wide calls, and issue kSortUnroll rounds
+// of loads before they use them.
+constexpr int kSortUnroll = 4;
 __global__ void k_cells_count(SortHalves H, const int32_t *cur_dev, const unsigned long long *n_dev, long long n_host,
                               int N, unsigned *counts)
 {
@@ -438,9 +464,17 @@ __global__ void k_cells_count(SortHalves H, const int32_t *cur_dev, const unsign
     __syncthreads();
     const SpeciesBufs A = H.h[cur_dev ? *cur_dev : 0];
     const long long n = sort_count_of(n_dev, n_host);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = A.cell[i];
-        if (c >= 0 && c < N) atomicAdd(&cnt_s[c], 1u);
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long w = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); w < n; w += kSortUnroll * stride) {
+        int cs[kSortUnroll];                            // loads first, then the counts
+#pragma unroll
+        for (int u = 0; u < kSortUnroll; ++u) {
+            const long long i = w + u * stride + lane;
+            cs[u] = i < n ? A.cell[i] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kSortUnroll; ++u) warp_agg_inc(cnt_s, cs[u], cs[u] >= 0 && cs[u] < N);
     }
     __syncthreads();
     for (int j = threadIdx.x; j < N; j += blockDim.x)
@@ -459,11 +493,14 @@ __global__ void __launch_bounds__(1024) k_cells_scan(const unsigned *counts, int
     if (threadIdx.x == 0) cursor[N] = (unsigned long long)ssm[N - 1];
 }
 
-constexpr int kSortChunk = 8192;
-
-// Each CTA reserves, per cell, one contiguous range for its chunk's particles
-// (one global atomic per touched cell), then places them with shared atomics.
-__global__ void k_cells_scatter(SortHalves H, const int32_t *cur_dev, const unsigned long long *n_dev, long long n_host,
+// Each CTA takes one contiguous chunk of the particles (chunk = n / grid,
+// rounded up to whole warps, so that every CTA of the grid works; the grid is
+// one wave of two 512-thread CTAs per SM).  It
+// reserves, per cell, one contiguous range for its chunk's particles (one
+// global atomic per touched cell), then places them with shared atomics,
+// kScatterUnroll particles per lane at a time with their loads issued first.
+constexpr int kScatterUnroll = 1;
+__global__ void __launch_bounds__(512, 2) k_cells_scatter(SortHalves H, const int32_t *cur_dev, const unsigned long long *n_dev, long long n_host,
                                 int N, unsigned long long *cursor)
 {
     extern __shared__ __align__(16) unsigned char xsm[];
@@ -474,10 +511,20 @@ __global__ void k_cells_scatter(SortHalves H, const int32_t *cur_dev, const unsi
     const int half = cur_dev ? *cur_dev : 0;
     const SpeciesBufs A = H.h[half], D = H.h[half ^ 1];
     const long long n = sort_count_of(n_dev, n_host);
-    const long long lo = (long long)blockIdx.x * kSortChunk, hi = min(lo + kSortChunk, n);
-    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const int c = A.cell[i];
-        if (c >= 0 && c < N) atomicAdd(&lcnt[c], 1u);
+    long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    chunk = (chunk + 31) & ~31ll;
+    const long long lo = min((long long)blockIdx.x * chunk, n), hi = min(lo + chunk, n);
+    const int lane = threadIdx.x & 31;
+    const long long T = blockDim.x;
+    for (long long w = lo + (threadIdx.x & ~31); w < hi; w += kSortUnroll * T) {
+        int cs[kSortUnroll];
+#pragma unroll
+        for (int u = 0; u < kSortUnroll; ++u) {
+            const long long i = w + u * T + lane;
+            cs[u] = i < hi ? A.cell[i] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kSortUnroll; ++u) warp_agg_inc(lcnt, cs[u], cs[u] >= 0 && cs[u] < N);
     }
     __syncthreads();
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
@@ -486,13 +533,29 @@ __global__ void k_cells_scatter(SortHalves H, const int32_t *cur_dev, const unsi
         lcnt[j] = 0u;
     }
     __syncthreads();
-    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const int c = A.cell[i];
-        if (c < 0 || c >= N) continue;
-        const unsigned long long p = base[c] + atomicAdd(&lcnt[c], 1u);
-        D.cell[p] = c; D.off[p] = A.off[i]; D.vx[p] = A.vx[i]; D.vy[p] = A.vy[i]; D.vz[p] = A.vz[i];
-        D.id[p] = A.id[i];
-        if (A.z) D.z[p] = A.z[i];
+    const bool has_z = A.z != nullptr;
+    for (long long w = lo + (threadIdx.x & ~31); w < hi; w += kScatterUnroll * T) {
+        int c[kScatterUnroll];
+        float o[kScatterUnroll], vx[kScatterUnroll], vy[kScatterUnroll], vz[kScatterUnroll], z[kScatterUnroll];
+        uint32_t id[kScatterUnroll];
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {         // all loads before the ranking and the stores
+            const long long i = w + u * T + lane;
+            c[u] = -1; o[u] = vx[u] = vy[u] = vz[u] = z[u] = 0.f; id[u] = 0u;
+            if (i < hi) {
+                c[u] = A.cell[i]; o[u] = A.off[i]; vx[u] = A.vx[i]; vy[u] = A.vy[i]; vz[u] = A.vz[i]; id[u] = A.id[i];
+                if (has_z) z[u] = A.z[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kScatterUnroll; ++u) {
+            const bool live = c[u] >= 0 && c[u] < N;
+            const unsigned r = warp_agg_inc(lcnt, c[u], live);
+            if (!live) continue;
+            const unsigned long long p = base[c[u]] + r;
+            D.cell[p] = c[u]; D.off[p] = o[u]; D.vx[p] = vx[u]; D.vy[p] = vy[u]; D.vz[p] = vz[u]; D.id[p] = id[u];
+            if (has_z) D.z[p] = z[u];
+        }
     }
 }
 

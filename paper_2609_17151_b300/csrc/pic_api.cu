@@ -3,6 +3,7 @@
 #include "pic_device.cuh"
 #include "particle_step.cuh"
 #include "field_sort.cuh"
+#include "sort_interval.h"
 
 #include <algorithm>
 #include <cmath>
@@ -352,8 +353,8 @@ cudaError_t launch_sort(pic_case *c, int sp)
     const int gc = (int)std::min<long long>(c->num_sms * 4, std::max<long long>(1, cap / 1024));
     k_cells_count<<<gc, 512, N * sizeof(unsigned), c->stream>>>(H, cur, n, 0, N, c->P.sort_count);
     k_cells_scan<<<1, 1024, N * sizeof(double), c->stream>>>(c->P.sort_count, N, c->P.sort_cursor);
-    const long long nchunks = (cap + kSortChunk - 1) / kSortChunk;
-    k_cells_scatter<<<(unsigned)nchunks, 512, 12 * (size_t)N, c->stream>>>(H, cur, n, 0, N, c->P.sort_cursor);
+    const int gs = (int)std::min<long long>(c->num_sms * 2, std::max<long long>(1, (cap + 511) / 512));   // one wave
+    k_cells_scatter<<<gs, 512, 12 * (size_t)N, c->stream>>>(H, cur, n, 0, N, c->P.sort_cursor);
     k_sort_finish<<<4, 256, 0, c->stream>>>(c->P, sp, c->P.sort_cursor + N);
     return cudaGetLastError();
 }
@@ -476,14 +477,9 @@ cudaError_t launch_sorts(pic_case *c)
 // ---------------------------------------------------------------------------
 // Autotuner, per species, of the sort interval K and of the step kernel's
 // launch shape.
-//  1. Sort interval: right after a sort, the step time grows as particles
-//     lose their cell order (and, with electrodes, as absorbed slots
-//     accumulate); a sort costs t_sort.  With t(k) ~ a + b k over the k-th
-//     step after a sort, the mean cost per step of a period K is
-//     a + b K / 2 + t_sort / K, minimised at K = sqrt(2 t_sort / b).  The
-//     tuner times one sort and kTuneSteps steps per species (default shape),
-//     fits a and b by least squares and keeps K in [4, 1024] (1024 when the
-//     steps do not slow down).
+//  1. Sort interval: the tuner times one sort and the kTuneSteps steps after
+//     it per species (default shape); choose_sort_interval (sort_interval.h)
+//     picks K in [4, 1024] from them.
 //  2. Launch shape: CTA size (256, 512 or 1024 threads) and particle tiles
 //     in flight through shared memory (0 = each thread loads its own chunk;
 //     1 or 2 = bulk-copy pipeline).  Fewer, larger CTAs flush fewer copies
@@ -630,20 +626,17 @@ pic_status autotune(pic_case *c, int64_t *left)
         if (s >= ns) continue;
         float ts = 0.f;
         CU(cudaEventElapsedTime(&ts, sev[2 * s], sev[2 * s + 1]));
-        double sx = 0, sy = 0, sxx = 0, sxy = 0;
+        double ty[kTuneSteps];                        // step k + 1 after the sort
         for (int k = 0; k < kTuneSteps; ++k) {
             float t = 0.f;
             CU(cudaEventElapsedTime(&t, tev[4 * k + 2 * s], tev[4 * k + 2 * s + 1]));
-            const double x = k + 1;
-            sx += x; sy += t; sxx += x * x; sxy += x * t;
+            ty[k] = t;
         }
-        const double n = kTuneSteps;
-        const double b = (n * sxy - sx * sy) / (n * sxx - sx * sx);
-        const double a = (sy - b * sx) / n;
-        if (b > 1e-4 * std::max(a, 1e-6)) r.K[s] = (int)std::lround(std::sqrt(2.0 * ts / b));
+        const SortIntervalFit fit = choose_sort_interval(ty, kTuneSteps, ts, 4, kMaxSortInterval);
+        r.K[s] = fit.K;
         r.K[s] = std::max(4, std::min(kMaxSortInterval, r.K[s]));
         c->tune_sort_ms[s] = ts;
-        c->tune_slope_ms[s] = (float)b;
+        c->tune_slope_ms[s] = (float)fit.slope;
         float shape_ms[kShapes] = {};
         for (int rnd = 0; rnd < kShapeRounds; ++rnd)
             for (int k = 0; k < kShapes; ++k) {
@@ -1546,8 +1539,8 @@ pic_status pic_sort_by_cell(int32_t n_cells, int64_t n, const int32_t *cell, con
         const int gc = (int)std::min<long long>(sms * 4, std::max<long long>(1, n / 1024));
         k_cells_count<<<gc, 512, N * sizeof(unsigned), st>>>(H, nullptr, nullptr, n, N, counts);
         k_cells_scan<<<1, 1024, N * sizeof(double), st>>>(counts, N, cursor);
-        k_cells_scatter<<<(unsigned)((n + kSortChunk - 1) / kSortChunk), 512, 12 * (size_t)N, st>>>(H, nullptr, nullptr,
-                                                                                                   n, N, cursor);
+        const int gs = (int)std::min<long long>(sms * 2, std::max<long long>(1, (n + 511) / 512));
+        k_cells_scatter<<<gs, 512, 12 * (size_t)N, st>>>(H, nullptr, nullptr, n, N, cursor);
         CU(cudaGetLastError());
     }
     if (n_live) CU(cudaMemcpyAsync(n_live, cursor + N, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
