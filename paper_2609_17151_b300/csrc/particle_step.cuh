@@ -354,20 +354,19 @@ __device__ __forceinline__ void vstore(T *dst, const T (&s)[CH])
     for (int q = 0; q < CH; ++q) e[q] = s[q];
     *reinterpret_cast<V *>(dst) = v;
 }
-// Chunk starting at slot i0 of arrays `src` (cell, off, vx, vy, vz, id, z);
-// `stride` elements between arrays when they are consecutive tiles in
-// shared memory.
+// Chunk starting at element e0 of the arrays of B (cell, off, vx, vy, vz, and
+// id, z when asked).
 template <int CH, bool ID, bool Z>
-__device__ __forceinline__ void load_chunk(Chunk<CH> &t, const SpeciesBufs &B, long long i0)
+__device__ __forceinline__ void load_chunk(Chunk<CH> &t, const SpeciesBufs &B, unsigned e0)
 {
     typedef VecOf<CH> V;
-    vload<typename V::I>(t.c, B.cell + i0);
-    vload<typename V::F>(t.o, B.off + i0);
-    vload<typename V::F>(t.vx, B.vx + i0);
-    vload<typename V::F>(t.vy, B.vy + i0);
-    vload<typename V::F>(t.vz, B.vz + i0);
-    if (ID) vload<typename V::U>(t.id, B.id + i0);
-    if (Z) vload<typename V::F>(t.z, B.z + i0);
+    vload<typename V::I>(t.c, B.cell + e0);
+    vload<typename V::F>(t.o, B.off + e0);
+    vload<typename V::F>(t.vx, B.vx + e0);
+    vload<typename V::F>(t.vy, B.vy + e0);
+    vload<typename V::F>(t.vz, B.vz + e0);
+    if (ID) vload<typename V::U>(t.id, B.id + e0);
+    if (Z) vload<typename V::F>(t.z, B.z + e0);
 }
 
 // Per-CTA shared state of the particle step besides the dynamic tables.
@@ -451,6 +450,14 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     const int half_e = ctrl->cur[0];
     const int half_i = P.n_species > 1 ? ctrl->cur[1] : 0;
     const SpeciesBufs B = P.buf[SP][half];
+    // The item's particles are addressed from base pointers shifted to its
+    // first particle (the same for every thread) with 32-bit offsets.
+    const long long item0 = beg * CH;
+    SpeciesBufs Bi = B;
+    Bi.cell += item0; Bi.off += item0; Bi.vx += item0; Bi.vy += item0; Bi.vz += item0; Bi.id += item0;
+    if (AXIAL) Bi.z += item0;
+    const unsigned n_ch = (unsigned)(end - beg);                               // chunks of the item
+    const unsigned item_n = (unsigned)min(n - item0, (long long)n_ch * CH);   // its particles below n
 
     const float dtdx = P.dtdx;
     const int lane = tid & 31, warp = tid >> 5;
@@ -484,7 +491,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     if (PIPE) {
 #pragma unroll
         for (int d = 0; d < D; ++d)
-            if (beg + d * T + tid < end) load_chunk<CH, LOAD_ID, AXIAL>(nx[d], B, (beg + d * T + tid) * CH);
+            if ((unsigned)(d * T + tid) < n_ch) load_chunk<CH, LOAD_ID, AXIAL>(nx[d], Bi, (unsigned)(d * T + tid) * CH);
     }
     for (int k = 0; k < n_tiles; ++k) {
         if (flush_left == 0) {
@@ -492,8 +499,8 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             flush_left = tiles_per_flush;
         }
         --flush_left;
-        const long long ch = beg + (long long)k * T + tid;
-        bool live_chunk = ch < end;
+        const unsigned ci = (unsigned)(k * T + tid);                          // chunk within the item
+        bool live_chunk = ci < n_ch;
         if (n_stages > 0) {
             // skip the wait once any warp of the CTA has given up on a tile
             const bool ok = !sh.tile_abort && mbar_wait_bounded(&sh.full[b], ctrl, (tile_phase >> b) & 1u);
@@ -501,13 +508,13 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             if (!ok) sh.tile_abort = 1u;
             live_chunk = live_chunk && ok;
         }
-        const long long i0 = ch * CH;
+        const unsigned e0 = ci * CH;                                          // its first particle
         Chunk<CH> t;
         if (PIPE) {
             t = nx[0];
 #pragma unroll
             for (int d = 0; d + 1 < D; ++d) nx[d] = nx[d + 1];
-            if (ch + (long long)D * T < end) load_chunk<CH, LOAD_ID, AXIAL>(nx[D - 1], B, (ch + (long long)D * T) * CH);
+            if (ci + (unsigned)(D * T) < n_ch) load_chunk<CH, LOAD_ID, AXIAL>(nx[D - 1], Bi, e0 + (unsigned)(D * T * CH));
         } else if (live_chunk) {
             if (n_stages > 0) {
                 const unsigned char *tl = tiles + ((size_t)b * kArr * T + tid) * 16u;
@@ -519,7 +526,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
                 vload<float4>(t.vz, reinterpret_cast<const float *>(tl + 4 * stride));
                 if (kArr == 6) vload<uint4>(t.id, reinterpret_cast<const uint32_t *>(tl + 5 * stride));
             } else {
-                load_chunk<CH, LOAD_ID, AXIAL>(t, B, i0);
+                load_chunk<CH, LOAD_ID, AXIAL>(t, Bi, e0);
             }
         }
         if (n_stages > 0) {
@@ -547,7 +554,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         float (&za)[CH] = t.z;
         int dc[CH];
         uint32_t df[CH];
-        const int n_valid = live_chunk ? (int)min((long long)CH, n - i0) : 0;   // particles of the chunk below n
+        const int n_valid = live_chunk ? (int)min((unsigned)CH, item_n - e0) : 0;   // particles of the chunk below n
 #pragma unroll
         for (int q = 0; q < CH; ++q) {
             dc[q] = -1;
@@ -640,20 +647,21 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         }
         // write back (never past n: slots beyond belong to this step's appends)
         if (live_chunk) {
-            if (i0 + CH <= n) {
+            if (n_valid == CH) {
                 typedef VecOf<CH> V;
-                vstore<typename V::I>(B.cell + i0, cc);
-                vstore<typename V::F>(B.off + i0, oo);
-                vstore<typename V::F>(B.vx + i0, vx);
-                vstore<typename V::F>(B.vy + i0, vy);
-                vstore<typename V::F>(B.vz + i0, vz);
-                if (AXIAL) vstore<typename V::F>(B.z + i0, za);
+                vstore<typename V::I>(Bi.cell + e0, cc);
+                vstore<typename V::F>(Bi.off + e0, oo);
+                vstore<typename V::F>(Bi.vx + e0, vx);
+                vstore<typename V::F>(Bi.vy + e0, vy);
+                vstore<typename V::F>(Bi.vz + e0, vz);
+                if (AXIAL) vstore<typename V::F>(Bi.z + e0, za);
             } else {
+#pragma unroll
                 for (int q = 0; q < CH; ++q) {
-                    if (i0 + q >= n) break;
-                    B.cell[i0 + q] = cc[q]; B.off[i0 + q] = oo[q];
-                    B.vx[i0 + q] = vx[q]; B.vy[i0 + q] = vy[q]; B.vz[i0 + q] = vz[q];
-                    if (AXIAL) B.z[i0 + q] = za[q];
+                    if (q >= n_valid) break;
+                    Bi.cell[e0 + q] = cc[q]; Bi.off[e0 + q] = oo[q];
+                    Bi.vx[e0 + q] = vx[q]; Bi.vy[e0 + q] = vy[q]; Bi.vz[e0 + q] = vz[q];
+                    if (AXIAL) Bi.z[e0 + q] = za[q];
                 }
             }
         }
