@@ -393,7 +393,8 @@ struct StepShared {
 // shared, completion on a per-buffer mbarrier), so that HBM streams while
 // the warps compute, and the warps read their chunk from shared memory.
 // Results are written straight back to global memory.
-template <int SP, bool PERIODIC, int MCC, bool STAGED, bool AXIAL>
+template <int SP, bool PERIODIC, int MCC, bool STAGED, bool AXIAL, int DCHUNK = kDirectChunk,
+          int DDEPTH = kDirectDepth>
 __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char *smem, StepShared &sh,
                                               unsigned &parity, unsigned &tile_phase, long long k_item,
                                               long long n_items)
@@ -414,8 +415,8 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     Ctrl *ctrl = P.ctrl;
     const int tid = threadIdx.x;
     const long long n = (long long)ctrl->n_active[SP];
-    constexpr int CH = STAGED ? 4 : kDirectChunk;        // particles per chunk
-    constexpr bool PIPE = !STAGED && kDirectPipeline;
+    constexpr int CH = STAGED ? 4 : DCHUNK;              // particles per chunk
+    constexpr bool PIPE = !STAGED && DDEPTH > 0;
     constexpr bool LOAD_ID = kArr == 6 || AXIAL;
     const long long n_chunks = (n + CH - 1) / CH;
     long long per = (n_chunks + n_items - 1) / n_items;
@@ -486,7 +487,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         for (int k = 0; k < n_tiles && k < n_stages; ++k) issue_tile(k, k);
 
     int flush_left = tiles_per_flush, b = 0;
-    constexpr int D = PIPE ? kDirectDepth : 1;
+    constexpr int D = PIPE ? DDEPTH : 1;
     Chunk<CH> nx[D] = {};                               // PIPE: the next D chunks, loads in flight
     if (PIPE) {
 #pragma unroll
@@ -796,13 +797,18 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_particle_step(const __grid_
 }
 
 // Out-of-line item for the batch kernel: each species' body keeps its own
-// register allocation instead of the union of both.
+// register allocation instead of the union of both.  The batch kernel runs
+// 512-thread CTAs with up to 128 registers a thread and its own chunk size and
+// look-ahead: on the 256-case small sweep, chunks of one with three ahead took
+// 0.97 ms a step, chunks of two with one or two ahead 0.99 and 1.02 ms.
+constexpr int kBatchChunk = 1, kBatchDepth = 3;
 template <int SP, bool PERIODIC, int MCC, bool STAGED>
 __device__ __noinline__ void particle_item_call(const StepConst &P, unsigned char *smem, StepShared &sh,
                                                unsigned &parity, unsigned &tile_phase, long long k_item,
                                                long long n_items)
 {
-    particle_item<SP, PERIODIC, MCC, STAGED, false>(P, smem, sh, parity, tile_phase, k_item, n_items);
+    particle_item<SP, PERIODIC, MCC, STAGED, false, kBatchChunk, kBatchDepth>(P, smem, sh, parity, tile_phase,
+                                                                             k_item, n_items);
 }
 
 // Many cases in one persistent launch: CTAs take (case, species, slice) work
