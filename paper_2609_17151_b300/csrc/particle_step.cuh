@@ -324,7 +324,6 @@ __host__ __device__ constexpr int step_arrays(int sp, bool periodic, int mcc)
 // were slower.  The staged path always moves chunks of four.
 constexpr int kDirectChunk = 2;
 constexpr int kDirectDepth = 1;
-constexpr bool kDirectPipeline = kDirectDepth > 0;
 
 // One chunk of CH consecutive particles of a species, in registers.
 template <int CH> struct VecOf;
@@ -387,8 +386,9 @@ struct StepShared {
 // bit s of `tile_phase` is the phase of tile buffer s.
 //
 // The slice is processed in tiles of one chunk per thread.  Without STAGED
-// each thread loads its chunks from global memory itself, issuing the loads of
-// chunk k + kDirectDepth before it computes chunk k; with STAGED and
+// each thread loads its chunks (DCHUNK particles each) from global memory
+// itself, issuing the loads of chunk k + DDEPTH before it computes chunk k
+// (DDEPTH = 0: no look-ahead); with STAGED and
 // S.stages = n > 0, n tiles stay in flight as bulk copies (global ->
 // shared, completion on a per-buffer mbarrier), so that HBM streams while
 // the warps compute, and the warps read their chunk from shared memory.
