@@ -469,7 +469,9 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     const int T = blockDim.x;                           // chunks per tile
     const int n_warps = T >> 5;
     const int n_tiles = (int)((end - beg + T - 1) / T);
-    const int tiles_per_flush = max(1, (kFlushParticles / 4) / T);   // histogram counter range
+    // histogram counter range: at most kFlushParticles particles between
+    // flushes (counted for chunks of four, the largest CH)
+    const int tiles_per_flush = max(1, (kFlushParticles / 4) / T);
     unsigned char *const tiles = smem + L.st_off;
     // tile k -> buffer b = k mod n_stages: one bulk copy per array, one mbarrier per buffer
     auto issue_tile = [&](int k, int b) {
