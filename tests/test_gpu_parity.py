@@ -496,6 +496,34 @@ def test_landau_damping_on_gpu():
         gc.close()
 
 
+def test_thirty_percent_seed_oneil_oscillation_on_gpu():
+    """The 30 % Langmuir wave of paper §3.1 (Fig. 3, right) on the GPU: the
+    field falls by more than a decade of energy, then grows again where
+    Landau damping would keep shrinking it, as on the oracle."""
+    from .test_oracle_pins import kinetic_root
+    klD = 0.38
+    _, g0 = kinetic_root(klD)
+    cfg, parts = W.langmuir_case(seed=1, k_lambda_d=klD, ppc=1000, slab=16, amp=0.3)
+    gc = gpu_case(cfg, parts)
+    amps = []
+    for _ in range(800):
+        gc.step(1)
+        _, E, _ = gc.field()
+        amps.append(abs(np.fft.rfft(E)[1]) * 2 / cfg["n_cells"])
+    gc.close()
+    amps = np.array(amps)
+    t = (np.arange(amps.size) + 1) * cfg["dt"] * 1e9
+    env = np.array([amps[max(0, i - 40):i + 1].max() for i in range(amps.size)])
+    first = np.where((t > 10) & (t < 30))[0]
+    i_min = first[np.argmin(env[first])]
+    assert env[i_min] / env[0] < 0.3
+    later = np.where((t > t[i_min]) & (t < t[i_min] + 35))[0]
+    i_max = later[np.argmax(env[later])]
+    rise = env[i_max] / env[i_min]
+    landau = math.exp(-g0 * cfg["info"]["omega_p"] * (t[i_max] - t[i_min]) * 1e-9)
+    assert rise > 1.8 and rise > 4.0 * landau, (rise, landau)
+
+
 def test_diagnostic_moments_match_oracle():
     cfg, parts = small_ccp(seed=11, n=20001, te=5.0)
     cfg["diag_interval"] = 2
