@@ -353,6 +353,38 @@ def test_checkpoint_resume_is_bit_identical():
 
 
 @pytest.mark.slow
+def test_ecdi_dominant_wavelength_in_a_fifteen_wavelength_box():
+    """Paper §3.6, Fig. 10: in the periodic azimuthal E x B box (xenon,
+    1e17 m^-3, B = 200 G, E = 20 kV/m) of fifteen cyclotron wavelengths
+    lambda_1 = 2 pi v_E / omega_ce, with axial renewal, the saturated ion
+    density is dominated by a wavelength near lambda_1.  The box resolves
+    wavelengths in steps of one mode in fifteen; this run settles on mode 16
+    (1.67 mm) with 15 and 17 next, so the check is one mode either side of 15,
+    a tolerance of 7 % where the paper reports 1.787 mm against 1.786 mm."""
+    E0, B0 = 2e4, 0.02
+    v_e = E0 / B0
+    w_ce = W.E_CHARGE * B0 / W.M_E
+    lam1 = 2 * math.pi * v_e / w_ce
+    assert abs(lam1 * 1e3 - 1.786) < 0.001
+    n_lam = 15
+    cfg, parts = W.ecdi_case(seed=3, n_cells=4096, ppc=488, length=n_lam * lam1)
+    cfg["species"][0].update(renew_temp_ev=10.0, renew_drift=(-v_e, 0.0, 0.0))
+    cfg["species"][1].update(renew_temp_ev=0.5, renew_drift=(0.0, 0.0, 0.0))
+    cfg["axial_length"] = 0.01
+    c = pic.Case(cfg, parts, sort_interval=1024)
+    c.step(80_000)                                      # growth and saturation (0.4 us)
+    c.moments(reset=True)
+    c.step(20_000)
+    m = c.moments(reset=True)
+    c.close()
+    assert m["renewed"][0] > 0                          # electrons leave the axial length
+    ni = m["dens_sum"][1] / m["n_steps"]
+    spec = np.abs(np.fft.rfft(ni - ni.mean()))
+    mode = int(np.argmax(spec[1:]) + 1)
+    assert n_lam - 1 <= mode <= n_lam + 1, (mode, np.argsort(spec[1:])[::-1][:5] + 1)
+
+
+@pytest.mark.slow
 def test_electrical_asymmetry_reverses_the_self_bias():
     """Paper §3.3: with V(t) = V0 [cos(2 pi f t + theta) + cos(4 pi f t)] on a
     series capacitor, the DC self-bias of the powered electrode is negative at
