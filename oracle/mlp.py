@@ -80,3 +80,34 @@ def adam(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     m = b1 * m + (1 - b1) * g
     v = b2 * v + (1 - b2) * g * g
     return p - lr * (m / (1 - b1**t)) / (np.sqrt(v / (1 - b2**t)) + eps), m, v
+
+
+def warmstart_nodes(y, n_points, n_cells, periodic, dx, weights, max_per_species=0):
+    """Profiles and particle counts of a warm start (the step from the network's
+    prediction to the particle loader): `y` = [log10 ne, log10 ni, Te] at
+    n_points points spanning [0, L]; each is interpolated linearly to the nodes
+    (node i at fraction i / n_cells of the span), densities exponentiated, Te
+    clipped at 0; the count of species s is the trapezoid integral of its
+    density over the cells divided by its weight, rounded to the nearest
+    integer, capped at max_per_species when that is positive.  Returns
+    (ne, ni, te, [n_e, n_i]) on the n_cells (periodic) or n_cells + 1 nodes."""
+    y = np.asarray(y, dtype=np.float64).ravel()
+    n_nodes = n_cells if periodic else n_cells + 1
+    s = np.arange(n_nodes) / n_cells * (n_points - 1)
+    k = np.minimum(np.floor(s).astype(int), n_points - 2)
+    t = s - k
+
+    def at(base):
+        return (1 - t) * y[base + k] + t * y[base + k + 1]
+
+    ne, ni = 10.0 ** at(0), 10.0 ** at(n_points)
+    te = np.maximum(0.0, at(2 * n_points))
+    counts = []
+    for d, w in zip((ne, ni), weights):
+        right = np.roll(d, -1) if periodic else d[1:]
+        total = float(np.sum(0.5 * (d[:n_cells] + right[:n_cells]) * dx))
+        n = int(np.floor(total / w + 0.5))
+        if max_per_species > 0:
+            n = min(n, max_per_species)
+        counts.append(n)
+    return ne, ni, te, counts

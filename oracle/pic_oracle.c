@@ -734,9 +734,9 @@ static int one_step(or_case *c)
             double xn = sp->xi[k] + v[0] * dtdx;                     /* 3 */
             margin = fminabs(margin, xn - floor(xn + 0.5));
             int absorbed = -1;
-            if (p->periodic) {
-                if (xn < 0) xn += N;
-                if (xn >= N) xn -= N;
+            if (p->periodic) {                                       /* x modulo the box, any distance */
+                xn -= N * floor(xn / N);
+                if (xn >= N) xn -= N;                                /* rounding of a tiny negative xn */
             } else if (xn < 0) {
                 absorbed = 0;
             } else if (xn >= N) {
