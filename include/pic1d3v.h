@@ -119,7 +119,8 @@ typedef struct {
 typedef struct pic_case pic_case;
 
 /* Create a case on the current CUDA device.  Copies the descriptor.
- * Errors: PIC_EINVAL (sizes, version), PIC_ENOMEM, PIC_ECUDA. */
+ * Errors: PIC_EINVAL (sizes, version, a floating-point field that is not finite),
+ *         PIC_ENOMEM, PIC_ECUDA. */
 pic_status pic_create_case(const pic_case_desc *desc, pic_case **out);
 
 /* Load one collision process of one species from a raw table (paper §1:
@@ -145,6 +146,23 @@ pic_status pic_load_xsec_table(pic_case *c, int species, int kind, double thresh
 pic_status pic_load_particles(pic_case *c, int species, int64_t n, const int32_t *cell,
                               const float *offset, const float *vx, const float *vy,
                               const float *vz, const uint32_t *id, int on_device);
+
+/* Load n particles of a species in SI units (paper §1's statement of the
+ * problem: positions along the gap, three velocity components), replacing
+ * the species' particles and restarting the case at step 0 like
+ * pic_load_particles.  x_m[k] in [0, L) (m); v_m_per_s is n x 3, row-major
+ * (vx, vy, vz of particle k at 3k .. 3k+2, m/s); id may be NULL (ids
+ * 0..n-1).  on_device = 1: the arrays are device pointers, else host.  The
+ * library converts on the device: xi = x * (1/dx) in FP64, cell = floor(xi),
+ * offset = xi - cell rounded to FP32 (an offset that rounds up to 1 moves to
+ * offset 0 of the next cell; in the last cell it stays just below 1),
+ * velocities rounded to FP32.  A position outside [0, L) or not finite is
+ * reported as PIC_EINVAL by the next synchronising call after the first
+ * step (the same validation as pic_load_particles).  The caller keeps
+ * ownership of its arrays.  Errors: PIC_EINVAL, PIC_ECAPACITY (n above the
+ * species capacity), PIC_ENOMEM, PIC_ECUDA. */
+pic_status pic_load_particles_si(pic_case *c, int species, int64_t n, const double *x_m,
+                                 const double *v_m_per_s, const uint32_t *id, int on_device);
 
 /* Load n particles of one species sampled on the GPU from profiles at the
  * nodes (n_nodes values each): number density (m^-3), giving the count per
@@ -176,8 +194,23 @@ pic_status pic_load_profile(pic_case *c, int species, int64_t n, const double *d
  * PIC_ESTATE (no particles loaded), PIC_ECUDA (launch failure). */
 pic_status pic_step(pic_case *c, int64_t n_steps);
 
-/* Wait for the case stream and report any error raised by device work. */
+/* Wait for the case stream and report any error raised by device work.  The
+ * device error word is sticky: the same status is reported again until
+ * pic_clear_error or the next load. */
 pic_status pic_sync(pic_case *c);
+
+/* Wait for the case stream and clear its device error word, so that a case
+ * whose step reported PIC_ETIMEOUT or PIC_ECAPACITY can go on (the step that
+ * raised it is not repeated). */
+pic_status pic_clear_error(pic_case *c);
+
+/* Polls of a staging barrier (the bulk copy of the node field and the
+ * collision tables into a step kernel's shared memory) before the step gives
+ * up on it and raises PIC_ETIMEOUT; default 2^22.  A wait that gives up still
+ * waits (bounded) for the copy it issued before the CTA leaves, so no copy
+ * is left writing into shared memory.  For tests of the timeout path: 0 makes
+ * every such wait give up at once.  Applies to this case's later steps. */
+pic_status pic_set_wait_limit(pic_case *c, uint32_t polls);
 
 /* Live particle count per species (synchronises). */
 pic_status pic_count(pic_case *c, int64_t n_alive[2]);
@@ -409,8 +442,27 @@ pic_status pic_mlp_gradients(pic_mlp *m, const float *X, const float *Y, int n, 
  * (may be NULL) receives the loss before each step. */
 pic_status pic_mlp_train(pic_mlp *m, const float *X, const float *Y, int n, int epochs, float lr,
                          float *loss_curve);
+/* One Adam step (the update pic_mlp_train applies: beta 0.9, 0.999, eps 1e-8,
+ * bias-corrected, step counter shared with pic_mlp_train) with the given
+ * host gradient, packed like the parameters. */
+pic_status pic_mlp_adam_step(pic_mlp *m, const float *grads, float lr);
 /* Outputs in physical units (normalisation undone). */
 pic_status pic_mlp_predict(pic_mlp *m, const float *X, int n, float *Y);
+/* Train the warm-start network on n_cases converged runs (paper §2: a run
+ * resumed from a converged state answers in minutes; the network stands in
+ * for a converged state of a case it has not seen).  params is n_cases x
+ * n_params; ne, ni (m^-3) and te (eV) are n_cases x n_points, on points
+ * spanning [0, L].  The targets are [log10 max(ne, 1e6), log10 max(ni, 1e6),
+ * te] (n_out = 3 n_points, the layout pic_warmstart_load reads); inputs are
+ * scaled by [in_lo, in_hi] (n_params each); outputs are standardised by the
+ * targets' mean and deviation (+1e-3) over the cases; then `epochs`
+ * full-batch Adam steps at lr, loss_curve (may be NULL) receiving the loss
+ * before each.  Errors: PIC_EINVAL (sizes that do not match the network, a
+ * negative or non-finite profile, in_hi <= in_lo), PIC_ECUDA. */
+pic_status pic_warmstart_train(pic_mlp *m, const double *params, const double *ne, const double *ni,
+                               const double *te, int n_cases, int n_params, int n_points,
+                               const double *in_lo, const double *in_hi, int epochs, float lr,
+                               float *loss_curve);
 pic_status pic_mlp_destroy(pic_mlp *m);
 /* Warm start of a case from the network: predict, for the n_params case
  * parameters, the profiles [log10 n_e (m^-3), log10 n_i (m^-3), T_e (eV)] at
@@ -437,7 +489,10 @@ pic_status pic_gemm_bf16(const float *A, int ar, int ac, const float *B, int br,
  * exits.  No cudaMalloc, cudaFree or allocating library routine is called.
  *   - The first call on a device looks up that array's device address
  *     (cudaGetSymbolAddress, once per device, with the device current); make
- *     that first call before any stream capture.
+ *     that first call before any stream capture.  The address is kept for the
+ *     life of the process: it does not survive cudaDeviceReset (which loads
+ *     the library's device code again), so do not call this entry point on a
+ *     device after resetting it.
  *   - Every call on a device shares the one array: calls whose GPU work can
  *     overlap (different streams without ordering, or concurrent host threads)
  *     race on it.  Serialise them.

@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -412,6 +413,59 @@ pic_status pic_mlp_train(pic_mlp *m, const float *X, const float *Y, int n, int 
     MCU(cudaGetLastError());
     MCU(cudaStreamSynchronize(m->stream));
     return PIC_OK;
+}
+
+pic_status pic_mlp_adam_step(pic_mlp *m, const float *grads, float lr)
+{
+    if (!m || !grads || !(lr > 0)) return mlp_fail(PIC_EINVAL, "bad Adam arguments");
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    MCU(cudaMemcpyAsync(m->g, grads, sizeof(float) * m->n_par, cudaMemcpyHostToDevice, m->stream));
+    m->adam_t++;
+    const float c1 = 1.0f / (1.0f - std::pow(b1, (float)m->adam_t));
+    const float c2 = 1.0f / (1.0f - std::pow(b2, (float)m->adam_t));
+    k_adam<<<blocks((long long)m->n_par), 256, 0, m->stream>>>(m->p, m->g, m->m, m->v, (int)m->n_par, lr, b1, b2, eps,
+                                                                c1, c2);
+    MCU(cudaGetLastError());
+    MCU(cudaStreamSynchronize(m->stream));
+    return PIC_OK;
+}
+
+pic_status pic_warmstart_train(pic_mlp *m, const double *params, const double *ne, const double *ni, const double *te,
+                               int n_cases, int n_params, int n_points, const double *in_lo, const double *in_hi,
+                               int epochs, float lr, float *loss_curve)
+{
+    if (!m || !params || !ne || !ni || !te || !in_lo || !in_hi || n_cases < 1 || n_params != m->n_in ||
+        n_points < 2 || 3 * n_points != m->n_out || epochs < 0 || !(lr > 0))
+        return mlp_fail(PIC_EINVAL, "bad warm-start training arguments");
+    const int no = m->n_out;
+    std::vector<float> X((size_t)n_cases * n_params), Y((size_t)n_cases * no);
+    for (size_t k = 0; k < X.size(); ++k) X[k] = (float)params[k];
+    for (int i = 0; i < n_cases; ++i)
+        for (int j = 0; j < n_points; ++j) {
+            const size_t a = (size_t)i * n_points + j, r = (size_t)i * no;
+            if (!(ne[a] >= 0) || !(ni[a] >= 0) || !std::isfinite(te[a]))
+                return mlp_fail(PIC_EINVAL, "negative or non-finite training profile");
+            Y[r + j] = (float)std::log10(std::max(ne[a], 1e6));
+            Y[r + n_points + j] = (float)std::log10(std::max(ni[a], 1e6));
+            Y[r + 2 * n_points + j] = (float)te[a];
+        }
+    std::vector<float> lo(n_params), hi(n_params), mean(no, 0.0f), sd(no, 0.0f);
+    for (int k = 0; k < n_params; ++k) {
+        lo[k] = (float)in_lo[k];
+        hi[k] = (float)in_hi[k];
+        if (!(hi[k] > lo[k])) return mlp_fail(PIC_EINVAL, "input range must have in_hi > in_lo");
+    }
+    for (int j = 0; j < no; ++j) {                   // per output: mean and deviation over the cases
+        double s = 0, s2 = 0;
+        for (int i = 0; i < n_cases; ++i) s += Y[(size_t)i * no + j];
+        const double mu = s / n_cases;
+        for (int i = 0; i < n_cases; ++i) s2 += (Y[(size_t)i * no + j] - mu) * (Y[(size_t)i * no + j] - mu);
+        mean[j] = (float)mu;
+        sd[j] = (float)(std::sqrt(s2 / n_cases) + 1e-3);
+    }
+    pic_status st = pic_mlp_set_normalization(m, lo.data(), hi.data(), mean.data(), sd.data());
+    if (st != PIC_OK) return st;
+    return pic_mlp_train(m, X.data(), Y.data(), n_cases, epochs, lr, loss_curve);
 }
 
 pic_status pic_mlp_predict(pic_mlp *m, const float *X, int n, float *Y)

@@ -49,15 +49,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity)
     return ok != 0;
 }
 
-// Bounded wait for the staging copy: gives up after a fixed number of polls,
-// raises kErrTimeout, then polls again (bounded) so no copy is left in
-// flight when the CTA returns.  Returns false if the data never arrived.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, Ctrl *ctrl, unsigned parity)
+// Bounded wait for a staging copy: gives up after `polls` polls and raises
+// kErrTimeout.  A copy that was issued may still be in flight then, writing
+// into this CTA's shared memory, so the wait goes on (bounded by kDrainPolls,
+// whatever `polls` is) until it lands before the caller leaves.  Returns
+// false if the data did not arrive within `polls`.
+constexpr int kDrainPolls = 1 << 22;
+constexpr unsigned kDefaultWaitPolls = 1u << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, Ctrl *ctrl, unsigned parity, unsigned polls)
 {
-    for (int i = 0; i < (1 << 22); ++i)
+    for (unsigned i = 0; i < polls; ++i)
         if (mbar_try_wait(mbar, parity)) return true;
     atomicOr(&ctrl->err, kErrTimeout);
-    for (int i = 0; i < (1 << 22); ++i)
+    for (int i = 0; i < kDrainPolls; ++i)
         if (mbar_try_wait(mbar, parity)) return false;
     return false;
 }
@@ -442,7 +446,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     if (tid < 2 + 2 * kMaxProc) s_cnt[tid] = 0u;
     if (tid < 2) s_abs[tid] = 0u;
     if (tid == 0) { sh.s_see = 0u; sh.s_see0 = 0u; sh.s_renew = 0u; }
-    const bool staged = mbar_wait_bounded(&sh.mbar, ctrl, parity);
+    const bool staged = mbar_wait_bounded(&sh.mbar, ctrl, parity, P.wait_polls);
     parity ^= 1u;
     if (!__syncthreads_and(staged)) return;
     if (n_stages > 0 && sh.tile_abort) return;          // this CTA gave up on its tiles earlier
@@ -506,7 +510,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         bool live_chunk = ci < n_ch;
         if (n_stages > 0) {
             // skip the wait once any warp of the CTA has given up on a tile
-            const bool ok = !sh.tile_abort && mbar_wait_bounded(&sh.full[b], ctrl, (tile_phase >> b) & 1u);
+            const bool ok = !sh.tile_abort && mbar_wait_bounded(&sh.full[b], ctrl, (tile_phase >> b) & 1u, P.wait_polls);
             tile_phase ^= 1u << b;
             if (!ok) sh.tile_abort = 1u;
             live_chunk = live_chunk && ok;
@@ -701,7 +705,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             // and the CTA streams no more tiles; wait, bounded, for every
             // buffer's last copy once
             if (tid == 0)
-                for (int j = 0; j < n_stages; ++j) mbar_wait_bounded(&sh.full[j], ctrl, (tile_phase >> j) & 1u);
+                for (int j = 0; j < n_stages; ++j) mbar_wait_bounded(&sh.full[j], ctrl, (tile_phase >> j) & 1u, 0u);
             return;
         }
     }

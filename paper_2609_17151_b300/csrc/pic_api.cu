@@ -38,6 +38,11 @@ pic_status fail(pic_status s, const std::string &msg)
         if (e_ != cudaSuccess) return fail(PIC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// Longest CUDA graph of steps replayed by pic_step; graphs of every length
+// 1..kGraphSteps are kept so that a run of steps cut short by a sort or by
+// the end of the call still replays a graph.
+constexpr int kGraphSteps = 16;
+
 struct Proc {
     int kind;
     double thr;
@@ -69,9 +74,10 @@ struct pic_case {
     int step_stages[2] = {0, 0};                // particle tiles in flight (0 = direct loads)
     float tune_shape_ms[2][6] = {};             // autotuner measurements, reported by pic_read_tuning
     float tune_sort_ms[2] = {}, tune_slope_ms[2] = {};
-    // CUDA graph of kGraphSteps steps (no sort), replayed by pic_step
-    cudaGraphExec_t graph = nullptr;
-    int graph_steps = 0;
+    // CUDA graphs of k = 1..kGraphSteps steps (no sort), replayed by pic_step,
+    // and the kernel arguments they captured (a change drops them)
+    cudaGraphExec_t graph[kGraphSteps + 1] = {};
+    StepConst graph_P{};
     int step_grid[2] = {0, 0};
     unsigned step_smem[2] = {0, 0};
     int step_grid_threads[2] = {0, 0}, step_grid_stages[2] = {-1, -1};   // shape the cached grid was computed for
@@ -431,6 +437,35 @@ __global__ void k_reset_counters(Ctrl *ctrl)
     ctrl->n_steps_acc = ctrl->n_diag_acc = 0;
 }
 
+// SI positions and velocities -> the internal layout.  xi = x / dx in FP64;
+// cell = floor(xi), offset = xi - cell rounded to FP32 (an offset that rounds
+// up to 1 moves to the next cell's 0, or stays below 1 in the last cell).  A
+// position outside [0, L) or not finite is stored as cell n_cells, which the
+// validation at the first step reports (PIC_EINVAL).
+__global__ void k_load_si(SpeciesBufs B, long long n, int N, double inv_dx, double len, const double *__restrict__ x,
+                          const double *__restrict__ v, const uint32_t *__restrict__ id)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const double xm = x[k];
+        int c = N;
+        float o = 0.0f;
+        if (xm >= 0.0 && xm < len) {
+            const double xi = xm * inv_dx;
+            const double fl = floor(xi);
+            c = (int)fl;
+            o = (float)(xi - fl);
+            if (o >= 1.0f) { o = 0.0f; c += 1; }
+            if (c >= N) { c = N - 1; o = 0.99999994f; }
+        }
+        B.cell[k] = c;
+        B.off[k] = o;
+        B.vx[k] = (float)v[3 * k];
+        B.vy[k] = (float)v[3 * k + 1];
+        B.vz[k] = (float)v[3 * k + 2];
+        B.id[k] = id ? id[k] : (uint32_t)k;
+    }
+}
+
 pic_status reset_moments(pic_case *c)
 {
     const size_t nn = (size_t)c->n_nodes;
@@ -453,9 +488,10 @@ namespace {
 
 void drop_graph(pic_case *c)
 {
-    if (c->graph) cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-    c->graph_steps = 0;
+    for (auto &g : c->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
 }
 
 // The kernels of one step (both species, field solve), launched on the case stream.
@@ -660,14 +696,16 @@ pic_status autotune(pic_case *c, int64_t *left)
 }
 
 // ---------------------------------------------------------------------------
-// CUDA graph of kGraphSteps steps.  Kernel arguments are captured by value,
-// so the graph is dropped whenever they change (load, tables).
+// CUDA graphs of 1..kGraphSteps steps.  Kernel arguments are captured by
+// value, so the graphs are dropped whenever they change (load, tables, launch
+// shape) and rebuilt together at the next replay, so that their set-up falls
+// in one call rather than in the middle of a caller's timed run.
 // ---------------------------------------------------------------------------
-constexpr int kGraphSteps = 16;
-
 pic_status build_graph(pic_case *c, int steps)
 {
-    drop_graph(c);
+    if (std::memcmp(&c->graph_P, &c->P, sizeof(StepConst)) != 0) drop_graph(c);
+    if (c->graph[steps]) return PIC_OK;
+    c->graph_P = c->P;
     long long saved[pic_case::kClasses];
     for (int k = 0; k < pic_case::kClasses; ++k) saved[k] = c->launches[k];
     cudaGraph_t g = nullptr;
@@ -680,10 +718,24 @@ pic_status build_graph(pic_case *c, int steps)
         if (g) cudaGraphDestroy(g);
         return fail(PIC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&c->graph, g, 0);
+    e = cudaGraphInstantiate(&c->graph[steps], g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(PIC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    c->graph_steps = steps;
+    if (e != cudaSuccess) {
+        c->graph[steps] = nullptr;
+        return fail(PIC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return PIC_OK;
+}
+
+// Every graph length a run of steps can need (at most the shortest sort interval).
+pic_status build_graphs(pic_case *c)
+{
+    int G = kGraphSteps;
+    for (int s = 0; s < c->d.n_species; ++s) G = std::min(G, c->sort_k[s]);
+    for (int k = 1; k <= G; ++k) {
+        pic_status st = build_graph(c, k);
+        if (st != PIC_OK) return st;
+    }
     return PIC_OK;
 }
 
@@ -739,8 +791,7 @@ pic_status load_finish(pic_case *c, int sp, int64_t n, const Ctrl &h)
     c->need_init = true;
     c->host_step = 0;
     c->since_sort[0] = c->since_sort[1] = 0;
-    drop_graph(c);
-    return PIC_OK;
+    return PIC_OK;                                   // graphs are dropped at replay if the load moved a buffer
 }
 
 } // namespace
@@ -791,6 +842,23 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
         if (!(desc->renew_temp_ev[s] >= 0)) return fail(PIC_EINVAL, "renew_temp_ev must be >= 0");
     for (int s = 0; s < desc->n_species; ++s)
         if (!(desc->mass_kg[s] > 0)) return fail(PIC_EINVAL, "species mass must be positive");
+    {   // every floating-point quantity of the descriptor must be finite
+        std::vector<double> v = {desc->length_m, desc->dt_s, desc->gas_density_m3, desc->gas_temp_k, desc->gas_mass_kg,
+                                 desc->see_gamma, desc->see_temp_ev, desc->background_charge_C_per_m3,
+                                 desc->const_nu_e_per_s, desc->blocking_cap_F_per_m2, desc->ifedf_emax_ev,
+                                 desc->axial_length_m};
+        for (int k = 0; k < 3; ++k) { v.push_back(desc->B_T[k]); v.push_back(desc->E_ext_V_per_m[k]); }
+        for (int h = 0; h < 4; ++h) {
+            v.push_back(desc->harm_freq_hz[h]); v.push_back(desc->harm_amp_v[h]); v.push_back(desc->harm_phase_rad[h]);
+        }
+        for (int s = 0; s < 2; ++s) {
+            v.push_back(desc->charge_C[s]); v.push_back(desc->mass_kg[s]); v.push_back(desc->weight_per_m2[s]);
+            v.push_back(desc->renew_temp_ev[s]);
+            for (int k = 0; k < 3; ++k) v.push_back(desc->renew_drift_m_per_s[s][k]);
+        }
+        for (double x : v)
+            if (!std::isfinite(x)) return fail(PIC_EINVAL, "a descriptor quantity is not finite");
+    }
     pic_case *c = new pic_case();
     c->d = *desc;
     c->autotune = c->d.sort_interval <= 0;
@@ -821,6 +889,7 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     P.eepf_lo = (float)(0.45 * N); P.eepf_hi = (float)(0.55 * N);
     P.inv_dlog = (float)(1.0 / (std::log(kEmax / kEmin) / (kNGrid - 1)));
     P.diag_interval = desc->diag_interval;
+    P.wait_polls = kDefaultWaitPolls;
     P.vol_interior = dx; P.vol_wall = desc->periodic ? dx : 0.5 * dx;
     P.bg_charge = desc->background_charge_C_per_m3;
     P.bg_r = P.bg_charge * dx * dx / kEps0;
@@ -950,6 +1019,42 @@ pic_status pic_load_particles(pic_case *c, int sp, int64_t n, const int32_t *cel
     return load_finish(c, sp, n, h);
 }
 
+pic_status pic_load_particles_si(pic_case *c, int sp, int64_t n, const double *x_m, const double *v_m_per_s,
+                                 const uint32_t *id, int on_device)
+{
+    if (!c || sp < 0 || sp >= c->d.n_species || n < 0) return fail(PIC_EINVAL, "bad load arguments");
+    if (n > 0 && (!x_m || !v_m_per_s)) return fail(PIC_EINVAL, "null particle array");
+    Ctrl h;
+    pic_status st = load_begin(c, sp, n, &h);
+    if (st != PIC_OK) return st;
+    if (n > 0) {
+        const double *dx_ = x_m, *dv = v_m_per_s;
+        const uint32_t *did = id;
+        void *tmp = nullptr;
+        if (!on_device) {                                 // staged through one device buffer
+            const size_t bytes = (size_t)n * (4 * sizeof(double)) + (id ? (size_t)n * 4 : 0);
+            CU(cudaMallocAsync(&tmp, bytes, c->stream));
+            double *tx = (double *)tmp, *tv = tx + n;
+            CU(cudaMemcpyAsync(tx, x_m, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            CU(cudaMemcpyAsync(tv, v_m_per_s, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            dx_ = tx;
+            dv = tv;
+            if (id) {
+                uint32_t *ti = (uint32_t *)(tv + 3 * n);
+                CU(cudaMemcpyAsync(ti, id, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+                did = ti;
+            }
+        }
+        const int grid = (int)std::min<long long>((n + 255) / 256, (long long)c->num_sms * 16);
+        k_load_si<<<grid, 256, 0, c->stream>>>(c->P.buf[sp][0], n, c->d.n_cells, 1.0 / c->P.dx, c->d.length_m, dx_, dv,
+                                               did);
+        CU(cudaGetLastError());
+        if (tmp) CU(cudaFreeAsync(tmp, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return load_finish(c, sp, n, h);
+}
+
 pic_status pic_load_profile(pic_case *c, int sp, int64_t n, const double *density, const double *temp_ev,
                             const double drift[3], uint32_t id_base)
 {
@@ -1039,45 +1144,50 @@ pic_status pic_step(pic_case *c, int64_t n_steps)
         if (st != PIC_OK) return st;
     }
     int64_t left = n_steps;
+    auto sort_due = [&]() -> pic_status {
+        for (int s = 0; s < c->d.n_species; ++s)
+            if (c->since_sort[s] >= c->sort_k[s]) {
+                CU(launch_sort(c, s));
+                c->since_sort[s] = 0;
+            }
+        return PIC_OK;
+    };
     while (left > 0) {
         if (c->autotune && !c->tuned && c->host_step > 0 && left >= kTuneTotalSteps) {
             pic_status st = autotune(c, &left);
             if (st != PIC_OK) return st;
             continue;
         }
-        // steps before the next sort of any species
+        pic_status st = sort_due();
+        if (st != PIC_OK) return st;
+        // steps before the next sort of any species (at least one)
         long long room = kGraphSteps;
-        int G = kGraphSteps;
-        for (int s = 0; s < c->d.n_species; ++s) {
-            room = std::min(room, c->sort_k[s] - c->since_sort[s]);
-            G = std::min(G, c->sort_k[s]);
-        }
-        // replay the graph when G steps fit before the next sort (steps run
-        // directly while profiling, and for the first step after a load)
-        if (!c->prof && c->host_step > 0 && left >= G && G <= room) {
-            if (!c->graph || c->graph_steps != G) {
-                pic_status st = build_graph(c, G);
+        for (int s = 0; s < c->d.n_species; ++s) room = std::min(room, c->sort_k[s] - c->since_sort[s]);
+        // replay a graph of that many steps (steps run directly while
+        // profiling, and for the first step after a load)
+        if (!c->prof && c->host_step > 0) {
+            const int seg = (int)std::min<long long>(left, room);
+            if (std::memcmp(&c->graph_P, &c->P, sizeof(StepConst)) != 0) drop_graph(c);
+            if (!c->graph[seg]) {
+                st = build_graphs(c);
+                if (st != PIC_OK) return st;
+                st = build_graph(c, seg);
                 if (st != PIC_OK) return st;
             }
-            CU(cudaGraphLaunch(c->graph, c->stream));
-            c->launches[KC_STEP] += (long long)G * c->d.n_species;
-            c->launches[KC_FIELD] += G;
-            c->host_step += G;
-            for (int s = 0; s < 2; ++s) c->since_sort[s] += G;
-            left -= G;
+            CU(cudaGraphLaunch(c->graph[seg], c->stream));
+            c->launches[KC_STEP] += (long long)seg * c->d.n_species;
+            c->launches[KC_FIELD] += seg;
+            c->host_step += seg;
+            for (int s = 0; s < 2; ++s) c->since_sort[s] += seg;
+            left -= seg;
         } else {
             CU(launch_one_step(c));
             c->host_step++;
             for (int s = 0; s < 2; ++s) c->since_sort[s]++;
             left--;
         }
-        for (int s = 0; s < c->d.n_species; ++s)
-            if (c->since_sort[s] >= c->sort_k[s]) {
-                CU(launch_sort(c, s));
-                c->since_sort[s] = 0;
-            }
     }
-    return PIC_OK;
+    return sort_due();
 }
 
 pic_status pic_sync(pic_case *c)
@@ -1085,6 +1195,23 @@ pic_status pic_sync(pic_case *c)
     if (!c) return fail(PIC_EINVAL, "null case");
     CU(cudaStreamSynchronize(c->stream));
     return device_error(c);
+}
+
+pic_status pic_clear_error(pic_case *c)
+{
+    if (!c) return fail(PIC_EINVAL, "null case");
+    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaMemsetAsync(&c->P.ctrl->err, 0, sizeof(unsigned), c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+pic_status pic_set_wait_limit(pic_case *c, uint32_t polls)
+{
+    if (!c) return fail(PIC_EINVAL, "null case");
+    c->P.wait_polls = polls;
+    drop_graph(c);                                   // captured launches carry the old limit
+    return PIC_OK;
 }
 
 pic_status pic_count(pic_case *c, int64_t n_alive[2])
@@ -1576,8 +1703,7 @@ struct pic_batch {
     int grid = 0;
     int sort_k = 64;
     long long host_step = 0, steps_since_sort = 0;
-    cudaGraphExec_t graph = nullptr;
-    int graph_steps = 0;
+    cudaGraphExec_t graph[kGraphSteps + 1] = {};   // graph[k]: k batch steps
     long long launches = 0;
 };
 
@@ -1646,9 +1772,10 @@ cudaError_t batch_one_step(pic_batch *b)
 
 void batch_drop_graph(pic_batch *b)
 {
-    if (b->graph) cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-    b->graph_steps = 0;
+    for (auto &g : b->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
 }
 
 pic_status batch_plan(pic_batch *b)
@@ -1755,7 +1882,7 @@ pic_status batch_plan(pic_batch *b)
 
 pic_status batch_build_graph(pic_batch *b, int steps)
 {
-    batch_drop_graph(b);
+    if (b->graph[steps]) return PIC_OK;
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
@@ -1765,10 +1892,12 @@ pic_status batch_build_graph(pic_batch *b, int steps)
         if (g) cudaGraphDestroy(g);
         return fail(PIC_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&b->graph, g, 0);
+    e = cudaGraphInstantiate(&b->graph[steps], g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(PIC_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
-    b->graph_steps = steps;
+    if (e != cudaSuccess) {
+        b->graph[steps] = nullptr;
+        return fail(PIC_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    }
     return PIC_OK;
 }
 
@@ -1829,17 +1958,26 @@ pic_status pic_batch_step(pic_batch *b, int64_t n_steps)
     int64_t left = n_steps;
     while (left > 0) {
         const int K = b->sort_k;
-        const int G = std::min(kGraphSteps, K);
-        if (b->host_step > 0 && left >= G && b->steps_since_sort + G <= K) {
-            if (!b->graph || b->graph_steps != G) {
-                pic_status st = batch_build_graph(b, G);
-                if (st != PIC_OK) return st;
+        if (b->steps_since_sort >= K) {
+            for (pic_case *c : b->cases) CU(launch_sorts(c));
+            b->launches += 4LL * b->cases.size() * b->cases[0]->d.n_species;
+            b->steps_since_sort = 0;
+        }
+        // steps before the next sort, replayed as one graph (every length up
+        // to the sort interval is built at the first replay)
+        const int seg = (int)std::min<long long>(std::min<long long>(left, kGraphSteps), K - b->steps_since_sort);
+        if (b->host_step > 0) {
+            if (!b->graph[seg]) {
+                for (int k = 1; k <= std::min(kGraphSteps, K); ++k) {
+                    pic_status st = batch_build_graph(b, k);
+                    if (st != PIC_OK) return st;
+                }
             }
-            CU(cudaGraphLaunch(b->graph, b->stream));
-            b->launches += (long long)batch_launches_per_step(b) * G;
-            b->host_step += G;
-            b->steps_since_sort += G;
-            left -= G;
+            CU(cudaGraphLaunch(b->graph[seg], b->stream));
+            b->launches += (long long)batch_launches_per_step(b) * seg;
+            b->host_step += seg;
+            b->steps_since_sort += seg;
+            left -= seg;
         } else {
             CU(batch_one_step(b));
             b->launches += batch_launches_per_step(b);
@@ -1847,11 +1985,11 @@ pic_status pic_batch_step(pic_batch *b, int64_t n_steps)
             b->steps_since_sort++;
             left--;
         }
-        if (b->steps_since_sort >= K) {
-            for (pic_case *c : b->cases) CU(launch_sorts(c));
-            b->launches += 4LL * b->cases.size() * b->cases[0]->d.n_species;
-            b->steps_since_sort = 0;
-        }
+    }
+    if (b->steps_since_sort >= b->sort_k) {
+        for (pic_case *c : b->cases) CU(launch_sorts(c));
+        b->launches += 4LL * b->cases.size() * b->cases[0]->d.n_species;
+        b->steps_since_sort = 0;
     }
     return PIC_OK;
 }

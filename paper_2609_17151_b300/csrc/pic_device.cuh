@@ -91,6 +91,7 @@ struct StepConst {
     float eepf_lo, eepf_hi;             // cells: central 10 % of the gap
     float inv_dlog;                     // 1 / (ln(emax/emin)/(NGRID-1)) for the ln-eps interpolation
     int diag_interval;
+    unsigned wait_polls;                // polls of a staging mbarrier before a step gives up (kErrTimeout)
     double dx, dt, eps0;
     double vol_interior, vol_wall;
     double bg_charge;

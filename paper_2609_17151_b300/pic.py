@@ -118,6 +118,9 @@ def _load_library():
     lib.pic_sort_by_cell.argtypes = [i32, i64] + [vp] * 12 + [vp, vp]
     lib.pic_sort_by_cell_noalloc.argtypes = [i32, i64] + [vp] * 12 + [vp, vp]
     lib.pic_load_profile.argtypes = [vp, C.c_int, i64, dp, dp, dp, C.c_uint32]
+    lib.pic_load_particles_si.argtypes = [vp, C.c_int, i64, vp, vp, vp, C.c_int]
+    lib.pic_clear_error.argtypes = [vp]
+    lib.pic_set_wait_limit.argtypes = [vp, C.c_uint32]
     lib.pic_batch_create.argtypes = [C.POINTER(CaseDesc), C.c_int, C.POINTER(vp)]
     lib.pic_batch_case.restype = vp
     lib.pic_batch_case.argtypes = [vp, C.c_int]
@@ -138,6 +141,9 @@ def _load_library():
     lib.pic_mlp_gradients.argtypes = [vp, fp, fp, C.c_int, fp, fp]
     lib.pic_mlp_train.argtypes = [vp, fp, fp, C.c_int, C.c_int, C.c_float, fp]
     lib.pic_mlp_predict.argtypes = [vp, fp, C.c_int, fp]
+    lib.pic_mlp_adam_step.argtypes = [vp, fp, C.c_float]
+    lib.pic_warmstart_train.argtypes = [vp, dp, dp, dp, dp, C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_float,
+                                        fp]
     lib.pic_mlp_destroy.argtypes = [vp]
     lib.pic_gemm_bf16.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
     lib.pic_warmstart_load.argtypes = [vp, vp, dp, C.c_int, C.c_int, C.c_double, C.c_uint32, i64]
@@ -268,6 +274,22 @@ def load_particles(h, species, cell, offset, vx, vy, vz, ids=None, on_device=Fal
         n = arrs[0].size
         args = [a.ctypes.data for a in arrs] + [None if idsa is None else idsa.ctypes.data]
     check(lib.pic_load_particles(h, species, n, *args, int(bool(on_device))))
+
+
+def load_particles_si(h, species, x_m, v_m_per_s, ids=None, on_device=False):
+    """pic_load_particles_si: positions (m) and an n x 3 velocity array (m/s), FP64."""
+    if on_device:
+        n = int(x_m.numel())
+        args = [_ptr(x_m), _ptr(v_m_per_s), _ptr(ids)]
+    else:
+        x = np.ascontiguousarray(x_m, dtype=np.float64)
+        v = np.ascontiguousarray(v_m_per_s, dtype=np.float64).reshape(-1, 3)
+        if v.shape[0] != x.size:
+            raise ValueError("v_m_per_s must be n x 3")
+        idsa = None if ids is None else np.ascontiguousarray(ids, dtype=np.uint32)
+        n = x.size
+        args = [x.ctypes.data, v.ctypes.data, None if idsa is None else idsa.ctypes.data]
+    check(lib.pic_load_particles_si(h, species, n, *args, int(bool(on_device))))
 
 
 def load_profile(h, species, n, density, temp_ev, drift=(0.0, 0.0, 0.0), id_base=0):
@@ -430,6 +452,22 @@ class MLP:
                                 curve.ctypes.data_as(C.POINTER(C.c_float)) if record else None))
         return curve
 
+    def adam_step(self, grads, lr):
+        g, pg = _f32(grads)
+        check(lib.pic_mlp_adam_step(self.h, pg, float(lr)))
+
+    def warmstart_train(self, params, ne, ni, te, in_lo, in_hi, epochs, lr=1e-3, record=True):
+        """pic_warmstart_train: params (cases x n_in), profiles (cases x points)."""
+        d = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        P, NE, NI, TE, LO, HI = (d(a) for a in (params, ne, ni, te, in_lo, in_hi))
+        dp_ = C.POINTER(C.c_double)
+        curve = np.zeros(max(int(epochs), 1), np.float32)
+        check(lib.pic_warmstart_train(self.h, P.ctypes.data_as(dp_), NE.ctypes.data_as(dp_), NI.ctypes.data_as(dp_),
+                                      TE.ctypes.data_as(dp_), P.shape[0], P.shape[1], NE.shape[1],
+                                      LO.ctypes.data_as(dp_), HI.ctypes.data_as(dp_), int(epochs), float(lr),
+                                      curve.ctypes.data_as(C.POINTER(C.c_float)) if record else None))
+        return curve[: int(epochs)]
+
     def predict(self, X):
         X, px = _f32(X)
         Y = np.zeros((X.shape[0], self.n_out), np.float32)
@@ -546,6 +584,15 @@ class Case:
 
     def load(self, sp, p, on_device=False):
         load_particles(self.h, sp, p["cell"], p["off"], p["vx"], p["vy"], p["vz"], p.get("id"), on_device)
+
+    def load_si(self, sp, x_m, v_m_per_s, ids=None, on_device=False):
+        load_particles_si(self.h, sp, x_m, v_m_per_s, ids, on_device)
+
+    def clear_error(self):
+        check(lib.pic_clear_error(self.h))
+
+    def set_wait_limit(self, polls):
+        check(lib.pic_set_wait_limit(self.h, int(polls)))
 
     def step(self, n=1):
         step(self.h, n)

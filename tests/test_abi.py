@@ -65,3 +65,24 @@ def test_descriptor_layout_matches_header():
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f in py._fields_:
             assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
+
+
+def test_non_finite_descriptor_is_rejected_before_any_device_work():
+    """Every floating-point quantity of the descriptor must be finite: a NaN or
+    an infinity is PIC_EINVAL from pic_create_case, checked before the call
+    touches a device (so this runs without a GPU)."""
+    import math
+
+    from paper_2609_17151_b300 import pic
+    from paper_2609_17151_b300 import workloads as W
+    cfg, _ = W.ccp_case(seed=1, n_cells=32, gap=32 * 5e-5, n_per_species=10)
+    bad = [("B", (0.0, math.nan, 0.0)), ("bg_charge", math.inf), ("see_gamma", math.nan),
+           ("harmonics", [(13.56e6, math.inf, 0.0)]), ("E_ext", (0.0, 0.0, -math.inf))]
+    for key, val in bad:
+        c = dict(cfg)
+        c[key] = val
+        d = pic.make_desc(c)
+        h = ctypes.c_void_p()
+        assert pic.lib.pic_create_case(ctypes.byref(d), ctypes.byref(h)) == 1, key
+        assert b"not finite" in pic.lib.pic_last_error(), key
+        assert not h.value

@@ -48,8 +48,12 @@ def test_noalloc_sort_matches_allocating_sort_twice(n_cells, n):
         n_ref = torch.zeros(1, dtype=torch.int64, device="cuda")
         n_got = torch.full((1,), -1, dtype=torch.int64, device="cuda")
         pic.sort_by_cell(n_cells, src, ref, n_ref)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         pic.sort_by_cell_noalloc(n_cells, src, got, n_got)
         torch.cuda.synchronize()
+        if call == 1:                                       # after the first call's one-time set-up
+            assert torch.cuda.mem_get_info()[0] == free_before, "the call changed free device memory"
         k = int(n_ref.item())
         assert int(n_got.item()) == k
         a, cells_ref = _canonical(ref, k)
