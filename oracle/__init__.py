@@ -86,6 +86,11 @@ def _load():
                                      C.POINTER(C.c_int32)]
     lib.or_get_field.argtypes = [P, dp, dp]
     lib.or_get_axial.argtypes = [P, C.c_int, dp]
+    lib.or_get_clock.argtypes = [P, C.c_int, C.POINTER(C.c_int32)]
+    lib.or_neg_log_u32.restype = C.c_float
+    lib.or_neg_log_u32.argtypes = [C.c_float]
+    lib.or_clock_state.restype = C.c_int32
+    lib.or_clock_state.argtypes = [C.c_float, C.c_float, dp]
     lib.or_get_deposit.argtypes = [P, C.c_int, C.POINTER(C.c_int64)]
     lib.or_get_numax.argtypes = [P, C.c_int, dp]
     lib.or_get_nu_table.argtypes = [P, C.c_int, C.c_int, dp]
@@ -131,6 +136,19 @@ def philox4x32_10(ctr, key):
 
 def uniform(r: int) -> float:
     return float(_lib.or_uniform(C.c_uint32(int(r) & 0xFFFFFFFF)))
+
+
+CLOCK_MAX = 131071
+
+
+def neg_log_u32(u: float) -> float:
+    """-ln(u) as the collision clock computes it (FP32)."""
+    return float(_lib.or_neg_log_u32(C.c_float(u)))
+
+
+def clock_state(u: float, lam: float) -> int:
+    """Clock state 2 k + c of a fresh gap from uniform u, lam = numax dt (both FP32)."""
+    return int(_lib.or_clock_state(C.c_float(u), C.c_float(lam), None))
 
 
 def deposit(n_cells: int, periodic: bool, xi) -> np.ndarray:
@@ -260,6 +278,12 @@ class Case:
         _lib.or_get_particles(self._h, sp, _d(out["xi"]), _d(out["vx"]), _d(out["vy"]), _d(out["vz"]),
                               out["id"].ctypes.data_as(C.POINTER(C.c_uint32)), _d(out["margin"]),
                               out["event"].ctypes.data_as(C.POINTER(C.c_int32)))
+        return out
+
+    def clock(self, sp) -> np.ndarray:
+        """Collision clock 2 k + c of each particle, in the order of ``particles``."""
+        out = np.zeros(self.count(sp), dtype=np.int32)
+        _lib.or_get_clock(self._h, sp, out.ctypes.data_as(C.POINTER(C.c_int32)))
         return out
 
     def axial(self, sp) -> np.ndarray:

@@ -70,7 +70,8 @@ double or_uniform(uint32_t r) { return ((double)(r >> 9) + 0.5) * (1.0 / 8388608
  * counter (id, n, sp<<16 | blk, 0), key (seed_lo, seed_hi). */
 static void draw(const or_case *c, uint32_t id, int64_t n, int sp, uint32_t blk, uint32_t out[4]);
 
-enum { BLK_MCC = 0, BLK_AUX = 1, BLK_NEWION = 2, BLK_SEE = 3, BLK_SEE_V = 4, BLK_RENEW = 5, BLK_CHILD = 0xFFFF };
+enum { BLK_MCC = 0, BLK_AUX = 1, BLK_NEWION = 2, BLK_SEE = 3, BLK_SEE_V = 4, BLK_RENEW = 5, BLK_GAP = 6,
+       BLK_CHILD = 0xFFFF };
 
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -80,6 +81,7 @@ typedef struct {
     double *margin;
     int32_t *event;
     double *z;                 /* axial excursion (m), used with axial renewal */
+    int32_t *clk;              /* collision clock: 2 k + c (see or_clock_state) */
 } species_t;
 
 typedef struct {
@@ -124,7 +126,7 @@ static int sp_reserve(species_t *s, int64_t cap)
     while (nc < cap) nc *= 2;
 #define GROW(f, T) do { void *q = realloc(s->f, (size_t)nc * sizeof(T)); if (!q) return -1; s->f = q; } while (0)
     GROW(xi, double); GROW(vx, double); GROW(vy, double); GROW(vz, double);
-    GROW(id, uint32_t); GROW(margin, double); GROW(event, int32_t); GROW(z, double);
+    GROW(id, uint32_t); GROW(margin, double); GROW(event, int32_t); GROW(z, double); GROW(clk, int32_t);
 #undef GROW
     s->cap = nc;
     return 0;
@@ -135,13 +137,14 @@ static int sp_push(species_t *s, double xi, double vx, double vy, double vz, uin
     if (sp_reserve(s, s->n + 1)) return -1;
     int64_t k = s->n++;
     s->xi[k] = xi; s->vx[k] = vx; s->vy[k] = vy; s->vz[k] = vz; s->id[k] = id;
-    s->margin[k] = INFINITY; s->event[k] = 0; s->z[k] = 0.0;
+    s->margin[k] = INFINITY; s->event[k] = 0; s->z[k] = 0.0; s->clk[k] = 0;
     return 0;
 }
 
 static void sp_free(species_t *s)
 {
     free(s->xi); free(s->vx); free(s->vy); free(s->vz); free(s->id); free(s->margin); free(s->event); free(s->z);
+    free(s->clk);
     memset(s, 0, sizeof(*s));
 }
 
@@ -497,17 +500,100 @@ static void box_muller(double a, double b, double *n0, double *n1)
 
 static double fminabs(double m, double v) { v = fabs(v); return v < m ? v : m; }
 
+/* ------------------------------------------------------------------------ */
+/* Null-collision clock (paper §4: free flights between collisions; §1's      */
+/* null-collision method).  With P = 1 - exp(-numax dt) the chance that a      */
+/* step is a collision candidate, the number G of non-candidate steps before   */
+/* the next candidate is geometric, P(G >= g) = exp(-g numax dt), and          */
+/* G = floor(-ln(u) / (numax dt)) for u uniform has exactly that law.  So     */
+/* instead of a uniform draw every step, each particle draws G once per        */
+/* candidate and counts it down.  A clock holds 2 k + c: k more non-candidate  */
+/* steps; at the step where k is 0 the particle is a candidate (c = 0), or,    */
+/* for a gap longer than OR_CLOCK_MAX steps (c = 1), that step is one more     */
+/* non-candidate step after which a fresh gap is drawn (the geometric law is   */
+/* memoryless, so this splits one long gap exactly).  The gap is evaluated in  */
+/* FP32 with every operation rounded once (IEEE), so that any implementation   */
+/* of these operations obtains the same integers.                              */
+/* ------------------------------------------------------------------------ */
+#define OR_CLOCK_MAX 131071
+
+/* -ln(u) for u in (0, 1), FP32: u = m 2^e with m in [sqrt(1/2), sqrt(2)),
+ * ln m = 2 atanh(s), s = (m - 1)/(m + 1), by the series 2 s (1 + s^2/3 + s^4/5
+ * + ... + s^10/11) (Abramowitz and Stegun 4.1.27; |s| < 0.172, so the first
+ * omitted term is below 1e-10 relative). */
+float or_neg_log_u32(float u)
+{
+    uint32_t b;
+    memcpy(&b, &u, sizeof b);
+    int e = (int)((b >> 23) & 0xFFu) - 127;
+    uint32_t mb = (b & 0x7FFFFFu) | 0x3F800000u;
+    float m;
+    memcpy(&m, &mb, sizeof m);
+    if (m > 1.41421354f) { m = m * 0.5f; e += 1; }
+    const float s = (m - 1.0f) / (m + 1.0f);
+    const float s2 = s * s;
+    float q = 1.0f / 11.0f;
+    q = fmaf(q, s2, 1.0f / 9.0f);
+    q = fmaf(q, s2, 1.0f / 7.0f);
+    q = fmaf(q, s2, 1.0f / 5.0f);
+    q = fmaf(q, s2, 1.0f / 3.0f);
+    q = fmaf(q, s2, 1.0f);
+    const float lnm = (s + s) * q;
+    return -fmaf((float)e, 0.693147182f, lnm);
+}
+
+/* clock state 2 k + c for a fresh gap from the uniform u (FP32 arithmetic) */
+int32_t or_clock_state(float u, float lam, double *margin)
+{
+    const float x = or_neg_log_u32(u) / lam;
+    if (margin) {
+        *margin = fminabs(*margin, (x - nearbyintf(x)) / fmax(x, 1.0));
+        *margin = fminabs(*margin, (x - (float)(OR_CLOCK_MAX + 1)) / (OR_CLOCK_MAX + 1.0));
+    }
+    if (x >= (float)(OR_CLOCK_MAX + 1)) return 2 * OR_CLOCK_MAX + 1;
+    return 2 * (int32_t)floorf(x);
+}
+
+static float clock_lambda(const or_case *c, int sp) { return (float)(c->numax[sp] * c->p.dt); }
+
+/* the clock of a particle created (or loaded) during step c->step */
+static int32_t first_clock(const or_case *c, int sp, uint32_t id)
+{
+    if (!(c->numax[sp] > 0)) return 0;
+    uint32_t r[4];
+    draw(c, id, c->step, sp, BLK_GAP, r);
+    return or_clock_state((float)or_uniform(r[0]), clock_lambda(c, sp), NULL);
+}
+
+/* append a particle created in this step to the pending list, with its clock */
+static void push_new(or_case *c, int sp, double xi, double vx, double vy, double vz, uint32_t id)
+{
+    species_t *pd = &c->pend[sp];
+    if (sp_push(pd, xi, vx, vy, vz, id)) return;
+    pd->clk[pd->n - 1] = first_clock(c, sp, id);
+}
+
+/* Count the clock down one step.  Returns 1 if this step is a collision
+ * candidate; then, or at the end of a long gap, a fresh gap is drawn from
+ * word 0 of the step's block-0 draw, which is returned in r. */
+static int clock_tick(or_case *c, int sp, int64_t k, uint32_t r[4], double *margin)
+{
+    species_t *s = &c->sp[sp];
+    const int32_t st = s->clk[k];
+    if (st >= 2) { s->clk[k] = st - 2; return 0; }
+    draw(c, s->id[k], c->step, sp, BLK_MCC, r);
+    s->clk[k] = or_clock_state((float)or_uniform(r[0]), clock_lambda(c, sp), margin);
+    return (st & 1) ? 0 : 1;
+}
+
 /* one electron collision test; returns event code, updates v and margin */
 static int collide_electron(or_case *c, int64_t k, double *margin)
 {
     species_t *s = &c->sp[0];
     double m = c->p.m[0];
     uint32_t r[4];
-    draw(c, s->id[k], c->step, 0, BLK_MCC, r);
-    double u0 = or_uniform(r[0]), u1 = or_uniform(r[1]);
-    double pnull = 1.0 - exp(-c->numax[0] * c->p.dt);
-    *margin = fminabs(*margin, u0 - pnull);
-    if (u0 >= pnull) return 0;
+    if (!clock_tick(c, 0, k, r, margin)) return 0;
+    double u1 = or_uniform(r[1]);
     c->cnt.candidates[0]++;
     double v2 = s->vx[k] * s->vx[k] + s->vy[k] * s->vy[k] + s->vz[k] * s->vz[k];
     double eps = 0.5 * m * v2 / ELEM;
@@ -553,13 +639,13 @@ static int collide_electron(or_case *c, int64_t k, double *margin)
         double ne[3];
         iso_dir(or_uniform(a[1]), or_uniform(a[2]), ne);
         double spe = sqrt(2.0 * eej * ELEM / m);
-        sp_push(&c->pend[0], s->xi[k], spe * ne[0], spe * ne[1], spe * ne[2], ids[0]);
+        push_new(c, 0, s->xi[k], spe * ne[0], spe * ne[1], spe * ne[2], ids[0]);
         if (c->p.n_species > 1) {
             double g0, g1, g2, g3;
             box_muller(or_uniform(b[0]), or_uniform(b[1]), &g0, &g1);
             box_muller(or_uniform(b[2]), or_uniform(b[3]), &g2, &g3);
             double vt = sqrt(KBOLTZ * c->p.gas_temp / c->p.m[1]);
-            sp_push(&c->pend[1], s->xi[k], vt * g0, vt * g1, vt * g2, ids[1]);
+            push_new(c, 1, s->xi[k], vt * g0, vt * g1, vt * g2, ids[1]);
         }
         c->cnt.ionizations++;
     }
@@ -571,11 +657,8 @@ static int collide_ion(or_case *c, int64_t k, double *margin)
     species_t *s = &c->sp[1];
     double m = c->p.m[1], M = c->p.gas_mass;
     uint32_t r[4], a[4];
-    draw(c, s->id[k], c->step, 1, BLK_MCC, r);
-    double u0 = or_uniform(r[0]), u1 = or_uniform(r[1]);
-    double pnull = 1.0 - exp(-c->numax[1] * c->p.dt);
-    *margin = fminabs(*margin, u0 - pnull);
-    if (u0 >= pnull) return 0;
+    if (!clock_tick(c, 1, k, r, margin)) return 0;
+    double u1 = or_uniform(r[1]);
     c->cnt.candidates[1]++;
     /* gas partner drawn from the Maxwellian at the gas temperature */
     draw(c, s->id[k], c->step, 1, BLK_AUX, a);
@@ -638,7 +721,7 @@ static void emit_secondary(or_case *c, uint32_t ion_id, int wall, double *margin
     double xi = wall == 0 ? d : N - d;
     if (xi >= N) xi = nextafter(N, 0.0);
     double vx = wall == 0 ? vn : -vn;
-    sp_push(&c->pend[0], xi, vx, vth * t0, vth * t1, ids[0]);
+    push_new(c, 0, xi, vx, vth * t0, vth * t1, ids[0]);
     c->cnt.see_emitted++;
     if (wall == 0) c->st_see0++;
 }
@@ -672,6 +755,8 @@ static void renew(or_case *c, int s, int64_t k)
 /* ------------------------------------------------------------------------ */
 static void initialise(or_case *c)
 {
+    for (int s = 0; s < c->p.n_species; ++s)                 /* every loaded particle's first gap */
+        for (int64_t k = 0; k < c->sp[s].n; ++k) c->sp[s].clk[k] = first_clock(c, s, c->sp[s].id[k]);
     solve_field(c, 0.0);
     if (c->p.rewind) {
         for (int s = 0; s < c->p.n_species; ++s) {
@@ -773,15 +858,17 @@ static int one_step(or_case *c)
             /* compact in place */
             sp->xi[keep] = sp->xi[k]; sp->vx[keep] = sp->vx[k]; sp->vy[keep] = sp->vy[k];
             sp->vz[keep] = sp->vz[k]; sp->id[keep] = sp->id[k]; sp->z[keep] = sp->z[k];
-            sp->margin[keep] = margin; sp->event[keep] = event;
+            sp->margin[keep] = margin; sp->event[keep] = event; sp->clk[keep] = sp->clk[k];
             ++keep;
         }
         sp->n = keep;
     }
     for (int s = 0; s < p->n_species; ++s) {                          /* 6 */
         species_t *pd = &c->pend[s];
-        for (int64_t k = 0; k < pd->n; ++k)
+        for (int64_t k = 0; k < pd->n; ++k) {
             if (sp_push(&c->sp[s], pd->xi[k], pd->vx[k], pd->vy[k], pd->vz[k], pd->id[k])) return -1;
+            c->sp[s].clk[c->sp[s].n - 1] = pd->clk[k];
+        }
     }
     if (p->circuit >= 1) {                                           /* charge reaching electrode 0 */
         double dq = p->q[0] * p->w[0] * (double)c->st_abs0[0];
@@ -862,6 +949,13 @@ int or_get_particles(const or_case *c, int sp, double *xi, double *vx, double *v
     if (id) memcpy(id, s->id, n * sizeof(uint32_t));
     if (margin) memcpy(margin, s->margin, n * sizeof(double));
     if (event) memcpy(event, s->event, n * sizeof(int32_t));
+    return 0;
+}
+
+int or_get_clock(const or_case *c, int sp, int32_t *clk)
+{
+    if (!c || sp < 0 || sp >= c->p.n_species || !clk) return -1;
+    memcpy(clk, c->sp[sp].clk, (size_t)c->sp[sp].n * sizeof(int32_t));
     return 0;
 }
 

@@ -97,6 +97,12 @@ int  or_get_particles(const or_case *c, int sp, double *xi, double *vx, double *
                       double *vz, uint32_t *id, double *margin, int32_t *event);
 /* axial excursion z (m) of each particle, same order as or_get_particles */
 int  or_get_axial(const or_case *c, int sp, double *z);
+/* collision clock 2 k + c of each particle, same order as or_get_particles */
+int  or_get_clock(const or_case *c, int sp, int32_t *clk);
+/* -ln(u) in FP32 (the gap arithmetic of the collision clock) */
+float or_neg_log_u32(float u);
+/* clock state 2 k + c of a fresh gap from uniform u with lam = numax dt (FP32) */
+int32_t or_clock_state(float u, float lam, double *margin);
 /* phi, E: n_nodes; R: n_nodes int64 raw deposit of species sp */
 int  or_get_field(const or_case *c, double *phi, double *E);
 int  or_get_deposit(const or_case *c, int sp, int64_t *R);

@@ -256,3 +256,46 @@ def test_uniform_charge_between_grounded_plates_gives_the_exact_field_at_every_n
     assert np.abs(phi - rho * x * (L - x) / (2 * EPS0)).max() <= 1e-12 * scale * L
     assert np.abs(Ef + rho * (L - 2 * x) / (2 * EPS0)).max() <= 1e-12 * scale
     assert abs(Ef[0] + scale) <= 1e-12 * scale and abs(Ef[-1] - scale) <= 1e-12 * scale
+
+
+# --------------------------------------------------------------------------- collision clock
+def _uniforms(n, seed):
+    """23-bit uniforms ((r >> 9) + 1/2) 2^-23, exact in FP32, as the method draws them"""
+    r = np.random.default_rng(seed).integers(0, 2**32, n, dtype=np.uint64)
+    return (((r >> 9).astype(np.float64) + 0.5) * 2.0**-23).astype(np.float32)
+
+
+def test_fp32_log_of_the_collision_clock_is_within_a_few_ulp():
+    """-ln(u) of the clock (FP32 atanh series, Abramowitz and Stegun 4.1.27)
+    against the FP64 logarithm: relative error below 3e-7 (a few FP32 ulp) at
+    random and at extreme uniforms; a wrong series coefficient, range
+    reduction or ln 2 fails."""
+    u = np.concatenate([_uniforms(100_000, 1), np.float32([2.0**-24, 0.5, 1 - 2.0**-24, 0.70710677, 0.70710683,
+                                                            0.25, 0.99, 1e-6])])
+    got = np.array([oracle.neg_log_u32(float(x)) for x in u])
+    want = -np.log(u.astype(np.float64))
+    assert np.max(np.abs(got - want) / want) < 3e-7
+
+
+def test_clock_gaps_follow_the_geometric_law():
+    """The gap G = floor(-ln u / lam) of the clock has P(G = g) = e^{-g lam}
+    (1 - e^{-lam}) (the number of non-candidate steps of the null-collision
+    method, paper §4); gaps above 131071 steps are cut, with probability
+    e^{-131072 lam}, into a continuation."""
+    u = _uniforms(200_000, 2)
+    lam = 0.05
+    st = np.array([oracle.clock_state(float(x), lam) for x in u])
+    assert np.all(st % 2 == 0)
+    g = st // 2
+    k = np.arange(80)
+    p = np.exp(-k * lam) * (1 - np.exp(-lam))
+    obs = np.bincount(np.minimum(g, 80), minlength=81)
+    exp_ = np.append(p, np.exp(-80 * lam)) * u.size
+    chi2 = float(np.sum((obs - exp_) ** 2 / exp_))
+    assert stats.chi2.sf(chi2, 80) > 1e-4, chi2
+    lam = 8e-6
+    st = np.array([oracle.clock_state(float(x), lam) for x in u[:50_000]])
+    cont = st % 2 == 1
+    pc = math.exp(-131072 * lam)
+    assert abs(cont.mean() - pc) < 5 * math.sqrt(pc * (1 - pc) / cont.size)
+    assert np.all(st[cont] == 2 * oracle.CLOCK_MAX + 1) and np.all(st[~cont] // 2 <= oracle.CLOCK_MAX)
