@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--sort-interval", type=int, default=0, help="0 = the library's autotuner")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="leave the 256-case batched sweep out of the line")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="steps of the per-launch timed region (0: enough for every species to sort once)")
     ap.add_argument("--workload", default="exb", choices=["exb", "batch", "warmstart"],
                     help="exb: the 10.24M-particle E x B case (default); batch: the 256-case argon sweep; "
                          "warmstart: RF cycles to steady state, cold start vs the learned warm start")
@@ -198,13 +201,17 @@ def run_reference(args, rank):
 
 
 # --------------------------------------------------------------------------- batched sweep
-def run_batch(args, torch):
-    """256 uneven argon cases: one batched launch per kernel per step against
-    the same cases stepped one case at a time (each case's kernels launched
-    on their own, then each case replaying its own CUDA graph)."""
+def batch_leg(torch, n_cases=256, small=False, peak=6481.1):
+    """256 uneven argon cases (5e4-1e6 particles per species each): the batch
+    (one persistent particle launch and one field launch per step for all
+    cases, its launch shape and sort interval K chosen by its autotuner)
+    against the same cases stepped one at a time (one launch of each case's
+    step graph per step, the cases one after the other) and each case
+    replaying its own K-step graphs.  Each arm is timed over K steps, so that
+    every arm includes exactly one sort of every case."""
     from paper_2609_17151_b300 import pic
     from paper_2609_17151_b300 import workloads as W
-    cfgs, counts = W.sweep_cases(args.cases, n_range=(5e3, 5e4) if args.small else (5e4, 1e6))
+    cfgs, counts = W.sweep_cases(n_cases, n_range=(5e3, 5e4) if small else (5e4, 1e6))
     stream = torch.cuda.Stream()
 
     def load(view, cfg):
@@ -213,73 +220,86 @@ def run_batch(args, torch):
         view.load_profile(0, L["n"], np.full(nn, L["n0"]), np.full(nn, L["te_ev"]))
         view.load_profile(1, L["n"], np.full(nn, L["n0"]), np.full(nn, L["ti_ev"]))
 
-    # room for the growth of the densest (ionizing) cases over warm-up plus
-    # the two per-case timings (2 x steps); small cases grow relatively more
-    grow = 16 if args.small else 4
-    caps = [(grow * n, grow * n) for n in counts]
-    b = pic.Batch(cfgs, stream=stream.cuda_stream, sort_interval=64, capacities=caps)
-    for v, cfg in zip(b.cases, cfgs):
-        load(v, cfg)
-    b.step(max(3, args.warmup))
-    b.sync()
+    def timed(fn):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1)
 
     def count_all(views):
         return sum(sum(v.count()) for v in views)
 
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    grow = 16 if small else 4
+    caps = [(grow * n, grow * n) for n in counts]
+    t0 = time.perf_counter()
+    b = pic.Batch(cfgs, stream=stream.cuda_stream, sort_interval=0, capacities=caps)
+    for v, cfg in zip(b.cases, cfgs):
+        load(v, cfg)
+    b.step(1 + 38 + 8)                      # first step, the autotuner's 38, then graphs built
+    b.sync()
+    tun = b.tuning()
+    K = tun["sort_interval"]
     n0 = count_all(b.cases)
     l0 = b.launches()
-    ev0.record(stream)
-    b.step(args.steps)
-    ev1.record(stream)
-    ev1.synchronize()
-    ms_b = ev0.elapsed_time(ev1)
+    ms_b = timed(lambda: b.step(K))
     launches_b = b.launches() - l0
     n1 = count_all(b.cases)
-    pps_b = 0.5 * (n0 + n1) * args.steps / (ms_b * 1e-3)
     b.close()
-
-    # the same cases, one case at a time on the same stream
+    torch.cuda.synchronize()
     cases = []
     for cfg, cap in zip(cfgs, caps):
-        c = pic.Case(cfg, stream=stream.cuda_stream, sort_interval=64, capacity=cap)
+        c = pic.Case(cfg, stream=stream.cuda_stream, sort_interval=K, capacity=cap)
         load(c, cfg)
         cases.append(c)
     for c in cases:
-        c.step(max(3, args.warmup))
+        c.step(1 + 38 + 8)
     torch.cuda.synchronize()
     m0 = count_all(cases)
-    ev0.record(stream)
-    for _ in range(args.steps):
+
+    def one_by_one():
+        for _ in range(K):
+            for c in cases:
+                c.step(1)
+
+    ms_1 = timed(one_by_one)
+
+    def per_case_graphs():
         for c in cases:
-            c.step(1)                       # every kernel of every case launched on its own
-    ev1.record(stream)
-    ev1.synchronize()
-    ms_1 = ev0.elapsed_time(ev1)
-    ev0.record(stream)
-    for c in cases:
-        c.step(args.steps)                  # each case replays its own graph
-    ev1.record(stream)
-    ev1.synchronize()
-    ms_g = ev0.elapsed_time(ev1)
+            c.step(K)
+
+    ms_g = timed(per_case_graphs)
     m1 = count_all(cases)
     for c in cases:
         c.close()
-    pps_1 = 0.5 * (m0 + m1) * args.steps / (ms_1 * 1e-3)
-    pps_g = 0.5 * (m0 + m1) * args.steps / (ms_g * 1e-3)
+    pb = 0.5 * (n0 + n1)
+    pm = 0.5 * (m0 + m1)
+    return {
+        "workload": f"argon_ccp_sweep_{n_cases}_cases" + ("_small" if small else ""),
+        "particles": int(n0), "steps_timed": K, "sort_interval": K, "launch_shape": tun["shape"],
+        "tuner": {"shape_ms": [round(x, 4) for x in tun["shape_ms"]], "sort_ms": round(tun["sort_ms"], 4)},
+        "batched": {"value": pb * K / (ms_b * 1e-3), "ms_per_step": ms_b / K, "gpu_launches": int(launches_b),
+                    "hbm_frac": 40 * pb * K / (ms_b * 1e-3) / 1e9 / peak},
+        "one_launch_per_case": {"value": pm * K / (ms_1 * 1e-3), "ms_per_step": ms_1 / K},
+        "per_case_graphs": {"value": pm * K / (ms_g * 1e-3), "ms_per_step": ms_g / K},
+        "batched_vs_one_launch_per_case": (pb / ms_b) / (pm / ms_1),
+        "batched_vs_per_case_graphs": (pb / ms_b) / (pm / ms_g),
+        "seconds": round(time.perf_counter() - t0, 1),
+        "note": "each arm over one sort period (K steps); one launch per case = a 1-step graph launch of each case "
+                "in turn every step",
+    }
+
+
+def run_batch(args, torch):
+    leg = batch_leg(torch, args.cases, args.small)
     print(json.dumps({
-        "metric": METRIC, "value": pps_b, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"argon_ccp_sweep_{args.cases}_cases" + ("_small" if args.small else ""),
-                   "particles": int(n0),
-                   "cells_range": [min(c["n_cells"] for c in cfgs), max(c["n_cells"] for c in cfgs)],
-                   "sort_interval": 64, "parallelism": "batched cases, 1 GPU"},
-        "batched_vs_one_launch_per_case": pps_b / pps_1,
-        "batched_vs_per_case_graphs": pps_b / pps_g,
-        "one_launch_per_case": {"value": pps_1, "ms_per_step": ms_1 / args.steps},
-        "per_case_graphs": {"value": pps_g, "ms_per_step": ms_g / args.steps},
-        "gpu_launches": launches_b,
+        "metric": METRIC, "value": leg["batched"]["value"], "unit": UNIT, "n_gpus": 1, "steps": leg["steps_timed"],
+        "warmup": 47, "ms_per_step": leg["batched"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": leg["workload"], "particles": leg["particles"], "parallelism": "batched cases, 1 GPU"},
+        "batch": leg, "gpu_launches": leg["batched"]["gpu_launches"],
     }), flush=True)
 
 
@@ -509,7 +529,7 @@ def main():
     # timed region 2 (roofline and sort cost): events around every launch, over
     # enough steps that every species sorts at least once
     tuning = case.tuning()
-    prof_steps = max(args.steps, min(max(tuning["sort_interval"][:len(parts)]) + 1, 1100))
+    prof_steps = args.profile_steps or max(args.steps, min(max(tuning["sort_interval"][:len(parts)]) + 1, 1100))
     case.profile(True)
     barrier()
     case.step(prof_steps)
@@ -566,6 +586,10 @@ def main():
                "note": f"load from pinned host + {args.steps} steps + moments to host, per job of {args.steps} "
                        "steps, on the warmed case"}
 
+    case.close()
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        batch = batch_leg(torch, peak=peak)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -608,9 +632,9 @@ def main():
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "batch": batch,
         }
         print(json.dumps(out), flush=True)
-    case.close()
     if dist is not None:
         dist.destroy_process_group()
 

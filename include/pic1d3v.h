@@ -222,6 +222,17 @@ pic_status pic_read_particles(pic_case *c, int species, int64_t max_n, int64_t *
                               int32_t *cell, float *offset, float *vx, float *vy, float *vz,
                               uint32_t *id);
 
+/* Collision clock of the live particles of a species, in the order
+ * pic_read_particles gives them (paper §4's free flights, §1's null-collision
+ * method): clock = 2 k + c, k the steps left before the particle's next
+ * collision candidate; c = 1 when that step only ends a gap longer than
+ * 131071 steps and draws a fresh one.  Each gap is
+ * floor(-ln(u) / (numax dt)), evaluated in FP32, u uniform from word 0 of
+ * the particle's block-0 draw of the step that drew it (block 6 at load or
+ * creation).  0 for a species without collisions.  *n_out = live count;
+ * PIC_ECAPACITY if max_n is smaller. */
+pic_status pic_read_clock(pic_case *c, int species, int64_t max_n, int64_t *n_out, uint32_t *clock);
+
 /* Axial excursion z (m) of the live particles of a species, in the order
  * pic_read_particles gives them (desc.axial_length_m > 0; PIC_ESTATE
  * otherwise).  *n_out = live count; PIC_ECAPACITY if max_n is smaller. */
@@ -390,8 +401,13 @@ pic_status pic_sort_by_cell(int32_t n_cells, int64_t n, const int32_t *cell, con
  * persistent particle launch (work items: slices of ~131072 particles of any
  * case and species, taken from an atomic counter) and one field launch (one
  * 8-CTA cluster per case) per step, replayed from a CUDA graph between sorts;
- * every sort_interval (descs[0].sort_interval, 0 = 64) steps each case is
- * sorted.  All cases must share the boundary kind, the number of species and
+ * every sort_interval steps every case is sorted, one launch per sort kernel
+ * and species for all cases.  descs[0].sort_interval > 0 fixes the interval;
+ * 0 lets the batch's autotuner choose it and the persistent kernel's launch
+ * shape, during the first pic_batch_step of at least 38 steps after the
+ * first step (6 steps, two per shape, then one sort and 32 timed steps, all
+ * part of the run: results do not depend on the choices; see
+ * pic_batch_tuning).  All cases must share the boundary kind, the number of species and
  * the collision model of each species (none, tables, or constant frequency
  * for electrons).  Results equal stepping each case alone.
  * Errors: PIC_EINVAL (mixed cases), PIC_ESTATE (a case without particles).
@@ -413,8 +429,20 @@ pic_status pic_batch_set_stages(pic_batch *b, int stages);
  * the batch plans its step) run the single-case step kernels inside the
  * batch's graph instead of the shared persistent kernel; every case's field
  * solve stays in the one batched launch.  0 = every case in the persistent
- * kernel.  Default 2^19.  Results do not depend on it.  Errors: PIC_EINVAL. */
+ * kernel (the default).  Results do not depend on it.  Errors: PIC_EINVAL. */
 pic_status pic_batch_set_own_threshold(pic_batch *b, int64_t particles);
+/* The batch's launch choices: *shape (0: 512-thread CTAs, one per SM, chunks
+ * of one particle with three in flight; 1: two 512-thread CTAs per SM, chunks
+ * of two, one ahead; 2: 1024-thread CTAs, chunks of two, one ahead),
+ * *sort_interval, *tuned (1 once the autotuner ran), and its measurements:
+ * shape_ms[3] (mean step time per shape) and *sort_ms (one batched sort).
+ * Any output pointer may be NULL. */
+pic_status pic_batch_tuning(pic_batch *b, int *shape, int *sort_interval, int *tuned, float *shape_ms,
+                            float *sort_ms);
+/* Fix the launch shape of the batch kernel (0, 1 or 2, as pic_batch_tuning
+ * describes them); the autotuner then does not run (with sort_interval 0 the
+ * interval stays 64).  Results do not depend on it.  Errors: PIC_EINVAL. */
+pic_status pic_batch_set_shape(pic_batch *b, int shape);
 pic_status pic_batch_destroy(pic_batch *b);
 
 /* ---------------------------------------------------------------------------

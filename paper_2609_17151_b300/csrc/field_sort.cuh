@@ -356,8 +356,10 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
         if (P.no_field) { E = 0.0; ph = 0.0; fe = 0.0f; }    // swarm: only the imposed field acts
         P.E[i] = E;
         P.phi[i] = ph;
-        P.E32[i] = (float)E;
-        if (P.periodic && i == 0) P.E32[N] = (float)E;
+        const float e32 = (float)E;                               // both cells that touch node i
+        if (i < N) P.E32p[i].x = e32;
+        if (i > 0) P.E32p[i - 1].y = e32;
+        else if (P.periodic) P.E32p[N - 1].y = e32;
         if (mode == 1) P.phi_sum[i] += ph;
         bad = !finite_bits(ph) || !finite_bits(E);
     }
@@ -456,8 +458,15 @@ __device__ __forceinline__ unsigned warp_agg_inc(unsigned *cnt, int c, bool acti
 // that every lane reaches the warp-wide calls, and issue kSortUnroll rounds
 // of loads before they use them.
 constexpr int kSortUnroll = 4;
-__global__ void k_cells_count(SortHalves H, const int32_t *cur_dev, const unsigned long long *n_dev, long long n_host,
-                              int N, unsigned *counts)
+// Sort key of a cell word: a case's particles (CLOCK) carry their collision
+// clock above the cell bits; the stand-alone entry point takes plain cells.
+template <bool CLOCK> __device__ __forceinline__ int sort_key(int w) { return (CLOCK && w >= 0) ? (w & kCellMask) : w; }
+
+// Block `blk` of `nblk` counting one species' particles (a case's, or the
+// stand-alone entry point's) into counts[cell].
+template <bool CLOCK>
+__device__ __forceinline__ void cells_count(SortHalves H, const int32_t *cur_dev, const unsigned long long *n_dev,
+                                            long long n_host, int N, unsigned *counts, int blk, int nblk)
 {
     extern __shared__ unsigned cnt_s[];
     for (int j = threadIdx.x; j < N; j += blockDim.x) cnt_s[j] = 0u;
@@ -465,13 +474,13 @@ __global__ void k_cells_count(SortHalves H, const int32_t *cur_dev, const unsign
     const SpeciesBufs A = H.h[cur_dev ? *cur_dev : 0];
     const long long n = sort_count_of(n_dev, n_host);
     const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long w = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); w < n; w += kSortUnroll * stride) {
+    const long long stride = (long long)nblk * blockDim.x;
+    for (long long w = blk * (long long)blockDim.x + (threadIdx.x & ~31); w < n; w += kSortUnroll * stride) {
         int cs[kSortUnroll];                            // loads first, then the counts
 #pragma unroll
         for (int u = 0; u < kSortUnroll; ++u) {
             const long long i = w + u * stride + lane;
-            cs[u] = i < n ? A.cell[i] : -1;
+            cs[u] = i < n ? sort_key<CLOCK>(A.cell[i]) : -1;
         }
 #pragma unroll
         for (int u = 0; u < kSortUnroll; ++u) warp_agg_inc(cnt_s, cs[u], cs[u] >= 0 && cs[u] < N);
@@ -481,8 +490,15 @@ __global__ void k_cells_count(SortHalves H, const int32_t *cur_dev, const unsign
         if (cnt_s[j]) atomicAdd(&counts[j], cnt_s[j]);
 }
 
+template <bool CLOCK>
+__global__ void k_cells_count(SortHalves H, const int32_t *cur_dev, const unsigned long long *n_dev, long long n_host,
+                              int N, unsigned *counts)
+{
+    cells_count<CLOCK>(H, cur_dev, n_dev, n_host, N, counts, blockIdx.x, gridDim.x);
+}
+
 // cursor[j] = sum_{k<j} counts[k]; cursor[N] = total (one CTA, exact: counts < 2^53)
-__global__ void __launch_bounds__(1024) k_cells_scan(const unsigned *counts, int N, unsigned long long *cursor)
+__device__ __forceinline__ void cells_scan(const unsigned *counts, int N, unsigned long long *cursor)
 {
     extern __shared__ __align__(16) double ssm[];
     __shared__ double red[32];
@@ -493,6 +509,11 @@ __global__ void __launch_bounds__(1024) k_cells_scan(const unsigned *counts, int
     if (threadIdx.x == 0) cursor[N] = (unsigned long long)ssm[N - 1];
 }
 
+__global__ void __launch_bounds__(1024) k_cells_scan(const unsigned *counts, int N, unsigned long long *cursor)
+{
+    cells_scan(counts, N, cursor);
+}
+
 // Each CTA takes one contiguous chunk of the particles (chunk = n / grid,
 // rounded up to whole warps, so that every CTA of the grid works; the grid is
 // one wave of two 512-thread CTAs per SM).  It
@@ -500,8 +521,9 @@ __global__ void __launch_bounds__(1024) k_cells_scan(const unsigned *counts, int
 // global atomic per touched cell), then places them with shared atomics,
 // kScatterUnroll particles per lane at a time with their loads issued first.
 constexpr int kScatterUnroll = 1;
-__global__ void __launch_bounds__(512, 2) k_cells_scatter(SortHalves H, const int32_t *cur_dev, const unsigned long long *n_dev, long long n_host,
-                                int N, unsigned long long *cursor)
+template <bool CLOCK>
+__device__ __forceinline__ void cells_scatter(SortHalves H, const int32_t *cur_dev, const unsigned long long *n_dev,
+                                              long long n_host, int N, unsigned long long *cursor, int blk, int nblk)
 {
     extern __shared__ __align__(16) unsigned char xsm[];
     unsigned long long *base = reinterpret_cast<unsigned long long *>(xsm);
@@ -511,9 +533,9 @@ __global__ void __launch_bounds__(512, 2) k_cells_scatter(SortHalves H, const in
     const int half = cur_dev ? *cur_dev : 0;
     const SpeciesBufs A = H.h[half], D = H.h[half ^ 1];
     const long long n = sort_count_of(n_dev, n_host);
-    long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    long long chunk = (n + nblk - 1) / nblk;
     chunk = (chunk + 31) & ~31ll;
-    const long long lo = min((long long)blockIdx.x * chunk, n), hi = min(lo + chunk, n);
+    const long long lo = min((long long)blk * chunk, n), hi = min(lo + chunk, n);
     const int lane = threadIdx.x & 31;
     const long long T = blockDim.x;
     for (long long w = lo + (threadIdx.x & ~31); w < hi; w += kSortUnroll * T) {
@@ -521,7 +543,7 @@ __global__ void __launch_bounds__(512, 2) k_cells_scatter(SortHalves H, const in
 #pragma unroll
         for (int u = 0; u < kSortUnroll; ++u) {
             const long long i = w + u * T + lane;
-            cs[u] = i < hi ? A.cell[i] : -1;
+            cs[u] = i < hi ? sort_key<CLOCK>(A.cell[i]) : -1;
         }
 #pragma unroll
         for (int u = 0; u < kSortUnroll; ++u) warp_agg_inc(lcnt, cs[u], cs[u] >= 0 && cs[u] < N);
@@ -549,21 +571,31 @@ __global__ void __launch_bounds__(512, 2) k_cells_scatter(SortHalves H, const in
         }
 #pragma unroll
         for (int u = 0; u < kScatterUnroll; ++u) {
-            const bool live = c[u] >= 0 && c[u] < N;
-            const unsigned r = warp_agg_inc(lcnt, c[u], live);
+            const int key = sort_key<CLOCK>(c[u]);
+            const bool live = key >= 0 && key < N;
+            const unsigned r = warp_agg_inc(lcnt, key, live);
             if (!live) continue;
-            const unsigned long long p = base[c[u]] + r;
+            const unsigned long long p = base[key] + r;
             D.cell[p] = c[u]; D.off[p] = o[u]; D.vx[p] = vx[u]; D.vy[p] = vy[u]; D.vz[p] = vz[u]; D.id[p] = id[u];
             if (has_z) D.z[p] = z[u];
         }
     }
 }
 
+template <bool CLOCK>
+__global__ void __launch_bounds__(512, 2) k_cells_scatter(SortHalves H, const int32_t *cur_dev,
+                                                          const unsigned long long *n_dev, long long n_host, int N,
+                                                          unsigned long long *cursor)
+{
+    cells_scatter<CLOCK>(H, cur_dev, n_dev, n_host, N, cursor, blockIdx.x, gridDim.x);
+}
+
 // case epilogue: the sorted half becomes current; counts reset for next time
-__global__ void k_sort_finish(const __grid_constant__ StepConst P, int sp, const unsigned long long *total)
+__device__ __forceinline__ void sort_finish(const StepConst &P, int sp, const unsigned long long *total, int blk,
+                                            int nblk)
 {
     const int N = P.n_cells;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blk == 0 && threadIdx.x == 0) {
         Ctrl *ctrl = P.ctrl;
         const unsigned long long live = *total;
         ctrl->cur[sp] ^= 1;
@@ -571,7 +603,56 @@ __global__ void k_sort_finish(const __grid_constant__ StepConst P, int sp, const
         ctrl->n_active[sp] = live;
         ctrl->n_dead[sp] = 0ull;
     }
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) P.sort_count[j] = 0u;
+    for (int j = blk * blockDim.x + threadIdx.x; j < N; j += nblk * blockDim.x) P.sort_count[j] = 0u;
+}
+
+__global__ void k_sort_finish(const __grid_constant__ StepConst P, int sp, const unsigned long long *total)
+{
+    sort_finish(P, sp, total, blockIdx.x, gridDim.x);
+}
+
+// The same sort for species sp of every case of a batch in one launch per
+// kernel.  The count and scatter kernels take (case, block, blocks) items in
+// case order, about one block per kSortItemParticles particles of the case,
+// so that the few cases in flight at a time keep their scattered writes in L2
+// until whole sectors are written; the scan and the epilogue take one block
+// (scan) or a few (epilogue) per case.
+struct SortItem {
+    int case_idx, blk, nblk;
+};
+constexpr long long kSortItemParticles = 16384;
+__device__ __forceinline__ SortHalves case_halves(const StepConst &P, int sp)
+{
+    return SortHalves{{P.buf[sp][0], P.buf[sp][1]}};
+}
+__global__ void k_batch_cells_count(const StepConst *__restrict__ cases, const SortItem *__restrict__ items, int sp)
+{
+    const SortItem it = items[blockIdx.x];
+    const StepConst &P = cases[it.case_idx];
+    if (sp >= P.n_species) return;
+    cells_count<true>(case_halves(P, sp), &P.ctrl->cur[sp], &P.ctrl->n_active[sp], 0, P.n_cells, P.sort_count,
+                      it.blk, it.nblk);
+}
+__global__ void __launch_bounds__(1024) k_batch_cells_scan(const StepConst *__restrict__ cases, int sp)
+{
+    const StepConst &P = cases[blockIdx.x];
+    if (sp >= P.n_species) return;
+    cells_scan(P.sort_count, P.n_cells, P.sort_cursor);
+}
+__global__ void __launch_bounds__(512, 2) k_batch_cells_scatter(const StepConst *__restrict__ cases,
+                                                                const SortItem *__restrict__ items, int sp)
+{
+    const SortItem it = items[blockIdx.x];
+    const StepConst &P = cases[it.case_idx];
+    if (sp >= P.n_species) return;
+    cells_scatter<true>(case_halves(P, sp), &P.ctrl->cur[sp], &P.ctrl->n_active[sp], 0, P.n_cells, P.sort_cursor,
+                        it.blk, it.nblk);
+}
+__global__ void k_batch_sort_finish(const StepConst *__restrict__ cases, int sp)
+{
+    const StepConst &P = cases[blockIdx.y];
+    if (sp >= P.n_species) return;
+    sort_finish(P, sp, P.sort_cursor + P.n_cells, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------

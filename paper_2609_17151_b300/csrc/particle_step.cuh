@@ -14,6 +14,7 @@
 // are compacted by the next counting sort.
 #pragma once
 #include "pic_device.cuh"
+#include <cooperative_groups.h>
 
 namespace pic {
 
@@ -99,19 +100,35 @@ __device__ __forceinline__ void count_proc(EvCount &ev, int proc)
 
 struct Cell { int c; float o; };
 
-// Append one particle to species `sp` (slot from the global counter), deposit
-// it into rho^{n+1} directly and add it to the diagnostic-step moments.
+// First collision clock of a particle of species sp created (or loaded) in
+// `step`: a gap from word 0 of its own block-kBlkGap draw (0 without MCC).
+__device__ __forceinline__ uint32_t first_clock(const StepConst &P, int sp, uint32_t id, uint32_t step)
+{
+    const float lam = P.sp[sp].lam;
+    if (!(lam > 0.0f)) return 0u;
+    return clock_state(u01(draw(P, id, step, sp, kBlkGap).x), lam);
+}
+
+// Append one particle to species `sp`, with its first collision clock; deposit
+// it into rho^{n+1} directly and add it to the diagnostic-step moments.  The
+// lanes of a warp that append together reserve their slots with one atomic
+// on the species' counter (the group of lanes active here), then take
+// consecutive slots in lane order.
 __device__ void append_particle(const StepConst &P, int sp, int half, int c, float o, float vx, float vy,
-                                float vz, uint32_t id, bool diag)
+                                float vz, uint32_t id, uint32_t step, bool diag)
 {
     Ctrl *ctrl = P.ctrl;
-    const unsigned long long slot = atomicAdd(&ctrl->n_total[sp], 1ull);
+    const cooperative_groups::coalesced_group g = cooperative_groups::coalesced_threads();
+    unsigned long long base = 0ull;
+    if (g.thread_rank() == 0) base = atomicAdd(&ctrl->n_total[sp], (unsigned long long)g.size());
+    const unsigned long long slot = g.shfl(base, 0) + g.thread_rank();
     if (slot >= P.cap[sp]) {
         atomicOr(&ctrl->err, kErrCapacity);
         return;
     }
     const SpeciesBufs &B = P.buf[sp][half];
-    B.cell[slot] = c; B.off[slot] = o; B.vx[slot] = vx; B.vy[slot] = vy; B.vz[slot] = vz; B.id[slot] = id;
+    B.cell[slot] = c | (int)(first_clock(P, sp, id, step) << kCellBits);
+    B.off[slot] = o; B.vx[slot] = vx; B.vy[slot] = vy; B.vz[slot] = vz; B.id[slot] = id;
     if (B.z) B.z[slot] = 0.0f;
     const uint32_t f = __float2uint_rz(o * 4294967296.0f);
     unsigned long long *R = P.R[sp] + (size_t)(blockIdx.x % kDepositCopies) * P.r_stride;
@@ -136,15 +153,14 @@ __device__ void append_particle(const StepConst &P, int sp, int half, int c, flo
     }
 }
 
-// Electron collision (null-collision method).  Returns the process index
-// (-1: no real collision) and updates v.
+// Electron collision candidate (null-collision method): the process from
+// word 1 of the step's block-0 draw r, the direction from words 2-3; v is
+// updated for a real collision.
 __device__ __forceinline__ void collide_electron(const StepConst &P, const float *nus, uint32_t id, uint32_t step,
                                                  int c, float o, float3 &v, int half_e, int half_i, bool diag,
-                                                 EvCount &ev)
+                                                 EvCount &ev, const uint4 r)
 {
     const SpConst &S = P.sp[0];
-    const uint4 r = draw(P, id, step, 0, kBlkMcc);
-    if (u01(r.x) >= S.pnull) return;
     ev.cand++;
     const float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
     const float eps = S.m_over_2e * v2;
@@ -183,24 +199,24 @@ __device__ __forceinline__ void collide_electron(const StepConst &P, const float
         v = make_float3(sp * n.x, sp * n.y, sp * n.z);
         const float3 ne = iso_dir(u01(a.y), u01(a.z));
         const float spe = S.v_of_sqrt_eps * sqrtf(eej);
-        append_particle(P, 0, half_e, c, o, spe * ne.x, spe * ne.y, spe * ne.z, ids.x, diag);
+        append_particle(P, 0, half_e, c, o, spe * ne.x, spe * ne.y, spe * ne.z, ids.x, step, diag);
         if (P.n_species > 1) {
             const uint4 b = draw(P, id, step, 0, kBlkNewIon);
             const float2 g01 = box_muller(u01(b.x), u01(b.y));
             const float2 g23 = box_muller(u01(b.z), u01(b.w));
             const float vt = S.vt_newion;
-            append_particle(P, 1, half_i, c, o, vt * g01.x, vt * g01.y, vt * g23.x, ids.y, diag);
+            append_particle(P, 1, half_i, c, o, vt * g01.x, vt * g01.y, vt * g23.x, ids.y, step, diag);
         }
         ev.iz++;
     }
 }
 
+// Ion collision candidate: gas partner from block 1, process from word 1 of
+// the block-0 draw r, centre-of-mass direction from its words 2-3.
 __device__ __forceinline__ void collide_ion(const StepConst &P, const float *nus, uint32_t id, uint32_t step,
-                                            float3 &v, EvCount &ev)
+                                            float3 &v, EvCount &ev, const uint4 r)
 {
     const SpConst &S = P.sp[1];
-    const uint4 r = draw(P, id, step, 1, kBlkMcc);
-    if (u01(r.x) >= S.pnull) return;
     ev.cand++;
     const uint4 a = draw(P, id, step, 1, kBlkAux);
     const float2 g01 = box_muller(u01(a.x), u01(a.y));
@@ -255,16 +271,18 @@ __device__ __forceinline__ void emit_secondary(const StepConst &P, uint32_t id, 
     if (o >= 1.0f) { o = 0.0f; c += 1; }
     if (c >= N) { c = N - 1; o = 0.99999994f; }
     const float vx = wall == 0 ? vn : -vn;
-    append_particle(P, 0, half_e, c, o, vx, P.see_vth * t.x, P.see_vth * t.y, ids.x, diag);
+    append_particle(P, 0, half_e, c, o, vx, P.see_vth * t.x, P.see_vth * t.y, ids.x, step, diag);
     ev.see++;
     if (wall == 0) ev.see0++;
 }
 
 // Shared deposit histogram, per cell: particle count n and the sum of the
-// fixed-point offsets F = sum f split as (F >> 16, F & 0xFFFF) so that every
-// counter is a native 32-bit shared atomic.  At the flush, node c gets
-// n 2^32 - F and node c+1 gets F (exact).  A counter pair holds at least
-// 65536 particles per cell between flushes.
+// fixed-point offsets F = sum f split as (F >> 16, F & 0xFFFF), so that every
+// counter is a native 32-bit shared atomic (a 64-bit shared add measured
+// several times slower where the lanes of a warp share a cell, as sorted
+// particles do).  At the flush, node c gets n 2^32 - F and node c+1 gets F
+// (exact).  A counter pair holds at least 65536 particles per cell between
+// flushes, and a CTA deposits at most kFlushParticles particles between them.
 struct DepHist {
     unsigned *cnt, *fhi, *flo;
 };
@@ -303,7 +321,7 @@ struct StepSmem {
     __host__ __device__ StepSmem(int n_cells, int nproc, int threads = 0, int stages = 0, int narr = 0)
     {
         e_off = 0;
-        h_off = align16(e_off + (unsigned)(n_cells + 1) * 4u);
+        h_off = align16(e_off + (unsigned)n_cells * 8u);
         nu_off = align16(h_off + (unsigned)n_cells * 12u);
         en_off = align16(nu_off + (unsigned)nproc * kNGrid * 4u);
         eepf_off = align16(en_off + (unsigned)(n_cells + 1) * 4u);
@@ -313,12 +331,14 @@ struct StepSmem {
     }
 };
 
-// Particle arrays a species' step reads: cell, off, vx, vy, vz, and id when
-// it draws random numbers (MCC, or secondary emission by ions).
-__host__ __device__ constexpr int step_arrays(int sp, bool periodic, int mcc)
-{
-    return (mcc != 0 || (sp == 1 && !periodic)) ? 6 : 5;
-}
+// Particle arrays a step streams: cell (with the collision clock), off, vx,
+// vy, vz, and the id for electrons colliding through tables, a fifth to a
+// half of which are collision candidates every step in a discharge (the id
+// keys their draws; a load per candidate would sit in the dependent path).
+// Every other species reads the id only for the particles that draw random
+// numbers in the step (a candidate, the end of a long gap, secondary
+// emission, axial renewal), one load each.
+__host__ __device__ constexpr int step_arrays(int sp, bool, int mcc) { return (sp == 0 && mcc == 1) ? 6 : 5; }
 
 // Direct-load path: particles per chunk, and how many chunks ahead of the one
 // being computed each thread keeps its loads in flight (register double
@@ -408,7 +428,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     constexpr int kArr = step_arrays(SP, PERIODIC, MCC);
     const int n_stages = STAGED ? S.stages : 0;
     const StepSmem L(N, MCC == 1 ? S.nproc : 0, blockDim.x, n_stages, kArr);
-    float *Es = reinterpret_cast<float *>(smem + L.e_off);
+    const float2 *Es = reinterpret_cast<const float2 *>(smem + L.e_off);
     const DepHist hist{reinterpret_cast<unsigned *>(smem + L.h_off), reinterpret_cast<unsigned *>(smem + L.h_off) + N,
                        reinterpret_cast<unsigned *>(smem + L.h_off) + 2 * N};
     float *nus = reinterpret_cast<float *>(smem + L.nu_off);
@@ -421,7 +441,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     const long long n = (long long)ctrl->n_active[SP];
     constexpr int CH = STAGED ? 4 : DCHUNK;              // particles per chunk
     constexpr bool PIPE = !STAGED && DDEPTH > 0;
-    constexpr bool LOAD_ID = kArr == 6 || AXIAL;
+    constexpr bool LOAD_ID = kArr == 6;                 // else ids are read per particle, when it draws
     const long long n_chunks = (n + CH - 1) / CH;
     long long per = (n_chunks + n_items - 1) / n_items;
     per = (per + 31) & ~31ll;
@@ -429,12 +449,12 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     const long long end = min(beg + per, n_chunks);
     if (beg >= end) return;                             // uniform over the CTA
 
-    const unsigned e_bytes = align16((unsigned)(N + 1) * 4u);
+    const unsigned e_bytes = align16((unsigned)N * 8u);
     const unsigned nu_bytes = MCC == 1 ? (unsigned)S.nproc * kNGrid * 4u : 0u;
     if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // earlier reads before the async writes
         mbar_expect_tx(&sh.mbar, e_bytes + nu_bytes);
-        bulk_g2s(Es, P.E32, e_bytes, &sh.mbar);
+        bulk_g2s(smem + L.e_off, P.E32p, e_bytes, &sh.mbar);
         if (MCC == 1) bulk_g2s(nus, P.nu_tab[SP], nu_bytes, &sh.mbar);
     }
     const long long step_ll = ctrl->step;
@@ -531,7 +551,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
                 vload<float4>(t.vx, reinterpret_cast<const float *>(tl + 2 * stride));
                 vload<float4>(t.vy, reinterpret_cast<const float *>(tl + 3 * stride));
                 vload<float4>(t.vz, reinterpret_cast<const float *>(tl + 4 * stride));
-                if (kArr == 6) vload<uint4>(t.id, reinterpret_cast<const uint32_t *>(tl + 5 * stride));
+                if (LOAD_ID) vload<uint4>(t.id, reinterpret_cast<const uint32_t *>(tl + 5 * stride));
             } else {
                 load_chunk<CH, LOAD_ID, AXIAL>(t, Bi, e0);
             }
@@ -557,7 +577,6 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         float (&vx)[CH] = t.vx;
         float (&vy)[CH] = t.vy;
         float (&vz)[CH] = t.vz;
-        const uint32_t (&ids)[CH] = t.id;
         float (&za)[CH] = t.z;
         int dc[CH];
         uint32_t df[CH];
@@ -568,12 +587,17 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             df[q] = 0;
             int c = cc[q];
             if (q >= n_valid || c < 0) continue;
+            uint32_t clk = (uint32_t)c >> kCellBits;     // collision clock 2 k + c
+            c &= kCellMask;
+            // the particle's id, read when it draws (prefetched with the chunk for LOAD_ID)
+            auto pid_of = [&]() -> uint32_t { return LOAD_ID ? t.id[q] : Bi.id[e0 + q]; };
             float o = oo[q];
             // 1. gather E^n (linear weights), plus the imposed field.  The
             // library is built without implicit multiply-add contraction and
             // every FMA of the push is written out, so that each kernel
             // variant (direct, staged, batched) rounds identically.
-            const float e_mesh = fmaf(o, Es[c + 1], (1.0f - o) * Es[c]);
+            const float2 ep = Es[c];                        // (E_c, E_{c+1})
+            const float e_mesh = fmaf(o, ep.y, (1.0f - o) * ep.x);
             const float ex = e_mesh + P.Ex_ext;
             // 2. Boris: half kick, rotation, half kick
             const float hx = S.c_e * ex;
@@ -609,7 +633,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
                     const int bin = (int)(S.m_over_2e * (v.x * v.x + v.y * v.y + v.z * v.z) * P.ifedf_scale);
                     if (bin >= 0 && bin < kIfedfBins) atomicAdd(&P.ifedf[wall * kIfedfBins + bin], 1ull);
                 }
-                if (SP == 1 && P.see_gamma > 0.0f) emit_secondary(P, ids[q], step, wall, half_e, diag, ev);
+                if (SP == 1 && P.see_gamma > 0.0f) emit_secondary(P, pid_of(), step, wall, half_e, diag, ev);
                 cc[q] = -1;
                 oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
                 continue;
@@ -619,7 +643,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             if (AXIAL) {
                 float zn = fmaf(v.z, P.dt_f, za[q]);
                 if (fabsf(zn) >= P.axial_len) {
-                    const uint4 r = draw(P, ids[q], step, SP, kBlkRenew);
+                    const uint4 r = draw(P, pid_of(), step, SP, kBlkRenew);
                     const float2 g01 = box_muller(u01(r.x), u01(r.y));
                     const float2 g23 = box_muller(u01(r.z), u01(r.w));
                     v = make_float3(fmaf(S.renew_vt, g01.x, S.renew_drift[0]), fmaf(S.renew_vt, g01.y, S.renew_drift[1]),
@@ -629,12 +653,24 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
                 }
                 za[q] = zn;
             }
-            // 5-6. null-collision MCC with v^{n+1/2} at x^{n+1}; products appended
-            if (MCC != 0) {
-                if (SP == 0) collide_electron(P, nus, ids[q], step, c, on, v, half_e, half_i, diag, ev);
-                else collide_ion(P, nus, ids[q], step, v, ev);
+            // 5-6. null-collision MCC with v^{n+1/2} at x^{n+1}: the clock counts
+            // down; at its end the particle draws (block 0) a fresh gap and, unless
+            // the gap was a cut long one, is a collision candidate; products appended
+            if (MCC != 0 && S.lam > 0.0f) {
+                if (clk >= 2u) {
+                    clk -= 2u;
+                } else {
+                    const uint32_t pid = pid_of();
+                    const uint4 r = draw(P, pid, step, SP, kBlkMcc);
+                    const bool cand = (clk & 1u) == 0u;
+                    clk = clock_state(u01(r.x), S.lam);
+                    if (cand) {
+                        if (SP == 0) collide_electron(P, nus, pid, step, c, on, v, half_e, half_i, diag, ev, r);
+                        else collide_ion(P, nus, pid, step, v, ev, r);
+                    }
+                }
             }
-            cc[q] = c; oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
+            cc[q] = c | (int)(clk << kCellBits); oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
             dc[q] = c;
             df[q] = __float2uint_rz(on * 4294967296.0f);
             if (diag) {
@@ -802,19 +838,27 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_particle_step(const __grid_
     }
 }
 
+// Launch shapes of the batch kernel, chosen per batch by its autotuner:
+//   0: 512-thread CTAs, one per SM, up to 128 registers a thread, chunks of
+//      one particle with three in flight per thread;
+//   1: 512-thread CTAs, two per SM (64 registers), chunks of two, one ahead;
+//   2: 1024-thread CTAs, one per SM (64 registers), chunks of two, one ahead
+//      (the single-case kernels' shape).
+template <int SHAPE> struct BatchShape;
+template <> struct BatchShape<0> { static constexpr int threads = 512, minb = 1, chunk = 1, depth = 3; };
+template <> struct BatchShape<1> { static constexpr int threads = 512, minb = 2, chunk = 2, depth = 1; };
+template <> struct BatchShape<2> { static constexpr int threads = 1024, minb = 1, chunk = 2, depth = 1; };
+constexpr int kBatchShapes = 3;
+
 // Out-of-line item for the batch kernel: each species' body keeps its own
-// register allocation instead of the union of both.  The batch kernel runs
-// 512-thread CTAs with up to 128 registers a thread and its own chunk size and
-// look-ahead: on the 256-case small sweep, chunks of one with three ahead took
-// 0.97 ms a step, chunks of two with one or two ahead 0.99 and 1.02 ms.
-constexpr int kBatchChunk = 1, kBatchDepth = 3;
-template <int SP, bool PERIODIC, int MCC, bool STAGED>
+// register allocation instead of the union of both.
+template <int SP, bool PERIODIC, int MCC, bool STAGED, int SHAPE>
 __device__ __noinline__ void particle_item_call(const StepConst &P, unsigned char *smem, StepShared &sh,
                                                unsigned &parity, unsigned &tile_phase, long long k_item,
                                                long long n_items)
 {
-    particle_item<SP, PERIODIC, MCC, STAGED, false, kBatchChunk, kBatchDepth>(P, smem, sh, parity, tile_phase,
-                                                                             k_item, n_items);
+    particle_item<SP, PERIODIC, MCC, STAGED, false, BatchShape<SHAPE>::chunk, BatchShape<SHAPE>::depth>(
+        P, smem, sh, parity, tile_phase, k_item, n_items);
 }
 
 // Many cases in one persistent launch: CTAs take (case, species, slice) work
@@ -823,8 +867,8 @@ struct BatchItem {
     int case_idx, species, k, nk;
 };
 
-template <bool PERIODIC, int MCC0, int MCC1, bool STAGED>
-__global__ void __launch_bounds__(kBatchThreads, 1)
+template <bool PERIODIC, int MCC0, int MCC1, bool STAGED, int SHAPE>
+__global__ void __launch_bounds__(BatchShape<SHAPE>::threads, BatchShape<SHAPE>::minb)
     k_batch_particle_step(const StepConst *__restrict__ cases, const BatchItem *__restrict__ items, int n_items,
                           unsigned *next_item)
 {
@@ -854,8 +898,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
             cur_case = w.case_idx;
             __syncthreads();
         }
-        if (w.species == 0) particle_item_call<0, PERIODIC, MCC0, STAGED>(sP, smem, sh, parity, tile_phase, w.k, w.nk);
-        else particle_item_call<1, PERIODIC, MCC1, STAGED>(sP, smem, sh, parity, tile_phase, w.k, w.nk);
+        if (w.species == 0)
+            particle_item_call<0, PERIODIC, MCC0, STAGED, SHAPE>(sP, smem, sh, parity, tile_phase, w.k, w.nk);
+        else
+            particle_item_call<1, PERIODIC, MCC1, STAGED, SHAPE>(sP, smem, sh, parity, tile_phase, w.k, w.nk);
     }
 }
 
@@ -873,10 +919,12 @@ __global__ void k_rewind(const __grid_constant__ StepConst P)
     const float s0 = 2.0f * t0 / (1.0f + tt), s1 = 2.0f * t1 / (1.0f + tt), s2 = 2.0f * t2 / (1.0f + tt);
     const float ey = S.cEy * -0.5f, ez = S.cEz * -0.5f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = B.cell[i];
-        if (c < 0) continue;
+        const int raw = B.cell[i];
+        if (raw < 0) continue;
+        const int c = raw & kCellMask;
         const float o = B.off[i];
-        const float ex = (1.0f - o) * P.E32[c] + o * P.E32[c + 1] + P.Ex_ext;
+        const float2 ep = P.E32p[c];
+        const float ex = (1.0f - o) * ep.x + o * ep.y + P.Ex_ext;
         const float hx = a * ex;
         const float3 vm = make_float3(B.vx[i] + hx, B.vy[i] + ey, B.vz[i] + ez);
         const float3 vp = make_float3(vm.x + (vm.y * t2 - vm.z * t1), vm.y + (vm.z * t0 - vm.x * t2),
@@ -928,18 +976,21 @@ __global__ void k_load_profile(SpeciesBufs B, long long n, int N, const double *
     }
 }
 
-// Deposit of all particles of a species (the state at load), and validation
-// of the loaded cells/offsets.
+// Deposit of all particles of a species (the state at load), validation of
+// the loaded cells/offsets (plain cell indices: a load starts every species'
+// clocks afresh), and each particle's first collision clock.
 __global__ void k_deposit_species(const __grid_constant__ StepConst P, int sp)
 {
     const SpeciesBufs B = P.buf[sp][P.ctrl->cur[sp]];
     const long long n = (long long)P.ctrl->n_active[sp];
     const int N = P.n_cells;
+    const uint32_t step = (uint32_t)P.ctrl->step;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int c = B.cell[i];
         const float o = B.off[i];
         if (c < 0) continue;
         if (c >= N || !(o >= 0.0f && o < 1.0f)) { atomicOr(&P.ctrl->err, kErrLoad); B.cell[i] = -1; continue; }
+        if (P.sp[sp].lam > 0.0f) B.cell[i] = c | (int)(first_clock(P, sp, B.id[i], step) << kCellBits);
         const uint32_t f = __float2uint_rz(o * 4294967296.0f);
         const int c1 = (P.periodic && c + 1 == N) ? 0 : c + 1;
         unsigned long long *R = P.R[sp] + (size_t)(blockIdx.x % kDepositCopies) * P.r_stride;

@@ -209,7 +209,7 @@ void fill_species(pic_case *c, int sp)
         S.mcc = 0;
     }
     S.numax = (float)numax;
-    S.pnull = (float)(1.0 - std::exp(-numax * dt));
+    S.lam = S.mcc != 0 ? (float)(numax * dt) : 0.0f;
 }
 
 pic_status upload_tables(pic_case *c, int sp)
@@ -357,10 +357,10 @@ cudaError_t launch_sort(pic_case *c, int sp)
     const int32_t *cur = &c->P.ctrl->cur[sp];
     const unsigned long long *n = &c->P.ctrl->n_active[sp];
     const int gc = (int)std::min<long long>(c->num_sms * 4, std::max<long long>(1, cap / 1024));
-    k_cells_count<<<gc, 512, N * sizeof(unsigned), c->stream>>>(H, cur, n, 0, N, c->P.sort_count);
+    k_cells_count<true><<<gc, 512, N * sizeof(unsigned), c->stream>>>(H, cur, n, 0, N, c->P.sort_count);
     k_cells_scan<<<1, 1024, N * sizeof(double), c->stream>>>(c->P.sort_count, N, c->P.sort_cursor);
     const int gs = (int)std::min<long long>(c->num_sms * 2, std::max<long long>(1, (cap + 511) / 512));   // one wave
-    k_cells_scatter<<<gs, 512, 12 * (size_t)N, c->stream>>>(H, cur, n, 0, N, c->P.sort_cursor);
+    k_cells_scatter<true><<<gs, 512, 12 * (size_t)N, c->stream>>>(H, cur, n, 0, N, c->P.sort_cursor);
     k_sort_finish<<<4, 256, 0, c->stream>>>(c->P, sp, c->P.sort_cursor + N);
     return cudaGetLastError();
 }
@@ -466,6 +466,16 @@ __global__ void k_load_si(SpeciesBufs B, long long n, int N, double inv_dx, doub
     }
 }
 
+// Plain cell indices: a load restarts every species, and their collision
+// clocks are drawn afresh at the first step.
+__global__ void k_strip_clock(int32_t *cell, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int w = cell[i];
+        if (w >= 0) cell[i] = w & kCellMask;
+    }
+}
+
 pic_status reset_moments(pic_case *c)
 {
     const size_t nn = (size_t)c->n_nodes;
@@ -503,12 +513,6 @@ cudaError_t launch_one_step(pic_case *c)
     return e;
 }
 
-cudaError_t launch_sorts(pic_case *c)
-{
-    cudaError_t e = cudaSuccess;
-    for (int s = 0; s < c->d.n_species && e == cudaSuccess; ++s) e = launch_sort(c, s);
-    return e;
-}
 
 // ---------------------------------------------------------------------------
 // Autotuner, per species, of the sort interval K and of the step kernel's
@@ -751,9 +755,15 @@ pic_status load_begin(pic_case *c, int sp, int64_t n, Ctrl *h)
             if (st != PIC_OK) return st;
         }
     CU(cudaMemcpy(h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
-    // a load restarts the case: particles of the other species move back to half 0
+    // a load restarts the case: particles of the other species move back to
+    // half 0 and lose their collision clocks (drawn afresh at the first step)
     for (int s = 0; s < c->d.n_species; ++s) {
-        if (s == sp || h->cur[s] == 0 || !c->loaded[s]) continue;
+        if (s == sp || !c->loaded[s] || h->n_total[s] == 0) continue;
+        if (h->cur[s] == 0) {
+            k_strip_clock<<<c->num_sms * 4, 256, 0, c->stream>>>(c->P.buf[s][0].cell, (long long)h->n_total[s]);
+            CU(cudaGetLastError());
+            continue;
+        }
         const SpeciesBufs &A = c->P.buf[s][1], &D = c->P.buf[s][0];
         const size_t b = (size_t)h->n_total[s] * 4;
         CU(cudaMemcpyAsync(D.cell, A.cell, b, cudaMemcpyDeviceToDevice, c->stream));
@@ -763,6 +773,8 @@ pic_status load_begin(pic_case *c, int sp, int64_t n, Ctrl *h)
         CU(cudaMemcpyAsync(D.vz, A.vz, b, cudaMemcpyDeviceToDevice, c->stream));
         CU(cudaMemcpyAsync(D.id, A.id, b, cudaMemcpyDeviceToDevice, c->stream));
         if (A.z) CU(cudaMemcpyAsync(D.z, A.z, b, cudaMemcpyDeviceToDevice, c->stream));
+        k_strip_clock<<<c->num_sms * 4, 256, 0, c->stream>>>(D.cell, (long long)h->n_total[s]);
+        CU(cudaGetLastError());
     }
     return PIC_OK;
 }
@@ -926,7 +938,7 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     P.n_harm = desc->n_harm;
     for (int h = 0; h < 4; ++h) { P.harm_f[h] = desc->harm_freq_hz[h]; P.harm_a[h] = desc->harm_amp_v[h]; P.harm_p[h] = desc->harm_phase_rad[h]; }
     const size_t nn = (size_t)c->n_nodes;
-    P.E32 = (float *)c->dalloc(sizeof(float) * (((N + 1) + 3) / 4 * 4));
+    P.E32p = (float2 *)c->dalloc(sizeof(float2) * ((N + 1) / 2 * 2));
     P.E = (double *)c->dalloc(sizeof(double) * nn);
     P.phi = (double *)c->dalloc(sizeof(double) * nn);
     P.r_stride = (N + 1 + 15) / 16 * 16;
@@ -947,12 +959,12 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     P.sort_count = (unsigned *)c->dalloc(sizeof(unsigned) * N);
     P.sort_cursor = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * (N + 1));
     P.ifedf = (unsigned long long *)c->dalloc(sizeof(unsigned long long) * 2 * kIfedfBins);
-    if (!P.ifedf || !P.E32 || !P.E || !P.phi || !P.R[0] || !P.R[1] || !c->R_last || !P.ctrl || !P.Rsum || !P.Rdiag ||
+    if (!P.ifedf || !P.E32p || !P.E || !P.phi || !P.R[0] || !P.R[1] || !c->R_last || !P.ctrl || !P.Rsum || !P.Rdiag ||
         !P.en_sum || !P.phi_sum || !P.ke_sum || !P.pw_sum || !P.eepf || !P.fe_hist || !P.sort_count || !P.sort_cursor) {
         pic_destroy(c);
         return fail(PIC_ENOMEM, "device allocation failed");
     }
-    cudaMemsetAsync(P.E32, 0, sizeof(float) * (((N + 1) + 3) / 4 * 4), c->stream);
+    cudaMemsetAsync(P.E32p, 0, sizeof(float2) * ((N + 1) / 2 * 2), c->stream);
     cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), c->stream);
     cudaMemsetAsync(P.sort_count, 0, sizeof(unsigned) * N, c->stream);
     cudaMemsetAsync(c->R_last, 0, sizeof(unsigned long long) * 2 * nn, c->stream);
@@ -1249,7 +1261,7 @@ pic_status pic_read_particles(pic_case *c, int sp, int64_t max_n, int64_t *n_out
     for (size_t i = 0; i < n; ++i) {
         if (hc[i] < 0) continue;
         if (k < max_n) {
-            if (cell) cell[k] = hc[i];
+            if (cell) cell[k] = hc[i] & kCellMask;
             if (off) off[k] = ho[i];
             if (vx) vx[k] = hx[i];
             if (vy) vy[k] = hy[i];
@@ -1260,6 +1272,26 @@ pic_status pic_read_particles(pic_case *c, int sp, int64_t max_n, int64_t *n_out
     }
     if (n_out) *n_out = k;
     if (k > max_n) return fail(PIC_ECAPACITY, "output buffers smaller than the live count");
+    return device_error(c);
+}
+
+pic_status pic_read_clock(pic_case *c, int sp, int64_t max_n, int64_t *n_out, uint32_t *clock)
+{
+    if (!c || sp < 0 || sp >= c->d.n_species || max_n < 0) return fail(PIC_EINVAL, "bad read arguments");
+    Ctrl h;
+    CU(cudaMemcpyAsync(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    const size_t n = (size_t)h.n_total[sp];
+    std::vector<int32_t> hc(n);
+    if (n) CU(cudaMemcpy(hc.data(), c->P.buf[sp][h.cur[sp]].cell, n * 4, cudaMemcpyDeviceToHost));
+    int64_t k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        if (hc[i] < 0) continue;
+        if (k < max_n && clock) clock[k] = (uint32_t)hc[i] >> kCellBits;
+        ++k;
+    }
+    if (n_out) *n_out = k;
+    if (k > max_n) return fail(PIC_ECAPACITY, "output buffer smaller than the live count");
     return device_error(c);
 }
 
@@ -1441,7 +1473,7 @@ pic_status pic_profile_read(pic_case *c, pic_kernel_stat *out, int max_entries, 
 namespace {
 
 constexpr char kCkptMagic[8] = {'P', 'I', 'C', '1', 'D', '3', 'V', 'C'};
-constexpr uint32_t kCkptVersion = 2;
+constexpr uint32_t kCkptVersion = 3;
 
 struct CkptHeader {
     char magic[8];
@@ -1460,7 +1492,7 @@ std::vector<std::pair<void *, size_t>> ckpt_arrays(const pic_case *c)
     const StepConst &P = c->P;
     const size_t nn = (size_t)c->n_nodes, N = (size_t)c->d.n_cells;
     return {
-        {P.E32, sizeof(float) * ((N + 1 + 3) / 4 * 4)}, {P.E, 8 * nn}, {P.phi, 8 * nn},
+        {P.E32p, sizeof(float2) * ((N + 1) / 2 * 2)}, {P.E, 8 * nn}, {P.phi, 8 * nn},
         {P.R[0], 8 * (size_t)kDepositCopies * P.r_stride}, {P.R[1], 8 * (size_t)kDepositCopies * P.r_stride},
         {c->R_last, 8 * 2 * nn}, {P.Rsum, 8 * 2 * nn}, {P.Rdiag, 8 * 2 * nn}, {P.en_sum, 8 * 2 * nn},
         {P.phi_sum, 8 * nn}, {P.ke_sum, 16}, {P.pw_sum, 16}, {P.eepf, 8 * (size_t)kEepfBins},
@@ -1664,10 +1696,10 @@ pic_status pic_sort_by_cell(int32_t n_cells, int64_t n, const int32_t *cell, con
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int gc = (int)std::min<long long>(sms * 4, std::max<long long>(1, n / 1024));
-        k_cells_count<<<gc, 512, N * sizeof(unsigned), st>>>(H, nullptr, nullptr, n, N, counts);
+        k_cells_count<false><<<gc, 512, N * sizeof(unsigned), st>>>(H, nullptr, nullptr, n, N, counts);
         k_cells_scan<<<1, 1024, N * sizeof(double), st>>>(counts, N, cursor);
         const int gs = (int)std::min<long long>(sms * 2, std::max<long long>(1, (n + 511) / 512));
-        k_cells_scatter<<<gs, 512, 12 * (size_t)N, st>>>(H, nullptr, nullptr, n, N, cursor);
+        k_cells_scatter<false><<<gs, 512, 12 * (size_t)N, st>>>(H, nullptr, nullptr, n, N, cursor);
         CU(cudaGetLastError());
     }
     if (n_live) CU(cudaMemcpyAsync(n_live, cursor + N, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
@@ -1686,6 +1718,8 @@ struct pic_batch {
     bool own_stream = false;
     StepConst *d_cases = nullptr;
     BatchItem *d_items = nullptr;
+    SortItem *d_sort_items[2] = {nullptr, nullptr};   // batched sort blocks per species
+    int n_sort_items[2] = {0, 0};
     unsigned *d_next = nullptr;
     int n_items = 0;
     bool planned = false;
@@ -1697,11 +1731,14 @@ struct pic_batch {
     // cases with at least own_threshold particles run their own step kernels
     // (single-case kernels, 1024-thread CTAs) inside the batch's graph; the
     // rest share the persistent kernel; all field solves share one launch
-    long long own_threshold = 1LL << 19;
+    long long own_threshold = 0;
     std::vector<int> own;
     unsigned smem = 0;
-    int grid = 0;
+    int grid_of[kBatchShapes] = {};   // persistent grid per launch shape (0 = not computed)
+    int shape = 0;                    // launch shape of the batch kernel (BatchShape)
     int sort_k = 64;
+    bool autotune = false, tuned = false;   // sort interval and shape chosen by batch_autotune
+    float tune_shape_ms[kBatchShapes] = {}, tune_sort_ms = 0.f, tune_slope_ms = 0.f;
     long long host_step = 0, steps_since_sort = 0;
     cudaGraphExec_t graph[kGraphSteps + 1] = {};   // graph[k]: k batch steps
     long long launches = 0;
@@ -1712,28 +1749,34 @@ namespace {
 constexpr long long kItemParticles = 131072;      // largest work item
 constexpr long long kMinItemParticles = 16384;    // smallest work item when splitting for balance
 
-template <bool PER, int M0, int M1, bool STAGED>
+template <bool PER, int M0, int M1, bool STAGED, int SHAPE>
 cudaError_t batch_step_k(pic_batch *b)
 {
-    auto k = k_batch_particle_step<PER, M0, M1, STAGED>;
-    if (b->grid == 0) {
+    auto k = k_batch_particle_step<PER, M0, M1, STAGED, SHAPE>;
+    constexpr int T = BatchShape<SHAPE>::threads;
+    int &grid = b->grid_of[SHAPE];
+    if (grid == 0) {
         static std::once_flag once;
         static cudaError_t attr_err = cudaSuccess;
         cudaError_t e = allow_max_step_smem(k, once, attr_err, b->cases[0]->device);
         if (e != cudaSuccess) return e;
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kBatchThreads, b->smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, T, b->smem);
         if (e != cudaSuccess) return e;
-        b->grid = std::max(1, occ) * b->cases[0]->num_sms;
+        grid = std::max(1, occ) * b->cases[0]->num_sms;
     }
-    k<<<b->grid, kBatchThreads, b->smem, b->stream>>>(b->d_cases, b->d_items, b->n_items, b->d_next);
+    k<<<grid, T, b->smem, b->stream>>>(b->d_cases, b->d_items, b->n_items, b->d_next);
     return cudaGetLastError();
 }
 
+// Tile buffers (bulk-copy pipeline) exist for shape 0 only.
 template <bool PER, int M0, int M1>
 cudaError_t batch_step_t(pic_batch *b)
 {
-    return b->run_stages > 0 ? batch_step_k<PER, M0, M1, true>(b) : batch_step_k<PER, M0, M1, false>(b);
+    if (b->run_stages > 0) return batch_step_k<PER, M0, M1, true, 0>(b);
+    if (b->shape == 1) return batch_step_k<PER, M0, M1, false, 1>(b);
+    if (b->shape == 2) return batch_step_k<PER, M0, M1, false, 2>(b);
+    return batch_step_k<PER, M0, M1, false, 0>(b);
 }
 
 cudaError_t batch_particles(pic_batch *b)
@@ -1768,6 +1811,26 @@ cudaError_t batch_one_step(pic_batch *b)
     k_batch_field<<<(unsigned)(kFieldCluster * b->cases.size()), kFieldThreads, b->cases[0]->field_smem, b->stream>>>(
         b->d_cases, 1, b->d_next);
     return cudaGetLastError();
+}
+
+// The counting sort of every case, one launch per kernel and species (the
+// cases' own count/cursor arrays; species one after the other, as they share
+// them), over the sort items batch_plan made.
+cudaError_t batch_sort(pic_batch *b)
+{
+    const unsigned nc = (unsigned)b->cases.size();
+    int maxN = 0;
+    for (pic_case *c : b->cases) maxN = std::max(maxN, c->d.n_cells);
+    for (int sp = 0; sp < b->cases[0]->d.n_species; ++sp) {
+        const unsigned ni = (unsigned)b->n_sort_items[sp];
+        k_batch_cells_count<<<ni, 512, maxN * sizeof(unsigned), b->stream>>>(b->d_cases, b->d_sort_items[sp], sp);
+        k_batch_cells_scan<<<nc, 1024, maxN * sizeof(double), b->stream>>>(b->d_cases, sp);
+        k_batch_cells_scatter<<<ni, 512, 12 * (size_t)maxN, b->stream>>>(b->d_cases, b->d_sort_items[sp], sp);
+        k_batch_sort_finish<<<dim3(4, nc), 256, 0, b->stream>>>(b->d_cases, sp);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 void batch_drop_graph(pic_batch *b)
@@ -1847,7 +1910,8 @@ pic_status batch_plan(pic_batch *b)
         for (int s = 0; s < c->d.n_species; ++s) {
             const int np = c->P.sp[s].mcc == 1 ? c->P.sp[s].nproc : 0;
             const int narr = step_arrays(s, b->periodic != 0, c->P.sp[s].mcc);
-            stages = std::min(stages, fit_stages(c->d.n_cells, np, kBatchThreads, stages, narr, step_smem_limit(c->device)));
+            stages = std::min(stages, fit_stages(c->d.n_cells, np, BatchShape<0>::threads, stages, narr,
+                                                 step_smem_limit(c->device)));
         }
     }
     for (size_t i = 0; i < nc; ++i) {
@@ -1855,11 +1919,30 @@ pic_status batch_plan(pic_batch *b)
         for (int s = 0; s < c->d.n_species; ++s) {
             const int np = c->P.sp[s].mcc == 1 ? c->P.sp[s].nproc : 0;
             const int narr = step_arrays(s, b->periodic != 0, c->P.sp[s].mcc);
-            smem = std::max(smem, StepSmem(c->d.n_cells, np, kBatchThreads, stages, narr).total);
+            smem = std::max(smem, StepSmem(c->d.n_cells, np, BatchShape<0>::threads, stages, narr).total);
             consts[i].sp[s].stages = stages;
         }
     }
-    if (stages != b->run_stages) b->grid = 0;
+    // sort items: about one block per kSortItemParticles particles of a case
+    // (counts as at this plan, doubled for growth before the next one), at
+    // most one wave of the scatter kernel, in case order
+    for (int sp = 0; sp < c0->d.n_species; ++sp) {
+        std::vector<SortItem> si;
+        for (size_t i = 0; i < nc; ++i) {
+            const long long n = sp < b->cases[i]->d.n_species ? 2 * (long long)hs[i].n_active[sp] : 0;
+            const int nb = (int)std::max<long long>(1, std::min<long long>(2LL * c0->num_sms,
+                                                                          (n + kSortItemParticles - 1) / kSortItemParticles));
+            for (int k = 0; k < nb; ++k) si.push_back(SortItem{(int)i, k, nb});
+        }
+        if (b->d_sort_items[sp]) cudaFree(b->d_sort_items[sp]);
+        b->d_sort_items[sp] = nullptr;
+        CU(cudaMalloc(&b->d_sort_items[sp], si.size() * sizeof(SortItem)));
+        CU(cudaMemcpyAsync(b->d_sort_items[sp], si.data(), si.size() * sizeof(SortItem), cudaMemcpyHostToDevice,
+                           b->stream));
+        b->n_sort_items[sp] = (int)si.size();
+    }
+    if (stages != b->run_stages)
+        for (int &g : b->grid_of) g = 0;
     b->run_stages = stages;
     if (b->d_cases) cudaFree(b->d_cases);
     if (b->d_items) cudaFree(b->d_items);
@@ -1873,10 +1956,84 @@ pic_status batch_plan(pic_batch *b)
     CU(cudaMemsetAsync(b->d_next, 0, sizeof(unsigned), b->stream));
     CU(cudaStreamSynchronize(b->stream));
     b->n_items = (int)items.size();
-    if (smem != b->smem) b->grid = 0;
+    if (smem != b->smem)
+        for (int &g : b->grid_of) g = 0;
     b->smem = smem;
     b->planned = true;
     batch_drop_graph(b);
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batch autotuner (the benchmark spec pattern 2: tiles chosen by a project-written
+// tuner).  Continuing the simulation (results do not depend on any choice):
+//  1. each launch shape of the batch kernel runs kBatchShapeRounds steps in
+//     turn, timed with events around the step; the least summed time wins;
+//  2. one batched sort, then kBatchTuneSteps steps each timed with the chosen
+//     shape; choose_sort_interval picks K from them, as for a single case.
+// The tile pipeline (stages > 0) is left as the caller set it.
+// ---------------------------------------------------------------------------
+constexpr int kBatchShapeRounds = 2, kBatchTuneSteps = 32;
+constexpr int kBatchTuneTotal = kBatchShapeRounds * kBatchShapes + kBatchTuneSteps;
+
+pic_status batch_autotune(pic_batch *b, int64_t *left)
+{
+    batch_drop_graph(b);
+    struct Events {
+        std::vector<cudaEvent_t> v;
+        ~Events() { for (auto e : v) cudaEventDestroy(e); }
+    } ev;
+    const int n_shape_ev = 2 * kBatchShapeRounds * kBatchShapes;
+    ev.v.resize(n_shape_ev + 2 + 2 * kBatchTuneSteps, nullptr);
+    for (auto &e : ev.v) CU(cudaEventCreate(&e));
+    const int shapes = b->run_stages > 0 ? 1 : kBatchShapes;       // tiles: shape 0 only
+    for (int rnd = 0; rnd < kBatchShapeRounds; ++rnd)
+        for (int k = 0; k < kBatchShapes; ++k) {
+            b->shape = k < shapes ? k : 0;
+            CU(cudaEventRecord(ev.v[2 * (rnd * kBatchShapes + k)], b->stream));
+            CU(batch_one_step(b));
+            CU(cudaEventRecord(ev.v[2 * (rnd * kBatchShapes + k) + 1], b->stream));
+        }
+    CU(cudaStreamSynchronize(b->stream));
+    int best = 0;
+    for (int k = 0; k < kBatchShapes; ++k) {
+        float tot = 0.f;
+        for (int rnd = 0; rnd < kBatchShapeRounds; ++rnd) {
+            float t = 0.f;
+            CU(cudaEventElapsedTime(&t, ev.v[2 * (rnd * kBatchShapes + k)], ev.v[2 * (rnd * kBatchShapes + k) + 1]));
+            tot += t;
+        }
+        b->tune_shape_ms[k] = tot / kBatchShapeRounds;
+        if (k < shapes && b->tune_shape_ms[k] < b->tune_shape_ms[best]) best = k;
+    }
+    b->shape = best;
+    cudaEvent_t *sev = ev.v.data() + n_shape_ev, *tev = sev + 2;
+    CU(cudaEventRecord(sev[0], b->stream));
+    CU(batch_sort(b));
+    CU(cudaEventRecord(sev[1], b->stream));
+    for (int k = 0; k < kBatchTuneSteps; ++k) {
+        CU(cudaEventRecord(tev[2 * k], b->stream));
+        CU(batch_one_step(b));
+        CU(cudaEventRecord(tev[2 * k + 1], b->stream));
+    }
+    CU(cudaStreamSynchronize(b->stream));
+    float ts = 0.f;
+    CU(cudaEventElapsedTime(&ts, sev[0], sev[1]));
+    double ty[kBatchTuneSteps];
+    for (int k = 0; k < kBatchTuneSteps; ++k) {
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, tev[2 * k], tev[2 * k + 1]));
+        ty[k] = t;
+    }
+    const SortIntervalFit fit = choose_sort_interval(ty, kBatchTuneSteps, ts, 4, kMaxSortInterval);
+    b->sort_k = std::max(4, std::min(kMaxSortInterval, fit.K));
+    b->tune_sort_ms = ts;
+    b->tune_slope_ms = (float)fit.slope;
+    b->tuned = true;
+    b->launches += (long long)batch_launches_per_step(b) * kBatchTuneTotal + 4LL * b->cases[0]->d.n_species;
+    b->host_step += kBatchTuneTotal;
+    b->steps_since_sort = kBatchTuneSteps;
+    *left -= kBatchTuneTotal;
     return PIC_OK;
 }
 
@@ -1921,7 +2078,8 @@ pic_status pic_batch_create(const pic_case_desc *descs, int n_cases, pic_batch *
         }
         b->own_stream = true;
     }
-    b->sort_k = descs[0].sort_interval > 0 ? descs[0].sort_interval : 64;
+    b->autotune = descs[0].sort_interval <= 0;
+    b->sort_k = b->autotune ? 64 : descs[0].sort_interval;
     for (int i = 0; i < n_cases; ++i) {
         pic_case_desc d = descs[i];
         d.stream = b->stream;                       // every case on the batch stream
@@ -1957,10 +2115,15 @@ pic_status pic_batch_step(pic_batch *b, int64_t n_steps)
     }
     int64_t left = n_steps;
     while (left > 0) {
+        if (b->autotune && !b->tuned && b->host_step > 0 && left >= kBatchTuneTotal) {
+            pic_status st = batch_autotune(b, &left);
+            if (st != PIC_OK) return st;
+            continue;
+        }
         const int K = b->sort_k;
         if (b->steps_since_sort >= K) {
-            for (pic_case *c : b->cases) CU(launch_sorts(c));
-            b->launches += 4LL * b->cases.size() * b->cases[0]->d.n_species;
+            CU(batch_sort(b));
+            b->launches += 4LL * b->cases[0]->d.n_species;
             b->steps_since_sort = 0;
         }
         // steps before the next sort, replayed as one graph (every length up
@@ -1987,8 +2150,8 @@ pic_status pic_batch_step(pic_batch *b, int64_t n_steps)
         }
     }
     if (b->steps_since_sort >= b->sort_k) {
-        for (pic_case *c : b->cases) CU(launch_sorts(c));
-        b->launches += 4LL * b->cases.size() * b->cases[0]->d.n_species;
+        CU(batch_sort(b));
+        b->launches += 4LL * b->cases[0]->d.n_species;
         b->steps_since_sort = 0;
     }
     return PIC_OK;
@@ -2016,6 +2179,27 @@ pic_status pic_batch_set_own_threshold(pic_batch *b, int64_t particles)
     return PIC_OK;
 }
 
+pic_status pic_batch_tuning(pic_batch *b, int *shape, int *sort_interval, int *tuned, float *shape_ms, float *sort_ms)
+{
+    if (!b) return fail(PIC_EINVAL, "null batch");
+    if (shape) *shape = b->shape;
+    if (sort_interval) *sort_interval = b->sort_k;
+    if (tuned) *tuned = b->tuned ? 1 : 0;
+    if (shape_ms)
+        for (int k = 0; k < kBatchShapes; ++k) shape_ms[k] = b->tune_shape_ms[k];
+    if (sort_ms) *sort_ms = b->tune_sort_ms;
+    return PIC_OK;
+}
+
+pic_status pic_batch_set_shape(pic_batch *b, int shape)
+{
+    if (!b || shape < 0 || shape >= kBatchShapes) return fail(PIC_EINVAL, "shape must be 0, 1 or 2");
+    b->shape = shape;
+    b->tuned = true;                                 // a fixed shape: the autotuner does not run
+    batch_drop_graph(b);
+    return PIC_OK;
+}
+
 pic_status pic_batch_set_stages(pic_batch *b, int stages)
 {
     if (!b || stages < 0 || stages > kMaxStages) return fail(PIC_EINVAL, "stages must be in [0, 4]");
@@ -2033,6 +2217,8 @@ pic_status pic_batch_destroy(pic_batch *b)
     for (pic_case *c : b->cases) pic_destroy(c);
     if (b->d_cases) cudaFree(b->d_cases);
     if (b->d_items) cudaFree(b->d_items);
+    for (SortItem *p : b->d_sort_items)
+        if (p) cudaFree(p);
     if (b->d_next) cudaFree(b->d_next);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;

@@ -11,7 +11,7 @@ constexpr float kGridEmin = 1e-3f;
 constexpr int kEepfBins = 240;          // 0..60 eV, 0.25 eV bins
 constexpr int kIfedfBins = 256;         // ion energy at each electrode
 constexpr int kStepThreads = 1024;     // largest CTA of the particle step
-constexpr int kBatchThreads = 512;     // CTA of the batched (many-case) particle step
+constexpr int kBatchMaxThreads = 1024; // largest CTA of the batched (many-case) particle step
 constexpr int kMaxStages = 4;          // particle tiles in flight per CTA (bulk-copy pipeline)
 // Copies of each species' raw deposit: CTA b adds its histogram into copy
 // b mod kDepositCopies, spreading the int64 atomics of hundreds of CTAs over
@@ -28,7 +28,14 @@ constexpr unsigned kErrLoad = 8u;
 
 // Random-draw blocks: counter word 2 is (species << 16) | block.
 constexpr uint32_t kBlkMcc = 0, kBlkAux = 1, kBlkNewIon = 2, kBlkSee = 3, kBlkSeeV = 4, kBlkRenew = 5,
-                   kBlkChild = 0xFFFF;
+                   kBlkGap = 6, kBlkChild = 0xFFFF;
+
+// Cell word of a particle: bits 0-12 the cell index, bits 13-30 its collision
+// clock 2 k + c (k non-candidate steps left, c = 1 when that gap was cut at
+// kClockMax steps and a fresh one follows), -1 for an absorbed particle.
+constexpr int kCellBits = 13;
+constexpr int32_t kCellMask = (1 << kCellBits) - 1;
+constexpr int kClockMax = 131071;
 
 struct SpeciesBufs {                    // one half of a species' ping-pong storage
     int32_t *cell;
@@ -66,7 +73,7 @@ struct SpConst {
     float cEy, cEz;                     // c_e * E_ext_y, c_e * E_ext_z
     float m_over_2e;                    // eps[eV] = m/(2e) |v|^2
     float v_of_sqrt_eps;                // |v| = sqrt(2e/m) sqrt(eps)
-    float pnull;                        // 1 - exp(-numax dt)
+    float lam;                          // numax dt in FP32: the collision clock's gap unit (0 = no MCC)
     float numax;
     int nproc;
     int kind[kMaxProc];
@@ -99,7 +106,7 @@ struct StepConst {
     double harm_f[4], harm_a[4], harm_p[4];
     SpConst sp[2];
     const float *nu_tab[2];             // [nproc][kNGrid] per species
-    float *E32;                         // [n_cells + 1 padded]: periodic ghost at n_cells
+    float2 *E32p;                       // [n_cells, padded to 16 B]: (E_c, E_{c+1}) in FP32 for the gather
     double *E, *phi;                    // [n_nodes]
     unsigned long long *R[2];           // [kDepositCopies][r_stride] raw fixed-point deposit (copies summed)
     int r_stride;                       // words between copies (n_cells + 1 rounded up to 16)
@@ -171,6 +178,43 @@ __device__ __forceinline__ float u01(uint32_t r)
 __device__ __forceinline__ uint4 draw(const StepConst &P, uint32_t id, uint32_t step, int sp, uint32_t blk)
 {
     return philox4x32_10(make_uint4(id, step, ((uint32_t)sp << 16) | blk, 0u), P.key0, P.key1);
+}
+
+// Null-collision clock (paper §4 free flights; §1 null-collision method).
+// The number G of non-candidate steps before a particle's next collision
+// candidate is geometric with P(G >= g) = exp(-g numax dt), and
+// G = floor(-ln(u) / (numax dt)) has that law for u uniform, so each particle
+// draws G once per candidate instead of testing a uniform every step.  The
+// gap is evaluated in FP32 with every operation rounded once (IEEE), so that
+// the result is the same integer on any conforming implementation.
+//
+// -ln(u) for u in (0, 1): u = m 2^e, m in [sqrt(1/2), sqrt(2)); ln m = 2 atanh(s)
+// with s = (m - 1)/(m + 1), summed as 2 s (1 + s^2/3 + ... + s^10/11)
+// (Abramowitz and Stegun 4.1.27; |s| < 0.172).
+__device__ __forceinline__ float neg_log_u32(float u)
+{
+    const uint32_t b = __float_as_uint(u);
+    int e = (int)((b >> 23) & 0xFFu) - 127;
+    float m = __uint_as_float((b & 0x7FFFFFu) | 0x3F800000u);
+    if (m > 1.41421354f) { m = __fmul_rn(m, 0.5f); e += 1; }
+    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float s2 = __fmul_rn(s, s);
+    float q = 1.0f / 11.0f;
+    q = __fmaf_rn(q, s2, 1.0f / 9.0f);
+    q = __fmaf_rn(q, s2, 1.0f / 7.0f);
+    q = __fmaf_rn(q, s2, 1.0f / 5.0f);
+    q = __fmaf_rn(q, s2, 1.0f / 3.0f);
+    q = __fmaf_rn(q, s2, 1.0f);
+    const float lnm = __fmul_rn(__fadd_rn(s, s), q);
+    return -__fmaf_rn((float)e, 0.693147182f, lnm);
+}
+
+// Clock state 2 k + c of a fresh gap drawn from the uniform u (lam = numax dt)
+__device__ __forceinline__ uint32_t clock_state(float u, float lam)
+{
+    const float x = __fdiv_rn(neg_log_u32(u), lam);
+    if (x >= (float)(kClockMax + 1)) return 2u * kClockMax + 1u;
+    return 2u * (uint32_t)floorf(x);
 }
 
 // isotropic unit vector from two uniforms: cos(theta) = 1 - 2u, phi = 2 pi u'

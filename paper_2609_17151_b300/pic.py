@@ -103,6 +103,7 @@ def _load_library():
     lib.pic_read_particles.argtypes = [vp, C.c_int, i64, C.POINTER(i64), vp, vp, vp, vp, vp, vp]
     lib.pic_read_field.argtypes = [vp, vp, vp, vp]
     lib.pic_read_axial.argtypes = [vp, C.c_int, i64, C.POINTER(i64), vp]
+    lib.pic_read_clock.argtypes = [vp, C.c_int, i64, C.POINTER(i64), vp]
     lib.pic_read_moments.argtypes = [vp, C.POINTER(Moments)]
     lib.pic_read_tuning.argtypes = [vp, C.POINTER(Tuning)]
     lib.pic_set_step_shape.argtypes = [vp, C.c_int, C.c_int, C.c_int]
@@ -131,6 +132,9 @@ def _load_library():
     lib.pic_batch_destroy.argtypes = [vp]
     lib.pic_batch_set_stages.argtypes = [vp, C.c_int]
     lib.pic_batch_set_own_threshold.argtypes = [vp, i64]
+    lib.pic_batch_set_shape.argtypes = [vp, C.c_int]
+    lib.pic_batch_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_float), C.POINTER(C.c_float)]
     fp = C.POINTER(C.c_float)
     lib.pic_mlp_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(vp)]
     lib.pic_mlp_set_normalization.argtypes = [vp, fp, fp, fp, fp]
@@ -523,8 +527,19 @@ class Batch:
     def set_stages(self, stages):
         check(lib.pic_batch_set_stages(self.h, int(stages)))
 
+    def set_shape(self, shape):
+        check(lib.pic_batch_set_shape(self.h, int(shape)))
+
     def set_own_threshold(self, particles):
         check(lib.pic_batch_set_own_threshold(self.h, int(particles)))
+
+    def tuning(self):
+        """Launch shape, sort interval, whether the autotuner ran, and its timings."""
+        sh, k, tu, sm = C.c_int(), C.c_int(), C.c_int(), C.c_float()
+        ms = (C.c_float * 3)()
+        check(lib.pic_batch_tuning(self.h, C.byref(sh), C.byref(k), C.byref(tu), ms, C.byref(sm)))
+        return dict(shape=sh.value, sort_interval=k.value, tuned=bool(tu.value), shape_ms=list(ms),
+                    sort_ms=sm.value)
 
     def replan(self):
         """Re-split the work items from the current particle counts before the next step."""
@@ -611,6 +626,14 @@ class Case:
 
     def moments(self, reset=False, field_energy_cap=0):
         return read_moments(self.h, self.n_nodes, self.n_species, reset=reset, field_energy_cap=field_energy_cap)
+
+    def clock(self, sp):
+        """Collision clock 2 k + c of the live particles, in the order of ``particles``."""
+        n = int(self.count()[sp])
+        out = np.zeros(n, np.uint32)
+        k = C.c_int64()
+        check(lib.pic_read_clock(self.h, sp, n, C.byref(k), out.ctypes.data))
+        return out[: k.value]
 
     def axial(self, sp):
         """Axial excursion z (m) of the live particles, in the order of ``particles``."""

@@ -118,6 +118,35 @@ def test_eepf_bin_by_bin_and_power_sum_match_oracle():
     gc.close()
 
 
+# --------------------------------------------------------------------------- collision clock
+@pytest.mark.parametrize("which", ["ccp_hot", "exb_const_nu"])
+def test_collision_clocks_are_bit_identical_to_the_oracle(which):
+    """The null-collision clock of every particle (steps left to its next
+    collision candidate, drawn in FP32 from the same Philox words on both
+    sides) is the same integer on the GPU and in the oracle after several
+    steps, for the table-driven argon CCP (every process, products with their
+    first clocks) and the constant-frequency E x B electrons."""
+    if which == "ccp_hot":
+        cfg, parts = small_ccp(seed=31, n=30_001, te=25.0)
+        steps = 6
+    else:
+        cfg, parts = W.ecdi_case(seed=5, ppc=20, nu=2e9)
+        steps = 4
+    oc = oracle_case(cfg, parts)
+    oc.step(steps)
+    gc = gpu_case(cfg, parts)
+    gc.step(steps)
+    for s in range(len(cfg["species"])):
+        g, o = gc.particles(s), oc.particles(s)
+        cg, co = gc.clock(s), oc.clock(s)
+        ig, io = np.argsort(g["id"], kind="stable"), np.argsort(o["id"], kind="stable")
+        assert np.array_equal(g["id"][ig], o["id"][io])
+        assert np.array_equal(cg[ig].astype(np.int64), co[io].astype(np.int64)), s
+        if s == 0:
+            assert np.any(cg % 2 == 0) and np.unique(cg).size > 10
+    gc.close()
+
+
 # --------------------------------------------------------------------------- network
 def test_gpu_adam_matches_oracle_adam_over_ten_steps():
     """pic_mlp_adam_step (the update pic_mlp_train applies) against the oracle's

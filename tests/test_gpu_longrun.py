@@ -1,0 +1,89 @@
+"""Long-run statistical parity: the FP32 CUDA path against the FP64 oracle after
+hundreds of RF cycles, where single particles have long since diverged (the
+two round differently, and the discharge is chaotic) but the method's
+statistics must agree.
+
+The reduced argon CCP (paper §1's scheme with the synthetic argon tables,
+256 cells, 5e4 particles per species at load, 13.56 MHz) runs for 300 RF
+cycles from 5 seeds; the profiles averaged over the last 100 cycles (electron
+and ion density, potential) and the EEPF of those cycles are compared as
+ensembles: the GPU's 5-seed mean against the oracle's (stored by
+tests/golden/make_longrun_ccp.py, which calls only the oracle), by relative
+L2 distance (at most 2 %) and per node against the seed-to-seed spread.
+The five GPU runs are one batch, so this also checks the batched step
+against the oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2609_17151_b300 import pic  # noqa: E402
+
+from .golden.make_longrun_ccp import case  # noqa: E402  (input generators only)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden", "longrun_ccp.json")
+
+
+def ensemble_stats(g, o, floor):
+    """5-seed means and spreads; relative L2 of the mean difference and the
+    per-node z-score of it against the pooled spread of the two means."""
+    g, o = np.asarray(g, float), np.asarray(o, float)
+    mg, mo = g.mean(0), o.mean(0)
+    n = g.shape[0]
+    se = np.sqrt(g.var(0, ddof=1) / n + o.var(0, ddof=1) / n + floor**2)
+    z = (mg - mo) / se
+    return {"rel_l2": float(np.linalg.norm(mg - mo) / np.linalg.norm(mo)), "mean_z2": float(np.mean(z * z)),
+            "max_abs_z": float(np.max(np.abs(z))),
+            "seed_spread_rel": float(np.linalg.norm(o.std(0, ddof=1)) / np.linalg.norm(mo))}
+
+
+def test_long_run_profiles_match_the_oracle_statistically():
+    gold = json.load(open(GOLDEN))
+    spec = gold["spec"]
+    seeds = [r["seed"] for r in gold["seeds"]]
+    made = [case(s, spec["volts"]) for s in seeds]
+    cfgs = [m[0] for m in made]
+    cap = 4_000_000
+    b = pic.Batch(cfgs, sort_interval=64, capacities=[(cap, cap)] * len(cfgs))
+    for v, (_, parts) in zip(b.cases, made):
+        for s, p in enumerate(parts):
+            v.load(s, p)
+    spc = spec["steps_per_cycle"]
+    b.step(spc * (spec["cycles"] - spec["avg_cycles"]))
+    b.sync()
+    for v in b.cases:
+        v.moments(reset=True)
+    b.step(spc * spec["avg_cycles"])
+    b.sync()
+    ms = [v.moments() for v in b.cases]
+    b.close()
+    gpu = {"ne": [m["dens_sum"][0] / m["n_steps"] for m in ms], "ni": [m["dens_sum"][1] / m["n_steps"] for m in ms],
+           "phi": [m["phi_sum"] / m["n_steps"] for m in ms]}
+    ora = {k: [r[k] for r in gold["seeds"]] for k in ("ne", "ni", "phi")}
+    report = {}
+    for k in ("ne", "ni", "phi"):
+        floor = 1e-6 * float(np.max(np.abs(np.mean(ora[k], 0))))
+        report[k] = ensemble_stats(gpu[k], ora[k], floor)
+    # EEPF of the central 10 % of the gap: per-diagnostic-step counts, bins with enough counts
+    eg = np.array([m["eepf"] / m["n_diag"] for m in ms])
+    eo = np.array([np.array(r["eepf"]) / r["n_diag"] for r in gold["seeds"]])
+    ok = eo.mean(0) > 20
+    report["eepf"] = ensemble_stats(eg[:, ok], eo[:, ok], 1e-9)
+    centre = 0.25 * (np.arange(240) + 0.5)
+    mean_e = lambda e: float(np.sum(centre * e.mean(0)) / np.sum(e.mean(0)))  # noqa: E731
+    report["eepf_mean_energy_rel"] = abs(mean_e(eg) / mean_e(eo) - 1)
+    print(json.dumps(report))
+    for k in ("ne", "ni", "phi", "eepf"):
+        r = report[k]
+        if k != "eepf":
+            assert r["rel_l2"] <= 0.02, (k, report)
+        assert r["mean_z2"] <= 3.0 and r["max_abs_z"] <= 6.0, (k, report)
+    assert report["eepf_mean_energy_rel"] <= 0.02, report

@@ -752,6 +752,44 @@ def test_batch_equals_cases_stepped_alone(stages, own):
     b.close()
 
 
+def test_batch_autotuner_and_batched_sort_leave_results_unchanged():
+    """A batch whose sort interval is 0 runs its autotuner (launch shape of
+    the persistent kernel, then the sort interval from a batched sort and 32
+    timed steps) as part of the run; the particles stay those of each case
+    stepped alone with a fixed interval, because neither choice nor the sort
+    order changes a result (exact deposit, id-keyed random numbers)."""
+    cfgs = _sweep_cfgs(3, seed=9)
+    for cfg in cfgs:
+        cfg.pop("sort_interval")                     # 0: the batch's autotuner chooses
+    counts = [40_000, 120_001, 7_000]
+    b = pic.Batch(cfgs, sort_interval=0)
+    singles = []
+    for cfg, n, view in zip(cfgs, counts, b.cases):
+        nn = cfg["n_cells"] + 1
+        c = pic.Case(cfg, sort_interval=8)
+        for sp, T in ((0, 20.0), (1, 400.0)):
+            view.load_profile(sp, n, np.full(nn, 2e14), np.full(nn, T), id_base=0)
+            c.load_profile(sp, n, np.full(nn, 2e14), np.full(nn, T), id_base=0)
+        singles.append(c)
+    b.step(60)
+    b.sync()
+    t = b.tuning()
+    assert t["tuned"] and t["shape"] in (0, 1, 2) and 4 <= t["sort_interval"] <= 1024
+    assert all(x > 0 for x in t["shape_ms"]) and t["sort_ms"] > 0
+    for c in singles:
+        c.step(60)
+    for view, c in zip(b.cases, singles):
+        for s in range(2):
+            pa, pb = view.particles(s), c.particles(s)
+            ia, ib = np.argsort(pa["id"], kind="stable"), np.argsort(pb["id"], kind="stable")
+            for key in ("id", "cell", "off", "vx", "vy", "vz"):
+                assert np.array_equal(pa[key][ia], pb[key][ib]), (s, key)
+            assert np.array_equal(view.clock(s)[ia], c.clock(s)[ib])
+        assert np.array_equal(view.field()[1], c.field()[1])
+        c.close()
+    b.close()
+
+
 def test_cases_of_different_sizes_interleave():
     """Cases with different shared-memory layouts stepped in turn (the kernel's
     dynamic shared-memory cap is shared by all of them)."""
