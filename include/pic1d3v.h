@@ -404,8 +404,8 @@ pic_status pic_sort_by_cell(int32_t n_cells, int64_t n, const int32_t *cell, con
  * every sort_interval steps every case is sorted, one launch per sort kernel
  * and species for all cases.  descs[0].sort_interval > 0 fixes the interval;
  * 0 lets the batch's autotuner choose it and the persistent kernel's launch
- * shape, during the first pic_batch_step of at least 38 steps after the
- * first step (6 steps, two per shape, then one sort and 32 timed steps, all
+ * shape, during the first pic_batch_step of at least 40 steps after the
+ * first step (8 steps, two per shape, then one sort and 32 timed steps, all
  * part of the run: results do not depend on the choices; see
  * pic_batch_tuning).  All cases must share the boundary kind, the number of species and
  * the collision model of each species (none, tables, or constant frequency
@@ -433,13 +433,13 @@ pic_status pic_batch_set_stages(pic_batch *b, int stages);
 pic_status pic_batch_set_own_threshold(pic_batch *b, int64_t particles);
 /* The batch's launch choices: *shape (0: 512-thread CTAs, one per SM, chunks
  * of one particle with three in flight; 1: two 512-thread CTAs per SM, chunks
- * of two, one ahead; 2: 1024-thread CTAs, chunks of two, one ahead),
- * *sort_interval, *tuned (1 once the autotuner ran), and its measurements:
- * shape_ms[3] (mean step time per shape) and *sort_ms (one batched sort).
- * Any output pointer may be NULL. */
+ * of two, one ahead; 2: 1024-thread CTAs, chunks of two, one ahead; 3:
+ * 640-thread CTAs, chunks of two, one ahead), *sort_interval, *tuned (1 once
+ * the autotuner ran), and its measurements: shape_ms[4] (mean step time per
+ * shape) and *sort_ms (one batched sort).  Any output pointer may be NULL. */
 pic_status pic_batch_tuning(pic_batch *b, int *shape, int *sort_interval, int *tuned, float *shape_ms,
                             float *sort_ms);
-/* Fix the launch shape of the batch kernel (0, 1 or 2, as pic_batch_tuning
+/* Fix the launch shape of the batch kernel (0 to 3, as pic_batch_tuning
  * describes them); the autotuner then does not run (with sort_interval 0 the
  * interval stays 64).  Results do not depend on it.  Errors: PIC_EINVAL. */
 pic_status pic_batch_set_shape(pic_batch *b, int shape);

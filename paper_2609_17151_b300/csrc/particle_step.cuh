@@ -281,16 +281,23 @@ __device__ __forceinline__ void emit_secondary(const StepConst &P, uint32_t id, 
 // counter is a native 32-bit shared atomic (a 64-bit shared add measured
 // several times slower where the lanes of a warp share a cell, as sorted
 // particles do).  At the flush, node c gets n 2^32 - F and node c+1 gets F
-// (exact).  A counter pair holds at least 65536 particles per cell between
-// flushes, and a CTA deposits at most kFlushParticles particles between them.
+// (exact).  A counter pair holds 65536 particles of one cell (the sums of
+// f >> 16 and f & 0xFFFF stay below 2^32); the histogram is flushed when a
+// cell passes kCellFlush of them (the count's atomic reports it), checked
+// every kFlushCheckTiles tiles, during which a cell gains at most
+// kFlushCheckTiles * 1024 * 4 = 32768 more (the largest tile: 1024 chunks of
+// four), so no cell exceeds 65536.  Particles spread over many cells
+// (unsorted) are thus flushed once per work item.
 struct DepHist {
     unsigned *cnt, *fhi, *flo;
+    unsigned *full;                                     // set when a cell passed kCellFlush
 };
-constexpr int kFlushParticles = 65536;
+constexpr unsigned kCellFlush = 32768;
+constexpr int kFlushCheckTiles = 8;
 
 __device__ __forceinline__ void hist_run(const DepHist &h, int c, unsigned n, unsigned long long sf)
 {
-    atomicAdd(&h.cnt[c], n);
+    if (atomicAdd(&h.cnt[c], n) + n > kCellFlush) *h.full = 1u;
     atomicAdd(&h.fhi[c], (unsigned)(sf >> 16));
     atomicAdd(&h.flo[c], (unsigned)(sf & 0xFFFFull));
 }
@@ -298,7 +305,8 @@ __device__ __forceinline__ void hist_run(const DepHist &h, int c, unsigned n, un
 // Add the CTA's histogram to the global deposit and clear it.
 __device__ __forceinline__ void hist_flush(const DepHist &h, int N, unsigned long long *R)
 {
-    __syncthreads();
+    __syncthreads();                                   // every hist_run of the CTA done
+    if (threadIdx.x == 0) *h.full = 0u;
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
         const unsigned n = h.cnt[c];
         if (n) {
@@ -400,6 +408,7 @@ struct StepShared {
     unsigned tile_abort;                                // a tile wait gave up: stop streaming
     unsigned s_cnt[2 + 2 * kMaxProc];                   // candidates, per process, ionizations
     unsigned s_abs[2], s_see, s_see0, s_renew;
+    unsigned hist_full;                                 // a deposit counter passed kCellFlush
     float s_red[2][kStepThreads / 32];
 };
 
@@ -430,7 +439,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     const StepSmem L(N, MCC == 1 ? S.nproc : 0, blockDim.x, n_stages, kArr);
     const float2 *Es = reinterpret_cast<const float2 *>(smem + L.e_off);
     const DepHist hist{reinterpret_cast<unsigned *>(smem + L.h_off), reinterpret_cast<unsigned *>(smem + L.h_off) + N,
-                       reinterpret_cast<unsigned *>(smem + L.h_off) + 2 * N};
+                       reinterpret_cast<unsigned *>(smem + L.h_off) + 2 * N, &sh.hist_full};
     float *nus = reinterpret_cast<float *>(smem + L.nu_off);
     float *hen = reinterpret_cast<float *>(smem + L.en_off);
     unsigned *heepf = reinterpret_cast<unsigned *>(smem + L.eepf_off);
@@ -465,7 +474,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     if (diag) for (int j = tid; j < kEepfBins; j += blockDim.x) heepf[j] = 0u;
     if (tid < 2 + 2 * kMaxProc) s_cnt[tid] = 0u;
     if (tid < 2) s_abs[tid] = 0u;
-    if (tid == 0) { sh.s_see = 0u; sh.s_see0 = 0u; sh.s_renew = 0u; }
+    if (tid == 0) { sh.s_see = 0u; sh.s_see0 = 0u; sh.s_renew = 0u; sh.hist_full = 0u; }
     const bool staged = mbar_wait_bounded(&sh.mbar, ctrl, parity, P.wait_polls);
     parity ^= 1u;
     if (!__syncthreads_and(staged)) return;
@@ -493,9 +502,6 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     const int T = blockDim.x;                           // chunks per tile
     const int n_warps = T >> 5;
     const int n_tiles = (int)((end - beg + T - 1) / T);
-    // histogram counter range: at most kFlushParticles particles between
-    // flushes (counted for chunks of four, the largest CH)
-    const int tiles_per_flush = max(1, (kFlushParticles / 4) / T);
     unsigned char *const tiles = smem + L.st_off;
     // tile k -> buffer b = k mod n_stages: one bulk copy per array, one mbarrier per buffer
     auto issue_tile = [&](int k, int b) {
@@ -512,7 +518,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     if (n_stages > 0 && tid == 0)
         for (int k = 0; k < n_tiles && k < n_stages; ++k) issue_tile(k, k);
 
-    int flush_left = tiles_per_flush, b = 0;
+    int check_left = kFlushCheckTiles, b = 0;
     constexpr int D = PIPE ? DDEPTH : 1;
     Chunk<CH> nx[D] = {};                               // PIPE: the next D chunks, loads in flight
     if (PIPE) {
@@ -521,11 +527,11 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             if ((unsigned)(d * T + tid) < n_ch) load_chunk<CH, LOAD_ID, AXIAL>(nx[d], Bi, (unsigned)(d * T + tid) * CH);
     }
     for (int k = 0; k < n_tiles; ++k) {
-        if (flush_left == 0) {
-            hist_flush(hist, N, R_cta);
-            flush_left = tiles_per_flush;
+        if (check_left == 0) {                           // uniform over the CTA
+            check_left = kFlushCheckTiles;
+            if (__syncthreads_or(sh.hist_full != 0u)) hist_flush(hist, N, R_cta);
         }
-        --flush_left;
+        --check_left;
         const unsigned ci = (unsigned)(k * T + tid);                          // chunk within the item
         bool live_chunk = ci < n_ch;
         if (n_stages > 0) {
@@ -843,12 +849,14 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_particle_step(const __grid_
 //      one particle with three in flight per thread;
 //   1: 512-thread CTAs, two per SM (64 registers), chunks of two, one ahead;
 //   2: 1024-thread CTAs, one per SM (64 registers), chunks of two, one ahead
-//      (the single-case kernels' shape).
+//      (the single-case kernels' shape);
+//   3: 640-thread CTAs, one per SM (96 registers), chunks of two, one ahead.
 template <int SHAPE> struct BatchShape;
 template <> struct BatchShape<0> { static constexpr int threads = 512, minb = 1, chunk = 1, depth = 3; };
 template <> struct BatchShape<1> { static constexpr int threads = 512, minb = 2, chunk = 2, depth = 1; };
 template <> struct BatchShape<2> { static constexpr int threads = 1024, minb = 1, chunk = 2, depth = 1; };
-constexpr int kBatchShapes = 3;
+template <> struct BatchShape<3> { static constexpr int threads = 640, minb = 1, chunk = 2, depth = 1; };
+constexpr int kBatchShapes = 4;
 
 // Out-of-line item for the batch kernel: each species' body keeps its own
 // register allocation instead of the union of both.

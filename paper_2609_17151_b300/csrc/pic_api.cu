@@ -1746,7 +1746,7 @@ struct pic_batch {
 
 namespace {
 
-constexpr long long kItemParticles = 131072;      // largest work item
+constexpr long long kItemParticles = 262144;      // largest work item
 constexpr long long kMinItemParticles = 16384;    // smallest work item when splitting for balance
 
 template <bool PER, int M0, int M1, bool STAGED, int SHAPE>
@@ -1776,6 +1776,7 @@ cudaError_t batch_step_t(pic_batch *b)
     if (b->run_stages > 0) return batch_step_k<PER, M0, M1, true, 0>(b);
     if (b->shape == 1) return batch_step_k<PER, M0, M1, false, 1>(b);
     if (b->shape == 2) return batch_step_k<PER, M0, M1, false, 2>(b);
+    if (b->shape == 3) return batch_step_k<PER, M0, M1, false, 3>(b);
     return batch_step_k<PER, M0, M1, false, 0>(b);
 }
 
@@ -1881,7 +1882,7 @@ pic_status batch_plan(pic_batch *b)
         else shared_total += n;
     }
     (void)total;
-    const long long target_items = 4LL * 2 * c0->num_sms;
+    const long long target_items = 3LL * c0->num_sms;
     const long long item_particles =
         std::min(kItemParticles, std::max(kMinItemParticles, (shared_total + target_items - 1) / target_items));
     size_t next_own = 0;
@@ -1903,6 +1904,12 @@ pic_status batch_plan(pic_batch *b)
             for (int k = 0; k < nk; ++k) items.push_back(BatchItem{(int)i, s, k, nk});
         }
     }
+    // largest items first: CTAs take them in list order, so the small ones fill the tail
+    std::stable_sort(items.begin(), items.end(), [&](const BatchItem &a, const BatchItem &b2) {
+        const long long na = (long long)hs[(size_t)a.case_idx].n_active[a.species] / a.nk;
+        const long long nb = (long long)hs[(size_t)b2.case_idx].n_active[b2.species] / b2.nk;
+        return na > nb;
+    });
     // tile buffers: as many as the largest case leaves room for (same for all cases)
     int stages = b->stages;
     for (size_t i = 0; i < nc; ++i) {
@@ -2193,7 +2200,7 @@ pic_status pic_batch_tuning(pic_batch *b, int *shape, int *sort_interval, int *t
 
 pic_status pic_batch_set_shape(pic_batch *b, int shape)
 {
-    if (!b || shape < 0 || shape >= kBatchShapes) return fail(PIC_EINVAL, "shape must be 0, 1 or 2");
+    if (!b || shape < 0 || shape >= kBatchShapes) return fail(PIC_EINVAL, "shape must be in [0, 3]");
     b->shape = shape;
     b->tuned = true;                                 // a fixed shape: the autotuner does not run
     batch_drop_graph(b);

@@ -536,7 +536,7 @@ class Batch:
     def tuning(self):
         """Launch shape, sort interval, whether the autotuner ran, and its timings."""
         sh, k, tu, sm = C.c_int(), C.c_int(), C.c_int(), C.c_float()
-        ms = (C.c_float * 3)()
+        ms = (C.c_float * 4)()
         check(lib.pic_batch_tuning(self.h, C.byref(sh), C.byref(k), C.byref(tu), ms, C.byref(sm)))
         return dict(shape=sh.value, sort_interval=k.value, tuned=bool(tu.value), shape_ms=list(ms),
                     sort_ms=sm.value)

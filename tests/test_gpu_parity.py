@@ -774,7 +774,7 @@ def test_batch_autotuner_and_batched_sort_leave_results_unchanged():
     b.step(60)
     b.sync()
     t = b.tuning()
-    assert t["tuned"] and t["shape"] in (0, 1, 2) and 4 <= t["sort_interval"] <= 1024
+    assert t["tuned"] and t["shape"] in (0, 1, 2, 3) and 4 <= t["sort_interval"] <= 1024
     assert all(x > 0 for x in t["shape_ms"]) and t["sort_ms"] > 0
     for c in singles:
         c.step(60)
