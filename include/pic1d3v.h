@@ -438,7 +438,18 @@ pic_status pic_batch_set_own_threshold(pic_batch *b, int64_t particles);
  * the autotuner ran), and its measurements: shape_ms[4] (mean step time per
  * shape) and *sort_ms (one batched sort).  Any output pointer may be NULL. */
 pic_status pic_batch_tuning(pic_batch *b, int *shape, int *sort_interval, int *tuned, float *shape_ms,
-                            float *sort_ms);
+                            float *sort_ms, float *step_ms);
+/* (step_ms[32]: the 32 steps the autotuner timed after its sort, in order.) */
+/* Run the autotuner again at the next pic_batch_step of at least 40 steps
+ * (the discharge of a sweep changes over its first RF cycles, and with it the
+ * cost of lost cell order). */
+pic_status pic_batch_retune(pic_batch *b);
+/* Leave case i out of the batch's steps (frozen != 0) or take it back (0):
+ * a frozen case keeps its state, takes no work item, no sort and no field
+ * solve, so that cases that have reached what the caller waits for (a steady
+ * state, say) stop costing GPU time while the others go on.  Takes effect at
+ * the next pic_batch_step (the batch re-plans).  Errors: PIC_EINVAL. */
+pic_status pic_batch_freeze(pic_batch *b, int i, int frozen);
 /* Fix the launch shape of the batch kernel (0 to 3, as pic_batch_tuning
  * describes them); the autotuner then does not run (with sort_interval 0 the
  * interval stays 64).  Results do not depend on it.  Errors: PIC_EINVAL. */

@@ -1714,6 +1714,8 @@ pic_status pic_sort_by_cell(int32_t n_cells, int64_t n, const int32_t *cell, con
 // ===========================================================================
 struct pic_batch {
     std::vector<pic_case *> cases;
+    std::vector<char> frozen;        // per case: left out of the steps (pic_batch_freeze)
+    std::vector<pic_case *> run;     // the cases the current plan steps, in case order
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     StepConst *d_cases = nullptr;
@@ -1739,6 +1741,7 @@ struct pic_batch {
     int sort_k = 64;
     bool autotune = false, tuned = false;   // sort interval and shape chosen by batch_autotune
     float tune_shape_ms[kBatchShapes] = {}, tune_sort_ms = 0.f, tune_slope_ms = 0.f;
+    float tune_step_ms[32] = {};      // the autotuner's timed steps after its sort (kBatchTuneSteps)
     long long host_step = 0, steps_since_sort = 0;
     cudaGraphExec_t graph[kGraphSteps + 1] = {};   // graph[k]: k batch steps
     long long launches = 0;
@@ -1758,12 +1761,12 @@ cudaError_t batch_step_k(pic_batch *b)
     if (grid == 0) {
         static std::once_flag once;
         static cudaError_t attr_err = cudaSuccess;
-        cudaError_t e = allow_max_step_smem(k, once, attr_err, b->cases[0]->device);
+        cudaError_t e = allow_max_step_smem(k, once, attr_err, b->run[0]->device);
         if (e != cudaSuccess) return e;
         int occ = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, T, b->smem);
         if (e != cudaSuccess) return e;
-        grid = std::max(1, occ) * b->cases[0]->num_sms;
+        grid = std::max(1, occ) * b->run[0]->num_sms;
     }
     k<<<grid, T, b->smem, b->stream>>>(b->d_cases, b->d_items, b->n_items, b->d_next);
     return cudaGetLastError();
@@ -1797,19 +1800,19 @@ cudaError_t batch_particles(pic_batch *b)
 
 int batch_launches_per_step(const pic_batch *b)
 {
-    return (b->n_items > 0 ? 1 : 0) + 1 + (int)b->own.size() * b->cases[0]->d.n_species;
+    return (b->n_items > 0 ? 1 : 0) + 1 + (int)b->own.size() * b->run[0]->d.n_species;
 }
 
 cudaError_t batch_one_step(pic_batch *b)
 {
     cudaError_t e = b->n_items > 0 ? batch_particles(b) : cudaSuccess;
     for (int i : b->own) {
-        pic_case *c = b->cases[(size_t)i];
+        pic_case *c = b->run[(size_t)i];
         if (e == cudaSuccess) e = launch_step_sp<0>(c);
         if (e == cudaSuccess && c->d.n_species > 1) e = launch_step_sp<1>(c);
     }
     if (e != cudaSuccess) return e;
-    k_batch_field<<<(unsigned)(kFieldCluster * b->cases.size()), kFieldThreads, b->cases[0]->field_smem, b->stream>>>(
+    k_batch_field<<<(unsigned)(kFieldCluster * b->run.size()), kFieldThreads, b->run[0]->field_smem, b->stream>>>(
         b->d_cases, 1, b->d_next);
     return cudaGetLastError();
 }
@@ -1819,10 +1822,10 @@ cudaError_t batch_one_step(pic_batch *b)
 // them), over the sort items batch_plan made.
 cudaError_t batch_sort(pic_batch *b)
 {
-    const unsigned nc = (unsigned)b->cases.size();
+    const unsigned nc = (unsigned)b->run.size();
     int maxN = 0;
-    for (pic_case *c : b->cases) maxN = std::max(maxN, c->d.n_cells);
-    for (int sp = 0; sp < b->cases[0]->d.n_species; ++sp) {
+    for (pic_case *c : b->run) maxN = std::max(maxN, c->d.n_cells);
+    for (int sp = 0; sp < b->run[0]->d.n_species; ++sp) {
         const unsigned ni = (unsigned)b->n_sort_items[sp];
         k_batch_cells_count<<<ni, 512, maxN * sizeof(unsigned), b->stream>>>(b->d_cases, b->d_sort_items[sp], sp);
         k_batch_cells_scan<<<nc, 1024, maxN * sizeof(double), b->stream>>>(b->d_cases, sp);
@@ -1844,8 +1847,17 @@ void batch_drop_graph(pic_batch *b)
 
 pic_status batch_plan(pic_batch *b)
 {
-    const size_t nc = b->cases.size();
-    for (pic_case *c : b->cases) {
+    b->run.clear();                                 // the cases this plan steps
+    for (size_t i = 0; i < b->cases.size(); ++i)
+        if (!b->frozen[i]) b->run.push_back(b->cases[i]);
+    batch_drop_graph(b);
+    for (int &g : b->grid_of) g = 0;
+    if (b->run.empty()) {
+        b->planned = true;
+        return PIC_OK;
+    }
+    const size_t nc = b->run.size();
+    for (pic_case *c : b->run) {
         for (int s = 0; s < c->d.n_species; ++s)
             if (!c->loaded[s] && !(s == 1 && c->loaded[0])) return fail(PIC_ESTATE, "a batch case has no particles");
         if (c->need_init) {
@@ -1853,7 +1865,7 @@ pic_status batch_plan(pic_batch *b)
             if (st != PIC_OK) return st;
         }
     }
-    const pic_case *c0 = b->cases[0];
+    const pic_case *c0 = b->run[0];
     b->periodic = c0->d.periodic;
     b->mcc0 = c0->P.sp[0].mcc;
     b->mcc1 = c0->d.n_species > 1 ? c0->P.sp[1].mcc : 0;
@@ -1868,16 +1880,16 @@ pic_status batch_plan(pic_batch *b)
     std::vector<Ctrl> hs(nc);
     long long total = 0;
     for (size_t i = 0; i < nc; ++i) {
-        CU(cudaMemcpyAsync(&hs[i], b->cases[i]->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+        CU(cudaMemcpyAsync(&hs[i], b->run[i]->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
     }
     CU(cudaStreamSynchronize(b->stream));
     for (size_t i = 0; i < nc; ++i)
-        for (int s = 0; s < b->cases[i]->d.n_species; ++s) total += (long long)hs[i].n_active[s];
+        for (int s = 0; s < b->run[i]->d.n_species; ++s) total += (long long)hs[i].n_active[s];
     b->own.clear();
     long long shared_total = 0;
     for (size_t i = 0; i < nc; ++i) {
         long long n = 0;
-        for (int s = 0; s < b->cases[i]->d.n_species; ++s) n += (long long)hs[i].n_active[s];
+        for (int s = 0; s < b->run[i]->d.n_species; ++s) n += (long long)hs[i].n_active[s];
         if (b->own_threshold > 0 && n >= b->own_threshold) b->own.push_back((int)i);
         else shared_total += n;
     }
@@ -1887,7 +1899,7 @@ pic_status batch_plan(pic_batch *b)
         std::min(kItemParticles, std::max(kMinItemParticles, (shared_total + target_items - 1) / target_items));
     size_t next_own = 0;
     for (size_t i = 0; i < nc; ++i) {
-        pic_case *c = b->cases[i];
+        pic_case *c = b->run[i];
         if (c->d.periodic != b->periodic || c->P.sp[0].mcc != b->mcc0 ||
             (c->d.n_species > 1 ? c->P.sp[1].mcc : 0) != b->mcc1)
             return fail(PIC_EINVAL, "batch cases differ in boundary or collision model");
@@ -1913,7 +1925,7 @@ pic_status batch_plan(pic_batch *b)
     // tile buffers: as many as the largest case leaves room for (same for all cases)
     int stages = b->stages;
     for (size_t i = 0; i < nc; ++i) {
-        const pic_case *c = b->cases[i];
+        const pic_case *c = b->run[i];
         for (int s = 0; s < c->d.n_species; ++s) {
             const int np = c->P.sp[s].mcc == 1 ? c->P.sp[s].nproc : 0;
             const int narr = step_arrays(s, b->periodic != 0, c->P.sp[s].mcc);
@@ -1922,7 +1934,7 @@ pic_status batch_plan(pic_batch *b)
         }
     }
     for (size_t i = 0; i < nc; ++i) {
-        const pic_case *c = b->cases[i];
+        const pic_case *c = b->run[i];
         for (int s = 0; s < c->d.n_species; ++s) {
             const int np = c->P.sp[s].mcc == 1 ? c->P.sp[s].nproc : 0;
             const int narr = step_arrays(s, b->periodic != 0, c->P.sp[s].mcc);
@@ -1936,7 +1948,7 @@ pic_status batch_plan(pic_batch *b)
     for (int sp = 0; sp < c0->d.n_species; ++sp) {
         std::vector<SortItem> si;
         for (size_t i = 0; i < nc; ++i) {
-            const long long n = sp < b->cases[i]->d.n_species ? 2 * (long long)hs[i].n_active[sp] : 0;
+            const long long n = sp < b->run[i]->d.n_species ? 2 * (long long)hs[i].n_active[sp] : 0;
             const int nb = (int)std::max<long long>(1, std::min<long long>(2LL * c0->num_sms,
                                                                           (n + kSortItemParticles - 1) / kSortItemParticles));
             for (int k = 0; k < nb; ++k) si.push_back(SortItem{(int)i, k, nb});
@@ -1981,6 +1993,7 @@ pic_status batch_plan(pic_batch *b)
 // The tile pipeline (stages > 0) is left as the caller set it.
 // ---------------------------------------------------------------------------
 constexpr int kBatchShapeRounds = 2, kBatchTuneSteps = 32;
+static_assert(kBatchTuneSteps <= 32, "pic_batch keeps 32 tuner step times");
 constexpr int kBatchTuneTotal = kBatchShapeRounds * kBatchShapes + kBatchTuneSteps;
 
 pic_status batch_autotune(pic_batch *b, int64_t *left)
@@ -2031,13 +2044,14 @@ pic_status batch_autotune(pic_batch *b, int64_t *left)
         float t = 0.f;
         CU(cudaEventElapsedTime(&t, tev[2 * k], tev[2 * k + 1]));
         ty[k] = t;
+        b->tune_step_ms[k] = t;
     }
     const SortIntervalFit fit = choose_sort_interval(ty, kBatchTuneSteps, ts, 4, kMaxSortInterval);
     b->sort_k = std::max(4, std::min(kMaxSortInterval, fit.K));
     b->tune_sort_ms = ts;
     b->tune_slope_ms = (float)fit.slope;
     b->tuned = true;
-    b->launches += (long long)batch_launches_per_step(b) * kBatchTuneTotal + 4LL * b->cases[0]->d.n_species;
+    b->launches += (long long)batch_launches_per_step(b) * kBatchTuneTotal + 4LL * b->run[0]->d.n_species;
     b->host_step += kBatchTuneTotal;
     b->steps_since_sort = kBatchTuneSteps;
     *left -= kBatchTuneTotal;
@@ -2097,6 +2111,7 @@ pic_status pic_batch_create(const pic_case_desc *descs, int n_cases, pic_batch *
             return st;
         }
         b->cases.push_back(c);
+        b->frozen.push_back(0);
     }
     if (cudaMalloc(&b->d_next, sizeof(unsigned)) != cudaSuccess) {
         pic_batch_destroy(b);
@@ -2120,6 +2135,7 @@ pic_status pic_batch_step(pic_batch *b, int64_t n_steps)
         pic_status st = batch_plan(b);
         if (st != PIC_OK) return st;
     }
+    if (b->run.empty()) return PIC_OK;                // every case frozen
     int64_t left = n_steps;
     while (left > 0) {
         if (b->autotune && !b->tuned && b->host_step > 0 && left >= kBatchTuneTotal) {
@@ -2130,7 +2146,7 @@ pic_status pic_batch_step(pic_batch *b, int64_t n_steps)
         const int K = b->sort_k;
         if (b->steps_since_sort >= K) {
             CU(batch_sort(b));
-            b->launches += 4LL * b->cases[0]->d.n_species;
+            b->launches += 4LL * b->run[0]->d.n_species;
             b->steps_since_sort = 0;
         }
         // steps before the next sort, replayed as one graph (every length up
@@ -2158,7 +2174,7 @@ pic_status pic_batch_step(pic_batch *b, int64_t n_steps)
     }
     if (b->steps_since_sort >= b->sort_k) {
         CU(batch_sort(b));
-        b->launches += 4LL * b->cases[0]->d.n_species;
+        b->launches += 4LL * b->run[0]->d.n_species;
         b->steps_since_sort = 0;
     }
     return PIC_OK;
@@ -2186,15 +2202,35 @@ pic_status pic_batch_set_own_threshold(pic_batch *b, int64_t particles)
     return PIC_OK;
 }
 
-pic_status pic_batch_tuning(pic_batch *b, int *shape, int *sort_interval, int *tuned, float *shape_ms, float *sort_ms)
+pic_status pic_batch_tuning(pic_batch *b, int *shape, int *sort_interval, int *tuned, float *shape_ms, float *sort_ms,
+                            float *step_ms)
 {
     if (!b) return fail(PIC_EINVAL, "null batch");
+    if (step_ms)
+        for (int k = 0; k < kBatchTuneSteps; ++k) step_ms[k] = b->tune_step_ms[k];
     if (shape) *shape = b->shape;
     if (sort_interval) *sort_interval = b->sort_k;
     if (tuned) *tuned = b->tuned ? 1 : 0;
     if (shape_ms)
         for (int k = 0; k < kBatchShapes; ++k) shape_ms[k] = b->tune_shape_ms[k];
     if (sort_ms) *sort_ms = b->tune_sort_ms;
+    return PIC_OK;
+}
+
+pic_status pic_batch_freeze(pic_batch *b, int i, int frozen)
+{
+    if (!b || i < 0 || i >= (int)b->cases.size()) return fail(PIC_EINVAL, "case index out of range");
+    CU(cudaStreamSynchronize(b->stream));
+    b->frozen[(size_t)i] = frozen ? 1 : 0;
+    b->planned = false;                              // re-planned at the next step
+    return PIC_OK;
+}
+
+pic_status pic_batch_retune(pic_batch *b)
+{
+    if (!b) return fail(PIC_EINVAL, "null batch");
+    b->autotune = true;
+    b->tuned = false;
     return PIC_OK;
 }
 

@@ -134,7 +134,9 @@ def _load_library():
     lib.pic_batch_set_own_threshold.argtypes = [vp, i64]
     lib.pic_batch_set_shape.argtypes = [vp, C.c_int]
     lib.pic_batch_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                     C.POINTER(C.c_float), C.POINTER(C.c_float)]
+                                     C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float)]
+    lib.pic_batch_retune.argtypes = [vp]
+    lib.pic_batch_freeze.argtypes = [vp, C.c_int, C.c_int]
     fp = C.POINTER(C.c_float)
     lib.pic_mlp_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(vp)]
     lib.pic_mlp_set_normalization.argtypes = [vp, fp, fp, fp, fp]
@@ -536,10 +538,16 @@ class Batch:
     def tuning(self):
         """Launch shape, sort interval, whether the autotuner ran, and its timings."""
         sh, k, tu, sm = C.c_int(), C.c_int(), C.c_int(), C.c_float()
-        ms = (C.c_float * 4)()
-        check(lib.pic_batch_tuning(self.h, C.byref(sh), C.byref(k), C.byref(tu), ms, C.byref(sm)))
+        ms, st = (C.c_float * 4)(), (C.c_float * 32)()
+        check(lib.pic_batch_tuning(self.h, C.byref(sh), C.byref(k), C.byref(tu), ms, C.byref(sm), st))
         return dict(shape=sh.value, sort_interval=k.value, tuned=bool(tu.value), shape_ms=list(ms),
-                    sort_ms=sm.value)
+                    sort_ms=sm.value, step_ms=list(st))
+
+    def retune(self):
+        check(lib.pic_batch_retune(self.h))
+
+    def freeze(self, i, frozen=True):
+        check(lib.pic_batch_freeze(self.h, int(i), int(bool(frozen))))
 
     def replan(self):
         """Re-split the work items from the current particle counts before the next step."""

@@ -175,7 +175,7 @@ def ecdi_case(seed: int = 1, n_cells: int = 2048, ppc: int = 2500, length: float
 
 
 def sweep_cases(n_cases: int = 256, seed: int = 2609, freq: float = 13.56e6, n0: float = 2e14,
-                n_range=(5e4, 1e6)):
+                n_range=(5e4, 1e6), steps_per_cycle: int = 1600):
     """Parameter sweep of argon CCPs (uneven sizes): pressure 10-300 mTorr,
     voltage 100-500 V, gap 2-6 cm, 256-2048 cells, 5e4-1e6 particles per
     species, drawn with numpy's Philox bit generator.  Returns the case
@@ -183,7 +183,10 @@ def sweep_cases(n_cases: int = 256, seed: int = 2609, freq: float = 13.56e6, n0:
     particles themselves are sampled on the device (uniform density n0,
     electrons 2 eV, ions at 300 K).  The drive is V0 sin(2 pi f t): it starts
     at zero, so the plasma shields the electrodes as the voltage rises
-    instead of meeting the full vacuum field at t = 0."""
+    instead of meeting the full vacuum field at t = 0.  The step is 1/1600 of
+    the period: at 1/400 the densest cases (300 mTorr, 500 V) ionize until
+    omega_pe dt passes the leapfrog limit of 2 (near 3e16 m^-3) within a few
+    periods, and then grow without bound."""
     rng = np.random.Generator(np.random.Philox(seed))
     cfgs, counts = [], []
     tables = argon_tables()
@@ -195,7 +198,7 @@ def sweep_cases(n_cases: int = 256, seed: int = 2609, freq: float = 13.56e6, n0:
         n = int(rng.uniform(*n_range))
         tg = 300.0
         cfg = dict(
-            name=f"sweep_{i}", periodic=0, n_cells=n_cells, length=gap, dt=1.0 / (freq * 400),
+            name=f"sweep_{i}", periodic=0, n_cells=n_cells, length=gap, dt=1.0 / (freq * steps_per_cycle),
             gas_density=mtorr * 1e-3 * TORR / (K_B * tg), gas_temp=tg, gas_mass=M_AR,
             harmonics=[(freq, volts, -0.5 * math.pi)], see_gamma=0.1, see_temp_ev=1.0,
             species=[dict(q=-E_CHARGE, m=M_E, w=n0 * gap / n), dict(q=E_CHARGE, m=M_AR, w=n0 * gap / n)],

@@ -790,6 +790,45 @@ def test_batch_autotuner_and_batched_sort_leave_results_unchanged():
     b.close()
 
 
+def test_frozen_batch_case_keeps_its_state_and_resumes_exactly():
+    """pic_batch_freeze leaves a case out of the batch's steps: its particles
+    and field do not change while the others go on, and once taken back it
+    continues as if it had been stepped alone for the same number of steps."""
+    cfgs = _sweep_cfgs(3, seed=13)
+    counts = [30_000, 50_001, 20_000]
+    b = pic.Batch(cfgs, sort_interval=8)
+    single = pic.Case(cfgs[1], sort_interval=8)
+    for cfg, n, view in zip(cfgs, counts, b.cases):
+        nn = cfg["n_cells"] + 1
+        for sp, T in ((0, 20.0), (1, 400.0)):
+            view.load_profile(sp, n, np.full(nn, 2e14), np.full(nn, T), id_base=0)
+            if view is b.cases[1]:
+                single.load_profile(sp, n, np.full(nn, 2e14), np.full(nn, T), id_base=0)
+    b.step(10)
+    b.freeze(1)
+    before = b.cases[1].particles(0)
+    phi_before = b.cases[1].field()[0]
+    other_before = b.cases[0].field()[0]
+    b.step(13)
+    b.sync()
+    after = b.cases[1].particles(0)
+    for key in ("id", "cell", "off", "vx"):
+        assert np.array_equal(before[key], after[key]), key
+    assert np.array_equal(phi_before, b.cases[1].field()[0])
+    assert not np.array_equal(other_before, b.cases[0].field()[0])
+    b.freeze(1, False)
+    b.step(7)
+    b.sync()
+    single.step(17)
+    for s in range(2):
+        pa, pb = b.cases[1].particles(s), single.particles(s)
+        ia, ib = np.argsort(pa["id"], kind="stable"), np.argsort(pb["id"], kind="stable")
+        for key in ("id", "cell", "off", "vx", "vy", "vz"):
+            assert np.array_equal(pa[key][ia], pb[key][ib]), (s, key)
+    single.close()
+    b.close()
+
+
 def test_cases_of_different_sizes_interleave():
     """Cases with different shared-memory layouts stepped in turn (the kernel's
     dynamic shared-memory cap is shared by all of them)."""
