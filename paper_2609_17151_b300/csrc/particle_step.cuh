@@ -153,26 +153,59 @@ __device__ void append_particle(const StepConst &P, int sp, int half, int c, flo
     }
 }
 
+// Constants of the per-particle loop, read once per work item.  The
+// single-case kernels take theirs from the kernel parameter (constant bank,
+// free as instruction operands); the batch kernel copies its case's into
+// shared memory, where every shared store or atomic of the loop would force a
+// reload before the next use.  Held in registers, both read them alike.
+struct Hot {
+    float ex_ext, c_e, cEy, cEz, tB[3], sB[3], lam;
+    int rot, nproc;
+    uint32_t key0, key1;
+    float numax, inv_dlog, m_over_2e;
+    float recoil, v_of_sqrt_eps;                        // electrons
+    float mu_over_2e, vt_gas, mfrac, Mfrac;             // ions
+};
+
+__device__ __forceinline__ Hot hot_of(const StepConst &P, const SpConst &S)
+{
+    Hot h;
+    h.ex_ext = P.Ex_ext; h.c_e = S.c_e; h.cEy = S.cEy; h.cEz = S.cEz;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { h.tB[k] = S.tB[k]; h.sB[k] = S.sB[k]; }
+    h.lam = S.lam; h.rot = S.rot; h.nproc = S.nproc;
+    h.key0 = P.key0; h.key1 = P.key1;
+    h.numax = S.numax; h.inv_dlog = P.inv_dlog; h.m_over_2e = S.m_over_2e;
+    h.recoil = S.recoil; h.v_of_sqrt_eps = S.v_of_sqrt_eps;
+    h.mu_over_2e = S.mu_over_2e; h.vt_gas = S.vt_gas; h.mfrac = S.mfrac; h.Mfrac = S.Mfrac;
+    return h;
+}
+
+__device__ __forceinline__ uint4 draw(const Hot &H, uint32_t id, uint32_t step, int sp, uint32_t blk)
+{
+    return philox4x32_10(make_uint4(id, step, ((uint32_t)sp << 16) | blk, 0u), H.key0, H.key1);
+}
+
 // Electron collision candidate (null-collision method): the process from
 // word 1 of the step's block-0 draw r, the direction from words 2-3; v is
 // updated for a real collision.
-__device__ __forceinline__ void collide_electron(const StepConst &P, const float *nus, uint32_t id, uint32_t step,
-                                                 int c, float o, float3 &v, int half_e, int half_i, bool diag,
-                                                 EvCount &ev, const uint4 r)
+__device__ __forceinline__ void collide_electron(const StepConst &P, const Hot &H, const float *nus, uint32_t id,
+                                                 uint32_t step, int c, float o, float3 &v, int half_e, int half_i,
+                                                 bool diag, EvCount &ev, const uint4 r)
 {
     const SpConst &S = P.sp[0];
     ev.cand++;
     const float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
-    const float eps = S.m_over_2e * v2;
-    const float x = u01(r.y) * S.numax;
+    const float eps = H.m_over_2e * v2;
+    const float x = u01(r.y) * H.numax;
     int proc = -1, kind = 0;
     float thr = 0.0f;
     if (S.mcc == 2) {
         proc = 0;
     } else {
-        const GridPos g = grid_pos(eps, P.inv_dlog);
+        const GridPos g = grid_pos(eps, H.inv_dlog);
         float cum = 0.0f;
-        for (int k = 0; k < S.nproc; ++k) {
+        for (int k = 0; k < H.nproc; ++k) {
             cum += nu_at(nus + k * kNGrid, g, eps, S.thr[k]);
             if (x < cum) { proc = k; kind = S.kind[k]; thr = S.thr[k]; break; }
         }
@@ -183,25 +216,25 @@ __device__ __forceinline__ void collide_electron(const StepConst &P, const float
     if (kind == 0) {                                    // elastic, atom at rest
         const float speed = sqrtf(v2);
         const float cchi = speed > 0.0f ? (v.x * n.x + v.y * n.y + v.z * n.z) / speed : 1.0f;
-        const float epsn = eps * (1.0f - S.recoil * (1.0f - cchi));
-        const float sp = S.v_of_sqrt_eps * sqrtf(fmaxf(epsn, 0.0f));
+        const float epsn = eps * (1.0f - H.recoil * (1.0f - cchi));
+        const float sp = H.v_of_sqrt_eps * sqrtf(fmaxf(epsn, 0.0f));
         v = make_float3(sp * n.x, sp * n.y, sp * n.z);
     } else if (kind == 1) {                             // excitation
-        const float sp = S.v_of_sqrt_eps * sqrtf(fmaxf(eps - thr, 0.0f));
+        const float sp = H.v_of_sqrt_eps * sqrtf(fmaxf(eps - thr, 0.0f));
         v = make_float3(sp * n.x, sp * n.y, sp * n.z);
     } else {                                            // ionization: share eps - thr
-        const uint4 a = draw(P, id, step, 0, kBlkAux);
-        const uint4 ids = draw(P, id, step, 0, kBlkChild);
+        const uint4 a = draw(H, id, step, 0, kBlkAux);
+        const uint4 ids = draw(H, id, step, 0, kBlkChild);
         const float avail = fmaxf(eps - thr, 0.0f);
         const float eej = u01(a.x) * avail;
         const float esc = avail - eej;
-        const float sp = S.v_of_sqrt_eps * sqrtf(esc);
+        const float sp = H.v_of_sqrt_eps * sqrtf(esc);
         v = make_float3(sp * n.x, sp * n.y, sp * n.z);
         const float3 ne = iso_dir(u01(a.y), u01(a.z));
-        const float spe = S.v_of_sqrt_eps * sqrtf(eej);
+        const float spe = H.v_of_sqrt_eps * sqrtf(eej);
         append_particle(P, 0, half_e, c, o, spe * ne.x, spe * ne.y, spe * ne.z, ids.x, step, diag);
         if (P.n_species > 1) {
-            const uint4 b = draw(P, id, step, 0, kBlkNewIon);
+            const uint4 b = draw(H, id, step, 0, kBlkNewIon);
             const float2 g01 = box_muller(u01(b.x), u01(b.y));
             const float2 g23 = box_muller(u01(b.z), u01(b.w));
             const float vt = S.vt_newion;
@@ -213,23 +246,23 @@ __device__ __forceinline__ void collide_electron(const StepConst &P, const float
 
 // Ion collision candidate: gas partner from block 1, process from word 1 of
 // the block-0 draw r, centre-of-mass direction from its words 2-3.
-__device__ __forceinline__ void collide_ion(const StepConst &P, const float *nus, uint32_t id, uint32_t step,
-                                            float3 &v, EvCount &ev, const uint4 r)
+__device__ __forceinline__ void collide_ion(const StepConst &P, const Hot &H, const float *nus, uint32_t id,
+                                            uint32_t step, float3 &v, EvCount &ev, const uint4 r)
 {
     const SpConst &S = P.sp[1];
     ev.cand++;
-    const uint4 a = draw(P, id, step, 1, kBlkAux);
+    const uint4 a = draw(H, id, step, 1, kBlkAux);
     const float2 g01 = box_muller(u01(a.x), u01(a.y));
     const float2 g23 = box_muller(u01(a.z), u01(a.w));
-    const float3 vg = make_float3(S.vt_gas * g01.x, S.vt_gas * g01.y, S.vt_gas * g23.x);
+    const float3 vg = make_float3(H.vt_gas * g01.x, H.vt_gas * g01.y, H.vt_gas * g23.x);
     const float3 g = make_float3(v.x - vg.x, v.y - vg.y, v.z - vg.z);
     const float g2 = g.x * g.x + g.y * g.y + g.z * g.z;
-    const float eps = S.mu_over_2e * g2;
-    const float x = u01(r.y) * S.numax;
-    const GridPos gp = grid_pos(eps, P.inv_dlog);
+    const float eps = H.mu_over_2e * g2;
+    const float x = u01(r.y) * H.numax;
+    const GridPos gp = grid_pos(eps, H.inv_dlog);
     float cum = 0.0f;
     int proc = -1, kind = 3;
-    for (int k = 0; k < S.nproc; ++k) {
+    for (int k = 0; k < H.nproc; ++k) {
         cum += nu_at(nus + k * kNGrid, gp, eps, S.thr[k]);
         if (x < cum) { proc = k; kind = S.kind[k]; break; }
     }
@@ -239,9 +272,9 @@ __device__ __forceinline__ void collide_ion(const StepConst &P, const float *nus
         v = vg;
     } else {                                            // isotropic in the centre-of-mass frame
         const float3 n = iso_dir(u01(r.z), u01(r.w));
-        const float f = S.Mfrac * sqrtf(g2);
-        v = make_float3(S.mfrac * v.x + S.Mfrac * vg.x + f * n.x, S.mfrac * v.y + S.Mfrac * vg.y + f * n.y,
-                        S.mfrac * v.z + S.Mfrac * vg.z + f * n.z);
+        const float f = H.Mfrac * sqrtf(g2);
+        v = make_float3(H.mfrac * v.x + H.Mfrac * vg.x + f * n.x, H.mfrac * v.y + H.Mfrac * vg.y + f * n.y,
+                        H.mfrac * v.z + H.Mfrac * vg.z + f * n.z);
     }
 }
 
@@ -319,34 +352,42 @@ __device__ __forceinline__ void hist_flush(const DepHist &h, int N, unsigned lon
     __syncthreads();
 }
 
-// Shared memory layout of the step kernel (bytes, 16-aligned pieces).  With
-// `stages` > 0 the particle tiles (one 4-particle chunk per thread, `narr`
-// arrays of 16 bytes per chunk) pass through `stages` buffers at the end.
+// Deferred draws: entries of a warp's draw queue (slot index within the work
+// item, candidate flag in bit 31).  A chunk of CH particles per lane adds at
+// most 32 CH entries, and the queue runs whenever 32 have gathered, so it
+// never holds more than 32 CH + 31.  0 without collisions.
+__host__ __device__ constexpr int draw_queue_cap(int mcc, int ch) { return mcc != 0 ? 32 * ch + 32 : 0; }
+
+// Shared memory layout of the step kernel (bytes, 16-aligned pieces): node
+// field, deposit histogram, collision table, diagnostic moments, each warp's
+// draw queue (`qcap` 4-byte entries).  With `stages` > 0 the particle tiles
+// (one 4-particle chunk per thread, `narr` arrays of 16 bytes per chunk) pass
+// through `stages` buffers at the end.
 __host__ __device__ inline unsigned align16(unsigned x) { return (x + 15u) & ~15u; }
 __host__ __device__ inline unsigned align128(unsigned x) { return (x + 127u) & ~127u; }
 struct StepSmem {
-    unsigned e_off, h_off, nu_off, en_off, eepf_off, st_off, st_bytes, total;
-    __host__ __device__ StepSmem(int n_cells, int nproc, int threads = 0, int stages = 0, int narr = 0)
+    unsigned e_off, h_off, nu_off, en_off, eepf_off, q_off, st_off, st_bytes, total;
+    __host__ __device__ StepSmem(int n_cells, int nproc, int threads = 0, int stages = 0, int narr = 0,
+                                 int qcap = 0)
     {
         e_off = 0;
         h_off = align16(e_off + (unsigned)n_cells * 8u);
         nu_off = align16(h_off + (unsigned)n_cells * 12u);
         en_off = align16(nu_off + (unsigned)nproc * kNGrid * 4u);
         eepf_off = align16(en_off + (unsigned)(n_cells + 1) * 4u);
-        st_off = align128(eepf_off + kEepfBins * 4u);
+        q_off = align16(eepf_off + kEepfBins * 4u);
+        const unsigned q_end = q_off + (unsigned)(threads / 32) * (unsigned)qcap * 4u;
+        st_off = align128(q_end);
         st_bytes = (unsigned)threads * 16u * (unsigned)narr;      // one stage
-        total = stages > 0 ? st_off + (unsigned)stages * st_bytes : align16(eepf_off + kEepfBins * 4u);
+        total = stages > 0 ? st_off + (unsigned)stages * st_bytes : align16(q_end);
     }
 };
 
 // Particle arrays a step streams: cell (with the collision clock), off, vx,
-// vy, vz, and the id for electrons colliding through tables, a fifth to a
-// half of which are collision candidates every step in a discharge (the id
-// keys their draws; a load per candidate would sit in the dependent path).
-// Every other species reads the id only for the particles that draw random
-// numbers in the step (a candidate, the end of a long gap, secondary
-// emission, axial renewal), one load each.
-__host__ __device__ constexpr int step_arrays(int sp, bool, int mcc) { return (sp == 0 && mcc == 1) ? 6 : 5; }
+// vy, vz.  The id is read only for the particles that draw random numbers in
+// the step (the end of a collision clock, secondary emission, axial
+// renewal), one load each, from the draw queue or in place.
+__host__ __device__ constexpr int step_arrays(int, bool, int) { return 5; }
 
 // Direct-load path: particles per chunk, and how many chunks ahead of the one
 // being computed each thread keeps its loads in flight (register double
@@ -365,7 +406,6 @@ template <> struct VecOf<1> { typedef int I; typedef float F; typedef uint32_t U
 template <int CH> struct Chunk {
     int c[CH];
     float o[CH], vx[CH], vy[CH], vz[CH], z[CH];
-    uint32_t id[CH];
 };
 // vector load / store of CH elements (address aligned to CH elements)
 template <class V, int CH, class T>
@@ -387,7 +427,7 @@ __device__ __forceinline__ void vstore(T *dst, const T (&s)[CH])
 }
 // Chunk starting at element e0 of the arrays of B (cell, off, vx, vy, vz, and
 // id, z when asked).
-template <int CH, bool ID, bool Z>
+template <int CH, bool Z>
 __device__ __forceinline__ void load_chunk(Chunk<CH> &t, const SpeciesBufs &B, unsigned e0)
 {
     typedef VecOf<CH> V;
@@ -396,7 +436,6 @@ __device__ __forceinline__ void load_chunk(Chunk<CH> &t, const SpeciesBufs &B, u
     vload<typename V::F>(t.vx, B.vx + e0);
     vload<typename V::F>(t.vy, B.vy + e0);
     vload<typename V::F>(t.vz, B.vz + e0);
-    if (ID) vload<typename V::U>(t.id, B.id + e0);
     if (Z) vload<typename V::F>(t.z, B.z + e0);
 }
 
@@ -433,10 +472,12 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
                                               long long n_items)
 {
     const SpConst &S = P.sp[SP];
+    const Hot H = hot_of(P, S);
     const int N = P.n_cells;
     constexpr int kArr = step_arrays(SP, PERIODIC, MCC);
     const int n_stages = STAGED ? S.stages : 0;
-    const StepSmem L(N, MCC == 1 ? S.nproc : 0, blockDim.x, n_stages, kArr);
+    constexpr int QCAP = draw_queue_cap(MCC, STAGED ? 4 : DCHUNK);
+    const StepSmem L(N, MCC == 1 ? S.nproc : 0, blockDim.x, n_stages, kArr, QCAP);
     const float2 *Es = reinterpret_cast<const float2 *>(smem + L.e_off);
     const DepHist hist{reinterpret_cast<unsigned *>(smem + L.h_off), reinterpret_cast<unsigned *>(smem + L.h_off) + N,
                        reinterpret_cast<unsigned *>(smem + L.h_off) + 2 * N, &sh.hist_full};
@@ -450,7 +491,6 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     const long long n = (long long)ctrl->n_active[SP];
     constexpr int CH = STAGED ? 4 : DCHUNK;              // particles per chunk
     constexpr bool PIPE = !STAGED && DDEPTH > 0;
-    constexpr bool LOAD_ID = kArr == 6;                 // else ids are read per particle, when it draws
     const long long n_chunks = (n + CH - 1) / CH;
     long long per = (n_chunks + n_items - 1) / n_items;
     per = (per + 31) & ~31ll;
@@ -518,13 +558,57 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     if (n_stages > 0 && tid == 0)
         for (int k = 0; k < n_tiles && k < n_stages; ++k) issue_tile(k, k);
 
+    // Diagnostic moments of a particle at (c, on) with velocity v^{n+1/2}.
+    auto moments = [&](int c, float on, const float3 &v) {
+        const float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
+        const float eps = H.m_over_2e * v2;
+        ke_acc += v2;
+        atomicAdd(&hen[c], eps * (1.0f - on));
+        atomicAdd(&hen[c + 1], eps * on);
+        if (SP == 0) {
+            const float xi = (float)c + on;
+            if (xi >= P.eepf_lo && xi < P.eepf_hi) {
+                const int bin = (int)(eps * 4.0f);
+                if (bin < kEepfBins) atomicAdd(&heepf[bin], 1u);
+            }
+        }
+    };
+    // Deferred draws.  A particle whose collision clock ends this step needs
+    // its random block, a new clock and, if it is a candidate, the collision;
+    // a few percent of the particles do each step, scattered over the lanes.
+    // Run in place, a warp would pass through that code once per chunk slot
+    // whenever any lane needed it, with one or two lanes active.  Instead the
+    // chunk is stored with the pushed state, the particle's slot is queued in
+    // the warp's part of shared memory, and the queue runs 32 at a time, one
+    // per lane, reading the particle back and writing its new clock and
+    // velocity over the stored ones.  The results are the same: the draw is
+    // keyed by the particle and the step, not by the lane that makes it.
+    uint32_t *const Q = reinterpret_cast<uint32_t *>(smem + L.q_off) + warp * QCAP;
+    int qn = 0;                                         // entries queued (warp-uniform)
+    auto run_queue = [&](int j) {                       // entry j of this warp's queue
+        const uint32_t w = Q[j];
+        const uint32_t e = w & 0x7fffffffu;
+        const uint32_t pid = Bi.id[e];
+        const int c = Bi.cell[e] & kCellMask;
+        float3 v = make_float3(Bi.vx[e], Bi.vy[e], Bi.vz[e]);
+        const float on = (diag || (SP == 0 && MCC == 1)) ? Bi.off[e] : 0.0f;   // appends, moments
+        const uint4 r = draw(H, pid, step, SP, kBlkMcc);
+        const uint32_t clk = clock_state(u01(r.x), H.lam);
+        if (w >> 31) {
+            if (SP == 0) collide_electron(P, H, nus, pid, step, c, on, v, half_e, half_i, diag, ev, r);
+            else collide_ion(P, H, nus, pid, step, v, ev, r);
+        }
+        Bi.cell[e] = c | (int)(clk << kCellBits);
+        Bi.vx[e] = v.x; Bi.vy[e] = v.y; Bi.vz[e] = v.z;
+        if (diag) moments(c, on, v);
+    };
     int check_left = kFlushCheckTiles, b = 0;
     constexpr int D = PIPE ? DDEPTH : 1;
     Chunk<CH> nx[D] = {};                               // PIPE: the next D chunks, loads in flight
     if (PIPE) {
 #pragma unroll
         for (int d = 0; d < D; ++d)
-            if ((unsigned)(d * T + tid) < n_ch) load_chunk<CH, LOAD_ID, AXIAL>(nx[d], Bi, (unsigned)(d * T + tid) * CH);
+            if ((unsigned)(d * T + tid) < n_ch) load_chunk<CH, AXIAL>(nx[d], Bi, (unsigned)(d * T + tid) * CH);
     }
     for (int k = 0; k < n_tiles; ++k) {
         if (check_left == 0) {                           // uniform over the CTA
@@ -547,7 +631,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             t = nx[0];
 #pragma unroll
             for (int d = 0; d + 1 < D; ++d) nx[d] = nx[d + 1];
-            if (ci + (unsigned)(D * T) < n_ch) load_chunk<CH, LOAD_ID, AXIAL>(nx[D - 1], Bi, e0 + (unsigned)(D * T * CH));
+            if (ci + (unsigned)(D * T) < n_ch) load_chunk<CH, AXIAL>(nx[D - 1], Bi, e0 + (unsigned)(D * T * CH));
         } else if (live_chunk) {
             if (n_stages > 0) {
                 const unsigned char *tl = tiles + ((size_t)b * kArr * T + tid) * 16u;
@@ -557,9 +641,8 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
                 vload<float4>(t.vx, reinterpret_cast<const float *>(tl + 2 * stride));
                 vload<float4>(t.vy, reinterpret_cast<const float *>(tl + 3 * stride));
                 vload<float4>(t.vz, reinterpret_cast<const float *>(tl + 4 * stride));
-                if (LOAD_ID) vload<uint4>(t.id, reinterpret_cast<const uint32_t *>(tl + 5 * stride));
             } else {
-                load_chunk<CH, LOAD_ID, AXIAL>(t, Bi, e0);
+                load_chunk<CH, AXIAL>(t, Bi, e0);
             }
         }
         if (n_stages > 0) {
@@ -586,17 +669,19 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         float (&za)[CH] = t.z;
         int dc[CH];
         uint32_t df[CH];
+        bool need[CH], cand[CH];                        // clock ended: queue the draw
         const int n_valid = live_chunk ? (int)min((unsigned)CH, item_n - e0) : 0;   // particles of the chunk below n
 #pragma unroll
         for (int q = 0; q < CH; ++q) {
             dc[q] = -1;
             df[q] = 0;
+            need[q] = false;
+            cand[q] = false;
             int c = cc[q];
             if (q >= n_valid || c < 0) continue;
             uint32_t clk = (uint32_t)c >> kCellBits;     // collision clock 2 k + c
             c &= kCellMask;
-            // the particle's id, read when it draws (prefetched with the chunk for LOAD_ID)
-            auto pid_of = [&]() -> uint32_t { return LOAD_ID ? t.id[q] : Bi.id[e0 + q]; };
+            auto pid_of = [&]() -> uint32_t { return Bi.id[e0 + q]; };    // read only when it draws
             float o = oo[q];
             // 1. gather E^n (linear weights), plus the imposed field.  The
             // library is built without implicit multiply-add contraction and
@@ -604,23 +689,23 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             // variant (direct, staged, batched) rounds identically.
             const float2 ep = Es[c];                        // (E_c, E_{c+1})
             const float e_mesh = fmaf(o, ep.y, (1.0f - o) * ep.x);
-            const float ex = e_mesh + P.Ex_ext;
+            const float ex = e_mesh + H.ex_ext;
             // 2. Boris: half kick, rotation, half kick
-            const float hx = S.c_e * ex;
-            float3 vm = make_float3(vx[q] + hx, vy[q] + S.cEy, vz[q] + S.cEz);
+            const float hx = H.c_e * ex;
+            float3 vm = make_float3(vx[q] + hx, vy[q] + H.cEy, vz[q] + H.cEz);
             float3 v;
-            if (S.rot == 0) {                               // no magnetic field: two half kicks
-                v = make_float3(vm.x + hx, vm.y + S.cEy, vm.z + S.cEz);
-            } else if (S.rot == 1) {                        // B along y: rotation in the x-z plane
-                const float vpx = fmaf(-vm.z, S.tB[1], vm.x), vpz = fmaf(vm.x, S.tB[1], vm.z);
-                v = make_float3(fmaf(-vpz, S.sB[1], vm.x) + hx, vm.y + S.cEy, fmaf(vpx, S.sB[1], vm.z) + S.cEz);
+            if (H.rot == 0) {                               // no magnetic field: two half kicks
+                v = make_float3(vm.x + hx, vm.y + H.cEy, vm.z + H.cEz);
+            } else if (H.rot == 1) {                        // B along y: rotation in the x-z plane
+                const float vpx = fmaf(-vm.z, H.tB[1], vm.x), vpz = fmaf(vm.x, H.tB[1], vm.z);
+                v = make_float3(fmaf(-vpz, H.sB[1], vm.x) + hx, vm.y + H.cEy, fmaf(vpx, H.sB[1], vm.z) + H.cEz);
             } else {                                        // v- + v- x t, then v- + v' x s
-                const float3 vp = make_float3(vm.x + fmaf(vm.y, S.tB[2], -(vm.z * S.tB[1])),
-                                              vm.y + fmaf(vm.z, S.tB[0], -(vm.x * S.tB[2])),
-                                              vm.z + fmaf(vm.x, S.tB[1], -(vm.y * S.tB[0])));
-                v = make_float3(vm.x + fmaf(vp.y, S.sB[2], -(vp.z * S.sB[1])) + hx,
-                                vm.y + fmaf(vp.z, S.sB[0], -(vp.x * S.sB[2])) + S.cEy,
-                                vm.z + fmaf(vp.x, S.sB[1], -(vp.y * S.sB[0])) + S.cEz);
+                const float3 vp = make_float3(vm.x + fmaf(vm.y, H.tB[2], -(vm.z * H.tB[1])),
+                                              vm.y + fmaf(vm.z, H.tB[0], -(vm.x * H.tB[2])),
+                                              vm.z + fmaf(vm.x, H.tB[1], -(vm.y * H.tB[0])));
+                v = make_float3(vm.x + fmaf(vp.y, H.sB[2], -(vp.z * H.sB[1])) + hx,
+                                vm.y + fmaf(vp.z, H.sB[0], -(vp.x * H.sB[2])) + H.cEy,
+                                vm.z + fmaf(vp.x, H.sB[1], -(vp.y * H.sB[0])) + H.cEz);
             }
             if (diag) pw_acc += v.x * e_mesh;
             // 3. move
@@ -661,38 +746,20 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             }
             // 5-6. null-collision MCC with v^{n+1/2} at x^{n+1}: the clock counts
             // down; at its end the particle draws (block 0) a fresh gap and, unless
-            // the gap was a cut long one, is a collision candidate; products appended
-            if (MCC != 0 && S.lam > 0.0f) {
+            // the gap was a cut long one, is a collision candidate; products
+            // appended.  The draw is queued (see run_queue).
+            if (MCC != 0 && H.lam > 0.0f) {
                 if (clk >= 2u) {
                     clk -= 2u;
                 } else {
-                    const uint32_t pid = pid_of();
-                    const uint4 r = draw(P, pid, step, SP, kBlkMcc);
-                    const bool cand = (clk & 1u) == 0u;
-                    clk = clock_state(u01(r.x), S.lam);
-                    if (cand) {
-                        if (SP == 0) collide_electron(P, nus, pid, step, c, on, v, half_e, half_i, diag, ev, r);
-                        else collide_ion(P, nus, pid, step, v, ev, r);
-                    }
+                    need[q] = true;
+                    cand[q] = (clk & 1u) == 0u;
                 }
             }
             cc[q] = c | (int)(clk << kCellBits); oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
             dc[q] = c;
             df[q] = __float2uint_rz(on * 4294967296.0f);
-            if (diag) {
-                const float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
-                const float eps = S.m_over_2e * v2;
-                ke_acc += v2;
-                atomicAdd(&hen[c], eps * (1.0f - on));
-                atomicAdd(&hen[c + 1], eps * on);
-                if (SP == 0) {
-                    const float xi = (float)c + on;
-                    if (xi >= P.eepf_lo && xi < P.eepf_hi) {
-                        const int b = (int)(eps * 4.0f);
-                        if (b < kEepfBins) atomicAdd(&heepf[b], 1u);
-                    }
-                }
-            }
+            if (diag && !need[q]) moments(c, on, v);
         }
         // write back (never past n: slots beyond belong to this step's appends)
         if (live_chunk) {
@@ -739,6 +806,26 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         } else if (acc_c >= 0) {
             hist_run(hist, acc_c, acc_n, acc_f);
         }
+        // queue the chunk's clock ends (slot order within the warp), run full batches
+        if (QCAP > 0) {
+            __syncwarp();                               // the chunk's stores, the last run's reads
+            const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                const unsigned m = __ballot_sync(0xffffffffu, need[q]);
+                if (need[q]) Q[qn + __popc(m & lt)] = (e0 + (unsigned)q) | (cand[q] ? 0x80000000u : 0u);
+                qn += __popc(m);
+            }
+            while (qn >= 32) {
+                qn -= 32;
+                __syncwarp();
+                run_queue(qn + lane);
+            }
+        }
+    }
+    if (QCAP > 0 && qn > 0) {                           // the rest of the queue
+        __syncwarp();
+        if (lane < qn) run_queue(lane);
     }
     if (n_stages > 0) {
         __syncthreads();

@@ -277,10 +277,10 @@ cudaError_t allow_max_step_smem(K k, std::once_flag &once, cudaError_t &err, int
 }
 
 // Tile buffers that fit next to the tables: `want`, fewer if shared memory is short.
-int fit_stages(int n_cells, int nproc, int threads, int want, int narr, int limit)
+int fit_stages(int n_cells, int nproc, int threads, int want, int narr, int qcap, int limit)
 {
     int st = std::max(0, std::min(want, kMaxStages));
-    while (st > 0 && StepSmem(n_cells, nproc, threads, st, narr).total > (unsigned)limit) --st;
+    while (st > 0 && StepSmem(n_cells, nproc, threads, st, narr, qcap).total > (unsigned)limit) --st;
     return st;
 }
 
@@ -296,8 +296,14 @@ cudaError_t launch_step_k(pic_case *c, int stages)
     if (e != cudaSuccess) return e;
     const int nproc = MCC == 1 ? c->P.sp[SP].nproc : 0;
     constexpr int narr = step_arrays(SP, PER, MCC);
-    const int threads = c->step_threads[SP];
-    const unsigned smem = StepSmem(c->d.n_cells, nproc, threads, stages, narr).total;
+    constexpr int qcap = draw_queue_cap(MCC, STAGED ? 4 : kDirectChunk);
+    // each warp's draw queue grows the CTA's shared memory: a CTA that does
+    // not fit next to the tables of the largest grids is halved
+    int threads = c->step_threads[SP];
+    while (threads > 64 &&
+           StepSmem(c->d.n_cells, nproc, threads, stages, narr, qcap).total > (unsigned)step_smem_limit(c->device))
+        threads /= 2;
+    const unsigned smem = StepSmem(c->d.n_cells, nproc, threads, stages, narr, qcap).total;
     if (c->step_smem[SP] != smem || c->step_grid[SP] == 0 || c->step_grid_threads[SP] != threads ||
         c->step_grid_stages[SP] != stages) {
         int occ = 0;
@@ -321,7 +327,7 @@ cudaError_t launch_step_t(pic_case *c)
     if (c->P.axial_len > 0.0f) return launch_step_k<SP, PER, MCC, false, true>(c, 0);
     const int nproc = MCC == 1 ? c->P.sp[SP].nproc : 0;
     const int stages = fit_stages(c->d.n_cells, nproc, c->step_threads[SP], c->step_stages[SP],
-                                  step_arrays(SP, PER, MCC), step_smem_limit(c->device));
+                                  step_arrays(SP, PER, MCC), draw_queue_cap(MCC, 4), step_smem_limit(c->device));
     return stages > 0 ? launch_step_k<SP, PER, MCC, true>(c, stages) : launch_step_k<SP, PER, MCC, false>(c, 0);
 }
 
@@ -1735,7 +1741,8 @@ struct pic_batch {
     // rest share the persistent kernel; all field solves share one launch
     long long own_threshold = 0;
     std::vector<int> own;
-    unsigned smem = 0;
+    int max_cells = 0, max_nproc = 0;   // largest grid and table of the cases (shared memory layout)
+    unsigned smem_of[kBatchShapes] = {};
     int grid_of[kBatchShapes] = {};   // persistent grid per launch shape (0 = not computed)
     int shape = 0;                    // launch shape of the batch kernel (BatchShape)
     int sort_k = 64;
@@ -1752,23 +1759,37 @@ namespace {
 constexpr long long kItemParticles = 262144;      // largest work item
 constexpr long long kMinItemParticles = 16384;    // smallest work item when splitting for balance
 
+// Shared memory of a batch launch shape: the largest case's tables, and the
+// draw queues of the shape's warps.
+template <int M0, int M1, bool STAGED, int SHAPE>
+unsigned batch_smem(const pic_batch *b)
+{
+    constexpr int ch = STAGED ? 4 : BatchShape<SHAPE>::chunk;
+    constexpr int qcap = draw_queue_cap(M0, ch) > draw_queue_cap(M1, ch) ? draw_queue_cap(M0, ch)
+                                                                            : draw_queue_cap(M1, ch);
+    return StepSmem(b->max_cells, b->max_nproc, BatchShape<SHAPE>::threads, STAGED ? b->run_stages : 0, 5, qcap)
+        .total;
+}
+
 template <bool PER, int M0, int M1, bool STAGED, int SHAPE>
 cudaError_t batch_step_k(pic_batch *b)
 {
     auto k = k_batch_particle_step<PER, M0, M1, STAGED, SHAPE>;
     constexpr int T = BatchShape<SHAPE>::threads;
+    const unsigned smem = batch_smem<M0, M1, STAGED, SHAPE>(b);
     int &grid = b->grid_of[SHAPE];
-    if (grid == 0) {
+    if (grid == 0 || b->smem_of[SHAPE] != smem) {
         static std::once_flag once;
         static cudaError_t attr_err = cudaSuccess;
         cudaError_t e = allow_max_step_smem(k, once, attr_err, b->run[0]->device);
         if (e != cudaSuccess) return e;
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, T, b->smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, T, smem);
         if (e != cudaSuccess) return e;
         grid = std::max(1, occ) * b->run[0]->num_sms;
+        b->smem_of[SHAPE] = smem;
     }
-    k<<<grid, T, b->smem, b->stream>>>(b->d_cases, b->d_items, b->n_items, b->d_next);
+    k<<<grid, T, smem, b->stream>>>(b->d_cases, b->d_items, b->n_items, b->d_next);
     return cudaGetLastError();
 }
 
@@ -1777,9 +1798,12 @@ template <bool PER, int M0, int M1>
 cudaError_t batch_step_t(pic_batch *b)
 {
     if (b->run_stages > 0) return batch_step_k<PER, M0, M1, true, 0>(b);
-    if (b->shape == 1) return batch_step_k<PER, M0, M1, false, 1>(b);
-    if (b->shape == 2) return batch_step_k<PER, M0, M1, false, 2>(b);
-    if (b->shape == 3) return batch_step_k<PER, M0, M1, false, 3>(b);
+    // a shape whose draw queues do not fit next to the largest case's tables
+    // runs as shape 0 (the fewest warps, chunks of one)
+    const unsigned lim = (unsigned)step_smem_limit(b->run[0]->device);
+    if (b->shape == 1 && batch_smem<M0, M1, false, 1>(b) <= lim) return batch_step_k<PER, M0, M1, false, 1>(b);
+    if (b->shape == 2 && batch_smem<M0, M1, false, 2>(b) <= lim) return batch_step_k<PER, M0, M1, false, 2>(b);
+    if (b->shape == 3 && batch_smem<M0, M1, false, 3>(b) <= lim) return batch_step_k<PER, M0, M1, false, 3>(b);
     return batch_step_k<PER, M0, M1, false, 0>(b);
 }
 
@@ -1872,7 +1896,6 @@ pic_status batch_plan(pic_batch *b)
     const int m = b->mcc0 * 3 + b->mcc1;
     if (m != 0 && m != 4 && m != 6)
         return fail(PIC_EINVAL, "batch supports: no collisions, tables for both species, or constant-frequency electrons");
-    unsigned smem = 0;
     std::vector<BatchItem> items;
     std::vector<StepConst> consts(nc);
     // current particle counts, then slices small enough that every CTA of the
@@ -1930,15 +1953,15 @@ pic_status batch_plan(pic_batch *b)
             const int np = c->P.sp[s].mcc == 1 ? c->P.sp[s].nproc : 0;
             const int narr = step_arrays(s, b->periodic != 0, c->P.sp[s].mcc);
             stages = std::min(stages, fit_stages(c->d.n_cells, np, BatchShape<0>::threads, stages, narr,
-                                                 step_smem_limit(c->device)));
+                                                 draw_queue_cap(c->P.sp[s].mcc, 4), step_smem_limit(c->device)));
         }
     }
+    int max_cells = 0, max_nproc = 0;
     for (size_t i = 0; i < nc; ++i) {
         const pic_case *c = b->run[i];
+        max_cells = std::max(max_cells, c->d.n_cells);
         for (int s = 0; s < c->d.n_species; ++s) {
-            const int np = c->P.sp[s].mcc == 1 ? c->P.sp[s].nproc : 0;
-            const int narr = step_arrays(s, b->periodic != 0, c->P.sp[s].mcc);
-            smem = std::max(smem, StepSmem(c->d.n_cells, np, BatchShape<0>::threads, stages, narr).total);
+            if (c->P.sp[s].mcc == 1) max_nproc = std::max(max_nproc, c->P.sp[s].nproc);
             consts[i].sp[s].stages = stages;
         }
     }
@@ -1975,9 +1998,8 @@ pic_status batch_plan(pic_batch *b)
     CU(cudaMemsetAsync(b->d_next, 0, sizeof(unsigned), b->stream));
     CU(cudaStreamSynchronize(b->stream));
     b->n_items = (int)items.size();
-    if (smem != b->smem)
-        for (int &g : b->grid_of) g = 0;
-    b->smem = smem;
+    b->max_cells = max_cells;
+    b->max_nproc = max_nproc;
     b->planned = true;
     batch_drop_graph(b);
     return PIC_OK;
