@@ -104,9 +104,9 @@ __device__ void block_exclusive_vec(const T (&v)[NV], T (&excl)[NV], T (&total)[
     __syncthreads();
 }
 
-// Poisson's equation (paper §1) and the node field, on a cluster of
-// kFieldCluster CTAs (one SM each), each owning a contiguous slice of nodes,
-// one node per thread.
+// Poisson's equation (paper §1) and the node field, on a cluster of CL CTAs
+// (one SM each; CL a power of two, CL * kFieldThreads > n_cells), each owning
+// a contiguous slice of nodes, one node per thread.
 // (phi_{i-1} - 2 phi_i + phi_{i+1}) / dx^2 = -rho_i / eps0 on the interior
 // nodes; bounded: phi_0 = V(t), phi_N = 0; periodic: neutralised rho, phi_0 = 0
 // on the N-1 interior equations (the one at node 0 then holds), mean of phi
@@ -137,6 +137,7 @@ struct FieldPart {
     unsigned long long r0[2];           // rank 0: raw deposit of node 0 (series-capacitor circuit)
 };
 
+template <int CL>
 __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
 {
     namespace cg = cooperative_groups;
@@ -152,7 +153,7 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
     __shared__ double g_b, g_d0, g_pm, g_phi0, g_qel;
     const int rank = (int)cl.block_rank();
     const int N = P.n_cells, nn = P.n_nodes, tid = threadIdx.x, ns = P.n_species;
-    const int per_cta = (N + 1 + kFieldCluster - 1) / kFieldCluster;   // <= kFieldThreads (n_cells <= 4096)
+    const int per_cta = (N + 1 + CL - 1) / CL;                      // <= kFieldThreads
     const int c_lo = min(rank * per_cta, N + 1), c_hi = min(c_lo + per_cta, N + 1);
     const int i = c_lo + tid;                                       // this thread's node
     const bool own = i < c_hi;
@@ -226,33 +227,33 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
     if (tid < 32) {
         const int lane = tid;
         FieldPart q{};
-        if (lane < kFieldCluster) q = *cl.map_shared_rank(&pub, lane);
+        if (lane < CL) q = *cl.map_shared_rank(&pub, lane);
         const int r_lo = min(lane * per_cta, N + 1), r_hi = min(r_lo + per_cta, N + 1);
-        const long long cnt = (lane < kFieldCluster && min(r_hi, N) > r_lo) ? min(r_hi, N) - r_lo : 0;
+        const long long cnt = (lane < CL && min(r_hi, N) > r_lo) ? min(r_hi, N) - r_lo : 0;
         const u128 k1 = (u128)(cnt * (cnt - 1) / 2);                 // sum over slice i<N of (i - c_lo)
         unsigned long long off[2], segtot[2], alltot[2];
         u128 qoff[2], qn[2], sq[2];
         for (int s = 0; s < 2; ++s) {
             unsigned long long inc = q.seg[s], at = q.all[s];
             const u128 A0 = q.qp[s];
-            for (int o = 1; o < kFieldCluster; o <<= 1) {
+            for (int o = 1; o < CL; o <<= 1) {
                 const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
                 if (lane >= o) inc += y;
                 at += __shfl_xor_sync(0xffffffffu, at, o);
             }
             off[s] = inc - q.seg[s];
-            segtot[s] = __shfl_sync(0xffffffffu, inc, kFieldCluster - 1);
+            segtot[s] = __shfl_sync(0xffffffffu, inc, CL - 1);
             alltot[s] = __shfl_sync(0xffffffffu, at, 0);
             const u128 A = (u128)cnt * off[s] + A0;                 // sum of P_s[m] over the slice's m < N
             u128 ainc = A;
-            for (int o = 1; o < kFieldCluster; o <<= 1) {
+            for (int o = 1; o < CL; o <<= 1) {
                 const u128 y = shfl_up_u128(ainc, o);
                 if (lane >= o) ainc += y;
             }
             qoff[s] = ainc - A;                                     // Q_s[r_lo]
-            qn[s] = shfl_u128(ainc, kFieldCluster - 1);             // Q_s[N]
+            qn[s] = shfl_u128(ainc, CL - 1);                        // Q_s[N]
             u128 B = (u128)cnt * qoff[s] + k1 * off[s] + q.qq[s];   // sum of Q_s[i] over the slice's i < N
-            for (int o = 1; o < kFieldCluster; o <<= 1) {
+            for (int o = 1; o < CL; o <<= 1) {
                 const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, (unsigned long long)B, o);
                 const unsigned long long hi2 = __shfl_xor_sync(0xffffffffu, (unsigned long long)(B >> 64), o);
                 B += ((u128)hi2 << 64) | lo2;
@@ -370,7 +371,12 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
         float t = 0.0f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += fred[w];
         if (any_bad) atomicOr(&ctrl->err, kErrNumeric);
-        if (mode == 1) P.fe_hist[(fe_n % (unsigned long long)P.fe_cap) * kFieldCluster + rank] = (double)t * P.fe_c;
+        if (mode == 1) {                                          // kFieldCluster slots per entry
+            double *fe_slot = P.fe_hist + (fe_n % (unsigned long long)P.fe_cap) * kFieldCluster;
+            fe_slot[rank] = (double)t * P.fe_c;
+            if (rank == 0)
+                for (int r2 = CL; r2 < kFieldCluster; ++r2) fe_slot[r2] = 0.0;
+        }
     }
     cl.barrier_wait();                                            // no CTA leaves while read remotely
     // Every rank has read the drive phases and counts (its global terms come
@@ -406,14 +412,23 @@ __global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldTh
 {
     grid_dep_wait();
     grid_dep_launch();
-    field_solve(P, mode);
+    field_solve<kFieldCluster>(P, mode);
 }
 
-// One cluster per case; also resets the batch work-item counter for the next step.
-__global__ void __cluster_dims__(kFieldCluster, 1, 1) __launch_bounds__(kFieldThreads)
-    k_batch_field(const StepConst *__restrict__ cases, int mode, unsigned *next_item)
+// Smallest power-of-two cluster whose CTAs hold a grid's nodes one per thread.
+__host__ __device__ constexpr int field_cluster_for(int n_cells)
 {
-    field_solve(cases[blockIdx.x / kFieldCluster], mode);
+    return n_cells + 1 <= kFieldThreads ? 1 : n_cells + 1 <= 2 * kFieldThreads ? 2 : n_cells + 1 <= 4 * kFieldThreads ? 4 : 8;
+}
+
+// The batch's field solves, one launch per cluster size: cluster k solves case
+// case_of[k] (the cases whose grids need CL CTAs).  The last launch of the
+// step also resets the batch work-item counter for the next step.
+template <int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kFieldThreads)
+    k_batch_field(const StepConst *__restrict__ cases, const int *__restrict__ case_of, int mode, unsigned *next_item)
+{
+    field_solve<CL>(cases[case_of[blockIdx.x / CL]], mode);
     if (blockIdx.x == 0 && threadIdx.x == 0 && next_item) *next_item = 0u;
 }
 

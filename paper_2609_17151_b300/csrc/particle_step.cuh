@@ -316,17 +316,17 @@ __device__ __forceinline__ void emit_secondary(const StepConst &P, uint32_t id, 
 // particles do).  At the flush, node c gets n 2^32 - F and node c+1 gets F
 // (exact).  A counter pair holds 65536 particles of one cell (the sums of
 // f >> 16 and f & 0xFFFF stay below 2^32); the histogram is flushed when a
-// cell passes kCellFlush of them (the count's atomic reports it), checked
-// every kFlushCheckTiles tiles, during which a cell gains at most
-// kFlushCheckTiles * 1024 * 4 = 32768 more (the largest tile: 1024 chunks of
-// four), so no cell exceeds 65536.  Particles spread over many cells
-// (unsorted) are thus flushed once per work item.
+// cell passes kCellFlush of them (the count's atomic reports it).  The CTA
+// checks the flag (one barrier) every kCellHeadroom / (particles per tile)
+// tiles, during which a cell gains at most kCellHeadroom more, so no cell
+// exceeds 65536.  Particles spread over many cells (unsorted) are thus
+// flushed once per work item.
 struct DepHist {
     unsigned *cnt, *fhi, *flo;
     unsigned *full;                                     // set when a cell passed kCellFlush
 };
 constexpr unsigned kCellFlush = 32768;
-constexpr int kFlushCheckTiles = 8;
+constexpr unsigned kCellHeadroom = 32768;
 
 __device__ __forceinline__ void hist_run(const DepHist &h, int c, unsigned n, unsigned long long sf)
 {
@@ -602,7 +602,8 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         Bi.vx[e] = v.x; Bi.vy[e] = v.y; Bi.vz[e] = v.z;
         if (diag) moments(c, on, v);
     };
-    int check_left = kFlushCheckTiles, b = 0;
+    const int check_every = max(1, (int)(kCellHeadroom / ((unsigned)T * (unsigned)CH)));
+    int check_left = check_every, b = 0;
     constexpr int D = PIPE ? DDEPTH : 1;
     Chunk<CH> nx[D] = {};                               // PIPE: the next D chunks, loads in flight
     if (PIPE) {
@@ -612,7 +613,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     }
     for (int k = 0; k < n_tiles; ++k) {
         if (check_left == 0) {                           // uniform over the CTA
-            check_left = kFlushCheckTiles;
+            check_left = check_every;
             if (__syncthreads_or(sh.hist_full != 0u)) hist_flush(hist, N, R_cta);
         }
         --check_left;
@@ -808,18 +809,25 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         }
         // queue the chunk's clock ends (slot order within the warp), run full batches
         if (QCAP > 0) {
-            __syncwarp();                               // the chunk's stores, the last run's reads
-            const unsigned lt = (1u << lane) - 1u;
+            unsigned m[CH], any = 0u;
 #pragma unroll
             for (int q = 0; q < CH; ++q) {
-                const unsigned m = __ballot_sync(0xffffffffu, need[q]);
-                if (need[q]) Q[qn + __popc(m & lt)] = (e0 + (unsigned)q) | (cand[q] ? 0x80000000u : 0u);
-                qn += __popc(m);
+                m[q] = __ballot_sync(0xffffffffu, need[q]);
+                any |= m[q];
             }
-            while (qn >= 32) {
-                qn -= 32;
-                __syncwarp();
-                run_queue(qn + lane);
+            if (any) {                                  // warp-uniform
+                __syncwarp();                           // the last run's reads before new entries
+                const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+                for (int q = 0; q < CH; ++q) {
+                    if (need[q]) Q[qn + __popc(m[q] & lt)] = (e0 + (unsigned)q) | (cand[q] ? 0x80000000u : 0u);
+                    qn += __popc(m[q]);
+                }
+                while (qn >= 32) {
+                    qn -= 32;
+                    __syncwarp();                       // the entries and the chunk's stores first
+                    run_queue(qn + lane);
+                }
             }
         }
     }
@@ -969,22 +977,24 @@ __global__ void __launch_bounds__(BatchShape<SHAPE>::threads, BatchShape<SHAPE>:
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ StepShared sh;
-    __shared__ int s_item;
+    __shared__ int s_item[2];
     __shared__ StepConst sP;                            // the item's case constants (read like parameters)
     if (threadIdx.x == 0) {
         mbar_init(&sh.mbar, 1);
         for (int b = 0; b < kMaxStages; ++b) { mbar_init(&sh.full[b], 1); sh.tile_rel[b] = 0u; }
         sh.tile_abort = 0u;
     }
+    if (threadIdx.x == 0) s_item[0] = (int)atomicAdd(next_item, 1u);
     __syncthreads();
     unsigned parity = 0, tile_phase = 0;
     int cur_case = -1;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(next_item, 1u);
-        __syncthreads();
-        const int it = s_item;
-        __syncthreads();
+    // The next item's index is taken while this one runs (two slots: the
+    // barrier that ends an item orders every read of one slot before thread 0
+    // writes it again).
+    for (int k = 0;; ++k) {
+        const int it = s_item[k & 1];
         if (it >= n_items) break;
+        if (threadIdx.x == 0) s_item[(k + 1) & 1] = (int)atomicAdd(next_item, 1u);
         const BatchItem w = items[it];
         if (w.case_idx != cur_case) {                   // copy the case's constants into shared memory
             const int *src = reinterpret_cast<const int *>(&cases[w.case_idx]);
@@ -997,6 +1007,7 @@ __global__ void __launch_bounds__(BatchShape<SHAPE>::threads, BatchShape<SHAPE>:
             particle_item_call<0, PERIODIC, MCC0, STAGED, SHAPE>(sP, smem, sh, parity, tile_phase, w.k, w.nk);
         else
             particle_item_call<1, PERIODIC, MCC1, STAGED, SHAPE>(sP, smem, sh, parity, tile_phase, w.k, w.nk);
+        __syncthreads();                                // s_item[(k + 1) & 1] written
     }
 }
 

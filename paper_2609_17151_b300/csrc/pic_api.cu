@@ -1729,6 +1729,8 @@ struct pic_batch {
     SortItem *d_sort_items[2] = {nullptr, nullptr};   // batched sort blocks per species
     int n_sort_items[2] = {0, 0};
     unsigned *d_next = nullptr;
+    int *d_field_cases = nullptr;   // run-case indices grouped by field cluster size (1, 2, 4, 8)
+    int n_field[4] = {}, field_off[4] = {};
     int n_items = 0;
     bool planned = false;
     int periodic = 0, mcc0 = 0, mcc1 = 0;
@@ -1824,7 +1826,9 @@ cudaError_t batch_particles(pic_batch *b)
 
 int batch_launches_per_step(const pic_batch *b)
 {
-    return (b->n_items > 0 ? 1 : 0) + 1 + (int)b->own.size() * b->run[0]->d.n_species;
+    int field = 0;
+    for (int g = 0; g < 4; ++g) field += b->n_field[g] > 0 ? 1 : 0;
+    return (b->n_items > 0 ? 1 : 0) + field + (int)b->own.size() * b->run[0]->d.n_species;
 }
 
 cudaError_t batch_one_step(pic_batch *b)
@@ -1836,9 +1840,22 @@ cudaError_t batch_one_step(pic_batch *b)
         if (e == cudaSuccess && c->d.n_species > 1) e = launch_step_sp<1>(c);
     }
     if (e != cudaSuccess) return e;
-    k_batch_field<<<(unsigned)(kFieldCluster * b->run.size()), kFieldThreads, b->run[0]->field_smem, b->stream>>>(
-        b->d_cases, 1, b->d_next);
-    return cudaGetLastError();
+    // one launch per cluster size, each cluster as small as its case's grid allows
+    const unsigned fsm = b->run[0]->field_smem;
+    unsigned *reset = b->d_next;
+    for (int g = 0; g < 4; ++g) {
+        const int n = b->n_field[g];
+        if (n == 0) continue;
+        const int *cl_cases = b->d_field_cases + b->field_off[g];
+        if (g == 0) k_batch_field<1><<<(unsigned)n, kFieldThreads, fsm, b->stream>>>(b->d_cases, cl_cases, 1, reset);
+        if (g == 1) k_batch_field<2><<<(unsigned)(2 * n), kFieldThreads, fsm, b->stream>>>(b->d_cases, cl_cases, 1, reset);
+        if (g == 2) k_batch_field<4><<<(unsigned)(4 * n), kFieldThreads, fsm, b->stream>>>(b->d_cases, cl_cases, 1, reset);
+        if (g == 3) k_batch_field<8><<<(unsigned)(8 * n), kFieldThreads, fsm, b->stream>>>(b->d_cases, cl_cases, 1, reset);
+        reset = nullptr;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // The counting sort of every case, one launch per kernel and species (the
@@ -1988,8 +2005,20 @@ pic_status batch_plan(pic_batch *b)
     b->run_stages = stages;
     if (b->d_cases) cudaFree(b->d_cases);
     if (b->d_items) cudaFree(b->d_items);
+    if (b->d_field_cases) cudaFree(b->d_field_cases);
     b->d_cases = nullptr;
     b->d_items = nullptr;
+    b->d_field_cases = nullptr;
+    // field solves grouped by cluster size
+    std::vector<int> fcases;
+    for (int g = 0; g < 4; ++g) {
+        b->field_off[g] = (int)fcases.size();
+        for (size_t i = 0; i < nc; ++i)
+            if (field_cluster_for(b->run[i]->d.n_cells) == (1 << g)) fcases.push_back((int)i);
+        b->n_field[g] = (int)fcases.size() - b->field_off[g];
+    }
+    CU(cudaMalloc(&b->d_field_cases, fcases.size() * sizeof(int)));
+    CU(cudaMemcpyAsync(b->d_field_cases, fcases.data(), fcases.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     CU(cudaMalloc(&b->d_cases, nc * sizeof(StepConst)));
     CU(cudaMalloc(&b->d_items, std::max<size_t>(1, items.size()) * sizeof(BatchItem)));
     CU(cudaMemcpyAsync(b->d_cases, consts.data(), nc * sizeof(StepConst), cudaMemcpyHostToDevice, b->stream));
@@ -2282,6 +2311,7 @@ pic_status pic_batch_destroy(pic_batch *b)
     for (pic_case *c : b->cases) pic_destroy(c);
     if (b->d_cases) cudaFree(b->d_cases);
     if (b->d_items) cudaFree(b->d_items);
+    if (b->d_field_cases) cudaFree(b->d_field_cases);
     for (SortItem *p : b->d_sort_items)
         if (p) cudaFree(p);
     if (b->d_next) cudaFree(b->d_next);
