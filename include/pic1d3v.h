@@ -431,12 +431,16 @@ pic_status pic_batch_set_stages(pic_batch *b, int stages);
  * solve stays in the one batched launch.  0 = every case in the persistent
  * kernel (the default).  Results do not depend on it.  Errors: PIC_EINVAL. */
 pic_status pic_batch_set_own_threshold(pic_batch *b, int64_t particles);
-/* The batch's launch choices: *shape (0: 512-thread CTAs, one per SM, chunks
- * of one particle with three in flight; 1: two 512-thread CTAs per SM, chunks
- * of two, one ahead; 2: 1024-thread CTAs, chunks of two, one ahead; 3:
- * 640-thread CTAs, chunks of two, one ahead), *sort_interval, *tuned (1 once
- * the autotuner ran), and its measurements: shape_ms[4] (mean step time per
- * shape) and *sort_ms (one batched sort).  Any output pointer may be NULL. */
+/* The batch's launch choices: *shape (the persistent kernel, CTAs taking work
+ * items from a counter: 0: 512-thread CTAs, one per SM, chunks of one
+ * particle with three in flight; 1: two 512-thread CTAs per SM, chunks of
+ * two, one ahead; 2: 1024-thread CTAs, chunks of two, one ahead; 3:
+ * 640-thread CTAs, chunks of two, one ahead; or one CTA per work item, the
+ * items and the cases' push constants in the kernel parameter, up to 256
+ * cases and one species per launch: 4: 1024-thread CTAs, 5: 640-thread
+ * CTAs), *sort_interval, *tuned (1 once the autotuner ran), and its
+ * measurements: shape_ms[6] (mean step time per shape) and *sort_ms (one
+ * batched sort).  Any output pointer may be NULL. */
 pic_status pic_batch_tuning(pic_batch *b, int *shape, int *sort_interval, int *tuned, float *shape_ms,
                             float *sort_ms, float *step_ms);
 /* (step_ms[32]: the 32 steps the autotuner timed after its sort, in order.) */
@@ -450,7 +454,7 @@ pic_status pic_batch_retune(pic_batch *b);
  * state, say) stop costing GPU time while the others go on.  Takes effect at
  * the next pic_batch_step (the batch re-plans).  Errors: PIC_EINVAL. */
 pic_status pic_batch_freeze(pic_batch *b, int i, int frozen);
-/* Fix the launch shape of the batch kernel (0 to 3, as pic_batch_tuning
+/* Fix the launch shape of the batch kernel (0 to 5, as pic_batch_tuning
  * describes them); the autotuner then does not run (with sort_interval 0 the
  * interval stays 64).  Results do not depend on it.  Errors: PIC_EINVAL. */
 pic_status pic_batch_set_shape(pic_batch *b, int shape);

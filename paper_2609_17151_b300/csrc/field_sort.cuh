@@ -421,6 +421,13 @@ __host__ __device__ constexpr int field_cluster_for(int n_cells)
     return n_cells + 1 <= kFieldThreads ? 1 : n_cells + 1 <= 2 * kFieldThreads ? 2 : n_cells + 1 <= 4 * kFieldThreads ? 4 : 8;
 }
 
+// Threads of a field CTA: one per node of its slice, in whole warps (the
+// block scans and barriers cost in proportion to the warps).
+__host__ __device__ constexpr int field_threads_for(int n_cells, int cl)
+{
+    return ((n_cells + 1 + cl - 1) / cl + 31) / 32 * 32 < 64 ? 64 : ((n_cells + 1 + cl - 1) / cl + 31) / 32 * 32;
+}
+
 // The batch's field solves, one launch per cluster size: cluster k solves case
 // case_of[k] (the cases whose grids need CL CTAs).  The last launch of the
 // step also resets the batch work-item counter for the next step.

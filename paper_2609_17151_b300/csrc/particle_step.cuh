@@ -104,7 +104,7 @@ struct Cell { int c; float o; };
 // `step`: a gap from word 0 of its own block-kBlkGap draw (0 without MCC).
 __device__ __forceinline__ uint32_t first_clock(const StepConst &P, int sp, uint32_t id, uint32_t step)
 {
-    const float lam = P.sp[sp].lam;
+    const float lam = P.push.sp[sp].lam;
     if (!(lam > 0.0f)) return 0u;
     return clock_state(u01(draw(P, id, step, sp, kBlkGap).x), lam);
 }
@@ -153,59 +153,31 @@ __device__ void append_particle(const StepConst &P, int sp, int half, int c, flo
     }
 }
 
-// Constants of the per-particle loop, read once per work item.  The
-// single-case kernels take theirs from the kernel parameter (constant bank,
-// free as instruction operands); the batch kernel copies its case's into
-// shared memory, where every shared store or atomic of the loop would force a
-// reload before the next use.  Held in registers, both read them alike.
-struct Hot {
-    float ex_ext, c_e, cEy, cEz, tB[3], sB[3], lam;
-    int rot, nproc;
-    uint32_t key0, key1;
-    float numax, inv_dlog, m_over_2e;
-    float recoil, v_of_sqrt_eps;                        // electrons
-    float mu_over_2e, vt_gas, mfrac, Mfrac;             // ions
-};
-
-__device__ __forceinline__ Hot hot_of(const StepConst &P, const SpConst &S)
+__device__ __forceinline__ uint4 draw(const CasePush &C, uint32_t id, uint32_t step, int sp, uint32_t blk)
 {
-    Hot h;
-    h.ex_ext = P.Ex_ext; h.c_e = S.c_e; h.cEy = S.cEy; h.cEz = S.cEz;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) { h.tB[k] = S.tB[k]; h.sB[k] = S.sB[k]; }
-    h.lam = S.lam; h.rot = S.rot; h.nproc = S.nproc;
-    h.key0 = P.key0; h.key1 = P.key1;
-    h.numax = S.numax; h.inv_dlog = P.inv_dlog; h.m_over_2e = S.m_over_2e;
-    h.recoil = S.recoil; h.v_of_sqrt_eps = S.v_of_sqrt_eps;
-    h.mu_over_2e = S.mu_over_2e; h.vt_gas = S.vt_gas; h.mfrac = S.mfrac; h.Mfrac = S.Mfrac;
-    return h;
-}
-
-__device__ __forceinline__ uint4 draw(const Hot &H, uint32_t id, uint32_t step, int sp, uint32_t blk)
-{
-    return philox4x32_10(make_uint4(id, step, ((uint32_t)sp << 16) | blk, 0u), H.key0, H.key1);
+    return philox4x32_10(make_uint4(id, step, ((uint32_t)sp << 16) | blk, 0u), C.key0, C.key1);
 }
 
 // Electron collision candidate (null-collision method): the process from
 // word 1 of the step's block-0 draw r, the direction from words 2-3; v is
 // updated for a real collision.
-__device__ __forceinline__ void collide_electron(const StepConst &P, const Hot &H, const float *nus, uint32_t id,
+__device__ __forceinline__ void collide_electron(const StepConst &P, const CasePush &C, const float *nus, uint32_t id,
                                                  uint32_t step, int c, float o, float3 &v, int half_e, int half_i,
                                                  bool diag, EvCount &ev, const uint4 r)
 {
     const SpConst &S = P.sp[0];
     ev.cand++;
     const float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
-    const float eps = H.m_over_2e * v2;
-    const float x = u01(r.y) * H.numax;
+    const float eps = S.m_over_2e * v2;
+    const float x = u01(r.y) * S.numax;
     int proc = -1, kind = 0;
     float thr = 0.0f;
     if (S.mcc == 2) {
         proc = 0;
     } else {
-        const GridPos g = grid_pos(eps, H.inv_dlog);
+        const GridPos g = grid_pos(eps, P.inv_dlog);
         float cum = 0.0f;
-        for (int k = 0; k < H.nproc; ++k) {
+        for (int k = 0; k < S.nproc; ++k) {
             cum += nu_at(nus + k * kNGrid, g, eps, S.thr[k]);
             if (x < cum) { proc = k; kind = S.kind[k]; thr = S.thr[k]; break; }
         }
@@ -216,25 +188,25 @@ __device__ __forceinline__ void collide_electron(const StepConst &P, const Hot &
     if (kind == 0) {                                    // elastic, atom at rest
         const float speed = sqrtf(v2);
         const float cchi = speed > 0.0f ? (v.x * n.x + v.y * n.y + v.z * n.z) / speed : 1.0f;
-        const float epsn = eps * (1.0f - H.recoil * (1.0f - cchi));
-        const float sp = H.v_of_sqrt_eps * sqrtf(fmaxf(epsn, 0.0f));
+        const float epsn = eps * (1.0f - S.recoil * (1.0f - cchi));
+        const float sp = S.v_of_sqrt_eps * sqrtf(fmaxf(epsn, 0.0f));
         v = make_float3(sp * n.x, sp * n.y, sp * n.z);
     } else if (kind == 1) {                             // excitation
-        const float sp = H.v_of_sqrt_eps * sqrtf(fmaxf(eps - thr, 0.0f));
+        const float sp = S.v_of_sqrt_eps * sqrtf(fmaxf(eps - thr, 0.0f));
         v = make_float3(sp * n.x, sp * n.y, sp * n.z);
     } else {                                            // ionization: share eps - thr
-        const uint4 a = draw(H, id, step, 0, kBlkAux);
-        const uint4 ids = draw(H, id, step, 0, kBlkChild);
+        const uint4 a = draw(C, id, step, 0, kBlkAux);
+        const uint4 ids = draw(C, id, step, 0, kBlkChild);
         const float avail = fmaxf(eps - thr, 0.0f);
         const float eej = u01(a.x) * avail;
         const float esc = avail - eej;
-        const float sp = H.v_of_sqrt_eps * sqrtf(esc);
+        const float sp = S.v_of_sqrt_eps * sqrtf(esc);
         v = make_float3(sp * n.x, sp * n.y, sp * n.z);
         const float3 ne = iso_dir(u01(a.y), u01(a.z));
-        const float spe = H.v_of_sqrt_eps * sqrtf(eej);
+        const float spe = S.v_of_sqrt_eps * sqrtf(eej);
         append_particle(P, 0, half_e, c, o, spe * ne.x, spe * ne.y, spe * ne.z, ids.x, step, diag);
         if (P.n_species > 1) {
-            const uint4 b = draw(H, id, step, 0, kBlkNewIon);
+            const uint4 b = draw(C, id, step, 0, kBlkNewIon);
             const float2 g01 = box_muller(u01(b.x), u01(b.y));
             const float2 g23 = box_muller(u01(b.z), u01(b.w));
             const float vt = S.vt_newion;
@@ -246,23 +218,23 @@ __device__ __forceinline__ void collide_electron(const StepConst &P, const Hot &
 
 // Ion collision candidate: gas partner from block 1, process from word 1 of
 // the block-0 draw r, centre-of-mass direction from its words 2-3.
-__device__ __forceinline__ void collide_ion(const StepConst &P, const Hot &H, const float *nus, uint32_t id,
+__device__ __forceinline__ void collide_ion(const StepConst &P, const CasePush &C, const float *nus, uint32_t id,
                                             uint32_t step, float3 &v, EvCount &ev, const uint4 r)
 {
     const SpConst &S = P.sp[1];
     ev.cand++;
-    const uint4 a = draw(H, id, step, 1, kBlkAux);
+    const uint4 a = draw(C, id, step, 1, kBlkAux);
     const float2 g01 = box_muller(u01(a.x), u01(a.y));
     const float2 g23 = box_muller(u01(a.z), u01(a.w));
-    const float3 vg = make_float3(H.vt_gas * g01.x, H.vt_gas * g01.y, H.vt_gas * g23.x);
+    const float3 vg = make_float3(S.vt_gas * g01.x, S.vt_gas * g01.y, S.vt_gas * g23.x);
     const float3 g = make_float3(v.x - vg.x, v.y - vg.y, v.z - vg.z);
     const float g2 = g.x * g.x + g.y * g.y + g.z * g.z;
-    const float eps = H.mu_over_2e * g2;
-    const float x = u01(r.y) * H.numax;
-    const GridPos gp = grid_pos(eps, H.inv_dlog);
+    const float eps = S.mu_over_2e * g2;
+    const float x = u01(r.y) * S.numax;
+    const GridPos gp = grid_pos(eps, P.inv_dlog);
     float cum = 0.0f;
     int proc = -1, kind = 3;
-    for (int k = 0; k < H.nproc; ++k) {
+    for (int k = 0; k < S.nproc; ++k) {
         cum += nu_at(nus + k * kNGrid, gp, eps, S.thr[k]);
         if (x < cum) { proc = k; kind = S.kind[k]; break; }
     }
@@ -272,9 +244,9 @@ __device__ __forceinline__ void collide_ion(const StepConst &P, const Hot &H, co
         v = vg;
     } else {                                            // isotropic in the centre-of-mass frame
         const float3 n = iso_dir(u01(r.z), u01(r.w));
-        const float f = H.Mfrac * sqrtf(g2);
-        v = make_float3(H.mfrac * v.x + H.Mfrac * vg.x + f * n.x, H.mfrac * v.y + H.Mfrac * vg.y + f * n.y,
-                        H.mfrac * v.z + H.Mfrac * vg.z + f * n.z);
+        const float f = S.Mfrac * sqrtf(g2);
+        v = make_float3(S.mfrac * v.x + S.Mfrac * vg.x + f * n.x, S.mfrac * v.y + S.Mfrac * vg.y + f * n.y,
+                        S.mfrac * v.z + S.Mfrac * vg.z + f * n.z);
     }
 }
 
@@ -467,12 +439,12 @@ struct StepShared {
 // Results are written straight back to global memory.
 template <int SP, bool PERIODIC, int MCC, bool STAGED, bool AXIAL, int DCHUNK = kDirectChunk,
           int DDEPTH = kDirectDepth>
-__device__ __forceinline__ void particle_item(const StepConst &P, unsigned char *smem, StepShared &sh,
+__device__ __forceinline__ void particle_item(const StepConst &P, const CasePush &C, unsigned char *smem, StepShared &sh,
                                               unsigned &parity, unsigned &tile_phase, long long k_item,
                                               long long n_items)
 {
     const SpConst &S = P.sp[SP];
-    const Hot H = hot_of(P, S);
+    const SpPush &H = C.sp[SP];                         // push constants (kernel parameter)
     const int N = P.n_cells;
     constexpr int kArr = step_arrays(SP, PERIODIC, MCC);
     const int n_stages = STAGED ? S.stages : 0;
@@ -561,7 +533,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
     // Diagnostic moments of a particle at (c, on) with velocity v^{n+1/2}.
     auto moments = [&](int c, float on, const float3 &v) {
         const float v2 = v.x * v.x + v.y * v.y + v.z * v.z;
-        const float eps = H.m_over_2e * v2;
+        const float eps = S.m_over_2e * v2;
         ke_acc += v2;
         atomicAdd(&hen[c], eps * (1.0f - on));
         atomicAdd(&hen[c + 1], eps * on);
@@ -592,11 +564,11 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
         const int c = Bi.cell[e] & kCellMask;
         float3 v = make_float3(Bi.vx[e], Bi.vy[e], Bi.vz[e]);
         const float on = (diag || (SP == 0 && MCC == 1)) ? Bi.off[e] : 0.0f;   // appends, moments
-        const uint4 r = draw(H, pid, step, SP, kBlkMcc);
+        const uint4 r = draw(C, pid, step, SP, kBlkMcc);
         const uint32_t clk = clock_state(u01(r.x), H.lam);
         if (w >> 31) {
-            if (SP == 0) collide_electron(P, H, nus, pid, step, c, on, v, half_e, half_i, diag, ev, r);
-            else collide_ion(P, H, nus, pid, step, v, ev, r);
+            if (SP == 0) collide_electron(P, C, nus, pid, step, c, on, v, half_e, half_i, diag, ev, r);
+            else collide_ion(P, C, nus, pid, step, v, ev, r);
         }
         Bi.cell[e] = c | (int)(clk << kCellBits);
         Bi.vx[e] = v.x; Bi.vy[e] = v.y; Bi.vz[e] = v.z;
@@ -690,7 +662,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, unsigned char 
             // variant (direct, staged, batched) rounds identically.
             const float2 ep = Es[c];                        // (E_c, E_{c+1})
             const float e_mesh = fmaf(o, ep.y, (1.0f - o) * ep.x);
-            const float ex = e_mesh + H.ex_ext;
+            const float ex = e_mesh + C.ex_ext;
             // 2. Boris: half kick, rotation, half kick
             const float hx = H.c_e * ex;
             float3 vm = make_float3(vx[q] + hx, vy[q] + H.cEy, vz[q] + H.cEz);
@@ -932,7 +904,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_particle_step(const __grid_
         grid_dep_launch();
     }
     unsigned parity = 0, tile_phase = 0;
-    particle_item<SP, PERIODIC, MCC, STAGED, AXIAL>(P, smem, sh, parity, tile_phase, blockIdx.x, gridDim.x);
+    particle_item<SP, PERIODIC, MCC, STAGED, AXIAL>(P, P.push, smem, sh, parity, tile_phase, blockIdx.x, gridDim.x);
     if (SP == 1) {
         grid_dep_launch();
         grid_dep_wait();
@@ -951,7 +923,9 @@ template <> struct BatchShape<0> { static constexpr int threads = 512, minb = 1,
 template <> struct BatchShape<1> { static constexpr int threads = 512, minb = 2, chunk = 2, depth = 1; };
 template <> struct BatchShape<2> { static constexpr int threads = 1024, minb = 1, chunk = 2, depth = 1; };
 template <> struct BatchShape<3> { static constexpr int threads = 640, minb = 1, chunk = 2, depth = 1; };
-constexpr int kBatchShapes = 4;
+// 0-3: the persistent kernel; 4, 5: the grid of work items (k_batch_grid) in
+// the launch shapes of 2 (1024 threads) and 3 (640 threads)
+constexpr int kBatchShapes = 6;
 
 // Out-of-line item for the batch kernel: each species' body keeps its own
 // register allocation instead of the union of both.
@@ -961,7 +935,7 @@ __device__ __noinline__ void particle_item_call(const StepConst &P, unsigned cha
                                                long long n_items)
 {
     particle_item<SP, PERIODIC, MCC, STAGED, false, BatchShape<SHAPE>::chunk, BatchShape<SHAPE>::depth>(
-        P, smem, sh, parity, tile_phase, k_item, n_items);
+        P, P.push, smem, sh, parity, tile_phase, k_item, n_items);
 }
 
 // Many cases in one persistent launch: CTAs take (case, species, slice) work
@@ -1011,11 +985,63 @@ __global__ void __launch_bounds__(BatchShape<SHAPE>::threads, BatchShape<SHAPE>:
     }
 }
 
+// Batched step as a grid of work items, one CTA each, for up to kGridCases
+// cases per launch.  The item list and every case's push constants travel in
+// the kernel parameter: a CTA's item comes from the parameter at blockIdx.x,
+// the same for all its threads, so the particle loop reads its case's push
+// constants from the constant bank, as the single-case kernel reads its own,
+// instead of from shared memory (where they cost an instruction and a
+// register each, and every shared store or atomic of the loop forces a
+// reload).  The other case constants are copied into shared memory once.
+// Items are listed largest first, and the block scheduler hands them to SMs
+// as they free up.
+constexpr int kGridCases = 256;
+constexpr int kGridItems = 1536;
+struct GridTable {
+    uint32_t item[kGridItems];          // case | k << 8 | nk << 19 (k, nk < 2048)
+    CasePush push[kGridCases];
+};
+static_assert(sizeof(GridTable) <= 32764, "a kernel parameter holds at most 32764 bytes");
+
+// One launch per species and table, chained by programmatic dependent
+// launches: a launch lets the next one start as its last CTAs start (the next
+// needs nothing it writes: each species processes its own first n_active
+// slots, appends go beyond them, deposits and counters are atomic) and waits
+// for the previous one before it exits, so that the last launch of a step
+// ends after all of them.
+template <int SP, bool PERIODIC, int MCC, int SHAPE>
+__global__ void __launch_bounds__(BatchShape<SHAPE>::threads, BatchShape<SHAPE>::minb)
+    k_batch_grid(const __grid_constant__ GridTable T, const StepConst *__restrict__ cases, int case0)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ StepShared sh;
+    __shared__ StepConst sP;
+    grid_dep_launch();
+    const uint32_t w = T.item[blockIdx.x];
+    const int ci = (int)(w & 0xFFu);
+    const long long k = (long long)((w >> 8) & 0x7FFu), nk = (long long)(w >> 19);
+    if (threadIdx.x == 0) {
+        mbar_init(&sh.mbar, 1);
+        for (int b = 0; b < kMaxStages; ++b) { mbar_init(&sh.full[b], 1); sh.tile_rel[b] = 0u; }
+        sh.tile_abort = 0u;
+    }
+    {
+        const int *src = reinterpret_cast<const int *>(&cases[case0 + ci]);
+        int *dst = reinterpret_cast<int *>(&sP);
+        for (int j = threadIdx.x; j < (int)(sizeof(StepConst) / sizeof(int)); j += blockDim.x) dst[j] = src[j];
+    }
+    __syncthreads();
+    unsigned parity = 0, tile_phase = 0;
+    particle_item<SP, PERIODIC, MCC, false, false, BatchShape<SHAPE>::chunk, BatchShape<SHAPE>::depth>(
+        sP, T.push[ci], smem, sh, parity, tile_phase, k, nk);
+    grid_dep_wait();
+}
+
 // Leapfrog start: v(0) -> v(-dt/2) by a Boris step of -dt/2 in E^0.
 template <int SP>
 __global__ void k_rewind(const __grid_constant__ StepConst P)
 {
-    const SpConst &S = P.sp[SP];
+    const SpPush &S = P.push.sp[SP];
     const SpeciesBufs B = P.buf[SP][P.ctrl->cur[SP]];
     const long long n = (long long)P.ctrl->n_active[SP];
     // half-step constants: a = q(-dt/2)/(2m) = -c_e/2; t = a B; s = 2t/(1+t^2)
@@ -1030,7 +1056,7 @@ __global__ void k_rewind(const __grid_constant__ StepConst P)
         const int c = raw & kCellMask;
         const float o = B.off[i];
         const float2 ep = P.E32p[c];
-        const float ex = (1.0f - o) * ep.x + o * ep.y + P.Ex_ext;
+        const float ex = (1.0f - o) * ep.x + o * ep.y + P.push.ex_ext;
         const float hx = a * ex;
         const float3 vm = make_float3(B.vx[i] + hx, B.vy[i] + ey, B.vz[i] + ez);
         const float3 vp = make_float3(vm.x + (vm.y * t2 - vm.z * t1), vm.y + (vm.z * t0 - vm.x * t2),
@@ -1096,7 +1122,7 @@ __global__ void k_deposit_species(const __grid_constant__ StepConst P, int sp)
         const float o = B.off[i];
         if (c < 0) continue;
         if (c >= N || !(o >= 0.0f && o < 1.0f)) { atomicOr(&P.ctrl->err, kErrLoad); B.cell[i] = -1; continue; }
-        if (P.sp[sp].lam > 0.0f) B.cell[i] = c | (int)(first_clock(P, sp, B.id[i], step) << kCellBits);
+        if (P.push.sp[sp].lam > 0.0f) B.cell[i] = c | (int)(first_clock(P, sp, B.id[i], step) << kCellBits);
         const uint32_t f = __float2uint_rz(o * 4294967296.0f);
         const int c1 = (P.periodic && c + 1 == N) ? 0 : c + 1;
         unsigned long long *R = P.R[sp] + (size_t)(blockIdx.x % kDepositCopies) * P.r_stride;

@@ -164,18 +164,19 @@ double reduced_mass(const pic_case *c, int sp)
 void fill_species(pic_case *c, int sp)
 {
     SpConst &S = c->P.sp[sp];
+    SpPush &H = c->P.push.sp[sp];
     const pic_case_desc &d = c->d;
     const double q = d.charge_C[sp], m = d.mass_kg[sp], dt = d.dt_s, M = d.gas_mass_kg;
     const double ce = q * dt / (2.0 * m);
     double t[3], tt = 0;
     for (int k = 0; k < 3; ++k) { t[k] = ce * d.B_T[k]; tt += t[k] * t[k]; }
-    S.c_e = (float)ce;
-    for (int k = 0; k < 3; ++k) { S.tB[k] = (float)t[k]; S.sB[k] = (float)(2.0 * t[k] / (1.0 + tt)); }
-    S.rot = (S.tB[0] == 0.0f && S.tB[1] == 0.0f && S.tB[2] == 0.0f) ? 0
-            : (S.tB[0] == 0.0f && S.tB[2] == 0.0f)                  ? 1
+    H.c_e = (float)ce;
+    for (int k = 0; k < 3; ++k) { H.tB[k] = (float)t[k]; H.sB[k] = (float)(2.0 * t[k] / (1.0 + tt)); }
+    H.rot = (H.tB[0] == 0.0f && H.tB[1] == 0.0f && H.tB[2] == 0.0f) ? 0
+            : (H.tB[0] == 0.0f && H.tB[2] == 0.0f)                  ? 1
                                                                     : 2;
-    S.cEy = (float)(ce * d.E_ext_V_per_m[1]);
-    S.cEz = (float)(ce * d.E_ext_V_per_m[2]);
+    H.cEy = (float)(ce * d.E_ext_V_per_m[1]);
+    H.cEz = (float)(ce * d.E_ext_V_per_m[2]);
     S.m_over_2e = (float)(m / (2.0 * kElem));
     S.v_of_sqrt_eps = (float)std::sqrt(2.0 * kElem / m);
     S.recoil = M > 0 ? (float)(2.0 * m / M) : 0.0f;
@@ -209,7 +210,7 @@ void fill_species(pic_case *c, int sp)
         S.mcc = 0;
     }
     S.numax = (float)numax;
-    S.lam = S.mcc != 0 ? (float)(numax * dt) : 0.0f;
+    H.lam = S.mcc != 0 ? (float)(numax * dt) : 0.0f;
 }
 
 pic_status upload_tables(pic_case *c, int sp)
@@ -348,8 +349,8 @@ cudaError_t launch_step_sp(pic_case *c)
 cudaError_t launch_field(pic_case *c, int mode)
 {
     Timed t(c, mode == 0 ? KC_INIT : KC_FIELD, 1);
-    cudaError_t e = launch_programmatic(k_field, dim3(kFieldCluster), dim3(kFieldThreads), c->field_smem, c->stream,
-                                        c->P, mode);
+    cudaError_t e = launch_programmatic(k_field, dim3(kFieldCluster), dim3(field_threads_for(c->d.n_cells, kFieldCluster)),
+                                        c->field_smem, c->stream, c->P, mode);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -899,8 +900,8 @@ pic_status pic_create_case(const pic_case_desc *desc, pic_case **out)
     const double dx = desc->length_m / N;
     P.dx = dx; P.dt = desc->dt_s; P.eps0 = kEps0;
     P.dtdx = (float)(desc->dt_s / dx);
-    P.Ex_ext = (float)desc->E_ext_V_per_m[0];
-    P.key0 = (uint32_t)desc->seed; P.key1 = (uint32_t)(desc->seed >> 32);
+    P.push.ex_ext = (float)desc->E_ext_V_per_m[0];
+    P.push.key0 = (uint32_t)desc->seed; P.push.key1 = (uint32_t)(desc->seed >> 32);
     P.see_gamma = (float)desc->see_gamma;
     P.see_vth = (float)std::sqrt(desc->see_temp_ev * kElem / desc->mass_kg[0]);
     P.see_dtdx = (float)(desc->dt_s / dx);
@@ -1110,7 +1111,7 @@ pic_status pic_load_profile(pic_case *c, int sp, int64_t n, const double *densit
         const double *dr = drift ? drift : z3;
         const int grid = (int)std::min<long long>((n + 255) / 256, (long long)c->num_sms * 16);
         k_load_profile<<<grid, 256, 0, c->stream>>>(c->P.buf[sp][0], n, N, d_cdf, d_dn, d_tn, vt, (float)dr[0],
-                                                    (float)dr[1], (float)dr[2], id_base, sp, c->P.key0, c->P.key1);
+                                                    (float)dr[1], (float)dr[2], id_base, sp, c->P.push.key0, c->P.push.key1);
         CU(cudaGetLastError());
         CU(cudaFreeAsync(tmp, c->stream));
         CU(cudaStreamSynchronize(c->stream));
@@ -1729,8 +1730,11 @@ struct pic_batch {
     SortItem *d_sort_items[2] = {nullptr, nullptr};   // batched sort blocks per species
     int n_sort_items[2] = {0, 0};
     unsigned *d_next = nullptr;
+    std::vector<GridTable> grid_tab;  // shape 4: one parameter table per launch of k_batch_grid
+    std::vector<int> grid_case0, grid_n, grid_sp;
+    bool grid_ok = false;           // every item fits the grid kernel's table
     int *d_field_cases = nullptr;   // run-case indices grouped by field cluster size (1, 2, 4, 8)
-    int n_field[4] = {}, field_off[4] = {};
+    int n_field[4] = {}, field_off[4] = {}, field_threads[4] = {};
     int n_items = 0;
     bool planned = false;
     int periodic = 0, mcc0 = 0, mcc1 = 0;
@@ -1795,6 +1799,34 @@ cudaError_t batch_step_k(pic_batch *b)
     return cudaGetLastError();
 }
 
+// Shape 4: the grid of work items, one launch per parameter table.
+template <bool PER, int M0, int M1, int SHAPE>
+cudaError_t batch_grid(pic_batch *b)
+{
+    auto k0 = k_batch_grid<0, PER, M0, SHAPE>;
+    auto k1 = k_batch_grid<1, PER, M1, SHAPE>;
+    static std::once_flag once0, once1;
+    static cudaError_t err0 = cudaSuccess, err1 = cudaSuccess;
+    cudaError_t e = allow_max_step_smem(k0, once0, err0, b->run[0]->device);
+    if (e == cudaSuccess) e = allow_max_step_smem(k1, once1, err1, b->run[0]->device);
+    if (e != cudaSuccess) return e;
+    const unsigned smem = batch_smem<M0, M1, false, SHAPE>(b);
+    for (size_t g = 0; g < b->grid_tab.size(); ++g) {
+        const dim3 grid((unsigned)b->grid_n[g]), block(BatchShape<SHAPE>::threads);
+        if (g == 0) {                               // after the previous step's field solve
+            if (b->grid_sp[g] == 0) k0<<<grid, block, smem, b->stream>>>(b->grid_tab[g], b->d_cases, b->grid_case0[g]);
+            else k1<<<grid, block, smem, b->stream>>>(b->grid_tab[g], b->d_cases, b->grid_case0[g]);
+            e = cudaGetLastError();
+        } else if (b->grid_sp[g] == 0) {
+            e = launch_programmatic(k0, grid, block, smem, b->stream, b->grid_tab[g], b->d_cases, b->grid_case0[g]);
+        } else {
+            e = launch_programmatic(k1, grid, block, smem, b->stream, b->grid_tab[g], b->d_cases, b->grid_case0[g]);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
 // Tile buffers (bulk-copy pipeline) exist for shape 0 only.
 template <bool PER, int M0, int M1>
 cudaError_t batch_step_t(pic_batch *b)
@@ -1803,6 +1835,8 @@ cudaError_t batch_step_t(pic_batch *b)
     // a shape whose draw queues do not fit next to the largest case's tables
     // runs as shape 0 (the fewest warps, chunks of one)
     const unsigned lim = (unsigned)step_smem_limit(b->run[0]->device);
+    if (b->shape == 4 && b->grid_ok && batch_smem<M0, M1, false, 2>(b) <= lim) return batch_grid<PER, M0, M1, 2>(b);
+    if (b->shape == 5 && b->grid_ok && batch_smem<M0, M1, false, 3>(b) <= lim) return batch_grid<PER, M0, M1, 3>(b);
     if (b->shape == 1 && batch_smem<M0, M1, false, 1>(b) <= lim) return batch_step_k<PER, M0, M1, false, 1>(b);
     if (b->shape == 2 && batch_smem<M0, M1, false, 2>(b) <= lim) return batch_step_k<PER, M0, M1, false, 2>(b);
     if (b->shape == 3 && batch_smem<M0, M1, false, 3>(b) <= lim) return batch_step_k<PER, M0, M1, false, 3>(b);
@@ -1828,7 +1862,8 @@ int batch_launches_per_step(const pic_batch *b)
 {
     int field = 0;
     for (int g = 0; g < 4; ++g) field += b->n_field[g] > 0 ? 1 : 0;
-    return (b->n_items > 0 ? 1 : 0) + field + (int)b->own.size() * b->run[0]->d.n_species;
+    const int particles = b->n_items == 0 ? 0 : (b->shape >= 4 && b->grid_ok) ? (int)b->grid_tab.size() : 1;
+    return particles + field + (int)b->own.size() * b->run[0]->d.n_species;
 }
 
 cudaError_t batch_one_step(pic_batch *b)
@@ -1847,10 +1882,11 @@ cudaError_t batch_one_step(pic_batch *b)
         const int n = b->n_field[g];
         if (n == 0) continue;
         const int *cl_cases = b->d_field_cases + b->field_off[g];
-        if (g == 0) k_batch_field<1><<<(unsigned)n, kFieldThreads, fsm, b->stream>>>(b->d_cases, cl_cases, 1, reset);
-        if (g == 1) k_batch_field<2><<<(unsigned)(2 * n), kFieldThreads, fsm, b->stream>>>(b->d_cases, cl_cases, 1, reset);
-        if (g == 2) k_batch_field<4><<<(unsigned)(4 * n), kFieldThreads, fsm, b->stream>>>(b->d_cases, cl_cases, 1, reset);
-        if (g == 3) k_batch_field<8><<<(unsigned)(8 * n), kFieldThreads, fsm, b->stream>>>(b->d_cases, cl_cases, 1, reset);
+        const unsigned T = (unsigned)b->field_threads[g];
+        if (g == 0) k_batch_field<1><<<(unsigned)n, T, fsm, b->stream>>>(b->d_cases, cl_cases, 1, reset);
+        if (g == 1) k_batch_field<2><<<(unsigned)(2 * n), T, fsm, b->stream>>>(b->d_cases, cl_cases, 1, reset);
+        if (g == 2) k_batch_field<4><<<(unsigned)(4 * n), T, fsm, b->stream>>>(b->d_cases, cl_cases, 1, reset);
+        if (g == 3) k_batch_field<8><<<(unsigned)(8 * n), T, fsm, b->stream>>>(b->d_cases, cl_cases, 1, reset);
         reset = nullptr;
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1962,6 +1998,33 @@ pic_status batch_plan(pic_batch *b)
         const long long nb = (long long)hs[(size_t)b2.case_idx].n_active[b2.species] / b2.nk;
         return na > nb;
     });
+    // shape 4: parameter tables of at most kGridCases cases and kGridItems
+    // items each, items in the list's (largest first) order
+    b->grid_tab.clear();
+    b->grid_case0.clear();
+    b->grid_n.clear();
+    b->grid_sp.clear();
+    b->grid_ok = true;
+    for (int sp = 0; sp < c0->d.n_species && b->grid_ok; ++sp)
+        for (size_t g0 = 0; g0 < nc && b->grid_ok; g0 += kGridCases) {
+            GridTable t{};
+            for (size_t i = 0; i < (size_t)kGridCases && g0 + i < nc; ++i) t.push[i] = consts[g0 + i].push;
+            int ni = 0;
+            auto flush = [&]() {
+                b->grid_tab.push_back(t);
+                b->grid_case0.push_back((int)g0);
+                b->grid_n.push_back(ni);
+                b->grid_sp.push_back(sp);
+                ni = 0;
+            };
+            for (const BatchItem &it : items) {
+                if (it.species != sp || (size_t)it.case_idx < g0 || (size_t)it.case_idx >= g0 + kGridCases) continue;
+                if (it.nk >= 2048) { b->grid_ok = false; break; }
+                t.item[ni++] = (uint32_t)((size_t)it.case_idx - g0) | ((uint32_t)it.k << 8) | ((uint32_t)it.nk << 19);
+                if (ni == kGridItems) flush();
+            }
+            if (ni > 0) flush();
+        }
     // tile buffers: as many as the largest case leaves room for (same for all cases)
     int stages = b->stages;
     for (size_t i = 0; i < nc; ++i) {
@@ -2013,8 +2076,12 @@ pic_status batch_plan(pic_batch *b)
     std::vector<int> fcases;
     for (int g = 0; g < 4; ++g) {
         b->field_off[g] = (int)fcases.size();
+        b->field_threads[g] = 64;
         for (size_t i = 0; i < nc; ++i)
-            if (field_cluster_for(b->run[i]->d.n_cells) == (1 << g)) fcases.push_back((int)i);
+            if (field_cluster_for(b->run[i]->d.n_cells) == (1 << g)) {
+                fcases.push_back((int)i);
+                b->field_threads[g] = std::max(b->field_threads[g], field_threads_for(b->run[i]->d.n_cells, 1 << g));
+            }
         b->n_field[g] = (int)fcases.size() - b->field_off[g];
     }
     CU(cudaMalloc(&b->d_field_cases, fcases.size() * sizeof(int)));
@@ -2287,7 +2354,7 @@ pic_status pic_batch_retune(pic_batch *b)
 
 pic_status pic_batch_set_shape(pic_batch *b, int shape)
 {
-    if (!b || shape < 0 || shape >= kBatchShapes) return fail(PIC_EINVAL, "shape must be in [0, 3]");
+    if (!b || shape < 0 || shape >= kBatchShapes) return fail(PIC_EINVAL, "shape must be in [0, 5]");
     b->shape = shape;
     b->tuned = true;                                 // a fixed shape: the autotuner does not run
     batch_drop_graph(b);

@@ -66,14 +66,25 @@ struct Ctrl {
     unsigned long long renewed[2];      // axial renewals per species
 };
 
-struct SpConst {
+// Constants of the push and of the collision clock, per species; with the
+// case's imposed field and Philox key they form CasePush, which a step kernel
+// reads from its kernel parameter (constant bank) in the particle loop.
+struct SpPush {
     float c_e;                          // q dt / (2 m): half electric kick per V/m
-    float tB[3], sB[3];                 // Boris rotation vectors t = (q dt / 2m) B, s = 2t/(1+t^2)
-    int rot;                            // 0: B = 0 (no rotation), 1: B along y only, 2: general B
     float cEy, cEz;                     // c_e * E_ext_y, c_e * E_ext_z
+    float tB[3], sB[3];                 // Boris rotation vectors t = (q dt / 2m) B, s = 2t/(1+t^2)
+    float lam;                          // numax dt in FP32: the collision clock's gap unit (0 = no MCC)
+    int rot;                            // 0: B = 0 (no rotation), 1: B along y only, 2: general B
+};
+struct CasePush {
+    float ex_ext;                       // imposed field along x
+    uint32_t key0, key1;                // Philox key
+    SpPush sp[2];
+};
+
+struct SpConst {
     float m_over_2e;                    // eps[eV] = m/(2e) |v|^2
     float v_of_sqrt_eps;                // |v| = sqrt(2e/m) sqrt(eps)
-    float lam;                          // numax dt in FP32: the collision clock's gap unit (0 = no MCC)
     float numax;
     int nproc;
     int kind[kMaxProc];
@@ -92,8 +103,7 @@ struct SpConst {
 struct StepConst {
     int n_cells, n_nodes, periodic, n_species;
     float dtdx;                         // dt / dx
-    float Ex_ext;                       // imposed field along x
-    uint32_t key0, key1;                // Philox key
+    CasePush push;
     float see_gamma, see_vth, see_dtdx;
     float eepf_lo, eepf_hi;             // cells: central 10 % of the gap
     float inv_dlog;                     // 1 / (ln(emax/emin)/(NGRID-1)) for the ln-eps interpolation
@@ -177,7 +187,7 @@ __device__ __forceinline__ float u01(uint32_t r)
 
 __device__ __forceinline__ uint4 draw(const StepConst &P, uint32_t id, uint32_t step, int sp, uint32_t blk)
 {
-    return philox4x32_10(make_uint4(id, step, ((uint32_t)sp << 16) | blk, 0u), P.key0, P.key1);
+    return philox4x32_10(make_uint4(id, step, ((uint32_t)sp << 16) | blk, 0u), P.push.key0, P.push.key1);
 }
 
 // Null-collision clock (paper §4 free flights; §1 null-collision method).

@@ -538,7 +538,7 @@ class Batch:
     def tuning(self):
         """Launch shape, sort interval, whether the autotuner ran, and its timings."""
         sh, k, tu, sm = C.c_int(), C.c_int(), C.c_int(), C.c_float()
-        ms, st = (C.c_float * 4)(), (C.c_float * 32)()
+        ms, st = (C.c_float * 6)(), (C.c_float * 32)()
         check(lib.pic_batch_tuning(self.h, C.byref(sh), C.byref(k), C.byref(tu), ms, C.byref(sm), st))
         return dict(shape=sh.value, sort_interval=k.value, tuned=bool(tu.value), shape_ms=list(ms),
                     sort_ms=sm.value, step_ms=list(st))

@@ -714,19 +714,23 @@ def _sweep_cfgs(n_cases, seed=5):
     return cfgs
 
 
-@pytest.mark.parametrize("stages,own", [(0, 0), (1, 0), (2, 0), (0, 100_000), (0, 1)])
-def test_batch_equals_cases_stepped_alone(stages, own):
+@pytest.mark.parametrize("stages,own,shape", [(0, 0, None), (1, 0, None), (2, 0, None), (0, 100_000, None),
+                                               (0, 1, None), (0, 0, 4), (0, 0, 5)])
+def test_batch_equals_cases_stepped_alone(stages, own, shape):
     """Heterogeneous argon cases (cells, gap, pressure, voltage, particle
     counts differ) stepped in one batch give bit-identical particles and
     fields to each case stepped on its own; the batch kernel loads its
     particles directly (0) or through 1-2 bulk-copy tile buffers, and cases
     above `own` particles run the single-case kernels inside the batch
-    (own = 1: every case; 0: none)."""
+    (own = 1: every case; 0: none); shapes 4 and 5 run the batch as a grid of
+    work items with the push constants in the kernel parameter."""
     cfgs = _sweep_cfgs(5)
     counts = [3000, 70_000, 150_000, 9_000, 260_001]
     b = pic.Batch(cfgs, sort_interval=8)
     b.set_stages(stages)
     b.set_own_threshold(own)
+    if shape is not None:
+        b.set_shape(shape)
     singles = []
     for cfg, n, view in zip(cfgs, counts, b.cases):
         nn = cfg["n_cells"] + 1
@@ -750,6 +754,41 @@ def test_batch_equals_cases_stepped_alone(stages, own):
         c.close()
     assert b.launches() > 0
     b.close()
+
+
+def test_grid_batch_over_several_parameter_tables_equals_the_persistent_kernel():
+    """300 small cases exceed one grid launch's parameter table (256 cases):
+    the grid shape then runs one launch per table and species, chained by
+    programmatic dependent launches, and gives the particles and fields of
+    the persistent kernel bit for bit."""
+    cfgs = _sweep_cfgs(300, seed=11)
+    res = []
+    for shape in (3, 4):
+        b = pic.Batch(cfgs, sort_interval=4)
+        for i, (cfg, view) in enumerate(zip(cfgs, b.cases)):
+            nn = cfg["n_cells"] + 1
+            n = 200 + 37 * (i % 11)
+            for sp, T in ((0, 20.0), (1, 400.0)):
+                view.load_profile(sp, n, np.full(nn, 2e14), np.full(nn, T), id_base=0)
+        b.set_shape(shape)
+        b.step(9)
+        b.sync()
+        assert b.tuning()["shape"] == shape
+        out = []
+        for view in b.cases:
+            parts = []
+            for s in range(2):
+                p = view.particles(s)
+                order = np.argsort(p["id"], kind="stable")
+                parts.append({k: p[k][order] for k in ("id", "cell", "off", "vx", "vy", "vz")})
+            out.append((parts, view.field()[1]))
+        res.append(out)
+        b.close()
+    for (pa, fa), (pb, fb) in zip(*res):
+        for s in range(2):
+            for key in pa[s]:
+                assert np.array_equal(pa[s][key], pb[s][key]), (s, key)
+        assert np.array_equal(fa, fb)
 
 
 def test_batch_autotuner_and_batched_sort_leave_results_unchanged():
