@@ -657,7 +657,20 @@ pic_status autotune(pic_case *c, int64_t *left)
         CU(launch_sort(c, s));
         CU(cudaEventRecord(sev[2 * s + 1], c->stream));
     }
+    int64_t alive0[2] = {0, 0}, alive1[2] = {0, 0};   // live particles around the timed steps
+    {
+        Ctrl h;
+        CU(cudaMemcpyAsync(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        for (int s = 0; s < ns; ++s) alive0[s] = (int64_t)(h.n_total[s] - h.n_dead[s]);
+    }
     for (int k = 0; k < kTuneSteps; ++k) CU(launch_one_step_timed(c, &tev[4 * k]));
+    {
+        Ctrl h;
+        CU(cudaMemcpyAsync(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        for (int s = 0; s < ns; ++s) alive1[s] = (int64_t)(h.n_total[s] - h.n_dead[s]);
+    }
     // 2. launch shapes, interleaved
     for (int rnd = 0; rnd < kShapeRounds; ++rnd)
         for (int k = 0; k < kShapes; ++k) {
@@ -679,6 +692,7 @@ pic_status autotune(pic_case *c, int64_t *left)
             CU(cudaEventElapsedTime(&t, tev[4 * k + 2 * s], tev[4 * k + 2 * s + 1]));
             ty[k] = t;
         }
+        normalise_to_count(ty, kTuneSteps, (double)alive0[s], (double)alive1[s]);
         const SortIntervalFit fit = choose_sort_interval(ty, kTuneSteps, ts, 4, kMaxSortInterval);
         r.K[s] = fit.K;
         r.K[s] = std::max(4, std::min(kMaxSortInterval, r.K[s]));
@@ -2149,12 +2163,26 @@ pic_status batch_autotune(pic_batch *b, int64_t *left)
     CU(cudaEventRecord(sev[0], b->stream));
     CU(batch_sort(b));
     CU(cudaEventRecord(sev[1], b->stream));
+    std::vector<Ctrl> hs(b->run.size());
+    auto alive = [&](double &a) -> pic_status {      // live particles of the stepped cases
+        for (size_t i = 0; i < b->run.size(); ++i)
+            CU(cudaMemcpyAsync(&hs[i], b->run[i]->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+        CU(cudaStreamSynchronize(b->stream));
+        a = 0;
+        for (size_t i = 0; i < b->run.size(); ++i)
+            for (int s = 0; s < b->run[i]->d.n_species; ++s) a += (double)(hs[i].n_total[s] - hs[i].n_dead[s]);
+        return PIC_OK;
+    };
+    double alive0 = 0, alive1 = 0;
+    pic_status st = alive(alive0);
+    if (st != PIC_OK) return st;
     for (int k = 0; k < kBatchTuneSteps; ++k) {
         CU(cudaEventRecord(tev[2 * k], b->stream));
         CU(batch_one_step(b));
         CU(cudaEventRecord(tev[2 * k + 1], b->stream));
     }
-    CU(cudaStreamSynchronize(b->stream));
+    st = alive(alive1);
+    if (st != PIC_OK) return st;
     float ts = 0.f;
     CU(cudaEventElapsedTime(&ts, sev[0], sev[1]));
     double ty[kBatchTuneSteps];
@@ -2164,6 +2192,7 @@ pic_status batch_autotune(pic_batch *b, int64_t *left)
         ty[k] = t;
         b->tune_step_ms[k] = t;
     }
+    normalise_to_count(ty, kBatchTuneSteps, alive0, alive1);
     const SortIntervalFit fit = choose_sort_interval(ty, kBatchTuneSteps, ts, 4, kMaxSortInterval);
     b->sort_k = std::max(4, std::min(kMaxSortInterval, fit.K));
     b->tune_sort_ms = ts;

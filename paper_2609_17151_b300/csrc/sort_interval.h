@@ -20,6 +20,20 @@ struct SortIntervalFit {
     double slope;     // growth per step used beyond the window (>= 0)
 };
 
+// Step times measured while the live particle count went from a0 to a1
+// (taken as linear over the window), rescaled to the count at the window's
+// start: a discharge that ionizes or loses particles changes the step time
+// by itself, and only the growth that a sort removes (lost cell order,
+// absorbed slots) belongs in the fit.
+inline void normalise_to_count(double *t, int n, double a0, double a1)
+{
+    if (!(a0 > 0) || !(a1 > 0)) return;
+    for (int k = 0; k < n; ++k) {
+        const double a = a0 + (a1 - a0) * (k + 0.5) / n;
+        t[k] *= a0 / a;
+    }
+}
+
 inline SortIntervalFit choose_sort_interval(const double *t, int n, double t_sort, int k_min, int k_max)
 {
     const int h0 = n / 2;

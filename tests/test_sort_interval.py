@@ -105,3 +105,57 @@ def test_accumulating_dead_slots_bound_the_period(chooser):
     assert 4 <= K < 1024
     assert slope > 0.0
     assert K == brute_force(t, 2.0, slope)
+
+
+NORM_DRIVER = r"""
+#include "sort_interval.h"
+#include <cstdio>
+#include <vector>
+int main() {
+    int n; double a0, a1, ts;
+    while (std::scanf("%d %lf %lf %lf", &n, &a0, &a1, &ts) == 4) {
+        std::vector<double> t(n);
+        for (auto &x : t) std::scanf("%lf", &x);
+        pic::normalise_to_count(t.data(), n, a0, a1);
+        const pic::SortIntervalFit f = pic::choose_sort_interval(t.data(), n, ts, 4, 1024);
+        std::printf("%d", f.K);
+        for (double x : t) std::printf(" %.17g", x);
+        std::printf("\n");
+    }
+    return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def normaliser(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    d = tmp_path_factory.mktemp("sortnorm")
+    src, exe = d / "drv.cpp", d / "drv"
+    src.write_text(NORM_DRIVER)
+    subprocess.check_call([cxx, "-O1", "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)])
+
+    def run(t, a0, a1, ts):
+        line = f"{len(t)} {a0!r} {a1!r} {ts!r} " + " ".join(repr(float(x)) for x in t) + "\n"
+        out = subprocess.run([str(exe)], input=line, capture_output=True, text=True, check=True).stdout.split()
+        return int(out[0]), np.array([float(x) for x in out[1:]])
+    return run
+
+
+def test_growth_of_the_particle_count_is_not_taken_for_lost_order(normaliser):
+    """Step times that grow only because the discharge gains particles (time
+    per particle constant) rescale to a flat window, so the sort interval goes
+    to its maximum; without a count change the times are left as they are,
+    and growth beyond the count's still shortens the interval."""
+    n = 32
+    a0, a1 = 1.0e8, 1.1e8
+    a = a0 + (a1 - a0) * (np.arange(n) + 0.5) / n
+    t = 2.5 * a / a0                                         # ms, proportional to the count
+    K, tn = normaliser(t, a0, a1, 8.0)
+    assert np.allclose(tn, 2.5, rtol=1e-12) and K == 1024
+    K0, t0 = normaliser(t, a0, a0, 8.0)
+    assert np.array_equal(t0, t) and K0 < 200                # read as lost order: sorts often
+    Kd, _ = normaliser(t * (1 + 0.004 * np.arange(n)), a0, a1, 8.0)
+    assert Kd < 1024
