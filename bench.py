@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--epochs", type=int, default=3000)
     ap.add_argument("--pilot", action="store_true")
     ap.add_argument("--cases", type=int, default=256)
+    ap.add_argument("--batch-shape", type=int, default=-1,
+                    help="batch: fixed launch shape (0-5) instead of the autotuner's choice (-1)")
     ap.add_argument("--small", action="store_true", help="batch: 5e3-5e4 particles per species per case")
     return ap.parse_args()
 
@@ -210,7 +212,7 @@ def run_reference(args, rank):
 WARM_STEPS = 120                 # batch leg: steps before the autotuner (past the load's first transient)
 
 
-def batch_leg(torch, n_cases=256, small=False, peak=6481.1):
+def batch_leg(torch, n_cases=256, small=False, peak=6481.1, shape=-1):
     """256 uneven argon cases (5e4-1e6 particles per species each): the batch
     (one persistent particle launch and one field launch per step for all
     cases, its launch shape and sort interval K chosen by its autotuner)
@@ -252,9 +254,10 @@ def batch_leg(torch, n_cases=256, small=False, peak=6481.1):
     # some steps first (past the load's first transient), then the autotuner,
     # then the graphs of the chosen interval are built
     b.step(1)
-    b.set_shape(3)
+    b.set_shape(3 if shape < 0 else shape)
     b.step(WARM_STEPS - 1)
-    b.retune()
+    if shape < 0:
+        b.retune()
     b.step(40 + 8)
     b.sync()
     tun = b.tuning()
@@ -312,7 +315,7 @@ def batch_leg(torch, n_cases=256, small=False, peak=6481.1):
 
 
 def run_batch(args, torch):
-    leg = batch_leg(torch, args.cases, args.small)
+    leg = batch_leg(torch, args.cases, args.small, shape=args.batch_shape)
     print(json.dumps({
         "metric": METRIC, "value": leg["batched"]["value"], "unit": UNIT, "n_gpus": 1, "steps": leg["steps_timed"],
         "warmup": leg["warmup_steps"], "ms_per_step": leg["batched"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
