@@ -397,17 +397,20 @@ pic_status pic_sort_by_cell(int32_t n_cells, int64_t n, const int32_t *cell, con
  * together.  Each case is an ordinary pic_case created from descs[i] on the
  * batch's stream (descs[0].stream, or one the batch creates); use
  * pic_batch_case(b, i) with the per-case calls to load tables and particles
- * and to read results.  pic_batch_step runs every case's steps with one
- * persistent particle launch (work items: slices of ~131072 particles of any
- * case and species, taken from an atomic counter) and one field launch (one
- * 8-CTA cluster per case) per step, replayed from a CUDA graph between sorts;
+ * and to read results.  pic_batch_step runs every case's steps with the
+ * particles of all cases split into work items (slices of 16384 to 262144
+ * particles of one case and species, largest first): either one persistent
+ * launch whose CTAs take items from an atomic counter, or a grid of one CTA
+ * per item, one launch per species and table of up to 256 cases (the items
+ * and the cases' push constants in the kernel parameter); then the field
+ * solves, one cluster per case of as few CTAs as its grid needs, one launch
+ * per cluster size.  The steps are replayed from CUDA graphs between sorts;
  * every sort_interval steps every case is sorted, one launch per sort kernel
  * and species for all cases.  descs[0].sort_interval > 0 fixes the interval;
- * 0 lets the batch's autotuner choose it and the persistent kernel's launch
- * shape, during the first pic_batch_step of at least 40 steps after the
- * first step (8 steps, two per shape, then one sort and 32 timed steps, all
- * part of the run: results do not depend on the choices; see
- * pic_batch_tuning).  All cases must share the boundary kind, the number of species and
+ * 0 lets the batch's autotuner choose it and the launch shape, during the
+ * first pic_batch_step of at least 44 steps after the first step (12 steps,
+ * two per shape, then one sort and 32 timed steps, all part of the run:
+ * results do not depend on the choices; see pic_batch_tuning).  All cases must share the boundary kind, the number of species and
  * the collision model of each species (none, tables, or constant frequency
  * for electrons).  Results equal stepping each case alone.
  * Errors: PIC_EINVAL (mixed cases), PIC_ESTATE (a case without particles).
@@ -427,9 +430,9 @@ int64_t pic_batch_launches(const pic_batch *b);
 pic_status pic_batch_set_stages(pic_batch *b, int stages);
 /* Cases with at least `particles` live particles (both species, counted when
  * the batch plans its step) run the single-case step kernels inside the
- * batch's graph instead of the shared persistent kernel; every case's field
- * solve stays in the one batched launch.  0 = every case in the persistent
- * kernel (the default).  Results do not depend on it.  Errors: PIC_EINVAL. */
+ * batch's graph instead of the shared batch kernels; every case's field
+ * solve stays in the batched launches.  0 = every case in the batch kernels
+ * (the default).  Results do not depend on it.  Errors: PIC_EINVAL. */
 pic_status pic_batch_set_own_threshold(pic_batch *b, int64_t particles);
 /* The batch's launch choices: *shape (the persistent kernel, CTAs taking work
  * items from a counter: 0: 512-thread CTAs, one per SM, chunks of one
@@ -444,7 +447,7 @@ pic_status pic_batch_set_own_threshold(pic_batch *b, int64_t particles);
 pic_status pic_batch_tuning(pic_batch *b, int *shape, int *sort_interval, int *tuned, float *shape_ms,
                             float *sort_ms, float *step_ms);
 /* (step_ms[32]: the 32 steps the autotuner timed after its sort, in order.) */
-/* Run the autotuner again at the next pic_batch_step of at least 40 steps
+/* Run the autotuner again at the next pic_batch_step of at least 44 steps
  * (the discharge of a sweep changes over its first RF cycles, and with it the
  * cost of lost cell order). */
 pic_status pic_batch_retune(pic_batch *b);

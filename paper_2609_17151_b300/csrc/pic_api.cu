@@ -2116,12 +2116,14 @@ pic_status batch_plan(pic_batch *b)
 }
 
 // ---------------------------------------------------------------------------
-// Batch autotuner (the benchmark spec pattern 2: tiles chosen by a project-written
-// tuner).  Continuing the simulation (results do not depend on any choice):
-//  1. each launch shape of the batch kernel runs kBatchShapeRounds steps in
+// Batch autotuner: the launch shape and the sort interval, chosen by
+// measurement while the simulation continues (results do not depend on any
+// choice):
+//  1. each launch shape of the batch kernels runs kBatchShapeRounds steps in
 //     turn, timed with events around the step; the least summed time wins;
 //  2. one batched sort, then kBatchTuneSteps steps each timed with the chosen
-//     shape; choose_sort_interval picks K from them, as for a single case.
+//     shape and rescaled by the live particle count; choose_sort_interval
+//     picks K from them, as for a single case.
 // The tile pipeline (stages > 0) is left as the caller set it.
 // ---------------------------------------------------------------------------
 constexpr int kBatchShapeRounds = 2, kBatchTuneSteps = 32;
