@@ -58,9 +58,10 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="leave the 256-case batched sweep out of the line")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="steps of the per-launch timed region (0: enough for every species to sort once)")
-    ap.add_argument("--workload", default="exb", choices=["exb", "batch", "warmstart"],
+    ap.add_argument("--workload", default="exb", choices=["exb", "batch", "warmstart", "configs"],
                     help="exb: the 10.24M-particle E x B case (default); batch: the 256-case argon sweep; "
-                         "warmstart: RF cycles to steady state, cold start vs the learned warm start")
+                         "warmstart: RF cycles to steady state, cold start vs the learned warm start; "
+                         "configs: GPU and oracle throughput of each single-case configuration")
     ap.add_argument("--train", type=int, default=128)
     ap.add_argument("--test", type=int, default=16)
     ap.add_argument("--max-cycles", type=int, default=1500)
@@ -206,6 +207,74 @@ def run_reference(args, rank):
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+# --------------------------------------------------------------------------- per-config table
+def config_case(name, seed=1):
+    """The single-case configurations: C0 Langmuir wave (6400 electrons, 64
+    cells), C1 argon CCP (2e5 + 2e5 particles, 512 cells, 400 steps a period),
+    C3 E x B box (2500 particles per cell per species, 2048 cells; C3s: 50 per
+    cell, the oracle's sample)."""
+    from paper_2609_17151_b300 import workloads as W
+    if name == "C0":
+        return W.langmuir_case(seed=seed)
+    if name == "C1":
+        return W.ccp_case(seed=seed)
+    return W.ecdi_case(seed=seed, ppc=2500 if name == "C3" else 50)
+
+
+def oracle_config_job(name, steps, seed=1, warm=1):
+    """The FP64 oracle, single thread, on one replica of a configuration:
+    `warm` untimed steps, then `steps` timed.  Returns (particles, seconds)."""
+    import oracle
+    from paper_2609_17151_b300 import workloads as W
+    cfg, parts = config_case(name, seed)
+    c = oracle.Case(cfg)
+    for s, p in enumerate(parts):
+        c.load_particles(s, W.as_xi(p), p["vx"], p["vy"], p["vz"], p["id"])
+    c.step(warm)
+    n = sum(c.count(s) for s in range(len(parts)))
+    t0 = time.perf_counter()
+    c.step(steps)
+    return n, time.perf_counter() - t0
+
+
+def run_configs(torch, peak):
+    """GPU particle-steps/s (CUDA events over graph replay, after 64 steps of
+    tuner, graph builds and first transient) and the FP64 oracle's, on one core
+    and on every host core (one replica each, spawned processes), for the
+    single-case configurations; one JSON line per configuration."""
+    import multiprocessing as mp
+    from paper_2609_17151_b300 import pic
+    cores = host_cores()
+    plan = {"C0": (2000, 2000), "C1": (400, 60), "C3": (200, 100)}    # GPU steps, oracle steps
+    for name, (gsteps, osteps) in plan.items():
+        cfg, parts = config_case(name)
+        stream = torch.cuda.Stream()
+        c = pic.Case(cfg, parts, stream=stream.cuda_stream)
+        c.step(64)
+        c.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(SLEEP_CYCLES)
+        ev0.record(stream)
+        c.step(gsteps)
+        ev1.record(stream)
+        ev1.synchronize()
+        n = sum(c.count())
+        c.close()
+        ms = ev0.elapsed_time(ev1) / gsteps
+        line = {"config": name, "particles": n, "gpu_ms_per_step": ms, "gpu_value": n / (ms * 1e-3),
+                "gpu_hbm_frac": ALGO_BYTES * n / (ms * 1e-3) / 1e9 / peak, "unit": UNIT}
+        oname = name if name != "C3" else "C3s"
+        on, odt = oracle_config_job(oname, osteps)
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            res = pool.starmap(oracle_config_job, [(oname, osteps, 1 + k) for k in range(cores)])
+        line.update(oracle_1_core=on * osteps / odt,
+                    oracle_all_cores=sum(r[0] for r in res) * osteps / max(r[1] for r in res), cores=cores,
+                    oracle_sample=f"{oname}: {on} particles per replica, {osteps} steps")
+        print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------- batched sweep
@@ -545,6 +614,11 @@ def main():
     if args.workload == "warmstart":
         if rank == 0:
             run_warmstart(args, torch)
+        return
+    if args.workload == "configs":
+        if rank == 0:
+            peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+            run_configs(torch, json.load(open(peaks_path))["hbm_gbs"] if os.path.exists(peaks_path) else 6400.0)
         return
     from paper_2609_17151_b300 import pic
     from paper_2609_17151_b300 import workloads as W
