@@ -161,9 +161,14 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
     const long long step = ctrl->step;
     const unsigned long long fe_n = ctrl->fe_n;
     const bool diag = mode == 1 && P.diag_interval > 0 && ((step + 1) % P.diag_interval) == 0;
+    // the drive's phases, read now for the global terms of step 3 (thread 0 only)
+    double drive_c[4] = {0.0, 0.0, 0.0, 0.0};
+    if (tid == 0 && mode == 1 && !P.periodic)
+        for (int h = 0; h < P.n_harm; ++h) drive_c[h] = ctrl->drive_c[h];
 
     // 1. raw deposit of the node (periodic: node N folds onto node 0); all loads issued first
     unsigned long long r[2] = {0ull, 0ull}, rs[2] = {0ull, 0ull}, rd[2] = {0ull, 0ull};
+    double ps_old = 0.0;                                            // potential sum, read with the deposits
     const bool real = own && i < nn;
     if (real) {
         unsigned long long v[2][kDepositCopies];
@@ -171,13 +176,15 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
         for (int s = 0; s < 2; ++s)
 #pragma unroll
             for (int k = 0; k < kDepositCopies; ++k) v[s][k] = s < ns ? P.R[s][k * P.r_stride + i] : 0ull;
-        if (mode == 1)
+        if (mode == 1) {
+            ps_old = P.phi_sum[i];
 #pragma unroll
             for (int s = 0; s < 2; ++s)
                 if (s < ns) {
                     rs[s] = P.Rsum[s * nn + i];
                     if (diag) rd[s] = P.Rdiag[s * nn + i];
                 }
+        }
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
@@ -208,9 +215,21 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
     {
         const u128 v2[2] = {own && i < N ? (u128)pv[0] : (u128)0, own && i < N ? (u128)pv[1] : (u128)0};
         block_exclusive_vec<u128, 2>(v2, e, qp_tot, wred);          // e_s[i] = sum_{c_lo <= m < i} p_s[m]
-        const u128 w2[2] = {own && i < N ? e[0] : (u128)0, own && i < N ? e[1] : (u128)0};
-        u128 dummy[2];
-        block_exclusive_vec<u128, 2>(w2, dummy, qq_tot, wred);
+        // the slice total of e_s[i] (a sum: no prefix needed)
+        u128 w2[2] = {own && i < N ? e[0] : (u128)0, own && i < N ? e[1] : (u128)0};
+        const int lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, (unsigned long long)w2[s], o);
+                const unsigned long long hi2 = __shfl_xor_sync(0xffffffffu, (unsigned long long)(w2[s] >> 64), o);
+                w2[s] += ((u128)hi2 << 64) | lo2;
+            }
+        if (lane == 0) { wred[warp][0] = w2[0]; wred[warp][1] = w2[1]; }
+        __syncthreads();
+        qq_tot[0] = qq_tot[1] = (u128)0;
+        if (tid == 0)
+            for (int w = 0; w < nw; ++w) { qq_tot[0] += wred[w][0]; qq_tot[1] += wred[w][1]; }
     }
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
@@ -267,7 +286,7 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
             double phi0 = 0.0;                                      // electrode voltage at this solve's time
             if (!P.periodic) {
                 if (mode == 0) phi0 = P.v_init;
-                else for (int h = 0; h < P.n_harm; ++h) phi0 = fma(P.harm_a[h], ctrl->drive_c[h], phi0);
+                else for (int h = 0; h < P.n_harm; ++h) phi0 = fma(P.harm_a[h], drive_c[h], phi0);
             }
             double b = P.bg_r;
             if (P.periodic) b = -(P.cq[0] * (double)(long long)alltot[0] + P.cq[1] * (double)(long long)alltot[1]) * P.inv_n;
@@ -361,7 +380,7 @@ __device__ __forceinline__ void field_solve(const StepConst &P, int mode)
         if (i < N) P.E32p[i].x = e32;
         if (i > 0) P.E32p[i - 1].y = e32;
         else if (P.periodic) P.E32p[N - 1].y = e32;
-        if (mode == 1) P.phi_sum[i] += ph;
+        if (mode == 1) P.phi_sum[i] = ps_old + ph;
         bad = !finite_bits(ph) || !finite_bits(E);
     }
     for (int o = 16; o > 0; o >>= 1) fe += __shfl_xor_sync(0xffffffffu, fe, o);
