@@ -715,7 +715,7 @@ def _sweep_cfgs(n_cases, seed=5):
 
 
 @pytest.mark.parametrize("stages,own,shape", [(0, 0, None), (1, 0, None), (2, 0, None), (0, 100_000, None),
-                                               (0, 1, None), (0, 0, 4), (0, 0, 5)])
+                                               (0, 1, None), (0, 0, 4), (0, 0, 5), (0, 100_000, 5)])
 def test_batch_equals_cases_stepped_alone(stages, own, shape):
     """Heterogeneous argon cases (cells, gap, pressure, voltage, particle
     counts differ) stepped in one batch give bit-identical particles and
