@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--test", type=int, default=16)
     ap.add_argument("--max-cycles", type=int, default=1500)
     ap.add_argument("--train-max-cycles", type=int, default=800)
+    ap.add_argument("--ref-cycles", type=int, default=1500,
+                    help="warmstart: periods the cold runs continue past the criterion for the long reference")
     ap.add_argument("--ws-cells", type=int, default=1024)
     ap.add_argument("--phase", default="all", choices=["all", "train-data", "evaluate"],
                     help="warmstart: all; or the training runs only (writing --data), or the rest from --data")
@@ -453,27 +455,33 @@ def run_warmstart(args, torch):
     §3.3's two-harmonic waveform; 3 cm, 1024 cells, 1600 steps per period),
     from a cold start against a start from the learned network.
 
-    1. Training data: args.train cases run to steady state in one batch.  The
-       network maps a case's parameters to profiles in physical units, which
-       do not depend on the particle weight, so these runs use about 1.25e5
-       particles per species at 1e16 m^-3 and start from the family's density
-       range (5e15 m^-3) to reach steady state sooner.  A case that reaches
-       steady state is frozen (no more GPU time).
+    1. Training data: args.train cases run to steady state in one batch, at
+       the held-out runs' particle weight (about 5e5 particles per species at
+       1e16 m^-3: the steady state of a PIC run moves with its particle count),
+       started from the family's density range (5e15 m^-3) to reach steady
+       state sooner.  A case that reaches steady state is frozen (no more GPU
+       time).
     2. The network (4-256-256-384) is trained on their last 10-cycle averages
        with pic_warmstart_train, the number of epochs chosen on a quarter of
        the training cases held out.
     3. The args.test held-out cases run twice in one batch: cold (uniform
        2e14 m^-3, the weight giving about 5e5 particles per species at
        1e16 m^-3) and warm (pic_warmstart_load from the network, same weight).
+    4. Long cold reference: the cold runs go on args.ref_cycles periods past
+       the criterion, the warm runs frozen; the ion density averaged over the
+       last 100 periods is each case's reference.  A warm start counts when
+       its final ion density is at least as close to the reference as the
+       cold run's (equal final-profile error), within 0.5 % (the noise of a
+       10-period average).
     Steady state: the 32-point ion density averaged over 10 cycles differs by
     < 1 % (relative L2) from the average 100 cycles earlier."""
     from paper_2609_17151_b300 import pic
     from paper_2609_17151_b300 import workloads as W
     n_train, n_test = (8, 2) if args.pilot else (args.train, args.test)
     n_cells = args.ws_cells
-    cfg_tr, par_tr = W.dual_frequency_family(n_train, seed=4, n_cells=n_cells, n0=5e15, n_init=62_500)
+    cfg_tr, par_tr = W.dual_frequency_family(n_train, seed=4, n_cells=n_cells, n0=5e15, n_init=250_000)
     cfg_te, par_te = W.dual_frequency_family(n_test, seed=5, n_cells=n_cells, n0=2e14, n_init=10_000)
-    cap_tr, cap_te = (1_000_000, 1_000_000), (3_000_000, 3_000_000)
+    cap_tr, cap_te = (3_000_000, 3_000_000), (3_000_000, 3_000_000)
     t0 = time.perf_counter()
 
     def emit(obj):
@@ -559,34 +567,53 @@ def run_warmstart(args, torch):
     emit({"phase": "test_loaded", "particles": [int(sum(v.count())) for v in te.cases]})
     te_done, te_prof = run_to_steady_state(te, args.max_cycles, spc, log=progress("test_runs"))
     t_te = time.perf_counter() - t2
+    # 4. long cold reference: cold runs on, warm runs frozen
+    t3 = time.perf_counter()
+    for i in range(2 * n_test):
+        te.freeze(i, i >= n_test)
+    te.replan()
+    te.step(max(0, args.ref_cycles - 100) * spc)
+    for v in te.cases[:n_test]:
+        v.moments(reset=True)
+    te.step(100 * spc)
+    refs = [profiles_on_points(v.moments(), v.n_nodes)[1] for v in te.cases[:n_test]]
+    t_ref = time.perf_counter() - t3
     te.close()
     net.close()
     res = []
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
     for j in range(n_test):
-        ref = te_prof[j][1]
-        err = float(np.linalg.norm(te_prof[n_test + j][1] - ref) / np.linalg.norm(ref))
         res.append({"params": par_te[j].tolist(), "cold_cycles": te_done[j], "warm_cycles": te_done[n_test + j],
-                    "final_ni_rel_l2_diff": err})
+                    "final_ni_rel_l2_diff": rel(te_prof[n_test + j][1], te_prof[j][1]),
+                    "cold_err_vs_reference": rel(te_prof[j][1], refs[j]),
+                    "warm_err_vs_reference": rel(te_prof[n_test + j][1], refs[j])})
     # a warm start counts when both runs reached the criterion and the warm run's
-    # final ion density matches the cold run's within 5 % (same steady state)
-    matched = [r for r in res if r["cold_cycles"] and r["warm_cycles"] and r["final_ni_rel_l2_diff"] < 0.05]
+    # final ion density is at least as close to the long reference as the cold run's
+    matched = [r for r in res if r["cold_cycles"] and r["warm_cycles"]
+               and r["warm_err_vs_reference"] <= r["cold_err_vs_reference"] + 0.005]
     ratios = [r["cold_cycles"] / r["warm_cycles"] for r in matched]
+    both = [r["cold_cycles"] / r["warm_cycles"] for r in res if r["cold_cycles"] and r["warm_cycles"]]
+    within5 = [r["cold_cycles"] / r["warm_cycles"] for r in res if r["cold_cycles"] and r["warm_cycles"]
+               and r["final_ni_rel_l2_diff"] < 0.05]
     emit({
         "metric": "RF cycles to steady state, cold start / learned warm start (median over held-out cases "
-                  "whose warm and cold final ion densities agree within 5 %)",
+                  "whose warm final ion density is at least as close to a long cold reference as the cold run's)",
         "value": float(np.median(ratios)) if ratios else None, "unit": "ratio", "higher_is_better": True,
         "mean_ratio": float(np.mean(ratios)) if ratios else None, "n_matched": len(matched),
+        "median_all_converged": float(np.median(both)) if both else None,
+        "median_final_within_5pct": float(np.median(within5)) if within5 else None,
         "n_test": n_test, "data": "synthetic",
         "config": {"workload": "dual_frequency_argon_ccp_family", "n_cells": n_cells, "gap_m": 0.03,
                    "steps_per_rf_period": spc, "train_cases": n_train, "train_converged": len(ok),
                    "test_cases": n_test,
-                   "particles_per_species_at_1e16": {"training_runs": 125_000, "held_out_runs": 500_000},
+                   "particles_per_species_at_1e16": {"training_runs": 500_000, "held_out_runs": 500_000},
                    "criterion": "32-point ion density, 10-cycle averages 100 cycles apart, relative L2 < 1%",
                    "max_cycles": args.max_cycles, "train_max_cycles": args.train_max_cycles,
                    "network": "4-256-256-384 GELU, BF16 tensor-core products", "max_epochs": args.epochs},
         "train_loss_first_last": [float(curve[0]), float(curve[-1])],
         "epochs_chosen": epochs, "validation_nmse": best_err,
-        "seconds": {"training_runs": t_tr, "training": t_train, "held_out_runs": t_te},
+        "seconds": {"training_runs": t_tr, "training": t_train, "held_out_runs": t_te, "reference": t_ref},
+        "reference_cycles_past_criterion": args.ref_cycles,
         "training_runs_done": tr_done,
         "cases": res,
     })
