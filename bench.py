@@ -733,16 +733,18 @@ def main():
     if not args.no_e2e:
         # end to end through the C ABI on the warmed case: load from pinned host
         # buffers, K steps, moments back to host
+        # (the synthetic ids are 0..n-1, which the library generates when id is NULL)
         pinned = []
         for p in parts:
-            pinned.append({k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in p.items()})
+            assert np.array_equal(p["id"], np.arange(p["id"].size, dtype=np.uint32))
+            pinned.append({k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in p.items() if k != "id"})
         h2d = sum(t.numel() * t.element_size() for p in pinned for t in p.values())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s, p in enumerate(pinned):
-            pic.check(pic.lib.pic_load_particles(case.h, s, p["id"].numel(), p["cell"].data_ptr(),
+            pic.check(pic.lib.pic_load_particles(case.h, s, p["cell"].numel(), p["cell"].data_ptr(),
                                                  p["off"].data_ptr(), p["vx"].data_ptr(), p["vy"].data_ptr(),
-                                                 p["vz"].data_ptr(), p["id"].data_ptr(), 0))
+                                                 p["vz"].data_ptr(), None, 0))
         case.step(args.steps)
         mom = case.moments()
         t1 = time.perf_counter()
@@ -750,8 +752,8 @@ def main():
                    + mom["eepf"].size) + 512
         e2e = {"value": n_particles * args.steps * world / (t1 - t0), "unit": UNIT,
                "h2d_bytes_per_step": int(round(h2d / args.steps)), "d2h_bytes_per_step": int(round(d2h / args.steps)),
-               "note": f"load from pinned host + {args.steps} steps + moments to host, per job of {args.steps} "
-                       "steps, on the warmed case"}
+               "note": f"load from pinned host (cell, offset, velocity; ids 0..n-1 generated by the library) + "
+                       f"{args.steps} steps + moments to host, per job of {args.steps} steps, on the warmed case"}
 
     case.close()
     batch = None
