@@ -781,13 +781,13 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
         }
         // queue the chunk's clock ends (slot order within the warp), run full batches
         if (QCAP > 0) {
-            unsigned m[CH], any = 0u;
+            bool mine = false;
 #pragma unroll
-            for (int q = 0; q < CH; ++q) {
-                m[q] = __ballot_sync(0xffffffffu, need[q]);
-                any |= m[q];
-            }
-            if (any) {                                  // warp-uniform
+            for (int q = 0; q < CH; ++q) mine = mine || need[q];
+            if (__any_sync(0xffffffffu, mine)) {        // warp-uniform; rare where collisions are
+                unsigned m[CH];
+#pragma unroll
+                for (int q = 0; q < CH; ++q) m[q] = __ballot_sync(0xffffffffu, need[q]);
                 __syncwarp();                           // the last run's reads before new entries
                 const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
