@@ -483,6 +483,13 @@ __global__ void k_strip_clock(int32_t *cell, long long n)
     }
 }
 
+// Ids 0..n-1 of a load that gives none.
+__global__ void k_iota_u32(uint32_t *id, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        id[i] = (uint32_t)i;
+}
+
 pic_status reset_moments(pic_case *c)
 {
     const size_t nn = (size_t)c->n_nodes;
@@ -1044,10 +1051,9 @@ pic_status pic_load_particles(pic_case *c, int sp, int64_t n, const int32_t *cel
         if (id) CU(cudaMemcpyAsync(B.id, id, n * 4, k, c->stream));
     }
     if (n > 0 && !id) {
-        std::vector<uint32_t> seq((size_t)n);
-        for (int64_t i = 0; i < n; ++i) seq[(size_t)i] = (uint32_t)i;
-        CU(cudaMemcpyAsync(B.id, seq.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
-        CU(cudaStreamSynchronize(c->stream));
+        const long long blocks = std::min<long long>((n + 255) / 256, 4LL * c->num_sms);
+        k_iota_u32<<<(unsigned)blocks, 256, 0, c->stream>>>(B.id, n);
+        CU(cudaGetLastError());
     }
     return load_finish(c, sp, n, h);
 }

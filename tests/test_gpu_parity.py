@@ -756,6 +756,44 @@ def test_batch_equals_cases_stepped_alone(stages, own, shape):
     b.close()
 
 
+def test_batch_field_solves_on_every_cluster_size_equal_the_single_case_solve():
+    """A batch solves each case's field on the fewest CTAs that hold its grid
+    (1, 2, 4 or 8, one node per thread); grids of 300, 800, 1500 and 3000 cells
+    need each size once.  The integer prefix sums make the field independent
+    of the slicing, so particles and fields equal each case stepped alone
+    (which always solves on eight CTAs) bit for bit."""
+    cfgs = []
+    for k, n_cells in enumerate((300, 800, 1500, 3000)):
+        cfg, _ = W.ccp_case(seed=40 + k, n_cells=n_cells, gap=n_cells * 5e-5, n_per_species=10, mtorr=50.0,
+                            volts=200.0, te_ev=5.0)
+        cfg["sort_interval"] = 8
+        cfgs.append(cfg)
+    b = pic.Batch(cfgs, sort_interval=8)
+    b.set_shape(5)
+    singles = []
+    for cfg, view in zip(cfgs, b.cases):
+        nn = cfg["n_cells"] + 1
+        c = pic.Case(cfg, sort_interval=8)
+        for sp, T in ((0, 5.0), (1, 400.0)):
+            view.load_profile(sp, 40 * cfg["n_cells"], np.full(nn, 2e14), np.full(nn, T), id_base=0)
+            c.load_profile(sp, 40 * cfg["n_cells"], np.full(nn, 2e14), np.full(nn, T), id_base=0)
+        singles.append(c)
+    b.step(5)
+    b.sync()
+    for c in singles:
+        c.step(5)
+    for view, c in zip(b.cases, singles):
+        fa, fb = view.field(), c.field()
+        assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1])
+        for s in range(2):
+            pa, pb = view.particles(s), c.particles(s)
+            ia, ib = np.argsort(pa["id"], kind="stable"), np.argsort(pb["id"], kind="stable")
+            for key in ("id", "cell", "off", "vx", "vy", "vz"):
+                assert np.array_equal(pa[key][ia], pb[key][ib]), (s, key)
+        c.close()
+    b.close()
+
+
 def test_grid_batch_over_several_parameter_tables_equals_the_persistent_kernel():
     """300 small cases exceed one grid launch's parameter table (256 cases):
     the grid shape then runs one launch per table and species, chained by
