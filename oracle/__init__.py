@@ -87,6 +87,8 @@ def _load():
     lib.or_get_field.argtypes = [P, dp, dp]
     lib.or_get_axial.argtypes = [P, C.c_int, dp]
     lib.or_get_clock.argtypes = [P, C.c_int, C.POINTER(C.c_int32)]
+    lib.or_get_loss_speed.argtypes = [P, C.c_int, dp]
+    lib.or_get_move.argtypes = [P, C.c_int, dp]
     lib.or_neg_log_u32.restype = C.c_float
     lib.or_neg_log_u32.argtypes = [C.c_float]
     lib.or_clock_state.restype = C.c_int32
@@ -278,6 +280,10 @@ class Case:
         _lib.or_get_particles(self._h, sp, _d(out["xi"]), _d(out["vx"]), _d(out["vy"]), _d(out["vz"]),
                               out["id"].ctypes.data_as(C.POINTER(C.c_uint32)), _d(out["margin"]),
                               out["event"].ctypes.data_as(C.POINTER(C.c_int32)))
+        out["vloss"] = np.zeros(n)          # speed before a threshold loss in the last step (0: none)
+        _lib.or_get_loss_speed(self._h, sp, _d(out["vloss"]))
+        out["xmove"] = np.zeros(n)          # cells of the move that placed it in the last step
+        _lib.or_get_move(self._h, sp, _d(out["xmove"]))
         return out
 
     def clock(self, sp) -> np.ndarray:

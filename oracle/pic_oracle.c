@@ -82,6 +82,8 @@ typedef struct {
     int32_t *event;
     double *z;                 /* axial excursion (m), used with axial renewal */
     int32_t *clk;              /* collision clock: 2 k + c (see or_clock_state) */
+    double *vloss;             /* diagnostic: speed before the last step's energy-loss collision */
+    double *xmove;             /* diagnostic: cells of the last step's move that placed the particle */
 } species_t;
 
 typedef struct {
@@ -127,6 +129,7 @@ static int sp_reserve(species_t *s, int64_t cap)
 #define GROW(f, T) do { void *q = realloc(s->f, (size_t)nc * sizeof(T)); if (!q) return -1; s->f = q; } while (0)
     GROW(xi, double); GROW(vx, double); GROW(vy, double); GROW(vz, double);
     GROW(id, uint32_t); GROW(margin, double); GROW(event, int32_t); GROW(z, double); GROW(clk, int32_t);
+    GROW(vloss, double); GROW(xmove, double);
 #undef GROW
     s->cap = nc;
     return 0;
@@ -137,14 +140,14 @@ static int sp_push(species_t *s, double xi, double vx, double vy, double vz, uin
     if (sp_reserve(s, s->n + 1)) return -1;
     int64_t k = s->n++;
     s->xi[k] = xi; s->vx[k] = vx; s->vy[k] = vy; s->vz[k] = vz; s->id[k] = id;
-    s->margin[k] = INFINITY; s->event[k] = 0; s->z[k] = 0.0; s->clk[k] = 0;
+    s->margin[k] = INFINITY; s->event[k] = 0; s->z[k] = 0.0; s->clk[k] = 0; s->vloss[k] = 0.0; s->xmove[k] = 0.0;
     return 0;
 }
 
 static void sp_free(species_t *s)
 {
     free(s->xi); free(s->vx); free(s->vy); free(s->vz); free(s->id); free(s->margin); free(s->event); free(s->z);
-    free(s->clk);
+    free(s->clk); free(s->vloss); free(s->xmove);
     memset(s, 0, sizeof(*s));
 }
 
@@ -566,11 +569,14 @@ static int32_t first_clock(const or_case *c, int sp, uint32_t id)
 }
 
 /* append a particle created in this step to the pending list, with its clock */
-static void push_new(or_case *c, int sp, double xi, double vx, double vy, double vz, uint32_t id)
+static void push_new(or_case *c, int sp, double xi, double vx, double vy, double vz, uint32_t id,
+                     double vloss, double xmove)
 {
     species_t *pd = &c->pend[sp];
     if (sp_push(pd, xi, vx, vy, vz, id)) return;
     pd->clk[pd->n - 1] = first_clock(c, sp, id);
+    pd->vloss[pd->n - 1] = vloss;
+    pd->xmove[pd->n - 1] = xmove;
 }
 
 /* Count the clock down one step.  Returns 1 if this step is a collision
@@ -615,6 +621,7 @@ static int collide_electron(or_case *c, int64_t k, double *margin)
     }
     c->cnt.collisions[0][proc]++;
     double speed = sqrt(v2);
+    if (kind == OR_EXCITATION || kind == OR_IONIZATION) s->vloss[k] = speed;
     double n[3];
     iso_dir(or_uniform(r[2]), or_uniform(r[3]), n);
     if (kind == OR_ELASTIC) {
@@ -639,13 +646,13 @@ static int collide_electron(or_case *c, int64_t k, double *margin)
         double ne[3];
         iso_dir(or_uniform(a[1]), or_uniform(a[2]), ne);
         double spe = sqrt(2.0 * eej * ELEM / m);
-        push_new(c, 0, s->xi[k], spe * ne[0], spe * ne[1], spe * ne[2], ids[0]);
+        push_new(c, 0, s->xi[k], spe * ne[0], spe * ne[1], spe * ne[2], ids[0], speed, s->xmove[k]);
         if (c->p.n_species > 1) {
             double g0, g1, g2, g3;
             box_muller(or_uniform(b[0]), or_uniform(b[1]), &g0, &g1);
             box_muller(or_uniform(b[2]), or_uniform(b[3]), &g2, &g3);
             double vt = sqrt(KBOLTZ * c->p.gas_temp / c->p.m[1]);
-            push_new(c, 1, s->xi[k], vt * g0, vt * g1, vt * g2, ids[1]);
+            push_new(c, 1, s->xi[k], vt * g0, vt * g1, vt * g2, ids[1], 0.0, s->xmove[k]);
         }
         c->cnt.ionizations++;
     }
@@ -721,7 +728,7 @@ static void emit_secondary(or_case *c, uint32_t ion_id, int wall, double *margin
     double xi = wall == 0 ? d : N - d;
     if (xi >= N) xi = nextafter(N, 0.0);
     double vx = wall == 0 ? vn : -vn;
-    push_new(c, 0, xi, vx, vth * t0, vth * t1, ids[0]);
+    push_new(c, 0, xi, vx, vth * t0, vth * t1, ids[0], 0.0, d);
     c->cnt.see_emitted++;
     if (wall == 0) c->st_see0++;
 }
@@ -812,11 +819,13 @@ static int one_step(or_case *c)
         for (int64_t k = 0; k < sp->n; ++k) {
             double margin = INFINITY;
             int event = 0;
+            sp->vloss[k] = 0.0;
             double E[3], v[3] = { sp->vx[k], sp->vy[k], sp->vz[k] };
             gather(c, sp->xi[k], E);                                 /* 1 */
             or_boris(qm, p->dt, E, p->B, v);                         /* 2 */
             sp->vx[k] = v[0]; sp->vy[k] = v[1]; sp->vz[k] = v[2];
             double xn = sp->xi[k] + v[0] * dtdx;                     /* 3 */
+            sp->xmove[k] = fabs(v[0] * dtdx);
             margin = fminabs(margin, xn - floor(xn + 0.5));
             int absorbed = -1;
             if (p->periodic) {                                       /* x modulo the box, any distance */
@@ -859,6 +868,7 @@ static int one_step(or_case *c)
             sp->xi[keep] = sp->xi[k]; sp->vx[keep] = sp->vx[k]; sp->vy[keep] = sp->vy[k];
             sp->vz[keep] = sp->vz[k]; sp->id[keep] = sp->id[k]; sp->z[keep] = sp->z[k];
             sp->margin[keep] = margin; sp->event[keep] = event; sp->clk[keep] = sp->clk[k];
+            sp->vloss[keep] = sp->vloss[k]; sp->xmove[keep] = sp->xmove[k];
             ++keep;
         }
         sp->n = keep;
@@ -868,6 +878,8 @@ static int one_step(or_case *c)
         for (int64_t k = 0; k < pd->n; ++k) {
             if (sp_push(&c->sp[s], pd->xi[k], pd->vx[k], pd->vy[k], pd->vz[k], pd->id[k])) return -1;
             c->sp[s].clk[c->sp[s].n - 1] = pd->clk[k];
+            c->sp[s].vloss[c->sp[s].n - 1] = pd->vloss[k];
+            c->sp[s].xmove[c->sp[s].n - 1] = pd->xmove[k];
         }
     }
     if (p->circuit >= 1) {                                           /* charge reaching electrode 0 */
@@ -949,6 +961,20 @@ int or_get_particles(const or_case *c, int sp, double *xi, double *vx, double *v
     if (id) memcpy(id, s->id, n * sizeof(uint32_t));
     if (margin) memcpy(margin, s->margin, n * sizeof(double));
     if (event) memcpy(event, s->event, n * sizeof(int32_t));
+    return 0;
+}
+
+int or_get_loss_speed(const or_case *c, int sp, double *v)
+{
+    if (!c || sp < 0 || sp >= c->p.n_species || !v) return -1;
+    memcpy(v, c->sp[sp].vloss, (size_t)c->sp[sp].n * sizeof(double));
+    return 0;
+}
+
+int or_get_move(const or_case *c, int sp, double *d)
+{
+    if (!c || sp < 0 || sp >= c->p.n_species || !d) return -1;
+    memcpy(d, c->sp[sp].xmove, (size_t)c->sp[sp].n * sizeof(double));
     return 0;
 }
 

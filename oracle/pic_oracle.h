@@ -95,6 +95,18 @@ int64_t or_count(const or_case *c, int sp);
  * (0 none, 1 null candidate, 2+k process k, -1 absorbed).  Either may be NULL. */
 int  or_get_particles(const or_case *c, int sp, double *xi, double *vx, double *vy,
                       double *vz, uint32_t *id, double *margin, int32_t *event);
+/* Diagnostic of the last step, same order as or_get_particles: an electron's
+ * speed (m/s) just before a collision that took a threshold energy from it
+ * (excitation or ionization), and for the electron an ionization ejects, its
+ * parent's; 0 for every other particle.  A test uses it to scale the
+ * comparison of the energy left after the loss, which cancels against the
+ * threshold and carries the rounding of the energy before it. */
+int  or_get_loss_speed(const or_case *c, int sp, double *v);
+/* Diagnostic of the last step, same order: the length in cells of the move
+ * that placed the particle (its own |v_x| dt/dx; for an ionization product
+ * its parent's; for a secondary electron its distance from the wall).  The
+ * FP32 rounding of a position grows with it. */
+int  or_get_move(const or_case *c, int sp, double *d);
 /* axial excursion z (m) of each particle, same order as or_get_particles */
 int  or_get_axial(const or_case *c, int sp, double *z);
 /* collision clock 2 k + c of each particle, same order as or_get_particles */

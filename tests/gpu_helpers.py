@@ -29,8 +29,17 @@ def compare_species(g, o, n_cells, periodic, *, tol_x=1e-5, tol_v=1e-5, margin_t
     decision of the oracle explains.
 
     Per step, a position may differ by tol_x cells plus tol_x of the cells moved
-    in a step (|v| dt/dx: FP32 rounding of the move scales with it), a velocity
-    by tol_v of the speed; both bounds grow linearly with the number of steps."""
+    in a step (|v| dt/dx, or the move of the parent that placed an ionization
+    product: FP32 rounding of the move scales with it), a velocity
+    by tol_v of the speed; both bounds grow linearly with the number of steps.
+
+    An electron that lost a threshold energy in the last step (excitation, or
+    either electron of an ionization) keeps the energy eps - eps_thr - ...,
+    which cancels against the threshold: the FP32 rounding of eps, about
+    2^-24 eps, becomes a relative error of eps / (eps - eps_thr) in what is
+    left, without bound as the remainder goes to zero.  For these the speed is
+    compared through the energy, relative to the energy before the loss
+    (|v_g^2 - v_o^2| / (2 v_before^2)), and the direction, relative to 1."""
     xg = g["cell"].astype(np.float64) + g["off"].astype(np.float64)
     xo = o["xi"]
     assert g["id"].size == o["id"].size, (g["id"].size, o["id"].size)
@@ -44,7 +53,17 @@ def compare_species(g, o, n_cells, periodic, *, tol_x=1e-5, tol_v=1e-5, margin_t
         dx = np.minimum(dx, n_cells - dx)
     sp = np.maximum(np.linalg.norm(vo, axis=1), vfloor)
     dv = np.linalg.norm(vg - vo, axis=1) / np.where(sp > 0, sp, 1.0)
-    tx = tol_x * steps * (1.0 + np.linalg.norm(vo, axis=1) * dtdx)
+    vl = o["vloss"][oo] if "vloss" in o else np.zeros(len(oo))
+    lost = vl > 0
+    if lost.any():
+        g2, o2 = np.sum(vg[lost] ** 2, 1), np.sum(vo[lost] ** 2, 1)
+        ug = vg[lost] / np.maximum(np.sqrt(g2), 1e-300)[:, None]
+        uo = vo[lost] / np.maximum(np.sqrt(o2), 1e-300)[:, None]
+        dv[lost] = np.maximum(np.abs(g2 - o2) / (2.0 * vl[lost] ** 2), np.linalg.norm(ug - uo, axis=1))
+    move = np.linalg.norm(vo, axis=1) * dtdx
+    if "xmove" in o:                     # an ionization product sits where its parent's move put it
+        move = np.maximum(move, o["xmove"][oo])
+    tx = tol_x * steps * (1.0 + move)
     bad = (dx > tx) | (dv > tol_v * steps)
     margin = o["margin"][oo]
     unexplained = bad & ~(margin < margin_tol)

@@ -134,6 +134,37 @@ def test_full_size_ccp_one_step():
     gc.close()
 
 
+@pytest.mark.parametrize("shape", [(1024, 0), (512, 2)])
+def test_largest_grid_ccp_matches_oracle(shape):
+    """The largest grid the library takes (4096 cells): the step's shared
+    memory (node field, deposit histogram, tables, moments and every warp's
+    draw queue) at its largest, in 1024-thread CTAs with direct loads and in
+    512-thread CTAs with two particle tiles in flight, and the field solve
+    with 513 nodes a CTA; hot electrons so that collisions of every kind are
+    queued.  One step against the oracle, every particle (at 49 particles a
+    cell a near-threshold decision that flips in one step moves enough charge
+    to nudge its neighbours' fields in the next, so longer comparisons belong
+    to the statistical tests), then the field solved from that step's deposit
+    (compared at 1e-4 of its largest value, as in the one-step Langmuir test:
+    a flipped decision moves one particle's charge)."""
+    cfg, parts = W.ccp_case(seed=7, n_cells=4096, gap=0.04, n_per_species=200_000, mtorr=100.0, volts=300.0,
+                            te_ev=20.0)
+    oc = oracle_case(cfg, parts)
+    oc.step(1)
+    gc = gpu_case(cfg, parts)
+    gc.set_step_shape(0, *shape)
+    gc.set_step_shape(1, *shape)
+    gc.step(1)
+    compare_all(cfg, gc, oc)
+    co = oc.counters()
+    assert co["ionizations"] > 0 and co["absorbed"].sum() > 0
+    phi_g, E_g, _ = gc.field()
+    phi_o, E_o = oc.field()[:2]
+    assert np.allclose(E_g, E_o, rtol=0, atol=1e-4 * np.abs(E_o).max())
+    assert np.allclose(phi_g, phi_o, rtol=0, atol=1e-4 * np.abs(phi_o).max())
+    gc.close()
+
+
 @pytest.mark.parametrize("shape", [(512, 0), (1024, 0), (512, 1), (1024, 1), (256, 2)])
 def test_full_size_exb_one_step(shape):
     """The 1.02e7-particle E x B workload (2048 cells, 2500 per cell per species)
