@@ -165,6 +165,59 @@ def test_largest_grid_ccp_matches_oracle(shape):
     gc.close()
 
 
+def _cell_ordered_ccp(seed, ppc, n_cells=1024):
+    cfg, parts = W.ccp_case(seed=seed, n_cells=n_cells, n_per_species=ppc * n_cells, te_ev=2.0)
+    for p in parts:
+        order = np.argsort(W.as_xi(p), kind="stable")
+        for k in list(p):
+            p[k] = np.ascontiguousarray(p[k][order])
+    return cfg, parts
+
+
+def _assert_deposit_of_own_particles(case, n_cells):
+    R = case.field()[2]
+    for s in range(2):
+        p = case.particles(s)
+        xi = p["cell"].astype(np.float64) + p["off"].astype(np.float64)
+        assert np.array_equal(R[s], oracle.deposit(n_cells, False, xi)), s
+
+
+@pytest.mark.parametrize("ppc", [20, 90, 700])
+@pytest.mark.parametrize("shape", [(1024, 0), (512, 0)])
+def test_step_deposit_is_the_exact_deposit_of_the_stepped_particles(ppc, shape):
+    """The step kernel deposits rho^{n+1} while it moves the particles: a
+    shared per-cell histogram, fed by one warp-wide reduction where all of a
+    warp's particles share a cell (cell-ordered ions at 700 a cell) and by
+    per-lane shared atomics otherwise (warps that straddle cells, at 90 and 20
+    a cell; electrons, which move several cells a step), flushed as int64.
+    Its raw deposit equals, bit for bit, the oracle's fixed-point CIC deposit
+    of the particles the step leaves (paper section 1: charge assignment)."""
+    cfg, parts = _cell_ordered_ccp(11 + ppc, ppc)
+    gc = gpu_case(cfg, parts)
+    gc.set_step_shape(0, *shape)
+    gc.set_step_shape(1, *shape)
+    gc.step(1)
+    _assert_deposit_of_own_particles(gc, cfg["n_cells"])
+    gc.close()
+
+
+def test_batch_step_deposit_is_the_exact_deposit_of_the_stepped_particles():
+    """The same for the batch's grid of work items (shape 5), three
+    cell-ordered cases at 20, 90 and 700 particles a cell in one launch per
+    species."""
+    cases = [_cell_ordered_ccp(31 + ppc, ppc) for ppc in (20, 90, 700)]
+    b = pic.Batch([c for c, _ in cases], sort_interval=8)
+    b.set_shape(5)
+    for view, (_, parts) in zip(b.cases, cases):
+        for sp, p in enumerate(parts):
+            view.load(sp, p)
+    b.step(1)
+    b.sync()
+    for view, (cfg, _) in zip(b.cases, cases):
+        _assert_deposit_of_own_particles(view, cfg["n_cells"])
+    b.close()
+
+
 @pytest.mark.parametrize("shape", [(512, 0), (1024, 0), (512, 1), (1024, 1), (256, 2)])
 def test_full_size_exb_one_step(shape):
     """The 1.02e7-particle E x B workload (2048 cells, 2500 per cell per species)
