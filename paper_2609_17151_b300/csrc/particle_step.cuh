@@ -109,27 +109,70 @@ __device__ __forceinline__ uint32_t first_clock(const StepConst &P, int sp, uint
     return clock_state(u01(draw(P, id, step, sp, kBlkGap).x), lam);
 }
 
+// Particles a CTA appends (ionization products, secondary electrons) are
+// staged in shared memory, up to kAppendCap per species, and written out at
+// the end of its work item after one reservation on each species' counter
+// (append_flush): an appending lane then waits on a shared atomic, not on a
+// global one that returns.  A case that can append (an ionization process,
+// or secondary emission by ions) has the buffer; the others none.
+constexpr unsigned kAppendCap = 256;
+constexpr int kAppendArrays = 6;                        // cell word, off, vx, vy, vz, id
+__host__ __device__ inline unsigned append_cap(const StepConst &P)
+{
+    if (P.n_species > 1 && !P.periodic && P.see_gamma > 0.0f) return kAppendCap;
+    const SpConst &S = P.sp[0];
+    if (S.mcc == 1)
+        for (int k = 0; k < S.nproc && k < kMaxProc; ++k)
+            if (S.kind[k] == PIC_IONIZATION) return kAppendCap;
+    return 0u;
+}
+struct AppBuf {
+    uint32_t *base;                                     // [2 species][kAppendArrays][cap] words
+    unsigned cap;                                       // entries per species (0: no buffer)
+    unsigned *n;                                        // [2] entries taken (may pass cap)
+};
+
 // Append one particle to species `sp`, with its first collision clock; deposit
 // it into rho^{n+1} directly and add it to the diagnostic-step moments.  The
-// lanes of a warp that append together reserve their slots with one atomic
-// on the species' counter (the group of lanes active here), then take
-// consecutive slots in lane order.
-__device__ void append_particle(const StepConst &P, int sp, int half, int c, float o, float vx, float vy,
-                                float vz, uint32_t id, uint32_t step, bool diag)
+// lanes of a warp that append together take consecutive entries of the CTA's
+// buffer with one shared atomic (the group of lanes active here); once the
+// buffer is full they reserve slots of the species' arrays with one global
+// atomic and store there.  A slot beyond the capacity raises kErrCapacity and
+// the particle is dropped (its deposit is already made: the case is in error).
+__device__ void append_particle(const StepConst &P, const AppBuf &ab, int sp, int half, int c, float o, float vx,
+                                float vy, float vz, uint32_t id, uint32_t step, bool diag)
 {
     Ctrl *ctrl = P.ctrl;
-    const cooperative_groups::coalesced_group g = cooperative_groups::coalesced_threads();
-    unsigned long long base = 0ull;
-    if (g.thread_rank() == 0) base = atomicAdd(&ctrl->n_total[sp], (unsigned long long)g.size());
-    const unsigned long long slot = g.shfl(base, 0) + g.thread_rank();
-    if (slot >= P.cap[sp]) {
-        atomicOr(&ctrl->err, kErrCapacity);
-        return;
+    const uint32_t cw = (uint32_t)c | (first_clock(P, sp, id, step) << kCellBits);
+    unsigned k = ab.cap;
+    if (ab.cap != 0u) {
+        const cooperative_groups::coalesced_group g = cooperative_groups::coalesced_threads();
+        unsigned k0 = 0u;
+        if (g.thread_rank() == 0) k0 = atomicAdd(&ab.n[sp], g.size());
+        k = g.shfl(k0, 0) + g.thread_rank();
     }
-    const SpeciesBufs &B = P.buf[sp][half];
-    B.cell[slot] = c | (int)(first_clock(P, sp, id, step) << kCellBits);
-    B.off[slot] = o; B.vx[slot] = vx; B.vy[slot] = vy; B.vz[slot] = vz; B.id[slot] = id;
-    if (B.z) B.z[slot] = 0.0f;
+    if (k < ab.cap) {
+        uint32_t *a = ab.base + (size_t)sp * kAppendArrays * ab.cap + k;
+        a[0] = cw;
+        a[ab.cap] = __float_as_uint(o);
+        a[2 * ab.cap] = __float_as_uint(vx);
+        a[3 * ab.cap] = __float_as_uint(vy);
+        a[4 * ab.cap] = __float_as_uint(vz);
+        a[5 * ab.cap] = id;
+    } else {
+        const cooperative_groups::coalesced_group g = cooperative_groups::coalesced_threads();
+        unsigned long long base = 0ull;
+        if (g.thread_rank() == 0) base = atomicAdd(&ctrl->n_total[sp], (unsigned long long)g.size());
+        const unsigned long long slot = g.shfl(base, 0) + g.thread_rank();
+        if (slot >= P.cap[sp]) {
+            atomicOr(&ctrl->err, kErrCapacity);
+        } else {
+            const SpeciesBufs &B = P.buf[sp][half];
+            B.cell[slot] = (int)cw;
+            B.off[slot] = o; B.vx[slot] = vx; B.vy[slot] = vy; B.vz[slot] = vz; B.id[slot] = id;
+            if (B.z) B.z[slot] = 0.0f;
+        }
+    }
     const uint32_t f = __float2uint_rz(o * 4294967296.0f);
     unsigned long long *R = P.R[sp] + (size_t)(blockIdx.x % kDepositCopies) * P.r_stride;
     atomicAdd(&R[c], (1ull << 32) - f);
@@ -160,10 +203,12 @@ __device__ __forceinline__ uint4 draw(const CasePush &C, uint32_t id, uint32_t s
 
 // Electron collision candidate (null-collision method): the process from
 // word 1 of the step's block-0 draw r, the direction from words 2-3; v is
-// updated for a real collision.
-__device__ __forceinline__ void collide_electron(const StepConst &P, const CasePush &C, const float *nus, uint32_t id,
-                                                 uint32_t step, int c, float o, float3 &v, int half_e, int half_i,
-                                                 bool diag, EvCount &ev, const uint4 r)
+// updated for a real collision.  An ionization sets eej, the energy of the
+// ejected electron (otherwise left negative): the products are made by
+// ionization_products, 32 at a time.
+__device__ __forceinline__ void collide_electron(const StepConst &P, const CasePush &C, const float *nus,
+                                                 uint32_t id, uint32_t step, float3 &v, EvCount &ev, const uint4 r,
+                                                 float &eej_out)
 {
     const SpConst &S = P.sp[0];
     ev.cand++;
@@ -196,23 +241,36 @@ __device__ __forceinline__ void collide_electron(const StepConst &P, const CaseP
         v = make_float3(sp * n.x, sp * n.y, sp * n.z);
     } else {                                            // ionization: share eps - thr
         const uint4 a = draw(C, id, step, 0, kBlkAux);
-        const uint4 ids = draw(C, id, step, 0, kBlkChild);
         const float avail = fmaxf(eps - thr, 0.0f);
         const float eej = u01(a.x) * avail;
         const float esc = avail - eej;
         const float sp = S.v_of_sqrt_eps * sqrtf(esc);
         v = make_float3(sp * n.x, sp * n.y, sp * n.z);
-        const float3 ne = iso_dir(u01(a.y), u01(a.z));
-        const float spe = S.v_of_sqrt_eps * sqrtf(eej);
-        append_particle(P, 0, half_e, c, o, spe * ne.x, spe * ne.y, spe * ne.z, ids.x, step, diag);
-        if (P.n_species > 1) {
-            const uint4 b = draw(C, id, step, 0, kBlkNewIon);
-            const float2 g01 = box_muller(u01(b.x), u01(b.y));
-            const float2 g23 = box_muller(u01(b.z), u01(b.w));
-            const float vt = S.vt_newion;
-            append_particle(P, 1, half_i, c, o, vt * g01.x, vt * g01.y, vt * g23.x, ids.y, step, diag);
-        }
+        eej_out = eej;
         ev.iz++;
+    }
+}
+
+// The products of an ionization by electron `id` at (c, o): the ejected
+// electron (energy eej, direction from words 1-2 of the block-kBlkAux draw)
+// and, with ions, the new ion (Maxwellian at the gas temperature), with the
+// ids of the block-kBlkChild draw.
+__device__ __forceinline__ void ionization_products(const StepConst &P, const CasePush &C, const AppBuf &ab,
+                                                    uint32_t id, uint32_t step, int c, float o, float eej,
+                                                    int half_e, int half_i, bool diag)
+{
+    const SpConst &S = P.sp[0];
+    const uint4 a = draw(C, id, step, 0, kBlkAux);
+    const uint4 ids = draw(C, id, step, 0, kBlkChild);
+    const float3 ne = iso_dir(u01(a.y), u01(a.z));
+    const float spe = S.v_of_sqrt_eps * sqrtf(eej);
+    append_particle(P, ab, 0, half_e, c, o, spe * ne.x, spe * ne.y, spe * ne.z, ids.x, step, diag);
+    if (P.n_species > 1) {
+        const uint4 b = draw(C, id, step, 0, kBlkNewIon);
+        const float2 g01 = box_muller(u01(b.x), u01(b.y));
+        const float2 g23 = box_muller(u01(b.z), u01(b.w));
+        const float vt = S.vt_newion;
+        append_particle(P, ab, 1, half_i, c, o, vt * g01.x, vt * g01.y, vt * g23.x, ids.y, step, diag);
     }
 }
 
@@ -251,8 +309,8 @@ __device__ __forceinline__ void collide_ion(const StepConst &P, const CasePush &
 }
 
 // Secondary electron from an ion that reached electrode `wall`.
-__device__ __forceinline__ void emit_secondary(const StepConst &P, uint32_t id, uint32_t step, int wall, int half_e,
-                                               bool diag, EvCount &ev)
+__device__ __forceinline__ void emit_secondary(const StepConst &P, const AppBuf &ab, uint32_t id, uint32_t step,
+                                               int wall, int half_e, bool diag, EvCount &ev)
 {
     const uint4 r = draw(P, id, step, 1, kBlkSee);
     if (u01(r.x) >= P.see_gamma) return;
@@ -276,7 +334,7 @@ __device__ __forceinline__ void emit_secondary(const StepConst &P, uint32_t id, 
     if (o >= 1.0f) { o = 0.0f; c += 1; }
     if (c >= N) { c = N - 1; o = 0.99999994f; }
     const float vx = wall == 0 ? vn : -vn;
-    append_particle(P, 0, half_e, c, o, vx, P.see_vth * t.x, P.see_vth * t.y, ids.x, step, diag);
+    append_particle(P, ab, 0, half_e, c, o, vx, P.see_vth * t.x, P.see_vth * t.y, ids.x, step, diag);
     ev.see++;
     if (wall == 0) ev.see0++;
 }
@@ -329,18 +387,25 @@ __device__ __forceinline__ void hist_flush(const DepHist &h, int N, unsigned lon
 // most 32 CH entries, and the queue runs whenever 32 have gathered, so it
 // never holds more than 32 CH + 31.  0 without collisions.
 __host__ __device__ constexpr int draw_queue_cap(int mcc, int ch) { return mcc != 0 ? 32 * ch + 32 : 0; }
+// Ionizations whose products are still to be made, per warp: entries of
+// (cell, offset, parent id, eej).  A queue run of 32 draws adds at most 32, and
+// products are made whenever 32 have gathered, so 63 at most are waiting.
+// Electrons with cross-section tables only.
+constexpr int kChildWords = 4;
+__host__ __device__ constexpr int child_queue_cap(int sp, int mcc) { return (sp == 0 && mcc == 1) ? 64 : 0; }
 
 // Shared memory layout of the step kernel (bytes, 16-aligned pieces): node
 // field, deposit histogram, collision table, diagnostic moments, each warp's
-// draw queue (`qcap` 4-byte entries).  With `stages` > 0 the particle tiles
+// draw queue (`qcap` 4-byte entries), the append buffer (`apcap` entries a
+// species), each warp's queue of ionizations (`ccap` entries).  With `stages` > 0 the particle tiles
 // (one 4-particle chunk per thread, `narr` arrays of 16 bytes per chunk) pass
 // through `stages` buffers at the end.
 __host__ __device__ inline unsigned align16(unsigned x) { return (x + 15u) & ~15u; }
 __host__ __device__ inline unsigned align128(unsigned x) { return (x + 127u) & ~127u; }
 struct StepSmem {
-    unsigned e_off, h_off, nu_off, en_off, eepf_off, q_off, st_off, st_bytes, total;
+    unsigned e_off, h_off, nu_off, en_off, eepf_off, q_off, app_off, cq_off, st_off, st_bytes, total;
     __host__ __device__ StepSmem(int n_cells, int nproc, int threads = 0, int stages = 0, int narr = 0,
-                                 int qcap = 0)
+                                 int qcap = 0, unsigned apcap = 0, int ccap = 0)
     {
         e_off = 0;
         h_off = align16(e_off + (unsigned)n_cells * 8u);
@@ -348,10 +413,12 @@ struct StepSmem {
         en_off = align16(nu_off + (unsigned)nproc * kNGrid * 4u);
         eepf_off = align16(en_off + (unsigned)(n_cells + 1) * 4u);
         q_off = align16(eepf_off + kEepfBins * 4u);
-        const unsigned q_end = q_off + (unsigned)(threads / 32) * (unsigned)qcap * 4u;
-        st_off = align128(q_end);
+        app_off = align16(q_off + (unsigned)(threads / 32) * (unsigned)qcap * 4u);
+        cq_off = align16(app_off + 2u * kAppendArrays * apcap * 4u);
+        const unsigned cq_end = cq_off + (unsigned)(threads / 32) * (unsigned)ccap * kChildWords * 4u;
+        st_off = align128(cq_end);
         st_bytes = (unsigned)threads * 16u * (unsigned)narr;      // one stage
-        total = stages > 0 ? st_off + (unsigned)stages * st_bytes : align16(q_end);
+        total = stages > 0 ? st_off + (unsigned)stages * st_bytes : align16(cq_end);
     }
 };
 
@@ -420,8 +487,41 @@ struct StepShared {
     unsigned s_cnt[2 + 2 * kMaxProc];                   // candidates, per process, ionizations
     unsigned s_abs[2], s_see, s_see0, s_renew;
     unsigned hist_full;                                 // a deposit counter passed kCellFlush
+    unsigned app_n[2];                                  // append buffer entries taken, per species
+    unsigned long long app_base[2];                     // slots reserved for them at the item's end
     float s_red[2][kStepThreads / 32];
 };
+
+// End of a work item: the CTA's staged appends go to the species' arrays, at
+// slots reserved with one atomic per species, in coalesced stores.
+__device__ __forceinline__ void append_flush(const StepConst &P, const AppBuf &ab, StepShared &sh, int half_e,
+                                             int half_i)
+{
+    __syncthreads();                                    // every append of the CTA staged
+    for (int sp = 0; sp < P.n_species; ++sp) {
+        const unsigned na = min(ab.n[sp], ab.cap);      // the same for every thread
+        if (na == 0u) continue;
+        if (threadIdx.x == 0) sh.app_base[sp] = atomicAdd(&P.ctrl->n_total[sp], (unsigned long long)na);
+        __syncthreads();
+        const unsigned long long base = sh.app_base[sp];
+        const SpeciesBufs &B = P.buf[sp][sp == 0 ? half_e : half_i];
+        const uint32_t *a = ab.base + (size_t)sp * kAppendArrays * ab.cap;
+        for (unsigned i = threadIdx.x; i < na; i += blockDim.x) {
+            const unsigned long long slot = base + i;
+            if (slot >= P.cap[sp]) {
+                atomicOr(&P.ctrl->err, kErrCapacity);
+                break;
+            }
+            B.cell[slot] = (int)a[i];
+            B.off[slot] = __uint_as_float(a[ab.cap + i]);
+            B.vx[slot] = __uint_as_float(a[2 * ab.cap + i]);
+            B.vy[slot] = __uint_as_float(a[3 * ab.cap + i]);
+            B.vz[slot] = __uint_as_float(a[4 * ab.cap + i]);
+            B.id[slot] = a[5 * ab.cap + i];
+            if (B.z) B.z[slot] = 0.0f;
+        }
+    }
+}
 
 // One work item: chunks (CH particles) [beg, end) of the k-th of nk equal
 // slices of species SP of one case.  Stages the case's node field and the
@@ -449,7 +549,10 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
     constexpr int kArr = step_arrays(SP, PERIODIC, MCC);
     const int n_stages = STAGED ? S.stages : 0;
     constexpr int QCAP = draw_queue_cap(MCC, STAGED ? 4 : DCHUNK);
-    const StepSmem L(N, MCC == 1 ? S.nproc : 0, blockDim.x, n_stages, kArr, QCAP);
+    const unsigned apcap = append_cap(P);
+    constexpr int KCAP = child_queue_cap(SP, MCC);
+    const StepSmem L(N, MCC == 1 ? S.nproc : 0, blockDim.x, n_stages, kArr, QCAP, apcap, KCAP);
+    const AppBuf ab{reinterpret_cast<uint32_t *>(smem + L.app_off), apcap, sh.app_n};
     const float2 *Es = reinterpret_cast<const float2 *>(smem + L.e_off);
     const DepHist hist{reinterpret_cast<unsigned *>(smem + L.h_off), reinterpret_cast<unsigned *>(smem + L.h_off) + N,
                        reinterpret_cast<unsigned *>(smem + L.h_off) + 2 * N, &sh.hist_full};
@@ -486,7 +589,10 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
     if (diag) for (int j = tid; j < kEepfBins; j += blockDim.x) heepf[j] = 0u;
     if (tid < 2 + 2 * kMaxProc) s_cnt[tid] = 0u;
     if (tid < 2) s_abs[tid] = 0u;
-    if (tid == 0) { sh.s_see = 0u; sh.s_see0 = 0u; sh.s_renew = 0u; sh.hist_full = 0u; }
+    if (tid == 0) {
+        sh.s_see = 0u; sh.s_see0 = 0u; sh.s_renew = 0u; sh.hist_full = 0u;
+        sh.app_n[0] = 0u; sh.app_n[1] = 0u;
+    }
     const bool staged = mbar_wait_bounded(&sh.mbar, ctrl, parity, P.wait_polls);
     parity ^= 1u;
     if (!__syncthreads_and(staged)) return;
@@ -557,22 +663,60 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
     // keyed by the particle and the step, not by the lane that makes it.
     uint32_t *const Q = reinterpret_cast<uint32_t *>(smem + L.q_off) + warp * QCAP;
     int qn = 0;                                         // entries queued (warp-uniform)
-    auto run_queue = [&](int j) {                       // entry j of this warp's queue
-        const uint32_t w = Q[j];
-        const uint32_t e = w & 0x7fffffffu;
-        const uint32_t pid = Bi.id[e];
-        const int c = Bi.cell[e] & kCellMask;
-        float3 v = make_float3(Bi.vx[e], Bi.vy[e], Bi.vz[e]);
-        const float on = (diag || (SP == 0 && MCC == 1)) ? Bi.off[e] : 0.0f;   // appends, moments
-        const uint4 r = draw(C, pid, step, SP, kBlkMcc);
-        const uint32_t clk = clock_state(u01(r.x), H.lam);
-        if (w >> 31) {
-            if (SP == 0) collide_electron(P, C, nus, pid, step, c, on, v, half_e, half_i, diag, ev, r);
-            else collide_ion(P, C, nus, pid, step, v, ev, r);
+    // Ionizations: the scattered electron is finished in the queue run, the
+    // products (two more draws for the ejected electron and the ion, and each
+    // one's first collision clock: four Philox blocks) wait in a second
+    // per-warp queue and are made 32 at a time, so that the few lanes of a
+    // run that ionize do not hold the warp through that code alone.
+    uint32_t *const KQ = reinterpret_cast<uint32_t *>(smem + L.cq_off) + warp * KCAP * kChildWords;
+    int kn = 0;                                         // ionizations queued (warp-uniform)
+    const unsigned lt_mask = (1u << lane) - 1u;
+    auto run_children = [&](int j, bool valid) {        // entry j of the ionization queue
+        if (SP == 0 && valid)
+            ionization_products(P, C, ab, KQ[2 * KCAP + j], step, (int)KQ[j], __uint_as_float(KQ[KCAP + j]),
+                                __uint_as_float(KQ[3 * KCAP + j]), half_e, half_i, diag);
+    };
+    auto run_queue = [&](int j, bool valid) {           // entry j of this warp's draw queue (every lane)
+        float eej = -1.0f;
+        int c = 0;
+        float on = 0.0f;
+        uint32_t pid = 0u;
+        if (valid) {
+            const uint32_t w = Q[j];
+            const uint32_t e = w & 0x7fffffffu;
+            pid = Bi.id[e];
+            c = Bi.cell[e] & kCellMask;
+            float3 v = make_float3(Bi.vx[e], Bi.vy[e], Bi.vz[e]);
+            on = (diag || (SP == 0 && MCC == 1)) ? Bi.off[e] : 0.0f;   // ionization products, moments
+            const uint4 r = draw(C, pid, step, SP, kBlkMcc);
+            const uint32_t clk = clock_state(u01(r.x), H.lam);
+            if (w >> 31) {
+                if (SP == 0) collide_electron(P, C, nus, pid, step, v, ev, r, eej);
+                else collide_ion(P, C, nus, pid, step, v, ev, r);
+            }
+            Bi.cell[e] = c | (int)(clk << kCellBits);
+            Bi.vx[e] = v.x; Bi.vy[e] = v.y; Bi.vz[e] = v.z;
+            if (diag) moments(c, on, v);
         }
-        Bi.cell[e] = c | (int)(clk << kCellBits);
-        Bi.vx[e] = v.x; Bi.vy[e] = v.y; Bi.vz[e] = v.z;
-        if (diag) moments(c, on, v);
+        if (KCAP > 0) {
+            const unsigned m = __ballot_sync(0xffffffffu, eej >= 0.0f);
+            if (m != 0u) {                              // warp-uniform
+                if (eej >= 0.0f) {
+                    const int k = kn + __popc(m & lt_mask);
+                    KQ[k] = (uint32_t)c;
+                    KQ[KCAP + k] = __float_as_uint(on);
+                    KQ[2 * KCAP + k] = pid;
+                    KQ[3 * KCAP + k] = __float_as_uint(eej);
+                }
+                kn += __popc(m);
+                if (kn >= 32) {
+                    kn -= 32;
+                    __syncwarp();                       // the entries first
+                    run_children(kn + lane, true);
+                    __syncwarp();                       // the run's reads before new entries
+                }
+            }
+        }
     };
     const int check_every = max(1, (int)(kCellHeadroom / ((unsigned)T * (unsigned)CH)));
     int check_left = check_every, b = 0;
@@ -697,7 +841,7 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
                     const int bin = (int)(S.m_over_2e * (v.x * v.x + v.y * v.y + v.z * v.z) * P.ifedf_scale);
                     if (bin >= 0 && bin < kIfedfBins) atomicAdd(&P.ifedf[wall * kIfedfBins + bin], 1ull);
                 }
-                if (SP == 1 && P.see_gamma > 0.0f) emit_secondary(P, pid_of(), step, wall, half_e, diag, ev);
+                if (SP == 1 && P.see_gamma > 0.0f) emit_secondary(P, ab, pid_of(), step, wall, half_e, diag, ev);
                 cc[q] = -1;
                 oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
                 continue;
@@ -798,15 +942,20 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
                 while (qn >= 32) {
                     qn -= 32;
                     __syncwarp();                       // the entries and the chunk's stores first
-                    run_queue(qn + lane);
+                    run_queue(qn + lane, true);
                 }
             }
         }
     }
     if (QCAP > 0 && qn > 0) {                           // the rest of the queue
         __syncwarp();
-        if (lane < qn) run_queue(lane);
+        run_queue(lane, lane < qn);
     }
+    if (KCAP > 0 && kn > 0) {                           // the rest of the ionizations
+        __syncwarp();
+        run_children(lane, lane < kn);
+    }
+    if (apcap != 0u) append_flush(P, ab, sh, half_e, half_i);
     if (n_stages > 0) {
         __syncthreads();
         if (sh.tile_abort) {

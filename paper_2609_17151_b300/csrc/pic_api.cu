@@ -278,10 +278,11 @@ cudaError_t allow_max_step_smem(K k, std::once_flag &once, cudaError_t &err, int
 }
 
 // Tile buffers that fit next to the tables: `want`, fewer if shared memory is short.
-int fit_stages(int n_cells, int nproc, int threads, int want, int narr, int qcap, int limit)
+int fit_stages(int n_cells, int nproc, int threads, int want, int narr, int qcap, unsigned apcap, int ccap,
+               int limit)
 {
     int st = std::max(0, std::min(want, kMaxStages));
-    while (st > 0 && StepSmem(n_cells, nproc, threads, st, narr, qcap).total > (unsigned)limit) --st;
+    while (st > 0 && StepSmem(n_cells, nproc, threads, st, narr, qcap, apcap, ccap).total > (unsigned)limit) --st;
     return st;
 }
 
@@ -300,11 +301,13 @@ cudaError_t launch_step_k(pic_case *c, int stages)
     constexpr int qcap = draw_queue_cap(MCC, STAGED ? 4 : kDirectChunk);
     // each warp's draw queue grows the CTA's shared memory: a CTA that does
     // not fit next to the tables of the largest grids is halved
+    const unsigned apcap = append_cap(c->P);
+    constexpr int ccap = child_queue_cap(SP, MCC);
     int threads = c->step_threads[SP];
-    while (threads > 64 &&
-           StepSmem(c->d.n_cells, nproc, threads, stages, narr, qcap).total > (unsigned)step_smem_limit(c->device))
+    while (threads > 64 && StepSmem(c->d.n_cells, nproc, threads, stages, narr, qcap, apcap, ccap).total >
+                               (unsigned)step_smem_limit(c->device))
         threads /= 2;
-    const unsigned smem = StepSmem(c->d.n_cells, nproc, threads, stages, narr, qcap).total;
+    const unsigned smem = StepSmem(c->d.n_cells, nproc, threads, stages, narr, qcap, apcap, ccap).total;
     if (c->step_smem[SP] != smem || c->step_grid[SP] == 0 || c->step_grid_threads[SP] != threads ||
         c->step_grid_stages[SP] != stages) {
         int occ = 0;
@@ -328,7 +331,8 @@ cudaError_t launch_step_t(pic_case *c)
     if (c->P.axial_len > 0.0f) return launch_step_k<SP, PER, MCC, false, true>(c, 0);
     const int nproc = MCC == 1 ? c->P.sp[SP].nproc : 0;
     const int stages = fit_stages(c->d.n_cells, nproc, c->step_threads[SP], c->step_stages[SP],
-                                  step_arrays(SP, PER, MCC), draw_queue_cap(MCC, 4), step_smem_limit(c->device));
+                                  step_arrays(SP, PER, MCC), draw_queue_cap(MCC, 4), append_cap(c->P),
+                                  child_queue_cap(SP, MCC), step_smem_limit(c->device));
     return stages > 0 ? launch_step_k<SP, PER, MCC, true>(c, stages) : launch_step_k<SP, PER, MCC, false>(c, 0);
 }
 
@@ -1785,15 +1789,18 @@ namespace {
 constexpr long long kItemParticles = 262144;      // largest work item
 constexpr long long kMinItemParticles = 16384;    // smallest work item when splitting for balance
 
-// Shared memory of a batch launch shape: the largest case's tables, and the
-// draw queues of the shape's warps.
+// Shared memory of a batch launch shape: the largest case's tables, the draw
+// queues of the shape's warps, an append buffer and the electrons'
+// ionization queues (every case's layout fits in it: a case without appends
+// lays out no buffer, the ions no ionization queue).
 template <int M0, int M1, bool STAGED, int SHAPE>
 unsigned batch_smem(const pic_batch *b)
 {
     constexpr int ch = STAGED ? 4 : BatchShape<SHAPE>::chunk;
     constexpr int qcap = draw_queue_cap(M0, ch) > draw_queue_cap(M1, ch) ? draw_queue_cap(M0, ch)
                                                                             : draw_queue_cap(M1, ch);
-    return StepSmem(b->max_cells, b->max_nproc, BatchShape<SHAPE>::threads, STAGED ? b->run_stages : 0, 5, qcap)
+    return StepSmem(b->max_cells, b->max_nproc, BatchShape<SHAPE>::threads, STAGED ? b->run_stages : 0, 5, qcap,
+                    kAppendCap, child_queue_cap(0, M0))
         .total;
 }
 
@@ -2053,7 +2060,8 @@ pic_status batch_plan(pic_batch *b)
             const int np = c->P.sp[s].mcc == 1 ? c->P.sp[s].nproc : 0;
             const int narr = step_arrays(s, b->periodic != 0, c->P.sp[s].mcc);
             stages = std::min(stages, fit_stages(c->d.n_cells, np, BatchShape<0>::threads, stages, narr,
-                                                 draw_queue_cap(c->P.sp[s].mcc, 4), step_smem_limit(c->device)));
+                                                 draw_queue_cap(c->P.sp[s].mcc, 4), kAppendCap,
+                                                 child_queue_cap(s, c->P.sp[s].mcc), step_smem_limit(c->device)));
         }
     }
     int max_cells = 0, max_nproc = 0;
