@@ -555,76 +555,134 @@ __global__ void __launch_bounds__(1024) k_cells_scan(const unsigned *counts, int
     cells_scan(counts, N, cursor);
 }
 
-// Each CTA takes one contiguous chunk of the particles (chunk = n / grid,
-// rounded up to whole warps, so that every CTA of the grid works; the grid is
-// one wave of two 512-thread CTAs per SM).  It
-// reserves, per cell, one contiguous range for its chunk's particles (one
-// global atomic per touched cell), then places them with shared atomics,
-// kScatterUnroll particles per lane at a time with their loads issued first.
-constexpr int kScatterUnroll = 1;
+// Exclusive prefix sums out[j] = sum_{k<j} in[j] of N shared counters by the
+// whole CTA (each thread a run of consecutive counters); returns the total.
+__device__ __forceinline__ unsigned block_exclusive_u32(const unsigned *in, unsigned *out, int N, unsigned *wsum)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
+    const int per = (N + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int j0 = tid * per;
+    unsigned own = 0u;
+    for (int k = 0; k < per; ++k)
+        if (j0 + k < N) own += in[j0 + k];
+    unsigned x = own;                                   // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned w = lane < nw ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) wsum[lane] = w;
+    }
+    __syncthreads();
+    unsigned run = (warp > 0 ? wsum[warp - 1] : 0u) + x - own;
+    for (int k = 0; k < per; ++k)
+        if (j0 + k < N) { out[j0 + k] = run; run += in[j0 + k]; }
+    return wsum[nw - 1];
+}
+
+// Scatter of the counting sort.  Each CTA takes one contiguous chunk of the
+// particles (chunk = n / blocks, in whole warps) and moves it in tiles of
+// kScatterTile, kScatterPer particles a thread, all loads first:
+//   1. ranks within the tile's cells (shared counters, one atomic per run of
+//      equal cells in a warp);
+//   2. the cells' offsets in the tile (a prefix sum over the cells), and one
+//      range per touched cell reserved on the global cursor;
+//   3. the tile laid out in shared memory in cell order;
+//   4. stores from the cell-ordered tile: consecutive threads write
+//      consecutive slots of a cell's run, so that a run of k particles costs
+//      about k/8 sectors an array instead of up to one sector a particle.
+// Shared memory: scatter_smem(N).  The order within a cell is unspecified.
+constexpr int kScatterThreads = 512;
+constexpr int kScatterPer = 4;
+constexpr int kScatterTile = kScatterThreads * kScatterPer;
+constexpr int kScatterArrays = 7;                       // cell word, off, vx, vy, vz, id, z
+__host__ __device__ constexpr size_t scatter_smem(int N)
+{
+    return (size_t)N * 16u + (size_t)kScatterTile * kScatterArrays * 4u;
+}
 template <bool CLOCK>
 __device__ __forceinline__ void cells_scatter(SortHalves H, const int32_t *cur_dev, const unsigned long long *n_dev,
                                               long long n_host, int N, unsigned long long *cursor, int blk, int nblk)
 {
     extern __shared__ __align__(16) unsigned char xsm[];
-    unsigned long long *base = reinterpret_cast<unsigned long long *>(xsm);
-    unsigned *lcnt = reinterpret_cast<unsigned *>(xsm + 8 * (size_t)N);
-    for (int j = threadIdx.x; j < N; j += blockDim.x) lcnt[j] = 0u;
-    __syncthreads();
+    unsigned long long *gbase = reinterpret_cast<unsigned long long *>(xsm);   // [N] reserved global slot
+    unsigned *tcnt = reinterpret_cast<unsigned *>(xsm + 8 * (size_t)N);         // [N] tile count
+    unsigned *toff = tcnt + N;                                                   // [N] tile offset
+    uint32_t *stg = reinterpret_cast<uint32_t *>(xsm + 16 * (size_t)N);         // [arrays][kScatterTile]
+    __shared__ unsigned wsum[kScatterThreads / 32];
+    const int tid = threadIdx.x;
+    for (int j = tid; j < N; j += kScatterThreads) tcnt[j] = 0u;
     const int half = cur_dev ? *cur_dev : 0;
     const SpeciesBufs A = H.h[half], D = H.h[half ^ 1];
     const long long n = sort_count_of(n_dev, n_host);
     long long chunk = (n + nblk - 1) / nblk;
     chunk = (chunk + 31) & ~31ll;
     const long long lo = min((long long)blk * chunk, n), hi = min(lo + chunk, n);
-    const int lane = threadIdx.x & 31;
-    const long long T = blockDim.x;
-    for (long long w = lo + (threadIdx.x & ~31); w < hi; w += kSortUnroll * T) {
-        int cs[kSortUnroll];
-#pragma unroll
-        for (int u = 0; u < kSortUnroll; ++u) {
-            const long long i = w + u * T + lane;
-            cs[u] = i < hi ? sort_key<CLOCK>(A.cell[i]) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < kSortUnroll; ++u) warp_agg_inc(lcnt, cs[u], cs[u] >= 0 && cs[u] < N);
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const unsigned k = lcnt[j];
-        base[j] = k ? atomicAdd(&cursor[j], (unsigned long long)k) : 0ull;
-        lcnt[j] = 0u;
-    }
-    __syncthreads();
     const bool has_z = A.z != nullptr;
-    for (long long w = lo + (threadIdx.x & ~31); w < hi; w += kScatterUnroll * T) {
-        int c[kScatterUnroll];
-        float o[kScatterUnroll], vx[kScatterUnroll], vy[kScatterUnroll], vz[kScatterUnroll], z[kScatterUnroll];
-        uint32_t id[kScatterUnroll];
+    __syncthreads();
+    for (long long t0 = lo; t0 < hi; t0 += kScatterTile) {
+        int key[kScatterPer];
+        uint32_t val[kScatterPer][kScatterArrays];
 #pragma unroll
-        for (int u = 0; u < kScatterUnroll; ++u) {         // all loads before the ranking and the stores
-            const long long i = w + u * T + lane;
-            c[u] = -1; o[u] = vx[u] = vy[u] = vz[u] = z[u] = 0.f; id[u] = 0u;
-            if (i < hi) {
-                c[u] = A.cell[i]; o[u] = A.off[i]; vx[u] = A.vx[i]; vy[u] = A.vy[i]; vz[u] = A.vz[i]; id[u] = A.id[i];
-                if (has_z) z[u] = A.z[i];
-            }
+        for (int u = 0; u < kScatterPer; ++u) {             // all loads first (coalesced)
+            const long long i = t0 + (long long)u * kScatterThreads + tid;
+            const bool in = i < hi;
+            const int c = in ? A.cell[i] : -1;
+            val[u][0] = (uint32_t)c;
+            val[u][1] = in ? __float_as_uint(A.off[i]) : 0u;
+            val[u][2] = in ? __float_as_uint(A.vx[i]) : 0u;
+            val[u][3] = in ? __float_as_uint(A.vy[i]) : 0u;
+            val[u][4] = in ? __float_as_uint(A.vz[i]) : 0u;
+            val[u][5] = in ? A.id[i] : 0u;
+            val[u][6] = (in && has_z) ? __float_as_uint(A.z[i]) : 0u;
+            key[u] = sort_key<CLOCK>(c);
         }
+        unsigned rk[kScatterPer];
 #pragma unroll
-        for (int u = 0; u < kScatterUnroll; ++u) {
-            const int key = sort_key<CLOCK>(c[u]);
-            const bool live = key >= 0 && key < N;
-            const unsigned r = warp_agg_inc(lcnt, key, live);
-            if (!live) continue;
-            const unsigned long long p = base[key] + r;
-            D.cell[p] = c[u]; D.off[p] = o[u]; D.vx[p] = vx[u]; D.vy[p] = vy[u]; D.vz[p] = vz[u]; D.id[p] = id[u];
-            if (has_z) D.z[p] = z[u];
+        for (int u = 0; u < kScatterPer; ++u) rk[u] = warp_agg_inc(tcnt, key[u], key[u] >= 0 && key[u] < N);
+        __syncthreads();
+        const unsigned m = block_exclusive_u32(tcnt, toff, N, wsum);   // live particles of the tile
+        for (int j = tid; j < N; j += kScatterThreads) {
+            const unsigned k = tcnt[j];
+            if (k) gbase[j] = atomicAdd(&cursor[j], (unsigned long long)k);
         }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kScatterPer; ++u) {
+            if (key[u] < 0 || key[u] >= N) continue;
+            const unsigned sl = toff[key[u]] + rk[u];
+#pragma unroll
+            for (int a = 0; a < kScatterArrays; ++a) stg[a * kScatterTile + sl] = val[u][a];
+        }
+        __syncthreads();
+        for (unsigned j = tid; j < m; j += kScatterThreads) {
+            const int c = (int)stg[j];
+            const int k = sort_key<CLOCK>(c);
+            const unsigned long long p = gbase[k] + (j - toff[k]);
+            tcnt[k] = 0u;                                   // every touched cell has a particle here
+            D.cell[p] = c;
+            D.off[p] = __uint_as_float(stg[kScatterTile + j]);
+            D.vx[p] = __uint_as_float(stg[2 * kScatterTile + j]);
+            D.vy[p] = __uint_as_float(stg[3 * kScatterTile + j]);
+            D.vz[p] = __uint_as_float(stg[4 * kScatterTile + j]);
+            D.id[p] = stg[5 * kScatterTile + j];
+            if (has_z) D.z[p] = __uint_as_float(stg[6 * kScatterTile + j]);
+        }
+        __syncthreads();                                    // the tile's reads before the next tile's writes
     }
 }
 
 template <bool CLOCK>
-__global__ void __launch_bounds__(512, 2) k_cells_scatter(SortHalves H, const int32_t *cur_dev,
+__global__ void __launch_bounds__(kScatterThreads, 1) k_cells_scatter(SortHalves H, const int32_t *cur_dev,
                                                           const unsigned long long *n_dev, long long n_host, int N,
                                                           unsigned long long *cursor)
 {
@@ -680,7 +738,7 @@ __global__ void __launch_bounds__(1024) k_batch_cells_scan(const StepConst *__re
     if (sp >= P.n_species) return;
     cells_scan(P.sort_count, P.n_cells, P.sort_cursor);
 }
-__global__ void __launch_bounds__(512, 2) k_batch_cells_scatter(const StepConst *__restrict__ cases,
+__global__ void __launch_bounds__(kScatterThreads, 1) k_batch_cells_scatter(const StepConst *__restrict__ cases,
                                                                 const SortItem *__restrict__ items, int sp)
 {
     const SortItem it = items[blockIdx.x];

@@ -359,6 +359,30 @@ cudaError_t launch_field(pic_case *c, int mode)
     return cudaGetLastError();
 }
 
+// The scatter's shared memory passes the default 48 KB above about 600
+// cells: each scatter kernel is allowed the size of the largest grid once.
+template <typename K>
+cudaError_t allow_scatter_smem(K k, std::once_flag &once, cudaError_t &err)
+{
+    std::call_once(once, [&] {
+        err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem(4096));
+    });
+    return err;
+}
+template <bool CLOCK>
+cudaError_t allow_cells_scatter()
+{
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    return allow_scatter_smem(k_cells_scatter<CLOCK>, once, err);
+}
+cudaError_t allow_batch_scatter()
+{
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    return allow_scatter_smem(k_batch_cells_scatter, once, err);
+}
+
 cudaError_t launch_sort(pic_case *c, int sp)
 {
     const int N = c->d.n_cells;
@@ -370,8 +394,10 @@ cudaError_t launch_sort(pic_case *c, int sp)
     const int gc = (int)std::min<long long>(c->num_sms * 4, std::max<long long>(1, cap / 1024));
     k_cells_count<true><<<gc, 512, N * sizeof(unsigned), c->stream>>>(H, cur, n, 0, N, c->P.sort_count);
     k_cells_scan<<<1, 1024, N * sizeof(double), c->stream>>>(c->P.sort_count, N, c->P.sort_cursor);
-    const int gs = (int)std::min<long long>(c->num_sms * 2, std::max<long long>(1, (cap + 511) / 512));   // one wave
-    k_cells_scatter<true><<<gs, 512, 12 * (size_t)N, c->stream>>>(H, cur, n, 0, N, c->P.sort_cursor);
+    const int gs = (int)std::min<long long>(c->num_sms, std::max<long long>(1, (cap + 2047) / 2048));   // one wave
+    cudaError_t e = allow_cells_scatter<true>();
+    if (e != cudaSuccess) return e;
+    k_cells_scatter<true><<<gs, kScatterThreads, scatter_smem(N), c->stream>>>(H, cur, n, 0, N, c->P.sort_cursor);
     k_sort_finish<<<4, 256, 0, c->stream>>>(c->P, sp, c->P.sort_cursor + N);
     return cudaGetLastError();
 }
@@ -1729,8 +1755,9 @@ pic_status pic_sort_by_cell(int32_t n_cells, int64_t n, const int32_t *cell, con
         const int gc = (int)std::min<long long>(sms * 4, std::max<long long>(1, n / 1024));
         k_cells_count<false><<<gc, 512, N * sizeof(unsigned), st>>>(H, nullptr, nullptr, n, N, counts);
         k_cells_scan<<<1, 1024, N * sizeof(double), st>>>(counts, N, cursor);
-        const int gs = (int)std::min<long long>(sms * 2, std::max<long long>(1, (n + 511) / 512));
-        k_cells_scatter<false><<<gs, 512, 12 * (size_t)N, st>>>(H, nullptr, nullptr, n, N, cursor);
+        const int gs = (int)std::min<long long>(sms, std::max<long long>(1, (n + 2047) / 2048));
+        CU(allow_cells_scatter<false>());
+        k_cells_scatter<false><<<gs, kScatterThreads, scatter_smem(N), st>>>(H, nullptr, nullptr, n, N, cursor);
         CU(cudaGetLastError());
     }
     if (n_live) CU(cudaMemcpyAsync(n_live, cursor + N, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
@@ -1933,7 +1960,10 @@ cudaError_t batch_sort(pic_batch *b)
         const unsigned ni = (unsigned)b->n_sort_items[sp];
         k_batch_cells_count<<<ni, 512, maxN * sizeof(unsigned), b->stream>>>(b->d_cases, b->d_sort_items[sp], sp);
         k_batch_cells_scan<<<nc, 1024, maxN * sizeof(double), b->stream>>>(b->d_cases, sp);
-        k_batch_cells_scatter<<<ni, 512, 12 * (size_t)maxN, b->stream>>>(b->d_cases, b->d_sort_items[sp], sp);
+        cudaError_t ea = allow_batch_scatter();
+        if (ea != cudaSuccess) return ea;
+        k_batch_cells_scatter<<<ni, kScatterThreads, scatter_smem(maxN), b->stream>>>(b->d_cases, b->d_sort_items[sp],
+                                                                                       sp);
         k_batch_sort_finish<<<dim3(4, nc), 256, 0, b->stream>>>(b->d_cases, sp);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
