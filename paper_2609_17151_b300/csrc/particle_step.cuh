@@ -593,11 +593,6 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
         sh.s_see = 0u; sh.s_see0 = 0u; sh.s_renew = 0u; sh.hist_full = 0u;
         sh.app_n[0] = 0u; sh.app_n[1] = 0u;
     }
-    const bool staged = mbar_wait_bounded(&sh.mbar, ctrl, parity, P.wait_polls);
-    parity ^= 1u;
-    if (!__syncthreads_and(staged)) return;
-    if (n_stages > 0 && sh.tile_abort) return;          // this CTA gave up on its tiles earlier
-
     const int half = ctrl->cur[SP];
     const int half_e = ctrl->cur[0];
     const int half_i = P.n_species > 1 ? ctrl->cur[1] : 0;
@@ -610,6 +605,21 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
     if (AXIAL) Bi.z += item0;
     const unsigned n_ch = (unsigned)(end - beg);                               // chunks of the item
     const unsigned item_n = (unsigned)min(n - item0, (long long)n_ch * CH);   // its particles below n
+    const int T = blockDim.x;                           // chunks per tile
+    // PIPE: the next D chunks, loads in flight; the first ones are issued
+    // before the wait for the node field, so that both arrive together
+    constexpr int D = PIPE ? DDEPTH : 1;
+    Chunk<CH> nx[D] = {};
+    if (PIPE) {
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+            if ((unsigned)(d * T + tid) < n_ch) load_chunk<CH, AXIAL>(nx[d], Bi, (unsigned)(d * T + tid) * CH);
+    }
+
+    const bool staged = mbar_wait_bounded(&sh.mbar, ctrl, parity, P.wait_polls);
+    parity ^= 1u;
+    if (!__syncthreads_and(staged)) return;
+    if (n_stages > 0 && sh.tile_abort) return;          // this CTA gave up on its tiles earlier
 
     const float dtdx = P.dtdx;
     const int lane = tid & 31, warp = tid >> 5;
@@ -617,7 +627,6 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
     EvCount ev{};
 
     unsigned long long *const R_cta = P.R[SP] + (size_t)(blockIdx.x % kDepositCopies) * P.r_stride;
-    const int T = blockDim.x;                           // chunks per tile
     const int n_warps = T >> 5;
     const int n_tiles = (int)((end - beg + T - 1) / T);
     unsigned char *const tiles = smem + L.st_off;
@@ -720,13 +729,6 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
     };
     const int check_every = max(1, (int)(kCellHeadroom / ((unsigned)T * (unsigned)CH)));
     int check_left = check_every, b = 0;
-    constexpr int D = PIPE ? DDEPTH : 1;
-    Chunk<CH> nx[D] = {};                               // PIPE: the next D chunks, loads in flight
-    if (PIPE) {
-#pragma unroll
-        for (int d = 0; d < D; ++d)
-            if ((unsigned)(d * T + tid) < n_ch) load_chunk<CH, AXIAL>(nx[d], Bi, (unsigned)(d * T + tid) * CH);
-    }
     for (int k = 0; k < n_tiles; ++k) {
         if (check_left == 0) {                           // uniform over the CTA
             check_left = check_every;
