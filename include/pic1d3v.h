@@ -286,8 +286,9 @@ pic_status pic_read_moments(pic_case *c, pic_moments *out);
  * and the step kernel's launch shape: CTA size (256, 512 or 1024 threads)
  * and particle tiles in flight through shared memory (0 = each thread loads
  * its own particles; 1 or 2 = bulk-copy pipeline); otherwise (1024, 0) and
- * desc.sort_interval stand.  shape_ms[s][k] is the mean step-kernel time of
- * candidate k = (1024,0), (512,0), (256,0), (1024,1), (512,1), (512,2); sort_ms
+ * desc.sort_interval stand.  shape_ms[s][k] is the fastest of three timed
+ * step-kernel launches of candidate k = (1024,0), (512,0), (256,0), (1024,1),
+ * (512,1), (512,2) (the tuner keeps the least); sort_ms
  * the time of one sort; slope_ms the growth of the step-kernel time per step
  * that the tuner extends beyond its timing window (the fitted slope of the
  * window's second half less two standard errors, not below zero; all zero
@@ -442,7 +443,7 @@ pic_status pic_batch_set_own_threshold(pic_batch *b, int64_t particles);
  * items and the cases' push constants in the kernel parameter, up to 256
  * cases and one species per launch: 4: 1024-thread CTAs, 5: 640-thread
  * CTAs), *sort_interval, *tuned (1 once the autotuner ran), and its
- * measurements: shape_ms[6] (mean step time per shape) and *sort_ms (one
+ * measurements: shape_ms[6] (fastest step of each shape over two rounds) and *sort_ms (one
  * batched sort).  Any output pointer may be NULL. */
 pic_status pic_batch_tuning(pic_batch *b, int *shape, int *sort_interval, int *tuned, float *shape_ms,
                             float *sort_ms, float *step_ms);

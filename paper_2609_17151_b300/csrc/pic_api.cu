@@ -571,7 +571,9 @@ cudaError_t launch_one_step(pic_case *c)
 //     lost their cell order.  Continuing from the state step 1 left
 //     (the particle order of the middle of a sort period), the candidates
 //     take turns, one step each, for kShapeRounds rounds; each species keeps
-//     the candidate with the least summed kernel time.
+//     the candidate whose fastest round is the fastest (a candidate's first
+//     launch can carry the loading of its kernel, or another one-off delay,
+//     which a mean over the rounds would count against it).
 // Particle results do not depend on any of these choices (the deposit is
 // exact integer arithmetic); only FP32/FP64 moment sums may change in their
 // last bits with the launch shape.  Results are kept per case shape for the
@@ -735,12 +737,13 @@ pic_status autotune(pic_case *c, int64_t *left)
         r.K[s] = std::max(4, std::min(kMaxSortInterval, r.K[s]));
         c->tune_sort_ms[s] = ts;
         c->tune_slope_ms[s] = (float)fit.slope;
-        float shape_ms[kShapes] = {};
+        float shape_ms[kShapes];
+        for (int k = 0; k < kShapes; ++k) shape_ms[k] = 3.0e38f;
         for (int rnd = 0; rnd < kShapeRounds; ++rnd)
             for (int k = 0; k < kShapes; ++k) {
                 float t = 0.f;
                 CU(cudaEventElapsedTime(&t, shev[4 * (rnd * kShapes + k) + 2 * s], shev[4 * (rnd * kShapes + k) + 2 * s + 1]));
-                shape_ms[k] += t / kShapeRounds;
+                shape_ms[k] = std::min(shape_ms[k], t);
             }
         int best = 0;
         for (int k = 1; k < kShapes; ++k)
@@ -2194,14 +2197,14 @@ pic_status batch_autotune(pic_batch *b, int64_t *left)
         }
     CU(cudaStreamSynchronize(b->stream));
     int best = 0;
-    for (int k = 0; k < kBatchShapes; ++k) {
-        float tot = 0.f;
+    for (int k = 0; k < kBatchShapes; ++k) {               // the fastest round of each shape
+        float best_t = 3.0e38f;
         for (int rnd = 0; rnd < kBatchShapeRounds; ++rnd) {
             float t = 0.f;
             CU(cudaEventElapsedTime(&t, ev.v[2 * (rnd * kBatchShapes + k)], ev.v[2 * (rnd * kBatchShapes + k) + 1]));
-            tot += t;
+            best_t = std::min(best_t, t);
         }
-        b->tune_shape_ms[k] = tot / kBatchShapeRounds;
+        b->tune_shape_ms[k] = best_t;
         if (k < shapes && b->tune_shape_ms[k] < b->tune_shape_ms[best]) best = k;
     }
     b->shape = best;
