@@ -165,6 +165,41 @@ def test_largest_grid_ccp_matches_oracle(shape):
     gc.close()
 
 
+@pytest.mark.parametrize("mode", ["1024", "512", "batch-grid"])
+def test_appends_beyond_a_ctas_buffer_match_oracle(mode):
+    """100 eV electrons in 300 mTorr argon: about one in seven ionizes in one
+    step, so a CTA appends about 600 particles of each species with 1024
+    threads, 300 with 512, and a work item of the batch's grid tens of
+    thousands: beyond the 256 a species that a CTA stages in shared memory,
+    the rest take their slots directly.  Every particle, the products
+    included, against the oracle after one step."""
+    n = 600_000
+    cfg, parts = W.ccp_case(seed=9, n_cells=256, gap=0.025, n_per_species=n, mtorr=300.0, volts=100.0,
+                            te_ev=100.0)
+    oc = oracle_case(cfg, parts)
+    oc.step(1)
+    co = oc.counters()
+    assert co["ionizations"] > n // 8
+    if mode == "batch-grid":
+        b = pic.Batch([cfg], sort_interval=8)
+        b.set_shape(5)
+        for sp, p in enumerate(parts):
+            b.cases[0].load(sp, p)
+        b.step(1)
+        b.sync()
+        compare_all(cfg, b.cases[0], oc)
+        assert b.cases[0].count()[1] == oc.count(1)
+        b.close()
+    else:
+        gc = gpu_case(cfg, parts)
+        gc.set_step_shape(0, int(mode), 0)
+        gc.set_step_shape(1, int(mode), 0)
+        gc.step(1)
+        compare_all(cfg, gc, oc)
+        assert gc.count()[1] == oc.count(1)
+        gc.close()
+
+
 def _cell_ordered_ccp(seed, ppc, n_cells=1024):
     cfg, parts = W.ccp_case(seed=seed, n_cells=n_cells, n_per_species=ppc * n_cells, te_ev=2.0)
     for p in parts:
