@@ -788,14 +788,12 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
         float (&za)[CH] = t.z;
         int dc[CH];
         uint32_t df[CH];
-        bool need[CH], cand[CH];                        // clock ended: queue the draw
+        unsigned needm = 0u, candm = 0u;                // bit q: clock ended (queue the draw), candidate
         const int n_valid = live_chunk ? (int)min((unsigned)CH, item_n - e0) : 0;   // particles of the chunk below n
 #pragma unroll
         for (int q = 0; q < CH; ++q) {
             dc[q] = -1;
             df[q] = 0;
-            need[q] = false;
-            cand[q] = false;
             int c = cc[q];
             if (q >= n_valid || c < 0) continue;
             uint32_t clk = (uint32_t)c >> kCellBits;     // collision clock 2 k + c
@@ -871,14 +869,14 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
                 if (clk >= 2u) {
                     clk -= 2u;
                 } else {
-                    need[q] = true;
-                    cand[q] = (clk & 1u) == 0u;
+                    needm |= 1u << q;
+                    candm |= ((clk & 1u) ^ 1u) << q;
                 }
             }
             cc[q] = c | (int)(clk << kCellBits); oo[q] = on; vx[q] = v.x; vy[q] = v.y; vz[q] = v.z;
             dc[q] = c;
             df[q] = __float2uint_rz(on * 4294967296.0f);
-            if (diag && !need[q]) moments(c, on, v);
+            if (diag && !((needm >> q) & 1u)) moments(c, on, v);
         }
         // write back (never past n: slots beyond belong to this step's appends)
         if (live_chunk) {
@@ -927,18 +925,15 @@ __device__ __forceinline__ void particle_item(const StepConst &P, const CasePush
         }
         // queue the chunk's clock ends (slot order within the warp), run full batches
         if (QCAP > 0) {
-            bool mine = false;
-#pragma unroll
-            for (int q = 0; q < CH; ++q) mine = mine || need[q];
-            if (__any_sync(0xffffffffu, mine)) {        // warp-uniform; rare where collisions are
+            if (__any_sync(0xffffffffu, needm != 0u)) {        // warp-uniform; rare where collisions are
                 unsigned m[CH];
 #pragma unroll
-                for (int q = 0; q < CH; ++q) m[q] = __ballot_sync(0xffffffffu, need[q]);
+                for (int q = 0; q < CH; ++q) m[q] = __ballot_sync(0xffffffffu, (needm >> q) & 1u);
                 __syncwarp();                           // the last run's reads before new entries
                 const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
                 for (int q = 0; q < CH; ++q) {
-                    if (need[q]) Q[qn + __popc(m[q] & lt)] = (e0 + (unsigned)q) | (cand[q] ? 0x80000000u : 0u);
+                    if ((needm >> q) & 1u) Q[qn + __popc(m[q] & lt)] = (e0 + (unsigned)q) | (((candm >> q) & 1u) << 31);
                     qn += __popc(m[q]);
                 }
                 while (qn >= 32) {
