@@ -449,9 +449,11 @@ __host__ __device__ constexpr int field_threads_for(int n_cells, int cl)
 
 // The batch's field solves, one launch per cluster size: cluster k solves case
 // case_of[k] (the cases whose grids need CL CTAs).  The last launch of the
-// step also resets the batch work-item counter for the next step.
+// step also resets the batch work-item counter for the next step.  Clusters
+// of 4 and 8 CTAs run two CTAs an SM (56 registers, some spilled): at one an
+// SM, with 96 registers, a sweep's largest grids solved in about four waves.
 template <int CL>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kFieldThreads)
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kFieldThreads, CL >= 4 ? 2 : 1)
     k_batch_field(const StepConst *__restrict__ cases, const int *__restrict__ case_of, int mode, unsigned *next_item)
 {
     field_solve<CL>(cases[case_of[blockIdx.x / CL]], mode);
