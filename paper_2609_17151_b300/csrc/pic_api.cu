@@ -1439,8 +1439,6 @@ pic_status pic_read_moments(pic_case *c, pic_moments *m)
     std::vector<unsigned long long> ee(kEepfBins), ifd(2 * kIfedfBins);
     CU(cudaMemcpyAsync(ee.data(), c->P.eepf, kEepfBins * 8, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(ifd.data(), c->P.ifedf, 2 * kIfedfBins * 8, cudaMemcpyDeviceToHost, c->stream));
-    std::vector<double> fe((size_t)c->P.fe_cap * kFieldCluster);
-    CU(cudaMemcpyAsync(fe.data(), c->P.fe_hist, fe.size() * 8, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     m->n_nodes = (int32_t)nn;
     m->step = h.step;
@@ -1471,14 +1469,26 @@ pic_status pic_read_moments(pic_case *c, pic_moments *m)
     m->electrode_charge = h.q_el;
     m->renewed[0] = (int64_t)h.renewed[0];
     m->renewed[1] = (int64_t)h.renewed[1];
-    const long long have = std::min<long long>((long long)h.fe_n, c->P.fe_cap);
+    // the oldest `want` entries of the ring that are still held: at most two
+    // contiguous pieces of it, copied only when asked for
+    const long long cap = c->P.fe_cap;
+    const long long have = std::min<long long>((long long)h.fe_n, cap);
     long long want = m->field_energy ? std::min<long long>(have, m->field_energy_cap) : 0;
-    for (long long i = 0; i < want; ++i) {
-        const long long idx = (long long)h.fe_n - have + i;
-        const size_t e0 = (size_t)(idx % c->P.fe_cap) * kFieldCluster;
-        double v = 0.0;
-        for (int r = 0; r < kFieldCluster; ++r) v += fe[e0 + r];      // rank order
-        m->field_energy[i] = v;
+    if (want > 0) {
+        std::vector<double> fe((size_t)want * kFieldCluster);
+        const long long p0 = ((long long)h.fe_n - have) % cap;
+        const long long n1 = std::min(want, cap - p0);
+        CU(cudaMemcpyAsync(fe.data(), c->P.fe_hist + (size_t)p0 * kFieldCluster, (size_t)n1 * kFieldCluster * 8,
+                           cudaMemcpyDeviceToHost, c->stream));
+        if (want > n1)
+            CU(cudaMemcpyAsync(fe.data() + (size_t)n1 * kFieldCluster, c->P.fe_hist,
+                               (size_t)(want - n1) * kFieldCluster * 8, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        for (long long i = 0; i < want; ++i) {
+            double v = 0.0;
+            for (int r = 0; r < kFieldCluster; ++r) v += fe[(size_t)i * kFieldCluster + r];   // rank order
+            m->field_energy[i] = v;
+        }
     }
     m->field_energy_n = want;
     pic_status st = device_error(c);

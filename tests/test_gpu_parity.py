@@ -678,6 +678,29 @@ def test_thirty_percent_seed_oneil_oscillation_on_gpu():
     assert rise > 1.8 and rise > 4.0 * landau, (rise, landau)
 
 
+@pytest.mark.parametrize("history,steps,want", [(0, 40, 25), (16, 50, 10), (16, 50, 16)])
+def test_field_energy_history_matches_oracle(history, steps, want):
+    """The field energy of each step (the sum over nodes of eps0 E^2 / 2 times
+    the node volume, the trace of paper section 3.1's Langmuir case) kept in
+    the case's ring of `field_history` entries (0: 65536), read back for the
+    oldest `want` entries still held, against the oracle's trace.  A ring of
+    16 after 50 steps holds steps 35-50 from slot 2 on, so reading all 16
+    takes two pieces."""
+    cfg, parts = W.langmuir_case(seed=1)
+    oc = oracle_case(cfg, parts)
+    oc.step(steps)
+    gc = gpu_case(cfg, parts, field_history=history)
+    gc.step(steps)
+    got = gc.moments(field_energy_cap=want)["field_energy"]
+    fo = oc.field_energy()
+    assert fo.size == steps
+    have = min(steps, history or 65536)
+    ref = fo[steps - have: steps - have + want]
+    assert got.size == want
+    assert np.allclose(got, ref, rtol=1e-4, atol=1e-4 * np.abs(fo).max())
+    gc.close()
+
+
 def test_diagnostic_moments_match_oracle():
     cfg, parts = small_ccp(seed=11, n=20001, te=5.0)
     cfg["diag_interval"] = 2
