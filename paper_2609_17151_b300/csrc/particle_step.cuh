@@ -434,6 +434,9 @@ __host__ __device__ constexpr int step_arrays(int, bool, int) { return 5; }
 // chunk ahead measured fastest on the E x B box: chunks of one with two to
 // four ahead, chunks of two with two ahead, and chunks of four without any
 // were slower.  The staged path always moves chunks of four.
+// Particles a load-time deposit CTA adds to its shared histogram between
+// flushes: a cell's sums of f >> 16 and f & 0xFFFF then stay below 2^31.
+constexpr int kDepositSpan = 32768;
 constexpr int kDirectChunk = 2;
 constexpr int kDirectDepth = 1;
 
@@ -1257,23 +1260,47 @@ __global__ void k_load_profile(SpeciesBufs B, long long n, int N, const double *
 // Deposit of all particles of a species (the state at load), validation of
 // the loaded cells/offsets (plain cell indices: a load starts every species'
 // clocks afresh), and each particle's first collision clock.
-__global__ void k_deposit_species(const __grid_constant__ StepConst P, int sp)
+__global__ void __launch_bounds__(256) k_deposit_species(const __grid_constant__ StepConst P, int sp)
 {
+    // the particles of a CTA's contiguous chunk go into a shared histogram
+    // (count, sum of f >> 16, sum of f & 0xFFFF per cell; 12 N bytes), flushed
+    // to the raw deposit after every kDepositSpan particles, so that no counter
+    // overflows and each cell costs two global atomics a flush instead of two
+    // a particle
+    extern __shared__ unsigned dsm[];
     const SpeciesBufs B = P.buf[sp][P.ctrl->cur[sp]];
     const long long n = (long long)P.ctrl->n_active[sp];
     const int N = P.n_cells;
     const uint32_t step = (uint32_t)P.ctrl->step;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = B.cell[i];
-        const float o = B.off[i];
-        if (c < 0) continue;
-        if (c >= N || !(o >= 0.0f && o < 1.0f)) { atomicOr(&P.ctrl->err, kErrLoad); B.cell[i] = -1; continue; }
-        if (P.push.sp[sp].lam > 0.0f) B.cell[i] = c | (int)(first_clock(P, sp, B.id[i], step) << kCellBits);
-        const uint32_t f = __float2uint_rz(o * 4294967296.0f);
-        const int c1 = (P.periodic && c + 1 == N) ? 0 : c + 1;
-        unsigned long long *R = P.R[sp] + (size_t)(blockIdx.x % kDepositCopies) * P.r_stride;
-        atomicAdd(&R[c], (1ull << 32) - f);
-        atomicAdd(&R[c1], (unsigned long long)f);
+    unsigned *cnt = dsm, *fhi = dsm + N, *flo = dsm + 2 * N;
+    for (int j = threadIdx.x; j < 3 * N; j += blockDim.x) dsm[j] = 0u;
+    const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    const long long lo = min((long long)blockIdx.x * chunk, n), hi = min(lo + chunk, n);
+    unsigned long long *R = P.R[sp] + (size_t)(blockIdx.x % kDepositCopies) * P.r_stride;
+    for (long long s0 = lo; s0 < hi; s0 += kDepositSpan) {
+        __syncthreads();                                // counters zero
+        const long long s1 = min(s0 + (long long)kDepositSpan, hi);
+        for (long long i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+            const int c = B.cell[i];
+            const float o = B.off[i];
+            if (c < 0) continue;
+            if (c >= N || !(o >= 0.0f && o < 1.0f)) { atomicOr(&P.ctrl->err, kErrLoad); B.cell[i] = -1; continue; }
+            if (P.push.sp[sp].lam > 0.0f) B.cell[i] = c | (int)(first_clock(P, sp, B.id[i], step) << kCellBits);
+            const uint32_t f = __float2uint_rz(o * 4294967296.0f);
+            atomicAdd(&cnt[c], 1u);
+            atomicAdd(&fhi[c], f >> 16);
+            atomicAdd(&flo[c], f & 0xFFFFu);
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < N; c += blockDim.x) {
+            const unsigned k = cnt[c];
+            if (k == 0u) continue;
+            const unsigned long long F = ((unsigned long long)fhi[c] << 16) + flo[c];
+            const int c1 = (P.periodic && c + 1 == N) ? 0 : c + 1;
+            atomicAdd(&R[c], ((unsigned long long)k << 32) - F);
+            atomicAdd(&R[c1], F);
+            cnt[c] = 0u; fhi[c] = 0u; flo[c] = 0u;
+        }
     }
 }
 

@@ -449,7 +449,7 @@ pic_status initialise(pic_case *c)
         CU(cudaMemsetAsync(c->P.R[s], 0, sizeof(unsigned long long) * kDepositCopies * c->P.r_stride, c->stream));
     Timed t(c, KC_INIT, c->d.n_species * (c->d.rewind ? 2 : 1));
     for (int s = 0; s < c->d.n_species; ++s) {
-        k_deposit_species<<<c->num_sms * 4, 256, 0, c->stream>>>(c->P, s);
+        k_deposit_species<<<c->num_sms * 4, 256, 12 * (size_t)c->d.n_cells, c->stream>>>(c->P, s);
         CU(cudaGetLastError());
     }
     CU(launch_field(c, 0));
