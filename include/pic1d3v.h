@@ -265,7 +265,9 @@ typedef struct {
     double *en_sum;                /* [n_species * n_nodes] sum w eps (eV m^-3), diagnostic steps */
     double *dens_diag_sum;         /* [n_species * n_nodes] density on diagnostic steps */
     double *eepf;                  /* [PIC_EEPF_BINS] electron counts in the central 10 % of the gap */
-    double *field_energy;          /* [field_energy_cap] field energy per area (J/m^2) per step */
+    double *field_energy;          /* [field_energy_cap] field energy per area (J/m^2) per step: the
+                                      oldest entries the ring of desc.field_history still holds, in
+                                      step order (NULL or cap 0: none is copied) */
     int64_t field_energy_cap;      /* in */
     int64_t field_energy_n;        /* out: entries written */
     int32_t reset;                 /* in: nonzero = clear the sums after reading */
