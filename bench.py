@@ -734,20 +734,39 @@ def main():
         # end to end through the C ABI on the warmed case: load from pinned host
         # buffers, K steps, moments back to host
         # (the synthetic ids are 0..n-1, which the library generates when id is NULL)
+        # Pinned host buffers from cudaHostAlloc: with torch's pin_memory the
+        # buffer allocated second uploaded at about 35 GB/s instead of 52.
+        from cuda.bindings import runtime as cudart
+        import ctypes
+        host_ptrs = []
+
+        def pinned_copy(a):
+            a = np.ascontiguousarray(a)
+            err, ptr = cudart.cudaHostAlloc(a.nbytes, cudart.cudaHostAllocDefault)
+            if int(err) != 0:
+                raise RuntimeError(f"cudaHostAlloc: {err}")
+            host_ptrs.append(ptr)
+            view = np.frombuffer((ctypes.c_char * a.nbytes).from_address(int(ptr)), dtype=a.dtype, count=a.size)
+            view[:] = a
+            return view
+
         pinned = []
         for p in parts:
             assert np.array_equal(p["id"], np.arange(p["id"].size, dtype=np.uint32))
-            pinned.append({k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in p.items() if k != "id"})
-        h2d = sum(t.numel() * t.element_size() for p in pinned for t in p.values())
+            pinned.append({k: pinned_copy(v) for k, v in p.items() if k != "id"})
+        h2d = sum(a.nbytes for p in pinned for a in p.values())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s, p in enumerate(pinned):
-            pic.check(pic.lib.pic_load_particles(case.h, s, p["cell"].numel(), p["cell"].data_ptr(),
-                                                 p["off"].data_ptr(), p["vx"].data_ptr(), p["vy"].data_ptr(),
-                                                 p["vz"].data_ptr(), None, 0))
+            pic.check(pic.lib.pic_load_particles(case.h, s, p["cell"].size, p["cell"].ctypes.data,
+                                                 p["off"].ctypes.data, p["vx"].ctypes.data, p["vy"].ctypes.data,
+                                                 p["vz"].ctypes.data, None, 0))
         case.step(args.steps)
         mom = case.moments()
         t1 = time.perf_counter()
+        pinned.clear()
+        for ptr in host_ptrs:
+            cudart.cudaFreeHost(ptr)
         d2h = 8 * (mom["dens_sum"].size + mom["phi_sum"].size + mom["en_sum"].size + mom["dens_diag_sum"].size
                    + mom["eepf"].size) + 512
         e2e = {"value": n_particles * args.steps * world / (t1 - t0), "unit": UNIT,
