@@ -59,6 +59,8 @@ struct pic_case {
     int n_nodes = 0;
     StepConst P{};
     std::vector<std::pair<void *, size_t>> allocs;
+    void *h_stage = nullptr;                    // pinned host staging of pic_read_moments
+    size_t h_stage_bytes = 0;
     std::vector<Proc> proc[2];
     float *d_nu[2] = {nullptr, nullptr};
     unsigned long long *R_last = nullptr;
@@ -1426,20 +1428,39 @@ pic_status pic_read_moments(pic_case *c, pic_moments *m)
     if (!c || !m || m->struct_size != sizeof(pic_moments)) return fail(PIC_EINVAL, "bad moments struct");
     const size_t nn = (size_t)c->n_nodes;
     const size_t ns = (size_t)c->d.n_species;
-    Ctrl h;
-    CU(cudaMemcpyAsync(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
-    double ke[2], pw[2];
-    CU(cudaMemcpyAsync(ke, c->P.ke_sum, 16, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaMemcpyAsync(pw, c->P.pw_sum, 16, cudaMemcpyDeviceToHost, c->stream));
-    std::vector<unsigned long long> rs(2 * nn), rd(2 * nn);
-    CU(cudaMemcpyAsync(rs.data(), c->P.Rsum, 2 * nn * 8, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaMemcpyAsync(rd.data(), c->P.Rdiag, 2 * nn * 8, cudaMemcpyDeviceToHost, c->stream));
-    if (m->phi_sum) CU(cudaMemcpyAsync(m->phi_sum, c->P.phi_sum, nn * 8, cudaMemcpyDeviceToHost, c->stream));
-    if (m->en_sum) CU(cudaMemcpyAsync(m->en_sum, c->P.en_sum, ns * nn * 8, cudaMemcpyDeviceToHost, c->stream));
-    std::vector<unsigned long long> ee(kEepfBins), ifd(2 * kIfedfBins);
-    CU(cudaMemcpyAsync(ee.data(), c->P.eepf, kEepfBins * 8, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaMemcpyAsync(ifd.data(), c->P.ifedf, 2 * kIfedfBins * 8, cudaMemcpyDeviceToHost, c->stream));
+    // every piece is copied into one pinned host buffer (asynchronous copies,
+    // one synchronisation), then out of it on the host
+    auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    const size_t o_ke = al(sizeof(Ctrl)), o_pw = o_ke + 16, o_rs = o_pw + 16, o_rd = o_rs + al(2 * nn * 8),
+                 o_phi = o_rd + al(2 * nn * 8), o_en = o_phi + al(nn * 8), o_ee = o_en + al(ns * nn * 8),
+                 o_ifd = o_ee + al(kEepfBins * 8), need = o_ifd + al(2 * kIfedfBins * 8);
+    if (c->h_stage_bytes < need) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->h_stage_bytes = 0;
+        CU(cudaMallocHost(&c->h_stage, need));
+        c->h_stage_bytes = need;
+    }
+    char *hb = static_cast<char *>(c->h_stage);
+    CU(cudaMemcpyAsync(hb, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(hb + o_ke, c->P.ke_sum, 16, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(hb + o_pw, c->P.pw_sum, 16, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(hb + o_rs, c->P.Rsum, 2 * nn * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(hb + o_rd, c->P.Rdiag, 2 * nn * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (m->phi_sum) CU(cudaMemcpyAsync(hb + o_phi, c->P.phi_sum, nn * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (m->en_sum) CU(cudaMemcpyAsync(hb + o_en, c->P.en_sum, ns * nn * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(hb + o_ee, c->P.eepf, kEepfBins * 8, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(hb + o_ifd, c->P.ifedf, 2 * kIfedfBins * 8, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
+    Ctrl h;
+    std::memcpy(&h, hb, sizeof(Ctrl));
+    const double *ke = reinterpret_cast<const double *>(hb + o_ke), *pw = reinterpret_cast<const double *>(hb + o_pw);
+    const unsigned long long *rs = reinterpret_cast<const unsigned long long *>(hb + o_rs);
+    const unsigned long long *rd = reinterpret_cast<const unsigned long long *>(hb + o_rd);
+    const unsigned long long *ee = reinterpret_cast<const unsigned long long *>(hb + o_ee);
+    const unsigned long long *ifd = reinterpret_cast<const unsigned long long *>(hb + o_ifd);
+    if (m->phi_sum) std::memcpy(m->phi_sum, hb + o_phi, nn * 8);
+    if (m->en_sum) std::memcpy(m->en_sum, hb + o_en, ns * nn * 8);
     m->n_nodes = (int32_t)nn;
     m->step = h.step;
     m->n_steps = (int64_t)h.n_steps_acc;
@@ -1711,6 +1732,7 @@ pic_status pic_destroy(pic_case *c)
     for (auto &e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     drop_graph(c);
     while (!c->allocs.empty()) c->dfree(c->allocs.back().first);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return PIC_OK;
